@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark: attempted spin updates per ns of population annealing on GB300.
+
+Workload (one "step" = one whole anneal of the batch, every hot-path stage):
+2D +-J Edwards-Anderson glass, L=16 periodic, R=5000, beta 0 -> 3 in 101
+temperatures, theta = 10 checkerboard Metropolis sweeps per temperature,
+nearest-integer resampling, 100 disorder samples x 2 independent populations,
+overlaps by index shift and between the two populations, free-energy-weighted
+averages over the two populations of each sample.  Inputs are seeded and
+synthetic (the paper's instances are not available).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  `value` is device-timed with the populations
+resident in HBM; `e2e` times the same work through the C ABI from host
+descriptors to host results (engine creation, uploads and result copies
+inside the timed region).  `--impl reference` times the CPU oracle on the
+host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "attempted spin updates/ns and PA runs/s (batched+served vs plain) at oracle-exact"
+UNIT = "attempted spin updates/ns"
+WORKLOAD = ("2D +-J EA glass L=16 periodic, R=5000, beta 0->3 in 101 steps, theta=10, nearest-integer "
+            "resampling, 100 disorder samples x 2 populations, index-shift + two-population overlaps, "
+            "free-energy-weighted averages")
+# Algorithmic integer work of one attempted update (issue slots of one lane):
+# a quarter of a Philox4x32-10 call (10 rounds x 4 instructions) plus the
+# acceptance compare and select.
+ALGO_INSTR_PER_UPDATE = 12.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--samples", type=int, default=100, help="disorder samples (2 populations each)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- CPU oracle
+def _oracle_job(args):
+    k, n_temps = args
+    sys.path.insert(0, ROOT)
+    import oracle as O
+    from paper_2207_05535_gb300 import workloads as W
+    d = W.glass_L16_R5000()[k]
+    r = O.OracleRun.from_desc(d)
+    t0 = time.perf_counter()
+    upd = 0
+    for i in range(1, n_temps):
+        assert r.step() == 0
+        upd += d.theta * d.N * int(r.record(i)["R"])
+    return upd, time.perf_counter() - t0
+
+
+def oracle_sample(n_temps=8, procs=None):
+    """The oracle as it stands on all host cores: each process anneals one
+    population of the workload through its first n_temps temperatures."""
+    procs = procs or os.cpu_count() or 1
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(procs) as pool:
+        res = pool.map(_oracle_job, [(k, n_temps) for k in range(procs)])
+    wall = time.perf_counter() - t0
+    upd = sum(u for u, _ in res)
+    return {"value": upd / (wall * 1e9), "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} populations of the workload (one per process) through their first {n_temps} "
+                      f"temperatures ({upd:.3e} attempted updates, {wall:.1f} s wall)"}
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 7:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[3 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- main
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        W_, K = args.warmup, args.steps
+        for _ in range(W_):
+            oracle_sample(n_temps=2)
+        vals, tot = [], 0.0
+        for _ in range(K):
+            t0 = time.perf_counter()
+            s = oracle_sample(n_temps=4)
+            tot += time.perf_counter() - t0
+            vals.append(s["value"])
+        v = statistics.median(vals)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
+            "warmup": W_, "ms_per_step": 1e3 * tot / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "bounded oracle sample per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": s["cores"], "kind": "oracle", "sample": s["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+        return
+
+    # CPU baseline first: a spawn pool, before any CUDA context exists
+    cpu = None
+    if rank == 0 and world >= 1 and args.gpus == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample()
+
+    import numpy as np
+    import torch
+    from paper_2207_05535_gb300 import _lib, build
+    from paper_2207_05535_gb300 import workloads as W
+
+    build.build()
+    _lib.load()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # weak scaling: every rank anneals its own batch (disorder samples offset by rank)
+    descs = W.glass_L16_R5000(n_samples=args.samples)
+    for d in descs:
+        d.disorder_id += 100000 * rank
+        d.run_id += 200000 * rank
+    n_ticks = max(d.n_beta for d in descs) - 1
+    idx = np.arange(len(descs), dtype=np.uint32)
+    stream = torch.cuda.Stream()
+    eng = _lib.Engine(descs, stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+
+    def one_step(use_graph=True):
+        eng.reset()
+        eng.step(n_ticks, use_graph)
+        return eng.weighted_average(idx, 2, _lib.PA_OK)
+
+    for _ in range(args.warmup):
+        one_step()
+    eng.sync()
+
+    # ---- timed region: K whole anneals, device-timed, L2 flushed between steps
+    clocks = Clocks(local) if rank == 0 else None
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = eng.launches
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[k][0].record(stream)
+        one_step()
+        ev[k][1].record(stream)
+    barrier()
+    launches = eng.launches - l0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    clk = clocks.stop() if clocks else None
+    updates = 0
+    runs_done = 0
+    for k in range(len(descs)):
+        rec = eng.records(k)
+        updates += int(sum(descs[k].theta * descs[k].N * int(r) for r in rec["R"][1:]))
+        runs_done += 1
+    upd_all = updates * args.steps
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        u = torch.tensor([float(upd_all)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(u)
+        upd_all = float(u.item())
+    value = upd_all / (t_max * 1e6)
+    runs_per_s = world * runs_done * args.steps / (t_max / 1e3)
+
+    # ---- per-kernel device time (eager launches bracketed by events), same work
+    _lib.pa_set_profiling(eng.h, True)
+    kt_tot = {}
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        _lib.pa_kernel_times(eng.h)
+        one_step(use_graph=False)
+        for kk, (t, n) in _lib.pa_kernel_times(eng.h).items():
+            a, b = kt_tot.get(kk, (0.0, 0))
+            kt_tot[kk] = (a + t, b + n)
+    _lib.pa_set_profiling(eng.h, False)
+    sweep_ms, sweep_n = kt_tot["sweep"]
+    pk, pk_kind = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tops = 152 * 4 * 32 * sm_mhz * 1e6 / 1e12  # lane-instruction issue rate, T/s
+    achieved_tops = updates * ALGO_INSTR_PER_UPDATE / (sweep_ms / args.steps * 1e-3) / 1e12
+    total_kernel_ms = sum(t for t, _ in kt_tot.values())
+
+    # ---- plain form: one run per engine, all on one stream (one run per launch)
+    plain = None
+    if not args.no_plain and rank == 0:
+        n_plain = 20
+        engines = [_lib.Engine([descs[k]], stream.cuda_stream) for k in range(n_plain)]
+        for e in engines:
+            e.reset()
+            e.step(n_ticks, False)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for e in engines:
+            e.reset()
+            e.step(n_ticks, False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b)
+        pupd = 0
+        for e, k in zip(engines, range(n_plain)):
+            rec = e.records(0)
+            pupd += int(sum(descs[k].theta * descs[k].N * int(r) for r in rec["R"][1:]))
+        for e in engines:
+            e.close()
+        plain = {"value": pupd / (pms * 1e6), "unit": UNIT, "runs": n_plain,
+                 "runs_per_s": n_plain / (pms / 1e3), "form": "one run per engine and per launch, one stream"}
+
+    # ---- end to end through the C ABI: host descriptors in, host results out
+    e2e = None
+    if not args.no_e2e:
+        es = []
+        h2d = d2h = 0
+        for k in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e = _lib.Engine(descs, stream.cuda_stream)
+            e.step(n_ticks, True)
+            e.weighted_average(idx, 2, 0)
+            for r in range(len(descs)):
+                e.records(r)
+            a_, b_ = _lib.pa_transfer_bytes(e.h)
+            e.close()
+            es.append(time.perf_counter() - t0)
+            h2d, d2h = a_, b_
+        e2e = {"value": updates * world / (statistics.median(es) * 1e9), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "includes": "pa_create (allocation, table upload, beta_0 draw) + anneal + weighted averages + "
+                           "all records copied to host + pa_destroy"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "runs_per_gpu": len(descs), "temperatures": n_ticks + 1,
+                       "attempted_updates_per_step": updates, "l2": "flushed between steps (256 MB write)",
+                       "form": "batched: all runs in one launch per kernel, anneal captured as a CUDA graph",
+                       "parallelism": f"replicas x{world} (independent runs per GPU)"},
+            "runs_per_s": runs_per_s,
+            "roofline": {"bound": "alu", "kernel": "sweep_kernel", "achieved": achieved_tops,
+                         "peak": peak_tops, "unit": "Tinstr/s", "frac": achieved_tops / peak_tops,
+                         "traffic": None,
+                         "basis": f"{ALGO_INSTR_PER_UPDATE:g} algorithmic lane-instructions per attempted update; "
+                                  f"peak = 152 SMs x 128 lanes x {sm_mhz:g} MHz ({pk_kind})",
+                         "sweep_ms_per_step": sweep_ms / args.steps,
+                         "sweep_share_of_kernel_time": sweep_ms / total_kernel_ms if total_kernel_ms else None},
+            "kernel_ms_per_step": {k: t / args.steps for k, (t, n) in kt_tot.items()},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "plain": plain,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    eng.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

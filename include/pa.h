@@ -1,0 +1,196 @@
+/*
+ * pa.h -- C ABI of the GB300 population-annealing engine (libpa.so).
+ *
+ * Population annealing (PA) anneals a population of R replicas of an Ising
+ * model through an inverse-temperature schedule beta_0 = 0 < beta_1 < ... ;
+ * at each step it reweights every replica by exp(-(beta_i - beta_{i-1}) H),
+ * resamples the population, equilibrates it with theta Metropolis sweeps and
+ * measures observables (arXiv:2207.05535, Sec. II.B, steps (i)-(vi); Eqs.
+ * tauBoltz, QBoltz).  Results of M independent runs are combined with the
+ * free-energy weights of Sec. IV (Eqs. appropriateWeight, simpleWeight).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a pa_status; nothing else crosses the ABI on error.
+ *  - Pointers named host_* or documented as "host" are host memory owned by
+ *    the caller; the engine copies what it needs and keeps no reference.
+ *  - The engine owns all device memory it allocates and frees it in
+ *    pa_destroy.  Work is enqueued asynchronously on the engine's CUDA stream;
+ *    device-side errors (capacity overflow, extinction, timeouts) are latched in
+ *    a device status word and returned by pa_sync and pa_weighted_average_runs;
+ *    pa_anneal_step refuses to continue once one is latched.  The read calls
+ *    (pa_records, pa_measure, pa_population) report CUDA errors only, so the
+ *    record of a run that stopped (its `status` field) stays readable.
+ *  - An engine is not thread safe: serialise calls on one engine.
+ *  - Randomness is counter-based Philox4x32-10 keyed by (seed, run_id) and the
+ *    counters listed in the engine's documentation, so a run's result does not
+ *    depend on which other runs share the engine.
+ */
+#ifndef PA_H
+#define PA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PA_OK = 0,
+    PA_ERR_INVALID_ARG = 1, /* a descriptor or argument is out of range */
+    PA_ERR_OOM = 2,         /* device or host allocation failed */
+    PA_ERR_CAPACITY = 3,    /* a run's population exceeded its capacity R_cap */
+    PA_ERR_EXTINCT = 4,     /* a run's population became empty */
+    PA_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    PA_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    PA_ERR_STATE = 7,       /* call not valid in the engine's current state */
+    PA_ERR_BUSY = 8         /* no room to admit another run */
+} pa_status;
+
+enum { PA_FERRO = 0, PA_EA_PMJ = 1 };          /* Eq. H_ferro (J = 1), Eq. H_SG (J = +-1) */
+enum { PA_NEAREST = 0, PA_MULTINOMIAL = 1 };   /* resampling of Sec. II.B step (iii) / Sec. IV.C */
+enum { PA_Q_NONE = 0, PA_Q_SHIFT = 1, PA_Q_PAIR = 2 }; /* overlap pairs of Sec. III.D (bit flags) */
+enum { PA_WEIGHT_FULL = 0, PA_WEIGHT_SIMPLE = 1 };     /* Eq. appropriateWeight / Eq. simpleWeight */
+
+/* One PA run (Sec. II.B): caller-owned, copied by pa_create. */
+typedef struct pa_run_desc {
+    uint32_t L;           /* linear lattice size, even, 4 <= L <= 256; N = L*L sites, periodic */
+    uint32_t model;       /* PA_FERRO or PA_EA_PMJ */
+    uint32_t R;           /* target population size R (Sec. II.B step (i)), >= 1 */
+    uint32_t R_cap;       /* capacity (>= R); 0 = R + 8 ceil(sqrt R) + 64 (R for multinomial) */
+    uint32_t theta;       /* Metropolis sweeps per temperature (Sec. V.A.1) */
+    uint32_t n_beta;      /* number of temperatures, >= 1 */
+    const double *beta;   /* host, n_beta entries, non-decreasing; beta[0] = 0 gives absolute F */
+    uint32_t seed;        /* Philox key word 0 */
+    uint32_t run_id;      /* Philox key word 1 (replica randomness) */
+    uint32_t disorder_id; /* Philox key word 1 for the +-J couplings */
+    uint32_t resample;    /* PA_NEAREST or PA_MULTINOMIAL */
+    uint32_t overlap;     /* PA_Q_* flags */
+    int32_t paired;       /* with PA_Q_PAIR: index (in this pa_create call) of the partner run, else -1 */
+    uint32_t reserved;    /* must be 0 */
+} pa_run_desc;
+
+/* Per-temperature record of one run (Sec. III.B-D, Eq. rho_t).  Integer sums
+ * are exact; ln Q_i and -beta_i F_i are FP64. */
+typedef struct pa_step_record {
+    double beta;          /* beta_i */
+    double lnQ;           /* ln Q_i (Eq. QBoltz); 0 at i = 0 */
+    double minus_betaF;   /* -beta_i F_i = N ln 2 + ln Q_1 + ... + ln Q_i (Eq. F), summed in step order */
+    int64_t sumE, sumE2;  /* sum_j H_j, sum_j H_j^2 over the R_i replicas */
+    int64_t sumAbsM, sumM2; /* sum_j |M_j|, sum_j M_j^2, M_j = sum_n s_n */
+    int64_t sum_c2;       /* sum over families of (family size)^2; rho_t = sum_c2 / R_i */
+    int64_t sum_absq;     /* sum over index-shift pairs of |N - 2 d| (N |q|) */
+    int64_t sum_absq_pair;/* same over pairs with the partner population */
+    uint32_t R;           /* R_i */
+    uint32_t R_target;    /* R */
+    uint32_t n_fam;       /* number of surviving families */
+    uint32_t max_fam;     /* largest family */
+    uint32_t n_q;         /* number of index-shift pairs, floor(R_i / 2) */
+    uint32_t n_q_pair;    /* number of pairs with the partner, min(R_i, R_i') */
+    uint32_t N;           /* number of spins */
+    uint32_t status;      /* 0, or the pa_status that stopped this run */
+} pa_step_record;
+
+/* Weighted averages at one temperature over M runs (Sec. IV). */
+typedef struct pa_wavg {
+    double beta;
+    double W_e, W_e2, W_m, W_m2; /* Eq. W_conf applied to e, e^2, |m|, m^2 */
+    double Wvar_c, Wvar_chi;     /* Eqs. Wvar_C, Wvar_Chi */
+    double W_c, W_chi;           /* Eq. W_conf applied to c and chi (lower bound, Eq. Wvar_bound) */
+    double W_minus_betaF;        /* Eq. W_F: -beta_i W[F_i] */
+    double W_absq, W_absq_pair;  /* Eq. W_conf applied to |q| */
+    double w_max;                /* largest weight */
+    double sum_w;                /* sum of the weights */
+} pa_wavg;
+
+typedef struct pa_engine pa_engine;
+
+/* Create an engine holding n_runs runs, allocate their device memory, draw the
+ * beta_0 = 0 populations (Sec. II.B step (i): uniform states), the couplings
+ * (Eq. H_SG) and measure step 0.  cuda_stream: a cudaStream_t to enqueue on,
+ * or NULL for a private non-blocking stream.  *out receives the engine.
+ * Errors: PA_ERR_INVALID_ARG (descriptor out of range; paired runs must share
+ * L, model, disorder_id and n_beta), PA_ERR_OOM, PA_ERR_CUDA. */
+pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, pa_engine **out);
+
+/* Return every run of the engine to its beta_0 population (same descriptors,
+ * same randomness, so the next anneal repeats the first one bit for bit)
+ * without reallocating: clears records, histograms and statuses, redraws the
+ * couplings and populations and measures step 0.  Asynchronous. */
+pa_status pa_reset(pa_engine *e);
+
+/* Advance every unfinished run by up to n_steps temperatures: resampling
+ * (Eqs. tauBoltz, QBoltz and step (iii)), theta checkerboard Metropolis sweeps
+ * at beta_i (step (iv)) and measurements (step (v)).  Asynchronous.  With
+ * use_graph != 0 the per-step launch sequence is captured once as a CUDA graph
+ * and replayed.  Errors surface at the next synchronising call. */
+pa_status pa_anneal_step(pa_engine *e, uint32_t n_steps, int use_graph);
+
+/* Block until the engine's queued work is done; returns the latched status. */
+pa_status pa_sync(pa_engine *e);
+
+/* Copy the records of run `run` (index in pa_create order) for steps
+ * 0..n_beta-1 into host_out[n_beta] (steps not reached yet are zero), and the
+ * overlap histograms over d = 0..N (d = Hamming distance, q = 1 - 2d/N) into
+ * host_qhist[n_beta][N+1] / host_qhist_pair[n_beta][N+1] when non-NULL.
+ * Synchronises. */
+pa_status pa_records(pa_engine *e, uint32_t run, pa_step_record *host_out, uint32_t *host_qhist,
+                     uint32_t *host_qhist_pair);
+
+/* Copy one record (and optional histograms, N+1 entries each). Synchronises. */
+pa_status pa_measure(pa_engine *e, uint32_t run, uint32_t step, pa_step_record *host_out, uint32_t *host_qhist,
+                     uint32_t *host_qhist_pair);
+
+/* Copy the current population of run `run`: host_spins[R_i][N] as int8 +-1
+ * (site n = y*L + x), energies, magnetisations and family ids (index of the
+ * beta_0 ancestor), each R_i entries, caller-sized to at least R_cap; *R_out = R_i;
+ * *step_out = current temperature index.  Any pointer may be NULL.  Synchronises. */
+pa_status pa_population(pa_engine *e, uint32_t run, int8_t *host_spins, int32_t *host_E, int32_t *host_M,
+                        uint32_t *host_fam, uint32_t *R_out, uint32_t *step_out);
+
+/* Weighted averages (Sec. IV) over groups of runs resident in the engine:
+ * group g holds runs run_idx[g*M .. g*M+M-1] (same N and n_beta).  Writes
+ * host_out[g][n_beta] and, when non-NULL, the weighted overlap distributions
+ * host_Pq[g][n_beta][N+1] / host_Pq_pair (Eq. W_conf_q).  weight_kind is
+ * PA_WEIGHT_FULL or PA_WEIGHT_SIMPLE.  Runs in FP64 on the device.  Synchronises. */
+pa_status pa_weighted_average_runs(pa_engine *e, const uint32_t *run_idx, uint32_t n_groups, uint32_t M,
+                                   uint32_t weight_kind, pa_wavg *host_out, double *host_Pq,
+                                   double *host_Pq_pair);
+
+/* Weighted averages from host records: recs[m*n_steps + i] for M runs of N spins,
+ * optional histograms qhist[(m*n_steps + i)*(N+1) + d].  Writes out[n_steps] and
+ * Pq / Pq_pair [n_steps][N+1] when non-NULL.  Computes on the device of the
+ * current CUDA context (stream: cudaStream_t or NULL); blocking. */
+pa_status pa_weighted_average(const pa_step_record *recs, const uint32_t *qhist, const uint32_t *qhist_pair,
+                              uint32_t M, uint32_t n_steps, uint32_t N, uint32_t weight_kind, pa_wavg *out,
+                              double *Pq, double *Pq_pair, void *cuda_stream);
+
+/* Number of kernels this engine has launched (graph replays count each node). */
+uint64_t pa_launch_count(const pa_engine *e);
+
+/* Kernel classes timed by the profiling mode. */
+enum { PA_K_RESAMPLE = 0, PA_K_SWEEP = 1, PA_K_OVERLAP = 2, PA_K_MEASURE = 3, PA_K_INIT = 4, PA_K_WAVG = 5,
+       PA_K_COUNT = 6 };
+
+/* Profiling mode: with on != 0 every kernel launch is bracketed by CUDA events
+ * on the engine's stream and pa_anneal_step launches eagerly (no graph). */
+pa_status pa_set_profiling(pa_engine *e, int on);
+
+/* Synchronise and return, per kernel class, the summed device time in ms and
+ * the number of launches timed since the previous call (arrays of PA_K_COUNT). */
+pa_status pa_kernel_times(pa_engine *e, double *ms_out, uint64_t *launches_out);
+
+/* Bytes this engine has copied host->device and device->host so far. */
+pa_status pa_transfer_bytes(const pa_engine *e, uint64_t *h2d, uint64_t *d2h);
+
+/* Free all device memory of the engine.  Synchronises first. */
+pa_status pa_destroy(pa_engine *e);
+
+/* Static description of a status code. */
+const char *pa_status_string(pa_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PA_H */

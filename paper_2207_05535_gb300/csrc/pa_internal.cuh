@@ -1,0 +1,105 @@
+// Internal layout shared by the engine's host code and its kernels.
+//
+// Device memory layout (one pool per engine, every run at its own offsets):
+//   spins[b]  uint32 [sum R_cap wstride]    replica j of a run at word spin_off + j wstride,
+//                                           site n -> bit (n & 31) of word (n >> 5),
+//                                           bit 1 = spin +1; buffer b = step & 1
+//   E[b], M[b], fam[b]   [sum R_cap]        energy, magnetisation, beta_0 ancestor
+//   parent, cnt          [sum R_cap]        parent map of the children, copy numbers r_j
+//   rec                  [sum n_beta]       per-temperature records (pa_step_record)
+//   qh, qhp              [sum n_beta (N+1)] overlap histograms over d (shift / pair)
+//   beta, wt, thr                           schedule, exp(-4 n dbeta_i) per step, Metropolis
+//                                           thresholds per step (shared by equal schedules)
+//   J                    [2 wstride] per run  packed "J = -1" bits of right / down bonds
+//   scratch              per run: level histogram (N+1 u32), level CDF (N+1 f64),
+//                        level fill counters (N+1 u32), members (R_cap u32)
+#pragma once
+
+#include <cstdint>
+
+#include "pa.h"
+
+namespace pa {
+
+constexpr uint32_t TAG_INIT = 1u, TAG_SWEEP = 2u, TAG_RESAMPLE = 3u, TAG_MULTINOMIAL = 4u, TAG_DISORDER = 5u;
+
+// status bits in the engine-wide device status word
+constexpr uint32_t ST_CAPACITY = 1u << PA_ERR_CAPACITY;
+constexpr uint32_t ST_EXTINCT = 1u << PA_ERR_EXTINCT;
+constexpr uint32_t ST_TIMEOUT = 1u << PA_ERR_TIMEOUT;
+
+struct RunDev {
+    uint32_t L, N, Lh, wstride;  // wstride: words per replica, a multiple of 4
+    uint32_t model, R, R_cap, theta;
+    uint32_t n_beta, seed, run_id, disorder_id;
+    uint32_t resample, overlap;
+    int32_t paired;
+    uint32_t pad0;
+    uint64_t rep_off;   // first replica slot (E, M, fam, parent, cnt)
+    uint64_t spin_off;  // first spin word (runs of different L have different wstride)
+    uint64_t rec_off, qh_off, beta_off, wt_off, thr_off, J_off, scr_off;
+    double ln2N;  // N ln 2 = ln Z(beta_0 = 0)
+};
+
+struct RunState {
+    uint32_t step;   // temperature index of the population held
+    uint32_t R_cur;  // R_step
+    uint32_t R_new;  // population size produced by the resampling in flight
+    uint32_t status; // 0 or a pa_status that stopped the run
+    double lnQ;      // ln Q of the resampling in flight
+};
+
+struct Pool {
+    const RunDev *runs;
+    RunState *st;
+    uint32_t *spins[2];
+    int32_t *E[2];
+    int32_t *M[2];
+    uint32_t *fam[2];
+    uint32_t *parent;
+    uint32_t *cnt;
+    pa_step_record *rec;
+    uint32_t *qh;
+    uint32_t *qhp;
+    const double *beta;
+    const double *wt;
+    const unsigned long long *thr;
+    uint32_t *J;
+    unsigned long long *scratch;
+    uint32_t *status;
+};
+
+// Sweep launch shape for one lattice size.
+struct SweepCfg {
+    uint32_t block;  // threads per CTA
+    uint32_t TPR;    // threads per replica (power of two)
+    uint32_t RPC;    // replicas per CTA
+    uint32_t G;      // Philox groups per colour = ceil(N / 8)
+    uint32_t PS;     // bytes per colour plane = 4 G
+    uint32_t smem;   // dynamic shared memory bytes
+};
+
+// Scratch words (64-bit) of one run.
+inline uint64_t scratch_words(uint32_t N, uint32_t R_cap)
+{
+    uint64_t n1 = N + 1;
+    return (n1 + 1) / 2 + n1 + (n1 + 1) / 2 + (uint64_t(R_cap) + 1) / 2 + 4;
+}
+
+// Launch wrappers implemented in pa_kernels.cu (all asynchronous on `s`).
+void launch_init_couplings(const Pool &P, uint32_t n_runs, cudaStream_t s);
+void launch_init_population(const Pool &P, uint32_t n_runs, uint32_t max_R, cudaStream_t s);
+void launch_resample(const Pool &P, uint32_t n_runs, cudaStream_t s);
+SweepCfg sweep_config(uint32_t L);
+void launch_sweep(const Pool &P, const uint32_t *group_runs, uint32_t n_group_runs, uint32_t max_Rcap,
+                  const SweepCfg &cfg, cudaStream_t s);
+void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, uint32_t max_Rcap, int init,
+                    cudaStream_t s);
+void launch_measure(const Pool &P, uint32_t n_runs, int init, cudaStream_t s);
+void launch_wavg(const pa_step_record *recs, const unsigned long long *rec_off, const uint32_t *qh,
+                 const uint32_t *qhp, const unsigned long long *qh_off, uint32_t n_groups, uint32_t M,
+                 uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w, double *Pq, double *Pqp,
+                 cudaStream_t s);
+cudaError_t prepare_kernels();
+
+}  // namespace pa

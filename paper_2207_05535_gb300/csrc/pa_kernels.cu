@@ -1,0 +1,878 @@
+// Kernels of the population-annealing hot path for sm_103a (GB300).
+//
+// One anneal step (arXiv:2207.05535, Sec. II.B steps (ii)-(v)) is four launches
+// over every run of the engine:
+//   resample_kernel  one CTA per run: energy-level histogram, FP64 normalisation
+//                    Q_i (Eq. QBoltz), copy numbers r_j (nearest-integer, or
+//                    multinomial), exclusive scan and the parent map that places
+//                    copies of one ancestor next to each other (Sec. V.A.1)
+//   sweep_kernel     per lattice size: each replica is gathered from its parent
+//                    (the resampling copy), unpacked into shared memory as two
+//                    checkerboard colour planes, swept theta times with Philox
+//                    thresholds (Sec. V.A.1), packed and written back
+//   overlap_kernel   XOR + popcount overlaps of index-shift pairs j <-> j+floor(R/2)
+//                    and of pairs with a partner population (Sec. III.D)
+//   measure_kernel   integer reductions of E, E^2, |M|, M^2, family statistics
+//                    (Eq. rho_t) and the free-energy running sum (Eq. F)
+// Nothing here allocates memory; no spin-wait exists in any kernel.
+//
+// Randomness: Philox4x32-10 (Salmon et al., SC'11), key (seed, run_id):
+//   init spin n of replica j   ctr (n>>2, j, 0, INIT<<24)                word n&3, bit 31
+//   coupling of site n         ctr (n>>2, 0, 0, DISORDER<<24), key (seed, disorder_id)
+//                              word n&3: bit 31 -> J_right = +1, bit 30 -> J_down = +1
+//   nearest-integer draw of j  ctr (j, 0, i, RESAMPLE<<24)               word 0
+//   multinomial draw d         ctr (d, 0, i, MULTINOMIAL<<24)            words 0,1 level; word 2 member
+//   Metropolis, sublattice k   ctr (k>>2, child, i, SWEEP<<24|t<<1|c)     word k&3
+// FP64 arithmetic that decides an integer uses explicit round-to-nearest
+// intrinsics (no contraction), in the same order as the plain definition.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pa_internal.cuh"
+
+namespace pa {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr uint32_t SMEM_BINS = 4096;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                               uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ uint32_t pick(const uint4 &u, uint32_t q)
+{
+    return q == 0 ? u.x : q == 1 ? u.y : q == 2 ? u.z : u.w;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        T w = __shfl_xor_sync(FULL, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_min(T v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        T w = __shfl_xor_sync(FULL, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+// Block-wide sum broadcast to every thread.  sh: >= 32 elements.
+template <typename T>
+__device__ T block_sum(T v, T *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    T r = lane < nw ? sh[lane] : T(0);
+    r = warp_sum(r);
+    __syncthreads();
+    return r;
+}
+
+template <typename T>
+__device__ T block_max(T v, T *sh, T ident)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_max(v);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    T r = lane < nw ? sh[lane] : ident;
+    r = warp_max(r);
+    __syncthreads();
+    return r;
+}
+
+template <typename T>
+__device__ T block_min(T v, T *sh, T ident)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_min(v);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    T r = lane < nw ? sh[lane] : ident;
+    r = warp_min(r);
+    __syncthreads();
+    return r;
+}
+
+// Exclusive prefix sum over the block (blockDim a multiple of 32); total to all.
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *sh, uint32_t &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = lane < nw ? sh[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t base = wid ? sh[wid - 1] : 0u;
+    total = sh[nw - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+// Inclusive max-scan over the block.
+__device__ uint32_t block_inclusive_max(uint32_t v, uint32_t *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x = y > x ? y : x;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = lane < nw ? sh[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, s, o);
+            if (lane >= o) s = y > s ? y : s;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t base = wid ? sh[wid - 1] : 0u;
+    __syncthreads();
+    return base > x ? base : x;
+}
+
+__device__ __forceinline__ uint32_t get_bit(const uint32_t *w, uint32_t n) { return (w[n >> 5] >> (n & 31)) & 1u; }
+
+__device__ __forceinline__ void set_status(const Pool &P, uint32_t run, uint32_t code)
+{
+    P.st[run].status = code;
+    atomicOr(P.status, 1u << code);
+}
+
+// --------------------------------------------------------------------------
+// Initialisation (Sec. II.B step (i) at beta_0 = 0; couplings of Eq. H_SG).
+// --------------------------------------------------------------------------
+__global__ void init_couplings_kernel(Pool P)
+{
+    const RunDev rd = P.runs[blockIdx.x];
+    uint32_t *Jr = P.J + rd.J_off, *Jd = Jr + rd.wstride;
+    for (uint32_t w = threadIdx.x; w < rd.wstride; w += blockDim.x) {
+        uint32_t wr = 0, wd = 0;
+        if (rd.model == PA_EA_PMJ) {
+            for (uint32_t g = 0; g < 8; ++g) {
+                const uint32_t n0 = 32 * w + 4 * g;
+                if (n0 >= rd.N) break;
+                const uint4 u = philox4x32_10(n0 >> 2, 0, 0, TAG_DISORDER << 24, rd.seed, rd.disorder_id);
+                for (uint32_t q = 0; q < 4; ++q) {
+                    if (n0 + q >= rd.N) break;
+                    const uint32_t v = pick(u, q);
+                    wr |= ((~v >> 31) & 1u) << (4 * g + q);  // bit set where J_right = -1
+                    wd |= ((~v >> 30) & 1u) << (4 * g + q);  // bit set where J_down = -1
+                }
+            }
+        }
+        Jr[w] = wr;
+        Jd[w] = wd;
+    }
+}
+
+// One warp per replica: uniform spins from Philox, then E and M exactly.
+__global__ void init_population_kernel(Pool P)
+{
+    const uint32_t run = blockIdx.y;
+    const RunDev rd = P.runs[run];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= rd.R) return;
+    uint32_t *s = P.spins[0] + rd.spin_off + (uint64_t)j * rd.wstride;
+    for (uint32_t w = lane; w < rd.wstride; w += 32) {
+        uint32_t word = 0;
+        for (uint32_t g = 0; g < 8; ++g) {
+            const uint32_t n0 = 32 * w + 4 * g;
+            if (n0 >= rd.N) break;
+            const uint4 u = philox4x32_10(n0 >> 2, j, 0, TAG_INIT << 24, rd.seed, rd.run_id);
+            for (uint32_t q = 0; q < 4; ++q)
+                if (n0 + q < rd.N) word |= (pick(u, q) >> 31) << (4 * g + q);
+        }
+        s[w] = word;
+    }
+    __syncwarp();
+    const uint32_t *Jr = P.J + rd.J_off, *Jd = Jr + rd.wstride;
+    const uint32_t L = rd.L;
+    int32_t unsat = 0, up = 0;
+    for (uint32_t n = lane; n < rd.N; n += 32) {
+        const uint32_t x = n % L, y = n / L;
+        const uint32_t b = get_bit(s, n);
+        const uint32_t br = get_bit(s, y * L + (x + 1 == L ? 0 : x + 1));
+        const uint32_t bd = get_bit(s, (y + 1 == L ? 0 : y + 1) * L + x);
+        unsat += (int32_t)((b ^ br ^ get_bit(Jr, n)) + (b ^ bd ^ get_bit(Jd, n)));
+        up += (int32_t)b;
+    }
+    unsat = warp_sum(unsat);
+    up = warp_sum(up);
+    if (lane == 0) {
+        P.E[0][rd.rep_off + j] = 2 * unsat - 2 * (int32_t)rd.N;  // H = (#unsatisfied) - (#satisfied)
+        P.M[0][rd.rep_off + j] = 2 * up - (int32_t)rd.N;
+        P.fam[0][rd.rep_off + j] = j;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Resampling (Sec. II.B steps (ii)-(iii), Eqs. tauBoltz and QBoltz).
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) resample_kernel(Pool P)
+{
+    __shared__ uint32_t sh_hist[SMEM_BINS];
+    __shared__ int32_t sh_i[32];
+    __shared__ uint32_t sh_u[33];
+    __shared__ double sh_S;
+    __shared__ uint32_t sh_carry;
+
+    const uint32_t run = blockIdx.x;
+    const RunDev rd = P.runs[run];
+    RunState *st = &P.st[run];
+    if (st->status) return;
+    const uint32_t i = st->step + 1;
+    if (i >= rd.n_beta) return;
+    const uint32_t Rprev = st->R_cur;
+    const int32_t *E = P.E[(i - 1) & 1] + rd.rep_off;
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+
+    // energy range of the population at beta_{i-1}
+    int32_t lo = INT32_MAX, hi = INT32_MIN;
+    for (uint32_t j = tid; j < Rprev; j += nt) {
+        const int32_t e = E[j];
+        lo = e < lo ? e : lo;
+        hi = e > hi ? e : hi;
+    }
+    const int32_t Emin = block_min(lo, sh_i, INT32_MAX);
+    const int32_t Emax = block_max(hi, sh_i, INT32_MIN);
+    const uint32_t nb = (uint32_t)(Emax - Emin) / 4u + 1u;  // energies differ by multiples of 4
+
+    unsigned long long *scr = P.scratch + rd.scr_off;
+    const uint32_t n1 = rd.N + 1;
+    uint32_t *g_hist = reinterpret_cast<uint32_t *>(scr);
+    double *cdf = reinterpret_cast<double *>(scr + (n1 + 1) / 2);
+    uint32_t *fill = reinterpret_cast<uint32_t *>(scr + (n1 + 1) / 2 + n1);
+    uint32_t *members = reinterpret_cast<uint32_t *>(scr + (n1 + 1) / 2 + n1 + (n1 + 1) / 2);
+    uint32_t *h = nb <= SMEM_BINS ? sh_hist : g_hist;
+    for (uint32_t n = tid; n < nb; n += nt) h[n] = 0;
+    __syncthreads();
+    for (uint32_t j = tid; j < Rprev; j += nt) atomicAdd(&h[(uint32_t)(E[j] - Emin) >> 2], 1u);
+    __syncthreads();
+
+    const double dbeta = P.beta[rd.beta_off + i] - P.beta[rd.beta_off + i - 1];
+    const double *w = P.wt + rd.wt_off + (uint64_t)i * n1;  // w[n] = exp(-4 n dbeta)
+    const bool multi = rd.resample == PA_MULTINOMIAL;
+    if (tid == 0) {
+        // S = sum_j exp(-dbeta (E_j - E_min)), level by level in ascending order
+        double S = 0.0;
+        for (uint32_t n = 0; n < nb; ++n) {
+            S = __dadd_rn(S, __dmul_rn((double)h[n], w[n]));
+            if (multi) cdf[n] = S;
+        }
+        sh_S = S;
+        st->lnQ = (-dbeta) * (double)Emin + log(S) - log((double)Rprev);
+    }
+    __syncthreads();
+    const double S = sh_S;
+    uint32_t *cnt = P.cnt + rd.rep_off;
+
+    if (multi) {
+        // stable list of replicas by level: members[first(n) + rank]
+        if (tid < 32) {
+            uint32_t acc = 0;
+            for (uint32_t base = 0; base < nb; base += 32) {  // fill[n] = first(n)
+                const uint32_t n = base + tid;
+                const uint32_t v = n < nb ? h[n] : 0u;
+                uint32_t x = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(FULL, x, o);
+                    if ((int)tid >= o) x += y;
+                }
+                if (n < nb) fill[n] = acc + x - v;
+                acc += __shfl_sync(FULL, x, 31);
+            }
+            __syncwarp();
+            for (uint32_t base = 0; base < Rprev; base += 32) {
+                const uint32_t j = base + tid;
+                const bool ok = j < Rprev;
+                const uint32_t n = ok ? (uint32_t)(E[j] - Emin) >> 2 : 0xffffffffu;
+                const unsigned peers = __match_any_sync(FULL, n);
+                const uint32_t rank = __popc(peers & ((1u << tid) - 1u));
+                uint32_t pos = 0;
+                if (ok) pos = fill[n] + rank;
+                __syncwarp();
+                if (ok) {
+                    members[pos] = j;
+                    if (rank == 0) fill[n] += __popc(peers);
+                }
+                __syncwarp();
+            }
+        }
+        for (uint32_t j = tid; j < Rprev; j += nt) cnt[j] = 0;
+        __syncthreads();
+        const uint32_t last = nb - 1;
+        for (uint32_t d = tid; d < rd.R; d += nt) {
+            const uint4 o = philox4x32_10(d, 0, i, TAG_MULTINOMIAL << 24, rd.seed, rd.run_id);
+            const unsigned long long u53 = ((unsigned long long)(o.x >> 5) << 26) | (unsigned long long)(o.y >> 6);
+            const double x = __dmul_rn(__dmul_rn((double)u53, 1.0 / 9007199254740992.0), S);
+            uint32_t a = 0, b = nb;  // first n with cdf[n] > x
+            while (a < b) {
+                const uint32_t m = (a + b) >> 1;
+                if (cdf[m] > x)
+                    b = m;
+                else
+                    a = m + 1;
+            }
+            const uint32_t lev = a < nb ? a : last;
+            const uint32_t idx = (uint32_t)(((unsigned long long)o.z * (unsigned long long)h[lev]) >> 32);
+            const uint32_t first = fill[lev] - h[lev];
+            atomicAdd(&cnt[members[first + idx]], 1u);
+        }
+        __syncthreads();
+    } else {
+        // nearest-integer resampling: r_j = floor(tau) + [u < tau - floor(tau)], tau = R w[n_j] / S
+        for (uint32_t j = tid; j < Rprev; j += nt) {
+            const double tau = __ddiv_rn(__dmul_rn((double)rd.R, w[(uint32_t)(E[j] - Emin) >> 2]), S);
+            const double fl = floor(tau);
+            const uint32_t u = philox4x32_10(j, 0, i, TAG_RESAMPLE << 24, rd.seed, rd.run_id).x;
+            const double uf = __dmul_rn((double)u, 2.3283064365386962890625e-10);
+            cnt[j] = (uint32_t)fl + (uf < __dsub_rn(tau, fl) ? 1u : 0u);
+        }
+        __syncthreads();
+    }
+
+    // exclusive scan of the copy numbers and the parent map (contiguous families)
+    if (tid == 0) sh_carry = 0;
+    __syncthreads();
+    uint32_t *parent = P.parent + rd.rep_off;
+    for (uint32_t base = 0; base < Rprev; base += nt) {
+        const uint32_t j = base + tid;
+        const uint32_t r = j < Rprev ? cnt[j] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(r, sh_u, tot);
+        const uint32_t o = sh_carry + ex;
+        for (uint32_t c = 0; c < r; ++c)
+            if (o + c < rd.R_cap) parent[o + c] = j;
+        __syncthreads();
+        if (tid == 0) sh_carry += tot;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const uint32_t Rn = sh_carry;
+        st->R_new = Rn;
+        if (Rn == 0)
+            set_status(P, run, PA_ERR_EXTINCT);
+        else if (Rn > rd.R_cap)
+            set_status(P, run, PA_ERR_CAPACITY);
+        if (Rn == 0 || Rn > rd.R_cap) P.rec[rd.rec_off + i].status = st->status;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Fused gather + theta checkerboard Metropolis sweeps (Sec. V.A.1).
+// Shared memory per replica: two colour planes of bytes, plane c holding the
+// sites of colour c = (x + y) & 1 in sublattice order k = n >> 1.  Every thread
+// owns Philox groups g (sites 4g..4g+3 of a colour): one Philox call gives the
+// four uniforms of a group.  A shared "bond mask" plane holds per site the
+// J = -1 bits of its right, left, down and up bonds.
+// --------------------------------------------------------------------------
+__global__ void sweep_kernel(Pool P, const uint32_t *group_runs, SweepCfg cfg)
+{
+    extern __shared__ __align__(16) uint8_t sm[];
+    const uint32_t run = group_runs[blockIdx.y];
+    const RunDev rd = P.runs[run];
+    const RunState st = P.st[run];
+    if (st.status) return;
+    const uint32_t i = st.step + 1;
+    if (i >= rd.n_beta) return;
+    const uint32_t Rn = st.R_new;
+    const uint32_t tile0 = blockIdx.x * cfg.RPC;
+    if (tile0 >= Rn) return;  // uniform over the CTA
+
+    const uint32_t L = rd.L, N = rd.N, Lh = rd.Lh, half = N >> 1, PS = cfg.PS;
+    const uint32_t rloc = threadIdx.x / cfg.TPR, tl = threadIdx.x % cfg.TPR;
+    const uint32_t child = tile0 + rloc;
+    const bool active = rloc < cfg.RPC && child < Rn;
+    uint8_t *planes = sm + (size_t)rloc * 2 * PS;
+    uint8_t *jm = sm + (size_t)cfg.RPC * 2 * PS;
+    int32_t *acc = reinterpret_cast<int32_t *>(jm + 2 * PS);
+
+    // bond masks (shared by all replicas of the run)
+    const uint32_t *Jr = P.J + rd.J_off, *Jd = Jr + rd.wstride;
+    for (uint32_t n = threadIdx.x; n < N; n += blockDim.x) {
+        const uint32_t x = n % L, y = n / L;
+        const uint32_t c = (x + y) & 1u;
+        uint32_t m = 0;
+        if (rd.model == PA_EA_PMJ) {
+            const uint32_t nl = y * L + (x == 0 ? L - 1 : x - 1);
+            const uint32_t nu = (y == 0 ? L - 1 : y - 1) * L + x;
+            m = get_bit(Jr, n) | (get_bit(Jr, nl) << 1) | (get_bit(Jd, n) << 2) | (get_bit(Jd, nu) << 3);
+        }
+        jm[c * PS + (n >> 1)] = (uint8_t)m;
+    }
+    if (threadIdx.x < 2 * cfg.RPC) acc[threadIdx.x] = 0;
+
+    // gather the parent (this is the resampling copy)
+    const uint32_t ob = (i - 1) & 1u, nbuf = i & 1u;
+    uint32_t parent = 0;
+    if (active) {
+        parent = P.parent[rd.rep_off + child];
+        const uint32_t *src = P.spins[ob] + rd.spin_off + (uint64_t)parent * rd.wstride;
+        const uint32_t nwords = (N + 31) >> 5;
+        for (uint32_t wi = tl; wi < nwords; wi += cfg.TPR) {
+            const uint32_t word = src[wi];
+            for (uint32_t b = 0; b < 32; ++b) {
+                const uint32_t n = 32 * wi + b;
+                if (n >= N) break;
+                const uint32_t c = ((n % L) + (n / L)) & 1u;
+                planes[c * PS + (n >> 1)] = (uint8_t)((word >> b) & 1u);
+            }
+        }
+    }
+    __syncthreads();
+
+    const unsigned long long T1 = P.thr[rd.thr_off + 2 * i], T2 = P.thr[rd.thr_off + 2 * i + 1];
+    int32_t dE = 0, dM = 0;
+    for (uint32_t t = 0; t < rd.theta; ++t) {
+        for (uint32_t c = 0; c < 2; ++c) {
+            if (active) {
+                uint8_t *mine = planes + c * PS;
+                const uint8_t *other = planes + (c ^ 1u) * PS;
+                const uint8_t *jmc = jm + c * PS;
+                for (uint32_t g = tl; g < cfg.G; g += cfg.TPR) {
+                    const uint4 u = philox4x32_10(g, child, i, (TAG_SWEEP << 24) | (t << 1) | c, rd.seed, rd.run_id);
+#pragma unroll
+                    for (uint32_t q = 0; q < 4; ++q) {
+                        const uint32_t k = 4 * g + q;
+                        if (k >= half) break;
+                        const uint32_t y = k / Lh, xp = k - y * Lh;
+                        const uint32_t x = 2 * xp + ((c + y) & 1u);
+                        const uint32_t xr = x + 1 == L ? 0 : x + 1, xl = x == 0 ? L - 1 : x - 1;
+                        const uint32_t yd = y + 1 == L ? 0 : y + 1, yu = y == 0 ? L - 1 : y - 1;
+                        const uint32_t s = mine[k], jb = jmc[k];
+                        const uint32_t unsat = (s ^ other[y * Lh + (xr >> 1)] ^ (jb & 1u)) +
+                                               (s ^ other[y * Lh + (xl >> 1)] ^ ((jb >> 1) & 1u)) +
+                                               (s ^ other[yd * Lh + xp] ^ ((jb >> 2) & 1u)) +
+                                               (s ^ other[yu * Lh + xp] ^ (jb >> 3));
+                        // dE = 8 - 4 unsat; accept if dE <= 0, else with probability T[dE/4] / 2^32
+                        const bool accept =
+                            unsat >= 2u || (unsigned long long)pick(u, q) < (unsat == 1u ? T1 : T2);
+                        if (accept) {
+                            mine[k] = (uint8_t)(s ^ 1u);
+                            dE += 8 - 4 * (int32_t)unsat;
+                            dM += 2 - 4 * (int32_t)s;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // pack and write the child
+    if (active) {
+        uint32_t *dst = P.spins[nbuf] + rd.spin_off + (uint64_t)child * rd.wstride;
+        for (uint32_t wi = tl; wi < rd.wstride; wi += cfg.TPR) {
+            uint32_t word = 0;
+            for (uint32_t b = 0; b < 32; ++b) {
+                const uint32_t n = 32 * wi + b;
+                if (n >= N) break;
+                const uint32_t c = ((n % L) + (n / L)) & 1u;
+                word |= (uint32_t)planes[c * PS + (n >> 1)] << b;
+            }
+            dst[wi] = word;
+        }
+        atomicAdd(&acc[2 * rloc], dE);
+        atomicAdd(&acc[2 * rloc + 1], dM);
+    }
+    __syncthreads();
+    if (active && tl == 0) {
+        const uint64_t pc = rd.rep_off + parent, cc = rd.rep_off + child;
+        P.E[nbuf][cc] = P.E[ob][pc] + acc[2 * rloc];
+        P.M[nbuf][cc] = P.M[ob][pc] + acc[2 * rloc + 1];
+        P.fam[nbuf][cc] = P.fam[ob][pc];
+    }
+}
+
+// --------------------------------------------------------------------------
+// Overlaps (Sec. III.D): d = popcount(s XOR s') over the packed spins.
+// --------------------------------------------------------------------------
+__global__ void overlap_kernel(Pool P, const uint32_t *q_runs, int init)
+{
+    __shared__ long long sh_l[32];
+    const uint32_t run = q_runs[blockIdx.y];
+    const RunDev rd = P.runs[run];
+    const RunState st = P.st[run];
+    if (st.status) return;
+    const uint32_t i = init ? 0u : st.step + 1;
+    if (i >= rd.n_beta) return;
+    const uint32_t R = init ? rd.R : st.R_new;
+    const uint32_t buf = i & 1u;
+    const uint32_t N = rd.N, ws = rd.wstride;
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    pa_step_record *rec = P.rec + rd.rec_off + i;
+
+    if (rd.overlap & PA_Q_SHIFT) {
+        const uint32_t h = R / 2;
+        if (blockIdx.x * blockDim.x < h) {
+            long long v = 0;
+            if (p < h) {
+                const uint4 *a = reinterpret_cast<const uint4 *>(P.spins[buf] + rd.spin_off + (uint64_t)p * ws);
+                const uint4 *b = reinterpret_cast<const uint4 *>(P.spins[buf] + rd.spin_off + (uint64_t)(p + h) * ws);
+                uint32_t d = 0;
+                for (uint32_t q = 0; q < ws / 4; ++q) {
+                    const uint4 x = a[q], y = b[q];
+                    d += __popc(x.x ^ y.x) + __popc(x.y ^ y.y) + __popc(x.z ^ y.z) + __popc(x.w ^ y.w);
+                }
+                atomicAdd(&P.qh[rd.qh_off + (uint64_t)i * (N + 1) + d], 1u);
+                const long long qn = (long long)N - 2 * (long long)d;
+                v = qn < 0 ? -qn : qn;
+            }
+            v = block_sum(v, sh_l);
+            if (threadIdx.x == 0) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_absq), (unsigned long long)v);
+                if (blockIdx.x == 0) rec->n_q = h;
+            }
+        }
+    }
+    if ((rd.overlap & PA_Q_PAIR) && rd.paired > (int32_t)run) {
+        const uint32_t pr = (uint32_t)rd.paired;
+        const RunDev rb = P.runs[pr];
+        const RunState sb = P.st[pr];
+        if (sb.status) return;
+        const uint32_t Rb = init ? rb.R : sb.R_new;
+        const uint32_t n = R < Rb ? R : Rb;
+        if (blockIdx.x * blockDim.x < n) {
+            long long v = 0;
+            if (p < n) {
+                const uint4 *a = reinterpret_cast<const uint4 *>(P.spins[buf] + rd.spin_off + (uint64_t)p * ws);
+                const uint4 *b = reinterpret_cast<const uint4 *>(P.spins[buf] + rb.spin_off + (uint64_t)p * ws);
+                uint32_t d = 0;
+                for (uint32_t q = 0; q < ws / 4; ++q) {
+                    const uint4 x = a[q], y = b[q];
+                    d += __popc(x.x ^ y.x) + __popc(x.y ^ y.y) + __popc(x.z ^ y.z) + __popc(x.w ^ y.w);
+                }
+                atomicAdd(&P.qhp[rd.qh_off + (uint64_t)i * (N + 1) + d], 1u);
+                atomicAdd(&P.qhp[rb.qh_off + (uint64_t)i * (N + 1) + d], 1u);
+                const long long qn = (long long)N - 2 * (long long)d;
+                v = qn < 0 ? -qn : qn;
+            }
+            v = block_sum(v, sh_l);
+            if (threadIdx.x == 0) {
+                pa_step_record *rb_rec = P.rec + rb.rec_off + i;
+                atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_absq_pair), (unsigned long long)v);
+                atomicAdd(reinterpret_cast<unsigned long long *>(&rb_rec->sum_absq_pair), (unsigned long long)v);
+                if (blockIdx.x == 0) {
+                    rec->n_q_pair = n;
+                    rb_rec->n_q_pair = n;
+                }
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Measurement (Sec. III.B, Eqs. e, m, c, chi through exact integer sums;
+// Eq. F running sum; Eq. rho_t through family run lengths).  Finishes the step.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) measure_kernel(Pool P, int init)
+{
+    __shared__ long long sh_l[32];
+    __shared__ uint32_t sh_u[33];
+    __shared__ uint32_t sh_carry;
+    const uint32_t run = blockIdx.x;
+    const RunDev rd = P.runs[run];
+    RunState *st = &P.st[run];
+    if (st->status) return;
+    const uint32_t i = init ? 0u : st->step + 1;
+    if (i >= rd.n_beta) return;
+    const uint32_t R = init ? rd.R : st->R_new;
+    const uint32_t b = i & 1u;
+    const int32_t *E = P.E[b] + rd.rep_off;
+    const int32_t *M = P.M[b] + rd.rep_off;
+    const uint32_t *fam = P.fam[b] + rd.rep_off;
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+
+    long long sE = 0, sE2 = 0, sAM = 0, sM2 = 0;
+    for (uint32_t j = tid; j < R; j += nt) {
+        const long long e = E[j], m = M[j];
+        sE += e;
+        sE2 += e * e;
+        sAM += m < 0 ? -m : m;
+        sM2 += m * m;
+    }
+    sE = block_sum(sE, sh_l);
+    sE2 = block_sum(sE2, sh_l);
+    sAM = block_sum(sAM, sh_l);
+    sM2 = block_sum(sM2, sh_l);
+
+    // families are contiguous: start(j) = last index <= j where the ancestor changes
+    long long c2 = 0;
+    uint32_t nfam = 0, cmax = 0;
+    if (tid == 0) sh_carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < R; base += nt) {
+        const uint32_t j = base + tid;
+        const bool ok = j < R;
+        const bool flag = ok && (j == 0 || fam[j] != fam[j - 1]);
+        uint32_t sj = block_inclusive_max(flag ? j : 0u, sh_u);
+        const uint32_t carry = sh_carry;
+        sj = sj > carry ? sj : carry;
+        if (ok) {
+            const uint32_t len = j - sj + 1;
+            c2 += 2 * (long long)(j - sj) + 1;  // sum over a family of (2r + 1) = size^2
+            nfam += flag ? 1u : 0u;
+            cmax = len > cmax ? len : cmax;
+        }
+        __syncthreads();
+        if (tid == nt - 1) sh_carry = sj;
+        __syncthreads();
+    }
+    c2 = block_sum(c2, sh_l);
+    nfam = (uint32_t)block_sum((long long)nfam, sh_l);
+    cmax = (uint32_t)block_max((long long)cmax, sh_l, 0ll);
+
+    if (tid == 0) {
+        pa_step_record *rec = P.rec + rd.rec_off + i;
+        const double lnQ = init ? 0.0 : st->lnQ;
+        rec->beta = P.beta[rd.beta_off + i];
+        rec->lnQ = lnQ;
+        rec->minus_betaF = init ? rd.ln2N : P.rec[rd.rec_off + i - 1].minus_betaF + lnQ;
+        rec->sumE = sE;
+        rec->sumE2 = sE2;
+        rec->sumAbsM = sAM;
+        rec->sumM2 = sM2;
+        rec->sum_c2 = c2;
+        rec->R = R;
+        rec->R_target = rd.R;
+        rec->n_fam = nfam;
+        rec->max_fam = cmax;
+        rec->N = rd.N;
+        rec->status = 0;
+        st->step = i;
+        st->R_cur = R;
+        st->R_new = R;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Weighted averages (Sec. IV, Eqs. appropriateWeight / simpleWeight, W_conf,
+// W_F, Wvar_C, Wvar_Chi) in FP64: one thread per group, sequential over steps
+// and runs m = 0..M-1.  w receives the weights [group][step][m].
+// --------------------------------------------------------------------------
+__global__ void wavg_kernel(const pa_step_record *recs, const unsigned long long *rec_off, uint32_t n_groups,
+                            uint32_t M, uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w)
+{
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_groups) return;
+    const unsigned long long *off = rec_off + (uint64_t)g * M;
+    double *wg = w + (uint64_t)g * n_steps * M;
+    const double Nd = (double)N;
+    double WF = Nd * log(2.0);
+    for (uint32_t i = 0; i < n_steps; ++i) {
+        double *wi = wg + (uint64_t)i * M;
+        double lmax = -INFINITY;
+        for (uint32_t m = 0; m < M; ++m) {
+            const pa_step_record *r = recs + off[m];
+            double lam = log((double)r[i].R) + r[i].minus_betaF;
+            if (kind == PA_WEIGHT_FULL)
+                for (uint32_t k = 1; k <= i; ++k) lam += log((double)r[k - 1].R / (double)r[k].R_target);
+            wi[m] = lam;
+            lmax = lam > lmax ? lam : lmax;
+        }
+        double z = 0.0;
+        for (uint32_t m = 0; m < M; ++m) {
+            wi[m] = exp(wi[m] - lmax);
+            z += wi[m];
+        }
+        pa_wavg o;
+        o.beta = recs[off[0] + i].beta;
+        o.W_e = o.W_e2 = o.W_m = o.W_m2 = o.W_c = o.W_chi = o.W_absq = o.W_absq_pair = 0.0;
+        o.w_max = 0.0;
+        o.sum_w = 0.0;
+        const double beta = o.beta;
+        for (uint32_t m = 0; m < M; ++m) {
+            wi[m] = wi[m] / z;
+            const pa_step_record *r = recs + off[m] + i;
+            const double Ri = (double)r->R;
+            const double e = (double)r->sumE / (Nd * Ri);
+            const double e2 = (double)r->sumE2 / (Nd * Nd * Ri);
+            const double mm = (double)r->sumAbsM / (Nd * Ri);
+            const double m2 = (double)r->sumM2 / (Nd * Nd * Ri);
+            const double c = beta * beta * Nd * (e2 - e * e);
+            const double chi = beta * Nd * (m2 - mm * mm);
+            const double wm = wi[m];
+            o.W_e += wm * e;
+            o.W_e2 += wm * e2;
+            o.W_m += wm * mm;
+            o.W_m2 += wm * m2;
+            o.W_c += wm * c;
+            o.W_chi += wm * chi;
+            if (r->n_q) o.W_absq += wm * ((double)r->sum_absq / (Nd * (double)r->n_q));
+            if (r->n_q_pair) o.W_absq_pair += wm * ((double)r->sum_absq_pair / (Nd * (double)r->n_q_pair));
+            o.sum_w += wm;
+            o.w_max = wm > o.w_max ? wm : o.w_max;
+        }
+        o.Wvar_c = beta * beta * Nd * (o.W_e2 - o.W_e * o.W_e);
+        o.Wvar_chi = beta * Nd * (o.W_m2 - o.W_m * o.W_m);
+        if (i > 0) {
+            const double *wp = wi - M;  // weights at beta_{i-1}
+            double lm = -INFINITY;
+            for (uint32_t m = 0; m < M; ++m) {
+                const double l = log(wp[m]) + recs[off[m] + i].lnQ;
+                lm = l > lm ? l : lm;
+            }
+            double zz = 0.0;
+            for (uint32_t m = 0; m < M; ++m) zz += exp(log(wp[m]) + recs[off[m] + i].lnQ - lm);
+            WF = WF + (lm + log(zz));
+        }
+        o.W_minus_betaF = WF;
+        out[(uint64_t)g * n_steps + i] = o;
+    }
+}
+
+// Weighted overlap distributions (Eq. W_conf_q): grid (steps, groups).
+__global__ void wavg_q_kernel(const pa_step_record *recs, const unsigned long long *rec_off, const uint32_t *qh,
+                              const uint32_t *qhp, const unsigned long long *qh_off, uint32_t M, uint32_t n_steps,
+                              uint32_t N, const double *w, double *Pq, double *Pqp)
+{
+    const uint32_t i = blockIdx.x, g = blockIdx.y;
+    const double *wi = w + ((uint64_t)g * n_steps + i) * M;
+    const unsigned long long *ro = rec_off + (uint64_t)g * M, *qo = qh_off + (uint64_t)g * M;
+    for (uint32_t d = threadIdx.x; d <= N; d += blockDim.x) {
+        double a = 0.0, b = 0.0;
+        for (uint32_t m = 0; m < M; ++m) {
+            const pa_step_record *r = recs + ro[m] + i;
+            const uint64_t q = qo[m] + (uint64_t)i * (N + 1) + d;
+            if (Pq && r->n_q) a += wi[m] * ((double)qh[q] / (double)r->n_q);
+            if (Pqp && r->n_q_pair) b += wi[m] * ((double)qhp[q] / (double)r->n_q_pair);
+        }
+        const uint64_t o = ((uint64_t)g * n_steps + i) * (N + 1) + d;
+        if (Pq) Pq[o] = a;
+        if (Pqp) Pqp[o] = b;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+cudaError_t prepare_kernels()
+{
+    return cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+void launch_init_couplings(const Pool &P, uint32_t n_runs, cudaStream_t s)
+{
+    init_couplings_kernel<<<n_runs, 256, 0, s>>>(P);
+}
+
+void launch_init_population(const Pool &P, uint32_t n_runs, uint32_t max_R, cudaStream_t s)
+{
+    dim3 grid((max_R + 3) / 4, n_runs);
+    init_population_kernel<<<grid, 128, 0, s>>>(P);
+}
+
+void launch_resample(const Pool &P, uint32_t n_runs, cudaStream_t s) { resample_kernel<<<n_runs, 512, 0, s>>>(P); }
+
+SweepCfg sweep_config(uint32_t L)
+{
+    SweepCfg c{};
+    const uint32_t N = L * L;
+    c.G = (N + 7) / 8;
+    uint32_t tpr = 1;
+    while (tpr < c.G) tpr <<= 1;
+    if (tpr <= 128) {
+        c.block = 128;
+        c.TPR = tpr;
+        c.RPC = 128 / tpr;
+    } else {
+        c.TPR = tpr < 1024 ? tpr : 1024;
+        c.block = c.TPR;
+        c.RPC = 1;
+    }
+    c.PS = 4 * c.G;
+    c.smem = c.RPC * 2 * c.PS + 2 * c.PS + 8 * c.RPC;
+    return c;
+}
+
+void launch_sweep(const Pool &P, const uint32_t *group_runs, uint32_t n_group_runs, uint32_t max_Rcap,
+                  const SweepCfg &cfg, cudaStream_t s)
+{
+    dim3 grid((max_Rcap + cfg.RPC - 1) / cfg.RPC, n_group_runs);
+    sweep_kernel<<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
+}
+
+void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, uint32_t max_Rcap, int init,
+                    cudaStream_t s)
+{
+    dim3 grid((max_Rcap + 255) / 256, n_q_runs);
+    overlap_kernel<<<grid, 256, 0, s>>>(P, q_runs, init);
+}
+
+void launch_measure(const Pool &P, uint32_t n_runs, int init, cudaStream_t s)
+{
+    measure_kernel<<<n_runs, 512, 0, s>>>(P, init);
+}
+
+void launch_wavg(const pa_step_record *recs, const unsigned long long *rec_off, const uint32_t *qh,
+                 const uint32_t *qhp, const unsigned long long *qh_off, uint32_t n_groups, uint32_t M,
+                 uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w, double *Pq, double *Pqp,
+                 cudaStream_t s)
+{
+    wavg_kernel<<<(n_groups + 63) / 64, 64, 0, s>>>(recs, rec_off, n_groups, M, n_steps, N, kind, out, w);
+    if (Pq || Pqp) {
+        dim3 grid(n_steps, n_groups);
+        wavg_q_kernel<<<grid, 256, 0, s>>>(recs, rec_off, qh, qhp, qh_off, M, n_steps, N, w, Pq, Pqp);
+    }
+}
+
+}  // namespace pa

@@ -1,0 +1,101 @@
+"""The C-ABI library: builds, loads, exports every symbol of include/pa.h, its
+structs match the Python mirrors, and argument validation runs before any CUDA
+call (so these tests need no GPU)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2207_05535_gb300 import _lib, build
+from paper_2207_05535_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pa.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pa_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.EXPORTS)
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
+    for n in names:
+        assert re.search(rf"\bT {n}$", out, re.M), n
+
+
+def test_struct_layouts_match_header(tmp_path):
+    prog = tmp_path / "sz.c"
+    prog.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "pa.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(pa_run_desc), sizeof(pa_step_record), sizeof(pa_wavg),
+         offsetof(pa_step_record, R), offsetof(pa_step_record, status), offsetof(pa_wavg, W_minus_betaF));
+  return 0;
+}
+''')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert vals[0] == C.sizeof(_lib.pa_run_desc)
+    assert vals[1] == _lib.RECORD_DTYPE.itemsize
+    assert vals[2] == _lib.WAVG_DTYPE.itemsize
+    assert vals[3] == _lib.RECORD_DTYPE.fields["R"][1]
+    assert vals[4] == _lib.RECORD_DTYPE.fields["status"][1]
+    assert vals[5] == _lib.WAVG_DTYPE.fields["W_minus_betaF"][1]
+
+
+def test_status_strings(lib):
+    for code in range(9):
+        assert _lib.pa_status_string(code)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(L=7), dict(L=2), dict(L=258), dict(R=0), dict(R_cap=10, R=20), dict(model=3), dict(resample=5),
+    dict(betas=np.array([0.0, 0.5, 0.4])), dict(betas=np.array([])), dict(overlap=8),
+])
+def test_invalid_descriptors_rejected_before_any_device_work(lib, bad):
+    args = dict(L=8, model=W.FERRO, R=16, theta=1, betas=np.array([0.0, 0.1]))
+    cap = bad.pop("R_cap", 0)
+    args.update(bad)
+    d = W.RunDesc(**args)
+    if cap:
+        d.R_cap = cap
+    with pytest.raises(_lib.PAError) as ei:
+        _lib.pa_create([d])
+    assert ei.value.code == 1
+
+
+def test_paired_runs_must_be_mutual(lib):
+    b = W.schedule(1.0, 3)
+    a = W.RunDesc(8, W.EA_PMJ, 16, 1, b, overlap=W.Q_PAIR, paired=1)
+    c = W.RunDesc(8, W.EA_PMJ, 16, 1, b, overlap=W.Q_PAIR, paired=0, run_id=1)
+    bad = W.RunDesc(10, W.EA_PMJ, 16, 1, b, overlap=W.Q_PAIR, paired=0, run_id=1)
+    with pytest.raises(_lib.PAError):
+        _lib.pa_create([a, bad])
+    with pytest.raises(_lib.PAError):
+        _lib.pa_create([W.RunDesc(8, W.EA_PMJ, 16, 1, b, overlap=W.Q_PAIR, paired=0)])
+    del c
+
+
+def test_oracle_and_engine_records_share_the_abi_layout():
+    import oracle as O
+    assert O.RECORD_DTYPE == _lib.RECORD_DTYPE
+    assert O.WAVG_DTYPE == _lib.WAVG_DTYPE
