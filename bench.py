@@ -168,7 +168,7 @@ def main():
     # CPU baseline first: a spawn pool, before any CUDA context exists
     cpu = None
     if rank == 0 and world >= 1 and args.gpus == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample()
+        cpu = oracle_sample(n_temps=25)
 
     import numpy as np
     import torch
@@ -263,8 +263,12 @@ def main():
     # ---- plain form: one run per engine, all on one stream (one run per launch)
     plain = None
     if not args.no_plain and rank == 0:
-        n_plain = 20
-        engines = [_lib.Engine([descs[k]], stream.cuda_stream) for k in range(n_plain)]
+        import dataclasses
+        n_plain = 20  # runs = 10 disorder samples, one sample (two paired populations) per engine
+        engines = []
+        for smp in range(n_plain // 2):
+            pair = [dataclasses.replace(descs[2 * smp + p_], paired=1 - p_) for p_ in range(2)]
+            engines.append(_lib.Engine(pair, stream.cuda_stream))
         for e in engines:
             e.reset()
             e.step(n_ticks, False)
@@ -278,13 +282,15 @@ def main():
         torch.cuda.synchronize()
         pms = a.elapsed_time(b)
         pupd = 0
-        for e, k in zip(engines, range(n_plain)):
-            rec = e.records(0)
-            pupd += int(sum(descs[k].theta * descs[k].N * int(r) for r in rec["R"][1:]))
+        for smp, e in enumerate(engines):
+            for p_ in range(2):
+                d_ = descs[2 * smp + p_]
+                rec = e.records(p_)
+                pupd += int(sum(d_.theta * d_.N * int(r) for r in rec["R"][1:]))
         for e in engines:
             e.close()
         plain = {"value": pupd / (pms * 1e6), "unit": UNIT, "runs": n_plain,
-                 "runs_per_s": n_plain / (pms / 1e3), "form": "one run per engine and per launch, one stream"}
+                 "runs_per_s": n_plain / (pms / 1e3), "form": "one disorder sample (two populations) per engine and per launch, no graph, one stream"}
 
     # ---- end to end through the C ABI: host descriptors in, host results out
     e2e = None
