@@ -165,6 +165,31 @@ pa_status pa_weighted_average(const pa_step_record *recs, const uint32_t *qhist,
                               uint32_t M, uint32_t n_steps, uint32_t N, uint32_t weight_kind, pa_wavg *out,
                               double *Pq, double *Pq_pair, void *cuda_stream);
 
+/* Limits of pa_weighted_average_noalloc's fixed scratch. */
+#define PA_NOALLOC_MAX_RUNS 4096u      /* M */
+#define PA_NOALLOC_MAX_WEIGHTS 65536u  /* M * n_steps */
+
+/* Weighted averages (same arithmetic as pa_weighted_average, no overlap
+ * distributions) for callers that cannot allocate device memory: work
+ * recorded inside a CUDA graph capture, serving loops that reserve all device
+ * memory up front and must not call into the allocator, or processes whose
+ * device memory belongs to another allocator.  The paper has no counterpart;
+ * this is a deployment variant.
+ *   d_recs: device pointer, M * n_steps records laid out [m][i] (run m, step i);
+ *   d_out:  device pointer, n_steps results; N: spins per run.
+ * Nothing is allocated or freed.  The scratch (record offsets and weights) is
+ * one fixed array of about 544 KiB in device memory that every GPU loading
+ * libpa.so holds until the process exits; M > PA_NOALLOC_MAX_RUNS or
+ * M * n_steps > PA_NOALLOC_MAX_WEIGHTS is rejected with PA_ERR_INVALID_ARG
+ * (and a message on stderr).  The first call on each device looks up the
+ * array's device address (with that device current); make that first call
+ * before any stream capture.  The work is enqueued on cuda_stream (a
+ * cudaStream_t or NULL) and the call returns without waiting.  Every call
+ * shares the one array: calls whose work overlaps on the GPU (other streams,
+ * or other host threads) race and must be serialised by the caller. */
+pa_status pa_weighted_average_noalloc(const pa_step_record *d_recs, uint32_t M, uint32_t n_steps, uint32_t N,
+                                      uint32_t weight_kind, pa_wavg *d_out, void *cuda_stream);
+
 /* Number of kernels this engine has launched (graph replays count each node). */
 uint64_t pa_launch_count(const pa_engine *e);
 

@@ -49,7 +49,7 @@ WAVG_DTYPE = np.dtype([
 ])
 
 EXPORTS = ["pa_create", "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population",
-           "pa_weighted_average_runs", "pa_weighted_average", "pa_launch_count", "pa_set_profiling",
+           "pa_weighted_average_runs", "pa_weighted_average", "pa_weighted_average_noalloc", "pa_launch_count", "pa_set_profiling",
            "pa_kernel_times", "pa_transfer_bytes", "pa_destroy", "pa_status_string"]
 KERNEL_KINDS = ["resample", "sweep", "overlap", "measure", "init", "wavg"]
 
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
         lib.pa_weighted_average_runs.argtypes = [vp, P(u32), u32, u32, u32, vp, P(C.c_double), P(C.c_double)]
         lib.pa_weighted_average.argtypes = [vp, P(u32), P(u32), u32, u32, u32, u32, vp, P(C.c_double),
                                             P(C.c_double), vp]
+        lib.pa_weighted_average_noalloc.argtypes = [vp, u32, u32, u32, u32, vp, vp]
         lib.pa_launch_count.argtypes = [vp]
         lib.pa_launch_count.restype = C.c_uint64
         lib.pa_set_profiling.argtypes = [vp, C.c_int]

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpa.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["pa_kernels.cu", "pa_engine.cu"]
+SOURCES = ["pa_kernels.cu", "pa_engine.cu", "pa_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
