@@ -113,6 +113,14 @@ typedef struct pa_engine pa_engine;
  * L, model, disorder_id and n_beta), PA_ERR_OOM, PA_ERR_CUDA. */
 pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, pa_engine **out);
 
+/* pa_create with options: flags = 0 or PA_CREATE_GENERIC_SWEEP, which keeps
+ * every lattice size on the general byte-plane sweep kernel instead of the
+ * bit-sliced kernel used for L = 8, 16, ..., 256 (both give identical results;
+ * the option exists to check that). */
+enum { PA_CREATE_GENERIC_SWEEP = 1 };
+pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, uint32_t flags,
+                       pa_engine **out);
+
 /* Return every run of the engine to its beta_0 population (same descriptors,
  * same randomness, so the next anneal repeats the first one bit for bit)
  * without reallocating: clears records, histograms and statuses, redraws the

@@ -48,7 +48,7 @@ WAVG_DTYPE = np.dtype([
     ("w_max", "f8"), ("sum_w", "f8"),
 ])
 
-EXPORTS = ["pa_create", "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population",
+EXPORTS = ["pa_create", "pa_create_ex", "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population",
            "pa_weighted_average_runs", "pa_weighted_average", "pa_weighted_average_noalloc", "pa_launch_count", "pa_set_profiling",
            "pa_kernel_times", "pa_transfer_bytes", "pa_destroy", "pa_status_string"]
 KERNEL_KINDS = ["resample", "sweep", "overlap", "measure", "init", "wavg"]
@@ -69,6 +69,7 @@ def load(path: str = LIB_PATH):
         lib = C.CDLL(path)
         P, u32, vp = C.POINTER, C.c_uint32, C.c_void_p
         lib.pa_create.argtypes = [P(pa_run_desc), u32, vp, P(vp)]
+        lib.pa_create_ex.argtypes = [P(pa_run_desc), u32, vp, u32, P(vp)]
         lib.pa_reset.argtypes = [vp]
         lib.pa_anneal_step.argtypes = [vp, u32, C.c_int]
         lib.pa_sync.argtypes = [vp]
@@ -123,6 +124,18 @@ def pa_create(runs, stream=None):
     h = C.c_void_p()
     s = C.c_void_p(stream) if stream else None
     _check(lib.pa_create(d, len(runs), s, C.byref(h)), "pa_create")
+    return h
+
+
+PA_CREATE_GENERIC_SWEEP = 1
+
+
+def pa_create_ex(runs, stream=None, flags=0):
+    lib = load()
+    d = make_descs(runs)
+    h = C.c_void_p()
+    s = C.c_void_p(stream) if stream else None
+    _check(lib.pa_create_ex(d, len(runs), s, flags, C.byref(h)), "pa_create_ex")
     return h
 
 
@@ -226,9 +239,9 @@ def pa_status_string(code):
 class Engine:
     """Owner of one pa_engine handle (context manager)."""
 
-    def __init__(self, runs, stream=None):
+    def __init__(self, runs, stream=None, flags=0):
         self.runs = list(runs)
-        self.h = pa_create(self.runs, stream)
+        self.h = pa_create_ex(self.runs, stream, flags) if flags else pa_create(self.runs, stream)
 
     def __enter__(self):
         return self

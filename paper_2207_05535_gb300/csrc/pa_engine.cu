@@ -24,6 +24,7 @@ using namespace pa;
 
 struct SweepGroup {
     uint32_t L;
+    int any_glass = 0;
     SweepCfg cfg;
     uint32_t max_Rcap;
     std::vector<uint32_t> runs;
@@ -170,8 +171,9 @@ void enqueue_tick(pa_engine *e)
 {
     timed_launch(e, PA_K_RESAMPLE, [&] { launch_resample(e->P, e->n_runs, e->stream); });
     for (auto &g : e->groups)
-        timed_launch(e, PA_K_SWEEP,
-                     [&] { launch_sweep(e->P, g.d_runs, (uint32_t)g.runs.size(), g.max_Rcap, g.cfg, e->stream); });
+        timed_launch(e, PA_K_SWEEP, [&] {
+            launch_sweep(e->P, g.d_runs, (uint32_t)g.runs.size(), g.max_Rcap, g.cfg, g.any_glass, e->stream);
+        });
     if (!e->q_runs.empty())
         timed_launch(e, PA_K_OVERLAP, [&] {
             launch_overlap(e->P, e->d_q_runs, (uint32_t)e->q_runs.size(), e->max_Rcap, 0, e->stream);
@@ -275,7 +277,12 @@ pa_status pa_destroy(pa_engine *e)
 
 pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, pa_engine **out)
 {
-    if (!out) return PA_ERR_INVALID_ARG;
+    return pa_create_ex(runs, n_runs, cuda_stream, 0u, out);
+}
+
+pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, uint32_t flags, pa_engine **out)
+{
+    if (!out || (flags & ~(uint32_t)PA_CREATE_GENERIC_SWEEP)) return PA_ERR_INVALID_ARG;
     *out = nullptr;
     pa_status vs = validate(runs, n_runs);
     if (vs != PA_OK) return vs;
@@ -310,8 +317,8 @@ pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream,
         x.L = d.L;
         x.N = d.L * d.L;
         x.Lh = d.L / 2;
-        uint32_t words = (x.N + 31) / 32;
-        x.wstride = (words + 3) / 4 * 4;
+        const uint32_t pw = (x.N + 63) / 64;  // words per colour plane
+        x.wstride = (2 * pw + 3) / 4 * 4;
         x.model = d.model;
         x.R = d.R;
         x.R_cap = default_cap(d);
@@ -332,7 +339,7 @@ pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream,
         x.qh_off = qh;
         if (d.overlap) qh += (uint64_t)d.n_beta * (x.N + 1);
         x.J_off = J;
-        J += 2ull * x.wstride;
+        J += 2ull * x.wstride + 8ull * pw;
         x.scr_off = scr;
         scr += scratch_words(x.N, x.R_cap);
         x.ln2N = (double)x.N * std::log(2.0);
@@ -371,12 +378,13 @@ pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream,
             g = group_of_L.emplace(d.L, e->groups.size()).first;
             SweepGroup sg;
             sg.L = d.L;
-            sg.cfg = sweep_config(d.L);
+            sg.cfg = sweep_config(d.L, (flags & PA_CREATE_GENERIC_SWEEP) ? 0 : 1);
             sg.max_Rcap = 0;
             e->groups.push_back(sg);
         }
         SweepGroup &sg = e->groups[g->second];
         sg.runs.push_back(r);
+        if (d.model == PA_EA_PMJ) sg.any_glass = 1;
         sg.max_Rcap = x.R_cap > sg.max_Rcap ? x.R_cap : sg.max_Rcap;
         if (d.overlap) e->q_runs.push_back(r);
     }
@@ -583,10 +591,13 @@ pa_status pa_population(pa_engine *e, uint32_t run, int8_t *host_spins, int32_t 
         PA_CUDA(cudaMemcpyAsync(words.data(), e->P.spins[b] + x.spin_off, sizeof(uint32_t) * words.size(),
                                 cudaMemcpyDeviceToHost, e->stream));
         PA_CUDA(cudaStreamSynchronize(e->stream));
+        const uint32_t pw = (x.N + 63) / 64;
         for (uint32_t j = 0; j < R; ++j)
-            for (uint32_t n = 0; n < x.N; ++n)
-                host_spins[(size_t)j * x.N + n] =
-                    ((words[(size_t)j * x.wstride + (n >> 5)] >> (n & 31)) & 1u) ? (int8_t)1 : (int8_t)-1;
+            for (uint32_t n = 0; n < x.N; ++n) {
+                const uint32_t c = ((n % x.L) + (n / x.L)) & 1u, k = n >> 1;
+                const uint32_t word = words[(size_t)j * x.wstride + c * pw + (k >> 5)];
+                host_spins[(size_t)j * x.N + n] = ((word >> (k & 31)) & 1u) ? (int8_t)1 : (int8_t)-1;
+            }
     }
     if (host_E && R)
         PA_CUDA(cudaMemcpyAsync(host_E, e->P.E[b] + x.rep_off, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, e->stream));

@@ -1,16 +1,20 @@
 // Internal layout shared by the engine's host code and its kernels.
 //
 // Device memory layout (one pool per engine, every run at its own offsets):
-//   spins[b]  uint32 [sum R_cap wstride]    replica j of a run at word spin_off + j wstride,
-//                                           site n -> bit (n & 31) of word (n >> 5),
-//                                           bit 1 = spin +1; buffer b = step & 1
+//   spins[b]  uint32 [sum R_cap wstride]    replica j of a run at word spin_off + j wstride:
+//                                           colour plane 0 in words [0, PW), plane 1 in
+//                                           [PW, 2 PW), PW = ceil(N/64); site n = y L + x has
+//                                           colour (x + y) & 1 and index k = n >> 1 (bit k & 31
+//                                           of word k >> 5); bit 1 = spin +1; buffer b = step & 1
 //   E[b], M[b], fam[b]   [sum R_cap]        energy, magnetisation, beta_0 ancestor
 //   parent, cnt          [sum R_cap]        parent map of the children, copy numbers r_j
 //   rec                  [sum n_beta]       per-temperature records (pa_step_record)
 //   qh, qhp              [sum n_beta (N+1)] overlap histograms over d (shift / pair)
 //   beta, wt, thr                           schedule, exp(-4 n dbeta_i) per step, Metropolis
 //                                           thresholds per step (shared by equal schedules)
-//   J                    [2 wstride] per run  packed "J = -1" bits of right / down bonds
+//   J                    per run: site-order "J = -1" bits of right / down bonds
+//                        (2 wstride words), then per colour plane word the four bond
+//                        masks (same, rotated, up, down neighbour) [2][4][PW]
 //   scratch              per run: level histogram (N+1 u32), level CDF (N+1 f64),
 //                        level fill counters (N+1 u32), members (R_cap u32)
 #pragma once
@@ -71,8 +75,9 @@ struct Pool {
 
 // Sweep launch shape for one lattice size.
 struct SweepCfg {
+    uint32_t fast;   // 1: bit-sliced kernel (L a power of two, 8..256)
     uint32_t block;  // threads per CTA
-    uint32_t TPR;    // threads per replica (power of two)
+    uint32_t TPR;    // threads per replica (power of two; fast kernel: words per plane)
     uint32_t RPC;    // replicas per CTA
     uint32_t G;      // Philox groups per colour = ceil(N / 8)
     uint32_t PS;     // bytes per colour plane = 4 G
@@ -90,9 +95,9 @@ inline uint64_t scratch_words(uint32_t N, uint32_t R_cap)
 void launch_init_couplings(const Pool &P, uint32_t n_runs, cudaStream_t s);
 void launch_init_population(const Pool &P, uint32_t n_runs, uint32_t max_R, cudaStream_t s);
 void launch_resample(const Pool &P, uint32_t n_runs, cudaStream_t s);
-SweepCfg sweep_config(uint32_t L);
+SweepCfg sweep_config(uint32_t L, int allow_fast);
 void launch_sweep(const Pool &P, const uint32_t *group_runs, uint32_t n_group_runs, uint32_t max_Rcap,
-                  const SweepCfg &cfg, cudaStream_t s);
+                  const SweepCfg &cfg, int any_glass, cudaStream_t s);
 void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, uint32_t max_Rcap, int init,
                     cudaStream_t s);
 void launch_measure(const Pool &P, uint32_t n_runs, int init, cudaStream_t s);

@@ -197,13 +197,38 @@ __device__ __forceinline__ void set_status(const Pool &P, uint32_t run, uint32_t
 }
 
 // --------------------------------------------------------------------------
+// Spin layout of a replica (HBM and the fast sweep's shared memory): two
+// colour planes, plane c holding the sites of colour c = (x + y) & 1 in
+// sublattice order k = n >> 1 (n = y L + x), bit k & 31 of word k >> 5, bit 1 =
+// spin +1.  Plane 0 occupies words [0, PW), plane 1 words [PW, 2 PW), PW =
+// ceil(N / 64).  Site of (c, k): y = k / (L/2), x = 2 (k mod L/2) + ((c + y) & 1).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t site_of(uint32_t L, uint32_t c, uint32_t k)
+{
+    const uint32_t Lh = L >> 1, y = k / Lh, xp = k - y * Lh;
+    return y * L + 2 * xp + ((c + y) & 1u);
+}
+
+__device__ __forceinline__ uint32_t spin_bit(const uint32_t *planes, uint32_t PW, uint32_t L, uint32_t n)
+{
+    const uint32_t x = n % L, y = n / L, c = (x + y) & 1u, k = n >> 1;
+    return (planes[c * PW + (k >> 5)] >> (k & 31)) & 1u;
+}
+
+// --------------------------------------------------------------------------
 // Initialisation (Sec. II.B step (i) at beta_0 = 0; couplings of Eq. H_SG).
+// Couplings are kept twice: site order (bit n of Jr / Jd: the right / down
+// bond of site n is J = -1) and, for the fast sweep, per colour plane word the
+// four bond masks of its sites: bond to the same-index neighbour, to the
+// rotated neighbour (index k -+ 1 within the row), up and down.
 // --------------------------------------------------------------------------
 __global__ void init_couplings_kernel(Pool P)
 {
     const RunDev rd = P.runs[blockIdx.x];
-    uint32_t *Jr = P.J + rd.J_off, *Jd = Jr + rd.wstride;
-    for (uint32_t w = threadIdx.x; w < rd.wstride; w += blockDim.x) {
+    const uint32_t SW = rd.wstride;          // site-order words (>= ceil(N/32))
+    const uint32_t PW = (rd.N + 63) / 64;    // plane words
+    uint32_t *Jr = P.J + rd.J_off, *Jd = Jr + SW, *Jp = Jd + SW;  // Jp: [c][4][PW]
+    for (uint32_t w = threadIdx.x; w < SW; w += blockDim.x) {
         uint32_t wr = 0, wd = 0;
         if (rd.model == PA_EA_PMJ) {
             for (uint32_t g = 0; g < 8; ++g) {
@@ -221,6 +246,29 @@ __global__ void init_couplings_kernel(Pool P)
         Jr[w] = wr;
         Jd[w] = wd;
     }
+    __syncthreads();
+    const uint32_t L = rd.L, half = rd.N >> 1;
+    for (uint32_t cw = threadIdx.x; cw < 2 * PW; cw += blockDim.x) {
+        const uint32_t c = cw / PW, w = cw - c * PW;
+        uint32_t js = 0, jr = 0, ju = 0, jd = 0;
+        for (uint32_t b = 0; b < 32; ++b) {
+            const uint32_t k = 32 * w + b;
+            if (k >= half) break;
+            const uint32_t n = site_of(L, c, k), x = n % L, y = n / L;
+            const uint32_t p = (c + y) & 1u;
+            const uint32_t right = get_bit(Jr, n), left = get_bit(Jr, y * L + (x == 0 ? L - 1 : x - 1));
+            const uint32_t down = get_bit(Jd, n), up = get_bit(Jd, (y == 0 ? L - 1 : y - 1) * L + x);
+            js |= (p ? left : right) << b;
+            jr |= (p ? right : left) << b;
+            ju |= up << b;
+            jd |= down << b;
+        }
+        uint32_t *o = Jp + c * 4 * PW;
+        o[w] = js;
+        o[PW + w] = jr;
+        o[2 * PW + w] = ju;
+        o[3 * PW + w] = jd;
+    }
 }
 
 // One warp per replica: uniform spins from Philox, then E and M exactly.
@@ -231,27 +279,28 @@ __global__ void init_population_kernel(Pool P)
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= rd.R) return;
+    const uint32_t L = rd.L, half = rd.N >> 1, PW = (rd.N + 63) / 64;
     uint32_t *s = P.spins[0] + rd.spin_off + (uint64_t)j * rd.wstride;
-    for (uint32_t w = lane; w < rd.wstride; w += 32) {
+    for (uint32_t cw = lane; cw < 2 * PW; cw += 32) {
+        const uint32_t c = cw / PW, w = cw - c * PW;
         uint32_t word = 0;
-        for (uint32_t g = 0; g < 8; ++g) {
-            const uint32_t n0 = 32 * w + 4 * g;
-            if (n0 >= rd.N) break;
-            const uint4 u = philox4x32_10(n0 >> 2, j, 0, TAG_INIT << 24, rd.seed, rd.run_id);
-            for (uint32_t q = 0; q < 4; ++q)
-                if (n0 + q < rd.N) word |= (pick(u, q) >> 31) << (4 * g + q);
+        for (uint32_t b = 0; b < 32; ++b) {
+            const uint32_t k = 32 * w + b;
+            if (k >= half) break;
+            const uint32_t n = site_of(L, c, k);
+            const uint4 u = philox4x32_10(n >> 2, j, 0, TAG_INIT << 24, rd.seed, rd.run_id);
+            word |= (pick(u, n & 3u) >> 31) << b;
         }
-        s[w] = word;
+        s[cw] = word;
     }
     __syncwarp();
     const uint32_t *Jr = P.J + rd.J_off, *Jd = Jr + rd.wstride;
-    const uint32_t L = rd.L;
     int32_t unsat = 0, up = 0;
     for (uint32_t n = lane; n < rd.N; n += 32) {
         const uint32_t x = n % L, y = n / L;
-        const uint32_t b = get_bit(s, n);
-        const uint32_t br = get_bit(s, y * L + (x + 1 == L ? 0 : x + 1));
-        const uint32_t bd = get_bit(s, (y + 1 == L ? 0 : y + 1) * L + x);
+        const uint32_t b = spin_bit(s, PW, L, n);
+        const uint32_t br = spin_bit(s, PW, L, y * L + (x + 1 == L ? 0 : x + 1));
+        const uint32_t bd = spin_bit(s, PW, L, (y + 1 == L ? 0 : y + 1) * L + x);
         unsat += (int32_t)((b ^ br ^ get_bit(Jr, n)) + (b ^ bd ^ get_bit(Jd, n)));
         up += (int32_t)b;
     }
@@ -418,12 +467,12 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P)
 }
 
 // --------------------------------------------------------------------------
-// Fused gather + theta checkerboard Metropolis sweeps (Sec. V.A.1).
-// Shared memory per replica: two colour planes of bytes, plane c holding the
-// sites of colour c = (x + y) & 1 in sublattice order k = n >> 1.  Every thread
-// owns Philox groups g (sites 4g..4g+3 of a colour): one Philox call gives the
-// four uniforms of a group.  A shared "bond mask" plane holds per site the
-// J = -1 bits of its right, left, down and up bonds.
+// Fused gather + theta checkerboard Metropolis sweeps (Sec. V.A.1), any even L.
+// Shared memory per replica: the two colour planes unpacked to one byte per
+// site.  Every thread owns Philox groups g (sublattice sites 4g..4g+3 of a
+// colour): one Philox call gives the four uniforms of a group.  A shared
+// "bond mask" plane holds per site the J = -1 bits of its right, left, down
+// and up bonds.
 // --------------------------------------------------------------------------
 __global__ void sweep_kernel(Pool P, const uint32_t *group_runs, SweepCfg cfg)
 {
@@ -438,7 +487,7 @@ __global__ void sweep_kernel(Pool P, const uint32_t *group_runs, SweepCfg cfg)
     const uint32_t tile0 = blockIdx.x * cfg.RPC;
     if (tile0 >= Rn) return;  // uniform over the CTA
 
-    const uint32_t L = rd.L, N = rd.N, Lh = rd.Lh, half = N >> 1, PS = cfg.PS;
+    const uint32_t L = rd.L, N = rd.N, Lh = rd.Lh, half = N >> 1, PS = cfg.PS, PW = (N + 63) / 64;
     const uint32_t rloc = threadIdx.x / cfg.TPR, tl = threadIdx.x % cfg.TPR;
     const uint32_t child = tile0 + rloc;
     const bool active = rloc < cfg.RPC && child < Rn;
@@ -467,14 +516,13 @@ __global__ void sweep_kernel(Pool P, const uint32_t *group_runs, SweepCfg cfg)
     if (active) {
         parent = P.parent[rd.rep_off + child];
         const uint32_t *src = P.spins[ob] + rd.spin_off + (uint64_t)parent * rd.wstride;
-        const uint32_t nwords = (N + 31) >> 5;
-        for (uint32_t wi = tl; wi < nwords; wi += cfg.TPR) {
-            const uint32_t word = src[wi];
+        for (uint32_t cw = tl; cw < 2 * PW; cw += cfg.TPR) {
+            const uint32_t c = cw / PW, w = cw - c * PW;
+            const uint32_t word = src[cw];
             for (uint32_t b = 0; b < 32; ++b) {
-                const uint32_t n = 32 * wi + b;
-                if (n >= N) break;
-                const uint32_t c = ((n % L) + (n / L)) & 1u;
-                planes[c * PS + (n >> 1)] = (uint8_t)((word >> b) & 1u);
+                const uint32_t k = 32 * w + b;
+                if (k >= half) break;
+                planes[c * PS + k] = (uint8_t)((word >> b) & 1u);
             }
         }
     }
@@ -521,15 +569,15 @@ __global__ void sweep_kernel(Pool P, const uint32_t *group_runs, SweepCfg cfg)
     // pack and write the child
     if (active) {
         uint32_t *dst = P.spins[nbuf] + rd.spin_off + (uint64_t)child * rd.wstride;
-        for (uint32_t wi = tl; wi < rd.wstride; wi += cfg.TPR) {
+        for (uint32_t cw = tl; cw < 2 * PW; cw += cfg.TPR) {
+            const uint32_t c = cw / PW, w = cw - c * PW;
             uint32_t word = 0;
             for (uint32_t b = 0; b < 32; ++b) {
-                const uint32_t n = 32 * wi + b;
-                if (n >= N) break;
-                const uint32_t c = ((n % L) + (n / L)) & 1u;
-                word |= (uint32_t)planes[c * PS + (n >> 1)] << b;
+                const uint32_t k = 32 * w + b;
+                if (k >= half) break;
+                word |= (uint32_t)planes[c * PS + k] << b;
             }
-            dst[wi] = word;
+            dst[cw] = word;
         }
         atomicAdd(&acc[2 * rloc], dE);
         atomicAdd(&acc[2 * rloc + 1], dM);
@@ -539,6 +587,169 @@ __global__ void sweep_kernel(Pool P, const uint32_t *group_runs, SweepCfg cfg)
         const uint64_t pc = rd.rep_off + parent, cc = rd.rep_off + child;
         P.E[nbuf][cc] = P.E[ob][pc] + acc[2 * rloc];
         P.M[nbuf][cc] = P.M[ob][pc] + acc[2 * rloc + 1];
+        P.fam[nbuf][cc] = P.fam[ob][pc];
+    }
+}
+
+// --------------------------------------------------------------------------
+// Bit-sliced sweep for L a power of two, 8 <= L <= 256 (Sec. V.A.1).
+// Each thread owns word w of both colour planes of one replica (32 sites of a
+// colour).  Per half-sweep it forms, as 32-bit masks, the spin of each
+// neighbour (same index, index rotated by one within the row, row above, row
+// below) from the other plane, the unsatisfied bonds x_d = s ^ n_d ^ J_d, their
+// count with a bit-sliced adder (c0 = count & 1, ge2 = count >= 2), and the
+// acceptance mask
+//      accept = ge2 | (c0 & B1) | B2,   B_m = [u < T_m]  (T_2 <= T_1),
+// i.e. dE = 8 - 4 count <= 0, or u < T_1 when dE = 4, or u < T_2 when dE = 8.
+// The 32 uniforms come from 8 Philox calls with the same counters as the
+// generic kernel, so both kernels (and the oracle) flip the same spins.
+// E and M of the child are recomputed from its final planes.
+// --------------------------------------------------------------------------
+template <bool SG>
+__global__ void __launch_bounds__(1024) sweep_pow2_kernel(Pool P, const uint32_t *group_runs, SweepCfg cfg)
+{
+    extern __shared__ __align__(16) uint32_t smw[];
+    const uint32_t run = group_runs[blockIdx.y];
+    const RunDev rd = P.runs[run];
+    const RunState st = P.st[run];
+    if (st.status) return;
+    const uint32_t i = st.step + 1;
+    if (i >= rd.n_beta) return;
+    const uint32_t Rn = st.R_new;
+    const uint32_t tile0 = blockIdx.x * cfg.RPC;
+    if (tile0 >= Rn) return;  // uniform over the CTA
+
+    const uint32_t HW = cfg.TPR;  // words per plane = threads per replica
+    const uint32_t Lh = rd.Lh, N = rd.N;
+    const uint32_t rloc = threadIdx.x / HW, w = threadIdx.x & (HW - 1);
+    const uint32_t child = tile0 + rloc;
+    const bool active = child < Rn;
+    uint32_t *pl = smw + rloc * 2 * HW;
+    int32_t *acc = reinterpret_cast<int32_t *>(smw + cfg.RPC * 2 * HW);
+    const bool wide = HW > 32;
+    if (wide && threadIdx.x < 2 * cfg.RPC) acc[threadIdx.x] = 0;
+
+    const uint32_t ob = (i - 1) & 1u, nbuf = i & 1u;
+    uint32_t own0 = 0, own1 = 0, parent = 0;
+    if (active) {
+        parent = P.parent[rd.rep_off + child];
+        const uint32_t *src = P.spins[ob] + rd.spin_off + (uint64_t)parent * rd.wstride;
+        own0 = src[w];
+        own1 = src[HW + w];
+    }
+    pl[w] = own0;
+    pl[HW + w] = own1;
+    uint32_t J[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    if (SG) {
+        const uint32_t *Jp = P.J + rd.J_off + 2 * rd.wstride;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int d = 0; d < 4; ++d) J[c][d] = Jp[(c * 4 + d) * HW + w];
+    }
+    // segment masks for rows shorter than a word (Lh = 4, 8, 16)
+    const uint32_t LOW = Lh == 4 ? 0x11111111u : Lh == 8 ? 0x01010101u : 0x00010001u;
+    const uint32_t HIGH = LOW << (Lh - 1);
+    const uint32_t EVEN = Lh == 4 ? 0x0F0F0F0Fu : Lh == 8 ? 0x00FF00FFu : 0x0000FFFFu;  // rows 0, 2, ...
+    const uint32_t WR = Lh >> 5;  // words per row when Lh >= 32
+    const uint32_t y_of_w = wide || Lh >= 32 ? w / (WR ? WR : 1) : 0;
+
+    const unsigned long long T1 = P.thr[rd.thr_off + 2 * i], T2 = P.thr[rd.thr_off + 2 * i + 1];
+    const uint32_t t1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T1;
+    const uint32_t t2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T2;
+    const uint32_t all1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : 0u;
+    const uint32_t all2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : 0u;
+    if (HW <= 32) __syncwarp(); else __syncthreads();
+
+    // neighbour masks of plane-c word w, read from plane (c ^ 1)
+    auto neighbours = [&](uint32_t c, uint32_t &same, uint32_t &rot, uint32_t &up, uint32_t &dn) {
+        const uint32_t *O = pl + (c ^ 1u) * HW;
+        if (Lh < 32) {
+            const uint32_t o = O[w], op = O[(w - 1) & (HW - 1)], on = O[(w + 1) & (HW - 1)];
+            same = o;
+            up = __funnelshift_l(op, o, Lh);  // bit k <- k - Lh
+            dn = __funnelshift_r(o, on, Lh);  // bit k <- k + Lh
+            const uint32_t rl = ((o << 1) & ~LOW) | ((o >> (Lh - 1)) & LOW);   // bit k <- k - 1 in the row
+            const uint32_t rr = ((o >> 1) & ~HIGH) | ((o << (Lh - 1)) & HIGH); // bit k <- k + 1 in the row
+            // rows with (c + y) even see the rotated neighbour at k - 1, odd rows at k + 1
+            rot = c == 0 ? ((rl & EVEN) | (rr & ~EVEN)) : ((rr & EVEN) | (rl & ~EVEN));
+        } else {
+            const uint32_t o = O[w];
+            same = o;
+            up = O[(w - WR) & (HW - 1)];
+            dn = O[(w + WR) & (HW - 1)];
+            const uint32_t base = y_of_w * WR, q = w - base;
+            if (((c + y_of_w) & 1u) == 0)
+                rot = (o << 1) | (O[base + ((q - 1) & (WR - 1))] >> 31);
+            else
+                rot = (o >> 1) | (O[base + ((q + 1) & (WR - 1))] << 31);
+        }
+    };
+
+    for (uint32_t t = 0; t < rd.theta; ++t) {
+#pragma unroll
+        for (uint32_t c = 0; c < 2; ++c) {
+            if (active) {
+                uint32_t same, rot, up, dn;
+                neighbours(c, same, rot, up, dn);
+                const uint32_t S = c ? own1 : own0;
+                const uint32_t x1 = S ^ same ^ J[c][0], x2 = S ^ rot ^ J[c][1];
+                const uint32_t x3 = S ^ up ^ J[c][2], x4 = S ^ dn ^ J[c][3];
+                const uint32_t a = x1 ^ x2, b = x1 & x2, e = x3 ^ x4, f = x3 & x4;
+                const uint32_t c0 = a ^ e, ge2 = b | f | (a & e);
+                uint32_t B1 = all1, B2 = all2;
+                const uint32_t ctr3 = (TAG_SWEEP << 24) | (t << 1) | c;
+#pragma unroll
+                for (uint32_t g = 0; g < 8; ++g) {
+                    const uint4 u = philox4x32_10(8 * w + g, child, i, ctr3, rd.seed, rd.run_id);
+                    B1 |= ((uint32_t)(u.x < t1) << (4 * g)) | ((uint32_t)(u.y < t1) << (4 * g + 1)) |
+                          ((uint32_t)(u.z < t1) << (4 * g + 2)) | ((uint32_t)(u.w < t1) << (4 * g + 3));
+                    B2 |= ((uint32_t)(u.x < t2) << (4 * g)) | ((uint32_t)(u.y < t2) << (4 * g + 1)) |
+                          ((uint32_t)(u.z < t2) << (4 * g + 2)) | ((uint32_t)(u.w < t2) << (4 * g + 3));
+                }
+                const uint32_t flip = ge2 | (c0 & B1) | B2;
+                if (c) {
+                    own1 = S ^ flip;
+                    pl[HW + w] = own1;
+                } else {
+                    own0 = S ^ flip;
+                    pl[w] = own0;
+                }
+            }
+            if (HW <= 32) __syncwarp(); else __syncthreads();
+        }
+    }
+
+    // child: planes, E from the final lattice (every bond touches one colour-0 site), M
+    int32_t unsat = 0, up1 = 0;
+    if (active) {
+        uint32_t *dst = P.spins[nbuf] + rd.spin_off + (uint64_t)child * rd.wstride;
+        dst[w] = own0;
+        dst[HW + w] = own1;
+        uint32_t same, rot, up, dn;
+        neighbours(0, same, rot, up, dn);
+        unsat = __popc(own0 ^ same ^ J[0][0]) + __popc(own0 ^ rot ^ J[0][1]) + __popc(own0 ^ up ^ J[0][2]) +
+                __popc(own0 ^ dn ^ J[0][3]);
+        up1 = __popc(own0) + __popc(own1);
+    }
+    if (!wide) {
+        for (uint32_t o = 1; o < HW; o <<= 1) {
+            unsat += __shfl_xor_sync(FULL, unsat, o);
+            up1 += __shfl_xor_sync(FULL, up1, o);
+        }
+    } else {
+        if (active) {
+            atomicAdd(&acc[2 * rloc], unsat);
+            atomicAdd(&acc[2 * rloc + 1], up1);
+        }
+        __syncthreads();
+        unsat = acc[2 * rloc];
+        up1 = acc[2 * rloc + 1];
+    }
+    if (active && w == 0) {
+        const uint64_t pc = rd.rep_off + parent, cc = rd.rep_off + child;
+        P.E[nbuf][cc] = 2 * unsat - 2 * (int32_t)N;
+        P.M[nbuf][cc] = 2 * up1 - (int32_t)N;
         P.fam[nbuf][cc] = P.fam[ob][pc];
     }
 }
@@ -807,7 +1018,12 @@ __global__ void wavg_q_kernel(const pa_step_record *recs, const unsigned long lo
 // ------------------------------------------------------------------ launchers
 cudaError_t prepare_kernels()
 {
-    return cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_pow2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_pow2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    return e;
 }
 
 void launch_init_couplings(const Pool &P, uint32_t n_runs, cudaStream_t s)
@@ -823,10 +1039,22 @@ void launch_init_population(const Pool &P, uint32_t n_runs, uint32_t max_R, cuda
 
 void launch_resample(const Pool &P, uint32_t n_runs, cudaStream_t s) { resample_kernel<<<n_runs, 512, 0, s>>>(P); }
 
-SweepCfg sweep_config(uint32_t L)
+SweepCfg sweep_config(uint32_t L, int allow_fast)
 {
     SweepCfg c{};
     const uint32_t N = L * L;
+    const bool pow2 = L >= 8 && L <= 256 && (L & (L - 1)) == 0;
+    if (pow2 && allow_fast) {
+        c.fast = 1;
+        c.TPR = N / 64;  // words per colour plane
+        c.block = c.TPR >= 128 ? c.TPR : 128;
+        c.RPC = c.block / c.TPR;
+        c.G = N / 8;
+        c.PS = 0;
+        c.smem = c.RPC * 2 * c.TPR * 4 + 8 * c.RPC;
+        return c;
+    }
+    c.fast = 0;
     c.G = (N + 7) / 8;
     uint32_t tpr = 1;
     while (tpr < c.G) tpr <<= 1;
@@ -845,10 +1073,15 @@ SweepCfg sweep_config(uint32_t L)
 }
 
 void launch_sweep(const Pool &P, const uint32_t *group_runs, uint32_t n_group_runs, uint32_t max_Rcap,
-                  const SweepCfg &cfg, cudaStream_t s)
+                  const SweepCfg &cfg, int any_glass, cudaStream_t s)
 {
     dim3 grid((max_Rcap + cfg.RPC - 1) / cfg.RPC, n_group_runs);
-    sweep_kernel<<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
+    if (!cfg.fast)
+        sweep_kernel<<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
+    else if (any_glass)
+        sweep_pow2_kernel<true><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
+    else
+        sweep_pow2_kernel<false><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
 }
 
 void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, uint32_t max_Rcap, int init,

@@ -201,3 +201,22 @@ def test_glass_L16_R5000_full_size_sampled_runs():
         for k in range(0, len(descs), 17):
             rec = eng.records(k)
             assert np.all(rec["status"] == 0) and np.all(rec["R"] > 4000)
+
+
+@pytest.mark.parametrize("L", [8, 16, 32, 64, 128, 256])
+def test_bitsliced_and_generic_sweeps_agree(L):
+    """The bit-sliced kernel (powers of two) and the byte-plane kernel flip the
+    same spins: whole anneals agree bit for bit for the ferromagnet and the glass."""
+    R = max(4, 20000 // (L * L) * 8)
+    b = W.schedule(1.5, 5)
+    descs = [W.RunDesc(L, W.FERRO, R, 2, b, seed=3, run_id=0),
+             W.RunDesc(L, W.EA_PMJ, R, 2, b, seed=3, run_id=1, disorder_id=9, overlap=W.Q_SHIFT)]
+    out = []
+    for flags in (0, _lib.PA_CREATE_GENERIC_SWEEP):
+        with _lib.Engine(descs, flags=flags) as eng:
+            eng.run_to_end()
+            out.append([(eng.records(k), eng.population(k)) for k in range(2)])
+    for (ra, pa), (rb, pb) in zip(out[0], out[1]):
+        assert np.array_equal(ra, rb)
+        for x, y in zip(pa, pb):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
