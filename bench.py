@@ -38,10 +38,13 @@ UNIT = "attempted spin updates/ns"
 WORKLOAD = ("2D +-J EA glass L=16 periodic, R=5000, beta 0->3 in 101 steps, theta=10, nearest-integer "
             "resampling, 100 disorder samples x 2 populations, index-shift + two-population overlaps, "
             "free-energy-weighted averages")
-# Algorithmic integer work of one attempted update (issue slots of one lane):
-# a quarter of a Philox4x32-10 call (10 rounds x 4 instructions) plus the
-# acceptance compare and select.
-ALGO_INSTR_PER_UPDATE = 12.0
+# Algorithmic work of one attempted update on the binding unit, the 32-bit
+# integer multiplier: a quarter of a Philox4x32-10 call, whose 10 rounds hold
+# two 32x32->64 multiplies each, i.e. 20 wide multiplies = 40 multiply-add
+# slots per call, 10 per update.  The multiplier retires 64 multiply-add lanes
+# per clock per SM.
+ALGO_MULADD_PER_UPDATE = 10.0
+MULADD_LANES_PER_SM = 64
 
 
 def parse():
@@ -256,8 +259,8 @@ def main():
     sweep_ms, sweep_n = kt_tot["sweep"]
     pk, pk_kind = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak_tops = 152 * 4 * 32 * sm_mhz * 1e6 / 1e12  # lane-instruction issue rate, T/s
-    achieved_tops = updates * ALGO_INSTR_PER_UPDATE / (sweep_ms / args.steps * 1e-3) / 1e12
+    peak_tops = 152 * MULADD_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # integer multiply-add slots, T/s
+    achieved_tops = updates * ALGO_MULADD_PER_UPDATE / (sweep_ms / args.steps * 1e-3) / 1e12
     total_kernel_ms = sum(t for t, _ in kt_tot.values())
 
     # ---- plain form: one run per engine, all on one stream (one run per launch)
@@ -324,11 +327,14 @@ def main():
                        "form": "batched: all runs in one launch per kernel, anneal captured as a CUDA graph",
                        "parallelism": f"replicas x{world} (independent runs per GPU)"},
             "runs_per_s": runs_per_s,
-            "roofline": {"bound": "alu", "kernel": "sweep_kernel", "achieved": achieved_tops,
-                         "peak": peak_tops, "unit": "Tinstr/s", "frac": achieved_tops / peak_tops,
+            "roofline": {"bound": "alu", "kernel": "sweep_pow2_kernel", "achieved": achieved_tops,
+                         "peak": peak_tops, "unit": "Tmuladd/s", "frac": achieved_tops / peak_tops,
                          "traffic": None,
-                         "basis": f"{ALGO_INSTR_PER_UPDATE:g} algorithmic lane-instructions per attempted update; "
-                                  f"peak = 152 SMs x 128 lanes x {sm_mhz:g} MHz ({pk_kind})",
+                         "basis": f"{ALGO_MULADD_PER_UPDATE:g} integer multiply-add slots per attempted update "
+                                  f"(Philox4x32-10: 40 per call, 4 updates per call); peak = 152 SMs x "
+                                  f"{MULADD_LANES_PER_SM} lanes x {sm_mhz:g} MHz, clock from MEASURED_PEAKS.json "
+                                  f"({pk_kind})",
+                         "updates_per_ns_sweep_only": updates / (sweep_ms / args.steps * 1e-3) / 1e9,
                          "sweep_ms_per_step": sweep_ms / args.steps,
                          "sweep_share_of_kernel_time": sweep_ms / total_kernel_ms if total_kernel_ms else None},
             "kernel_ms_per_step": {k: t / args.steps for k, (t, n) in kt_tot.items()},

@@ -82,6 +82,7 @@ struct SweepCfg {
     uint32_t G;      // Philox groups per colour = ceil(N / 8)
     uint32_t PS;     // bytes per colour plane = 4 G
     uint32_t smem;   // dynamic shared memory bytes
+    uint32_t WPT;    // fast kernel: plane words per thread
 };
 
 // Scratch words (64-bit) of one run.

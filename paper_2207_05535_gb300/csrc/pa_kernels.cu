@@ -593,20 +593,59 @@ __global__ void sweep_kernel(Pool P, const uint32_t *group_runs, SweepCfg cfg)
 
 // --------------------------------------------------------------------------
 // Bit-sliced sweep for L a power of two, 8 <= L <= 256 (Sec. V.A.1).
-// Each thread owns word w of both colour planes of one replica (32 sites of a
-// colour).  Per half-sweep it forms, as 32-bit masks, the spin of each
-// neighbour (same index, index rotated by one within the row, row above, row
-// below) from the other plane, the unsatisfied bonds x_d = s ^ n_d ^ J_d, their
-// count with a bit-sliced adder (c0 = count & 1, ge2 = count >= 2), and the
-// acceptance mask
+// Each thread owns WPT words of both colour planes of one replica (32 sites of
+// a colour per word).  Per half-sweep and word it forms, as 32-bit masks, the
+// spin of each neighbour (same index, index rotated by one within the row, row
+// above, row below) from the other plane, the unsatisfied bonds
+// x_d = s ^ n_d ^ J_d, their count with a bit-sliced adder (c0 = count & 1,
+// ge2 = count >= 2), and the acceptance mask
 //      accept = ge2 | (c0 & B1) | B2,   B_m = [u < T_m]  (T_2 <= T_1),
 // i.e. dE = 8 - 4 count <= 0, or u < T_1 when dE = 4, or u < T_2 when dE = 8.
 // The 32 uniforms come from 8 Philox calls with the same counters as the
 // generic kernel, so both kernels (and the oracle) flip the same spins.
 // E and M of the child are recomputed from its final planes.
+//
+// Throughput (GB300): Philox4x32-10 dominates.  Each round is two
+// 32x32->64 multiplies (multiplier pipe, half rate, two passes each) and two
+// 3-input XORs (integer pipe); the multiplier bounds the kernel at about
+// 40 multiply-add slots per Philox call.  The round keys are precomputed and
+// the first round's multiply of the temperature counter is hoisted.
 // --------------------------------------------------------------------------
-template <bool SG>
-__global__ void __launch_bounds__(1024) sweep_pow2_kernel(Pool P, const uint32_t *group_runs, SweepCfg cfg)
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ void philox_keys(PhiloxKeys &K, uint32_t seed, uint32_t id)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        K.k0[r] = seed + (uint32_t)r * 0x9E3779B9u;
+        K.k1[r] = id + (uint32_t)r * 0xBB67AE85u;
+    }
+}
+
+// Philox4x32-10 with precomputed round keys; the first round's multiply of
+// counter word 2 (the temperature index, fixed for the kernel) is passed in.
+__device__ __forceinline__ uint4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c3, uint32_t hi1_0, uint32_t lo1_0,
+                                           const PhiloxKeys &K)
+{
+    uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    uint32_t x0 = hi1_0 ^ c1 ^ K.k0[0], x1 = lo1_0, x2 = hi0 ^ c3 ^ K.k1[0], x3 = lo0;
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        hi0 = __umulhi(0xD2511F53u, x0);
+        lo0 = 0xD2511F53u * x0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
+        x0 = hi1 ^ x1 ^ K.k0[r];
+        x1 = lo1;
+        x2 = hi0 ^ x3 ^ K.k1[r];
+        x3 = lo0;
+    }
+    return make_uint4(x0, x1, x2, x3);
+}
+
+template <bool SG, int WPT>
+__global__ void __launch_bounds__(256) sweep_pow2_kernel(Pool P, const uint32_t *group_runs, SweepCfg cfg)
 {
     extern __shared__ __align__(16) uint32_t smw[];
     const uint32_t run = group_runs[blockIdx.y];
@@ -619,50 +658,63 @@ __global__ void __launch_bounds__(1024) sweep_pow2_kernel(Pool P, const uint32_t
     const uint32_t tile0 = blockIdx.x * cfg.RPC;
     if (tile0 >= Rn) return;  // uniform over the CTA
 
-    const uint32_t HW = cfg.TPR;  // words per plane = threads per replica
+    const uint32_t TPR = cfg.TPR, HW = TPR * WPT;  // threads per replica, words per plane
     const uint32_t Lh = rd.Lh, N = rd.N;
-    const uint32_t rloc = threadIdx.x / HW, w = threadIdx.x & (HW - 1);
+    const uint32_t rloc = threadIdx.x / TPR, tl = threadIdx.x & (TPR - 1);
     const uint32_t child = tile0 + rloc;
     const bool active = child < Rn;
     uint32_t *pl = smw + rloc * 2 * HW;
     int32_t *acc = reinterpret_cast<int32_t *>(smw + cfg.RPC * 2 * HW);
-    const bool wide = HW > 32;
+    const bool wide = TPR > 32;
     if (wide && threadIdx.x < 2 * cfg.RPC) acc[threadIdx.x] = 0;
 
     const uint32_t ob = (i - 1) & 1u, nbuf = i & 1u;
-    uint32_t own0 = 0, own1 = 0, parent = 0;
-    if (active) {
-        parent = P.parent[rd.rep_off + child];
-        const uint32_t *src = P.spins[ob] + rd.spin_off + (uint64_t)parent * rd.wstride;
-        own0 = src[w];
-        own1 = src[HW + w];
+    uint32_t own[WPT][2];
+    uint32_t parent = 0;
+    if (active) parent = P.parent[rd.rep_off + child];
+    const uint32_t *src = P.spins[ob] + rd.spin_off + (uint64_t)parent * rd.wstride;
+#pragma unroll
+    for (int q = 0; q < WPT; ++q) {
+        const uint32_t w = tl + q * TPR;
+        own[q][0] = active ? src[w] : 0u;
+        own[q][1] = active ? src[HW + w] : 0u;
+        pl[w] = own[q][0];
+        pl[HW + w] = own[q][1];
     }
-    pl[w] = own0;
-    pl[HW + w] = own1;
-    uint32_t J[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-    if (SG) {
-        const uint32_t *Jp = P.J + rd.J_off + 2 * rd.wstride;
+    uint32_t J[WPT][2][4];
+#pragma unroll
+    for (int q = 0; q < WPT; ++q)
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
-            for (int d = 0; d < 4; ++d) J[c][d] = Jp[(c * 4 + d) * HW + w];
+            for (int d = 0; d < 4; ++d) J[q][c][d] = 0;
+    if (SG) {
+        const uint32_t *Jp = P.J + rd.J_off + 2 * rd.wstride;
+#pragma unroll
+        for (int q = 0; q < WPT; ++q)
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int d = 0; d < 4; ++d) J[q][c][d] = Jp[(c * 4 + d) * HW + tl + q * TPR];
     }
     // segment masks for rows shorter than a word (Lh = 4, 8, 16)
     const uint32_t LOW = Lh == 4 ? 0x11111111u : Lh == 8 ? 0x01010101u : 0x00010001u;
-    const uint32_t HIGH = LOW << (Lh - 1);
+    const uint32_t HIGH = LOW << ((Lh - 1) & 31);
     const uint32_t EVEN = Lh == 4 ? 0x0F0F0F0Fu : Lh == 8 ? 0x00FF00FFu : 0x0000FFFFu;  // rows 0, 2, ...
     const uint32_t WR = Lh >> 5;  // words per row when Lh >= 32
-    const uint32_t y_of_w = wide || Lh >= 32 ? w / (WR ? WR : 1) : 0;
 
     const unsigned long long T1 = P.thr[rd.thr_off + 2 * i], T2 = P.thr[rd.thr_off + 2 * i + 1];
     const uint32_t t1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T1;
     const uint32_t t2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T2;
     const uint32_t all1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : 0u;
     const uint32_t all2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : 0u;
-    if (HW <= 32) __syncwarp(); else __syncthreads();
+    PhiloxKeys K;
+    philox_keys(K, rd.seed, rd.run_id);
+    const uint32_t hi1_0 = __umulhi(0xCD9E8D57u, i), lo1_0 = 0xCD9E8D57u * i;
+    if (TPR <= 32) __syncwarp(); else __syncthreads();
 
     // neighbour masks of plane-c word w, read from plane (c ^ 1)
-    auto neighbours = [&](uint32_t c, uint32_t &same, uint32_t &rot, uint32_t &up, uint32_t &dn) {
+    auto neighbours = [&](uint32_t c, uint32_t w, uint32_t &same, uint32_t &rot, uint32_t &up, uint32_t &dn) {
         const uint32_t *O = pl + (c ^ 1u) * HW;
         if (Lh < 32) {
             const uint32_t o = O[w], op = O[(w - 1) & (HW - 1)], on = O[(w + 1) & (HW - 1)];
@@ -678,8 +730,8 @@ __global__ void __launch_bounds__(1024) sweep_pow2_kernel(Pool P, const uint32_t
             same = o;
             up = O[(w - WR) & (HW - 1)];
             dn = O[(w + WR) & (HW - 1)];
-            const uint32_t base = y_of_w * WR, q = w - base;
-            if (((c + y_of_w) & 1u) == 0)
+            const uint32_t y = w / WR, base = y * WR, q = w - base;
+            if (((c + y) & 1u) == 0)
                 rot = (o << 1) | (O[base + ((q - 1) & (WR - 1))] >> 31);
             else
                 rot = (o >> 1) | (O[base + ((q + 1) & (WR - 1))] << 31);
@@ -690,33 +742,35 @@ __global__ void __launch_bounds__(1024) sweep_pow2_kernel(Pool P, const uint32_t
 #pragma unroll
         for (uint32_t c = 0; c < 2; ++c) {
             if (active) {
-                uint32_t same, rot, up, dn;
-                neighbours(c, same, rot, up, dn);
-                const uint32_t S = c ? own1 : own0;
-                const uint32_t x1 = S ^ same ^ J[c][0], x2 = S ^ rot ^ J[c][1];
-                const uint32_t x3 = S ^ up ^ J[c][2], x4 = S ^ dn ^ J[c][3];
-                const uint32_t a = x1 ^ x2, b = x1 & x2, e = x3 ^ x4, f = x3 & x4;
-                const uint32_t c0 = a ^ e, ge2 = b | f | (a & e);
-                uint32_t B1 = all1, B2 = all2;
                 const uint32_t ctr3 = (TAG_SWEEP << 24) | (t << 1) | c;
 #pragma unroll
-                for (uint32_t g = 0; g < 8; ++g) {
-                    const uint4 u = philox4x32_10(8 * w + g, child, i, ctr3, rd.seed, rd.run_id);
-                    B1 |= ((uint32_t)(u.x < t1) << (4 * g)) | ((uint32_t)(u.y < t1) << (4 * g + 1)) |
-                          ((uint32_t)(u.z < t1) << (4 * g + 2)) | ((uint32_t)(u.w < t1) << (4 * g + 3));
-                    B2 |= ((uint32_t)(u.x < t2) << (4 * g)) | ((uint32_t)(u.y < t2) << (4 * g + 1)) |
-                          ((uint32_t)(u.z < t2) << (4 * g + 2)) | ((uint32_t)(u.w < t2) << (4 * g + 3));
+                for (int q = 0; q < WPT; ++q) {
+                    const uint32_t w = tl + q * TPR;
+                    uint32_t same, rot, up, dn;
+                    neighbours(c, w, same, rot, up, dn);
+                    const uint32_t S = own[q][c];
+                    const uint32_t x1 = S ^ same ^ J[q][c][0], x2 = S ^ rot ^ J[q][c][1];
+                    const uint32_t x3 = S ^ up ^ J[q][c][2], x4 = S ^ dn ^ J[q][c][3];
+                    const uint32_t a = x1 ^ x2, b = x1 & x2, e = x3 ^ x4, f = x3 & x4;
+                    const uint32_t c0 = a ^ e, ge2 = b | f | (a & e);
+                    // bits of distinct sites never collide, so the packing can add
+                    uint32_t B1 = 0, B2 = 0;
+#pragma unroll
+                    for (uint32_t g = 0; g < 8; ++g) {
+                        const uint4 u = philox_rk(8 * w + g, child, ctr3, hi1_0, lo1_0, K);
+                        B1 += ((uint32_t)(u.x < t1) << (4 * g)) + ((uint32_t)(u.y < t1) << (4 * g + 1)) +
+                              ((uint32_t)(u.z < t1) << (4 * g + 2)) + ((uint32_t)(u.w < t1) << (4 * g + 3));
+                        B2 += ((uint32_t)(u.x < t2) << (4 * g)) + ((uint32_t)(u.y < t2) << (4 * g + 1)) +
+                              ((uint32_t)(u.z < t2) << (4 * g + 2)) + ((uint32_t)(u.w < t2) << (4 * g + 3));
+                    }
+                    const uint32_t flip = ge2 | (c0 & (B1 | all1)) | B2 | all2;
+                    own[q][c] = S ^ flip;
                 }
-                const uint32_t flip = ge2 | (c0 & B1) | B2;
-                if (c) {
-                    own1 = S ^ flip;
-                    pl[HW + w] = own1;
-                } else {
-                    own0 = S ^ flip;
-                    pl[w] = own0;
-                }
+                // all of this colour's words are updated before any is published
+#pragma unroll
+                for (int q = 0; q < WPT; ++q) pl[c * HW + tl + q * TPR] = own[q][c];
             }
-            if (HW <= 32) __syncwarp(); else __syncthreads();
+            if (TPR <= 32) __syncwarp(); else __syncthreads();
         }
     }
 
@@ -724,16 +778,21 @@ __global__ void __launch_bounds__(1024) sweep_pow2_kernel(Pool P, const uint32_t
     int32_t unsat = 0, up1 = 0;
     if (active) {
         uint32_t *dst = P.spins[nbuf] + rd.spin_off + (uint64_t)child * rd.wstride;
-        dst[w] = own0;
-        dst[HW + w] = own1;
-        uint32_t same, rot, up, dn;
-        neighbours(0, same, rot, up, dn);
-        unsat = __popc(own0 ^ same ^ J[0][0]) + __popc(own0 ^ rot ^ J[0][1]) + __popc(own0 ^ up ^ J[0][2]) +
-                __popc(own0 ^ dn ^ J[0][3]);
-        up1 = __popc(own0) + __popc(own1);
+#pragma unroll
+        for (int q = 0; q < WPT; ++q) {
+            const uint32_t w = tl + q * TPR;
+            dst[w] = own[q][0];
+            dst[HW + w] = own[q][1];
+            uint32_t same, rot, up, dn;
+            neighbours(0, w, same, rot, up, dn);
+            const uint32_t S = own[q][0];
+            unsat += __popc(S ^ same ^ J[q][0][0]) + __popc(S ^ rot ^ J[q][0][1]) + __popc(S ^ up ^ J[q][0][2]) +
+                     __popc(S ^ dn ^ J[q][0][3]);
+            up1 += __popc(own[q][0]) + __popc(own[q][1]);
+        }
     }
     if (!wide) {
-        for (uint32_t o = 1; o < HW; o <<= 1) {
+        for (uint32_t o = 1; o < TPR; o <<= 1) {
             unsat += __shfl_xor_sync(FULL, unsat, o);
             up1 += __shfl_xor_sync(FULL, up1, o);
         }
@@ -746,7 +805,7 @@ __global__ void __launch_bounds__(1024) sweep_pow2_kernel(Pool P, const uint32_t
         unsat = acc[2 * rloc];
         up1 = acc[2 * rloc + 1];
     }
-    if (active && w == 0) {
+    if (active && tl == 0) {
         const uint64_t pc = rd.rep_off + parent, cc = rd.rep_off + child;
         P.E[nbuf][cc] = 2 * unsat - 2 * (int32_t)N;
         P.M[nbuf][cc] = 2 * up1 - (int32_t)N;
@@ -928,18 +987,21 @@ __global__ void wavg_kernel(const pa_step_record *recs, const unsigned long long
     const unsigned long long *off = rec_off + (uint64_t)g * M;
     double *wg = w + (uint64_t)g * n_steps * M;
     const double Nd = (double)N;
+    // pass 1: log weights lambda(i, m) = ln R_i + (-beta_i F_i) [+ sum_{k<=i} ln(R_{k-1} / R)]
+    for (uint32_t m = 0; m < M; ++m) {
+        const pa_step_record *r = recs + off[m];
+        double lsum = 0.0;
+        for (uint32_t i = 0; i < n_steps; ++i) {
+            if (kind == PA_WEIGHT_FULL && i > 0) lsum += log((double)r[i - 1].R / (double)r[i].R_target);
+            wg[(uint64_t)i * M + m] = log((double)r[i].R) + r[i].minus_betaF + lsum;
+        }
+    }
+    // pass 2: normalise per temperature and average
     double WF = Nd * log(2.0);
     for (uint32_t i = 0; i < n_steps; ++i) {
         double *wi = wg + (uint64_t)i * M;
         double lmax = -INFINITY;
-        for (uint32_t m = 0; m < M; ++m) {
-            const pa_step_record *r = recs + off[m];
-            double lam = log((double)r[i].R) + r[i].minus_betaF;
-            if (kind == PA_WEIGHT_FULL)
-                for (uint32_t k = 1; k <= i; ++k) lam += log((double)r[k - 1].R / (double)r[k].R_target);
-            wi[m] = lam;
-            lmax = lam > lmax ? lam : lmax;
-        }
+        for (uint32_t m = 0; m < M; ++m) lmax = wi[m] > lmax ? wi[m] : lmax;
         double z = 0.0;
         for (uint32_t m = 0; m < M; ++m) {
             wi[m] = exp(wi[m] - lmax);
@@ -1019,10 +1081,6 @@ __global__ void wavg_q_kernel(const pa_step_record *recs, const unsigned long lo
 cudaError_t prepare_kernels()
 {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sweep_pow2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sweep_pow2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     return e;
 }
 
@@ -1045,16 +1103,19 @@ SweepCfg sweep_config(uint32_t L, int allow_fast)
     const uint32_t N = L * L;
     const bool pow2 = L >= 8 && L <= 256 && (L & (L - 1)) == 0;
     if (pow2 && allow_fast) {
+        const uint32_t HW = N / 64;  // words per colour plane
         c.fast = 1;
-        c.TPR = N / 64;  // words per colour plane
+        c.WPT = HW > 256 ? HW / 256 : 1;
+        c.TPR = HW / c.WPT;
         c.block = c.TPR >= 128 ? c.TPR : 128;
         c.RPC = c.block / c.TPR;
         c.G = N / 8;
         c.PS = 0;
-        c.smem = c.RPC * 2 * c.TPR * 4 + 8 * c.RPC;
+        c.smem = c.RPC * 2 * HW * 4 + 8 * c.RPC;
         return c;
     }
     c.fast = 0;
+    c.WPT = 1;
     c.G = (N + 7) / 8;
     uint32_t tpr = 1;
     while (tpr < c.G) tpr <<= 1;
@@ -1078,10 +1139,14 @@ void launch_sweep(const Pool &P, const uint32_t *group_runs, uint32_t n_group_ru
     dim3 grid((max_Rcap + cfg.RPC - 1) / cfg.RPC, n_group_runs);
     if (!cfg.fast)
         sweep_kernel<<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
+    else if (cfg.WPT == 1 && any_glass)
+        sweep_pow2_kernel<true, 1><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
+    else if (cfg.WPT == 1)
+        sweep_pow2_kernel<false, 1><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
     else if (any_glass)
-        sweep_pow2_kernel<true><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
+        sweep_pow2_kernel<true, 4><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
     else
-        sweep_pow2_kernel<false><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
+        sweep_pow2_kernel<false, 4><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
 }
 
 void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, uint32_t max_Rcap, int init,
