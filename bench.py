@@ -35,9 +35,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "attempted spin updates/ns and PA runs/s (batched+served vs plain) at oracle-exact"
 UNIT = "attempted spin updates/ns"
-WORKLOAD = ("2D +-J EA glass L=16 periodic, R=5000, beta 0->3 in 101 steps, theta=10, nearest-integer "
-            "resampling, 100 disorder samples x 2 populations, index-shift + two-population overlaps, "
-            "free-energy-weighted averages")
+WORKLOADS = {
+    "glass_L16_R5000": ("2D +-J EA glass L=16 periodic, R=5000, beta 0->3 in 101 steps, theta=10, nearest-integer "
+                        "resampling, 100 disorder samples x 2 populations, index-shift + two-population overlaps, "
+                        "free-energy-weighted averages over the two populations of each sample"),
+    "ising_L8_R500": ("2D Ising FM L=8 periodic, R=500, beta 0->0.5 in 51 steps, theta=10, nearest-integer "
+                      "resampling, M=20 runs from seed 1, free-energy-weighted averages over the 20 runs"),
+    "uneven_4096": ("4096 independent 2D Ising FM runs, L drawn from {16,32,64,128}, R from {1e3,1e4,5e4} by seed, "
+                    "beta 0->1 in 101 steps, theta=10, one launch per kernel per step over all runs"),
+    "ising_L256_R1e5": ("2D Ising FM L=256 periodic, R=1e5, beta 0->0.44 in 201 steps, theta=20, "
+                        "M=16 runs, free-energy-weighted averages over the runs"),
+}
+WORKLOAD = WORKLOADS["glass_L16_R5000"]
 # Algorithmic work of one attempted update on the binding unit, the 32-bit
 # integer multiplier: a quarter of a Philox4x32-10 call, whose 10 rounds hold
 # two 32x32->64 multiplies each, i.e. 20 wide multiplies = 40 multiply-add
@@ -53,7 +62,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--samples", type=int, default=100, help="disorder samples (2 populations each)")
+    ap.add_argument("--workload", default="glass_L16_R5000", choices=sorted(WORKLOADS))
+    ap.add_argument("--samples", type=int, default=100, help="glass: disorder samples (2 populations each)")
+    ap.add_argument("--runs", type=int, default=0, help="ising/uneven: number of runs (0 = the workload's)")
+    ap.add_argument("--max-temps", type=int, default=0,
+                    help="anneal only the first T temperatures of the schedule (0 = all); reported in config")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -61,12 +74,25 @@ def parse():
 
 
 # ---------------------------------------------------------------- CPU oracle
-def _oracle_job(args):
-    k, n_temps = args
-    sys.path.insert(0, ROOT)
-    import oracle as O
+def _workload_descs(wl, runs=0):
     from paper_2207_05535_gb300 import workloads as W
-    d = W.glass_L16_R5000()[k]
+    if wl == "glass_L16_R5000":
+        return W.glass_L16_R5000()
+    if wl == "ising_L8_R500":
+        return W.ising_L8_R500(M=runs or 20)
+    if wl == "uneven_4096":
+        return W.batched_uneven(n_runs=runs or 4096)
+    return W.ising_L256_R1e5(M=runs or 16)
+
+
+def _oracle_job(args):
+    wl, k, n_temps, r_max = args
+    sys.path.insert(0, ROOT)
+    import dataclasses
+    import oracle as O
+    d = _workload_descs(wl)[k]
+    if r_max and d.R > r_max:
+        d = dataclasses.replace(d, R=r_max, R_cap=0)
     r = O.OracleRun.from_desc(d)
     t0 = time.perf_counter()
     upd = 0
@@ -76,21 +102,31 @@ def _oracle_job(args):
     return upd, time.perf_counter() - t0
 
 
-def oracle_sample(n_temps=8, procs=None):
-    """The oracle as it stands on all host cores: each process anneals one
-    population of the workload through its first n_temps temperatures."""
+# bounded oracle samples per workload: (temperatures, population cap)
+ORACLE_SAMPLE = {"glass_L16_R5000": (25, 0), "ising_L8_R500": (51, 0), "uneven_4096": (2, 2000),
+                 "ising_L256_R1e5": (2, 200)}
+
+
+def oracle_sample(wl="glass_L16_R5000", n_temps=None, procs=None):
+    """The oracle as it stands on all host cores: each process anneals one run
+    of the workload (population capped for the largest workloads) through its
+    first n_temps temperatures."""
     procs = procs or os.cpu_count() or 1
+    nt, r_max = ORACLE_SAMPLE[wl]
+    n_temps = n_temps or nt
+    n_runs = len(_workload_descs(wl))
     import oracle
     oracle.build()
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(procs) as pool:
-        res = pool.map(_oracle_job, [(k, n_temps) for k in range(procs)])
+        res = pool.map(_oracle_job, [(wl, k % n_runs, n_temps, r_max) for k in range(procs)])
     wall = time.perf_counter() - t0
     upd = sum(u for u, _ in res)
+    cap = f", populations capped at R={r_max}" if r_max else ""
     return {"value": upd / (wall * 1e9), "unit": UNIT, "cores": procs, "kind": "oracle",
-            "sample": f"{procs} populations of the workload (one per process) through their first {n_temps} "
-                      f"temperatures ({upd:.3e} attempted updates, {wall:.1f} s wall)"}
+            "sample": f"{procs} runs of the workload (one per process) through their first {n_temps} "
+                      f"temperatures{cap} ({upd:.3e} attempted updates, {wall:.1f} s wall)"}
 
 
 # ---------------------------------------------------------------- clocks
@@ -150,12 +186,13 @@ def main():
         if rank != 0:
             return
         W_, K = args.warmup, args.steps
+        nt, _ = ORACLE_SAMPLE[args.workload]
         for _ in range(W_):
-            oracle_sample(n_temps=2)
+            oracle_sample(args.workload, n_temps=2)
         vals, tot = [], 0.0
         for _ in range(K):
             t0 = time.perf_counter()
-            s = oracle_sample(n_temps=4)
+            s = oracle_sample(args.workload, n_temps=max(2, min(nt, 4)))
             tot += time.perf_counter() - t0
             vals.append(s["value"])
         v = statistics.median(vals)
@@ -163,7 +200,8 @@ def main():
             "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
             "warmup": W_, "ms_per_step": 1e3 * tot / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "bounded oracle sample per step"},
+            "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
+                       "sample": "bounded oracle sample per step"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": s["cores"], "kind": "oracle", "sample": s["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
         return
@@ -171,7 +209,7 @@ def main():
     # CPU baseline first: a spawn pool, before any CUDA context exists
     cpu = None
     if rank == 0 and world >= 1 and args.gpus == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(n_temps=25)
+        cpu = oracle_sample(args.workload)
 
     import numpy as np
     import torch
@@ -191,8 +229,21 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # weak scaling: every rank anneals its own batch (disorder samples offset by rank)
-    descs = W.glass_L16_R5000(n_samples=args.samples)
+    # weak scaling: every rank anneals its own batch (disorder samples / runs offset by rank)
+    wl = args.workload
+    if wl == "glass_L16_R5000":
+        descs, M_avg = W.glass_L16_R5000(n_samples=args.samples), 2
+    elif wl == "ising_L8_R500":
+        descs = W.ising_L8_R500(M=args.runs or 20)
+        M_avg = len(descs)
+    elif wl == "uneven_4096":
+        descs, M_avg = W.batched_uneven(n_runs=args.runs or 4096), 0
+    else:
+        descs = W.ising_L256_R1e5(M=args.runs or 16)
+        M_avg = len(descs)
+    if args.max_temps:
+        for d in descs:
+            d.betas = d.betas[:args.max_temps]
     for d in descs:
         d.disorder_id += 100000 * rank
         d.run_id += 200000 * rank
@@ -205,7 +256,9 @@ def main():
     def one_step(use_graph=True):
         eng.reset()
         eng.step(n_ticks, use_graph)
-        return eng.weighted_average(idx, 2, _lib.PA_OK)
+        if M_avg:
+            return eng.weighted_average(idx, M_avg, 0)
+        eng.sync()
 
     for _ in range(args.warmup):
         one_step()
@@ -267,11 +320,12 @@ def main():
     plain = None
     if not args.no_plain and rank == 0:
         import dataclasses
-        n_plain = 20  # runs = 10 disorder samples, one sample (two paired populations) per engine
-        engines = []
-        for smp in range(n_plain // 2):
-            pair = [dataclasses.replace(descs[2 * smp + p_], paired=1 - p_) for p_ in range(2)]
-            engines.append(_lib.Engine(pair, stream.cuda_stream))
+        # one run (one disorder sample of two paired populations for the glass) per engine and per launch
+        if wl == "glass_L16_R5000":
+            units = [[dataclasses.replace(descs[2 * smp + p_], paired=1 - p_) for p_ in range(2)] for smp in range(10)]
+        else:
+            units = [[dataclasses.replace(d)] for d in descs[:min(len(descs), 20)]]
+        engines = [_lib.Engine(u, stream.cuda_stream) for u in units]
         for e in engines:
             e.reset()
             e.step(n_ticks, False)
@@ -284,16 +338,17 @@ def main():
         b.record(stream)
         torch.cuda.synchronize()
         pms = a.elapsed_time(b)
-        pupd = 0
-        for smp, e in enumerate(engines):
-            for p_ in range(2):
-                d_ = descs[2 * smp + p_]
-                rec = e.records(p_)
+        pupd, nruns = 0, 0
+        for u, e in zip(units, engines):
+            for k, d_ in enumerate(u):
+                rec = e.records(k)
                 pupd += int(sum(d_.theta * d_.N * int(r) for r in rec["R"][1:]))
+                nruns += 1
         for e in engines:
             e.close()
-        plain = {"value": pupd / (pms * 1e6), "unit": UNIT, "runs": n_plain,
-                 "runs_per_s": n_plain / (pms / 1e3), "form": "one disorder sample (two populations) per engine and per launch, no graph, one stream"}
+        plain = {"value": pupd / (pms * 1e6), "unit": UNIT, "runs": nruns, "runs_per_s": nruns / (pms / 1e3),
+                 "form": "one run (glass: one disorder sample of two populations) per engine and per launch, "
+                         "no graph, one stream"}
 
     # ---- end to end through the C ABI: host descriptors in, host results out
     e2e = None
@@ -305,7 +360,8 @@ def main():
             t0 = time.perf_counter()
             e = _lib.Engine(descs, stream.cuda_stream)
             e.step(n_ticks, True)
-            e.weighted_average(idx, 2, 0)
+            if M_avg:
+                e.weighted_average(idx, M_avg, 0)
             for r in range(len(descs)):
                 e.records(r)
             a_, b_ = _lib.pa_transfer_bytes(e.h)
@@ -322,7 +378,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "runs_per_gpu": len(descs), "temperatures": n_ticks + 1,
+            "config": {"workload": WORKLOADS[wl], "name": wl, "runs_per_gpu": len(descs), "temperatures": n_ticks + 1,
                        "attempted_updates_per_step": updates, "l2": "flushed between steps (256 MB write)",
                        "form": "batched: all runs in one launch per kernel, anneal captured as a CUDA graph",
                        "parallelism": f"replicas x{world} (independent runs per GPU)"},
@@ -338,6 +394,8 @@ def main():
                          "sweep_ms_per_step": sweep_ms / args.steps,
                          "sweep_share_of_kernel_time": sweep_ms / total_kernel_ms if total_kernel_ms else None},
             "kernel_ms_per_step": {k: t / args.steps for k, (t, n) in kt_tot.items()},
+            "sweep_shapes": [{"L": L_, "words_per_thread": w_, "block": b_, "autotuned": bool(t_)}
+                             for (L_, w_, b_, t_) in _lib.pa_sweep_shapes(eng.h)],
             "gpu_launches": launches,
             "clocks": clk,
             "plain": plain,

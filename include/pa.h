@@ -113,11 +113,14 @@ typedef struct pa_engine pa_engine;
  * L, model, disorder_id and n_beta), PA_ERR_OOM, PA_ERR_CUDA. */
 pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, pa_engine **out);
 
-/* pa_create with options: flags = 0 or PA_CREATE_GENERIC_SWEEP, which keeps
- * every lattice size on the general byte-plane sweep kernel instead of the
- * bit-sliced kernel used for L = 8, 16, ..., 256 (both give identical results;
- * the option exists to check that). */
-enum { PA_CREATE_GENERIC_SWEEP = 1 };
+/* pa_create with options (bit flags):
+ *   PA_CREATE_GENERIC_SWEEP keeps every lattice size on the general byte-plane
+ *     sweep kernel instead of the bit-sliced kernel used for L = 8, 16, ..., 256
+ *     (both give identical results; the option exists to check that);
+ *   PA_CREATE_NO_AUTOTUNE skips timing the bit-sliced kernel's launch shapes on
+ *     the first anneal step and uses the default shape.
+ * Results never depend on the launch shape. */
+enum { PA_CREATE_GENERIC_SWEEP = 1, PA_CREATE_NO_AUTOTUNE = 2 };
 pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, uint32_t flags,
                        pa_engine **out);
 
@@ -200,6 +203,12 @@ pa_status pa_weighted_average_noalloc(const pa_step_record *d_recs, uint32_t M, 
 
 /* Number of kernels this engine has launched (graph replays count each node). */
 uint64_t pa_launch_count(const pa_engine *e);
+
+/* Launch shape of the sweep for lattice-size group `group` (groups in order of
+ * first appearance of each L): words of a colour plane per thread (0 for the
+ * byte-plane kernel), threads per CTA, and whether it was chosen by timing. */
+pa_status pa_sweep_shape(const pa_engine *e, uint32_t group, uint32_t *L, uint32_t *words_per_thread,
+                         uint32_t *block, uint32_t *tuned);
 
 /* Kernel classes timed by the profiling mode. */
 enum { PA_K_RESAMPLE = 0, PA_K_SWEEP = 1, PA_K_OVERLAP = 2, PA_K_MEASURE = 3, PA_K_INIT = 4, PA_K_WAVG = 5,

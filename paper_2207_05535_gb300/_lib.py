@@ -50,7 +50,7 @@ WAVG_DTYPE = np.dtype([
 
 EXPORTS = ["pa_create", "pa_create_ex", "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population",
            "pa_weighted_average_runs", "pa_weighted_average", "pa_weighted_average_noalloc", "pa_launch_count", "pa_set_profiling",
-           "pa_kernel_times", "pa_transfer_bytes", "pa_destroy", "pa_status_string"]
+           "pa_kernel_times", "pa_transfer_bytes", "pa_sweep_shape", "pa_destroy", "pa_status_string"]
 KERNEL_KINDS = ["resample", "sweep", "overlap", "measure", "init", "wavg"]
 
 _lock = threading.Lock()
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
         lib.pa_weighted_average_noalloc.argtypes = [vp, u32, u32, u32, u32, vp, vp]
         lib.pa_launch_count.argtypes = [vp]
         lib.pa_launch_count.restype = C.c_uint64
+        lib.pa_sweep_shape.argtypes = [vp, u32, P(u32), P(u32), P(u32), P(u32)]
         lib.pa_set_profiling.argtypes = [vp, C.c_int]
         lib.pa_kernel_times.argtypes = [vp, P(C.c_double), P(C.c_uint64)]
         lib.pa_transfer_bytes.argtypes = [vp, P(C.c_uint64), P(C.c_uint64)]
@@ -128,6 +129,7 @@ def pa_create(runs, stream=None):
 
 
 PA_CREATE_GENERIC_SWEEP = 1
+PA_CREATE_NO_AUTOTUNE = 2
 
 
 def pa_create_ex(runs, stream=None, flags=0):
@@ -208,6 +210,18 @@ def pa_weighted_average(recs, N, kind=0, qh=None, qh_pair=None, stream=None):
 
 def pa_launch_count(h):
     return int(load().pa_launch_count(h))
+
+
+def pa_sweep_shapes(h):
+    """[(L, words_per_thread, block, tuned)] for every lattice-size group."""
+    out, g = [], 0
+    lib = load()
+    while True:
+        v = [C.c_uint32() for _ in range(4)]
+        if lib.pa_sweep_shape(h, g, *[C.byref(x) for x in v]) != PA_OK:
+            return out
+        out.append(tuple(int(x.value) for x in v))
+        g += 1
 
 
 def pa_set_profiling(h, on=True):

@@ -25,10 +25,16 @@ using namespace pa;
 struct SweepGroup {
     uint32_t L;
     int any_glass = 0;
-    SweepCfg cfg;
+    SweepCfg cfg;                     // chosen launch shape
+    std::vector<SweepCfg> candidates; // timed on the first anneal step when more than one
+    bool tuned = false;
+    float tuned_ms = 0.f;
     uint32_t max_Rcap;
     std::vector<uint32_t> runs;
-    uint32_t *d_runs = nullptr;
+    std::vector<uint32_t> n_tiles;   // per candidate: total tiles (prefix of ceil(R_cap / RPC))
+    uint32_t *d_runs = nullptr;      // run indices, then per candidate its tile map (n + 1 entries)
+    uint32_t pick = 0;               // chosen candidate
+    const uint32_t *tile_map(uint32_t c) const { return d_runs + runs.size() + (size_t)c * (runs.size() + 1); }
 };
 
 struct pa_engine {
@@ -40,6 +46,9 @@ struct pa_engine {
     std::vector<SweepGroup> groups;
     std::vector<uint32_t> q_runs;
     uint32_t *d_q_runs = nullptr;
+    uint32_t *d_init_tiles = nullptr;  // prefix of ceil(R / 4) over all runs
+    uint32_t init_tiles = 0;
+    uint32_t max_pw = 1;  // largest colour-plane word count of any run
     uint32_t max_Rcap = 0, max_R = 0, max_nbeta = 0;
     Pool P{};
     std::vector<void *> allocs;
@@ -167,12 +176,83 @@ void timed_launch(pa_engine *e, int kind, F &&launch)
     e->timed.push_back(t);
 }
 
+pa_status upload_tile_maps(pa_engine *e, SweepGroup &g)
+{
+    std::vector<uint32_t> h(g.runs);
+    g.n_tiles.clear();
+    for (const SweepCfg &c : g.candidates) {
+        uint64_t acc = 0;
+        h.push_back(0u);
+        for (uint32_t r : g.runs) {
+            acc += (e->rd[r].R_cap + c.RPC - 1) / c.RPC;
+            if (acc > 0x7fffffffull) return PA_ERR_INVALID_ARG;  // beyond one launch's grid
+            h.push_back((uint32_t)acc);
+        }
+        g.n_tiles.push_back((uint32_t)acc);
+    }
+    cudaError_t err = cudaMemcpy(g.d_runs, h.data(), sizeof(uint32_t) * h.size(), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return cuda_fail(err, "tile maps");
+    e->h2d += sizeof(uint32_t) * h.size();
+    return PA_OK;
+}
+
+// One eager anneal step that times every candidate sweep shape of the groups
+// not tuned yet on the real data and keeps the fastest.  Each candidate reads
+// the same parents and writes the same children, so running several is
+// harmless; the last launch leaves the children in place.
+pa_status enqueue_tuning_tick(pa_engine *e)
+{
+    launch_resample(e->P, e->n_runs, e->stream);
+    e->launches += 1;
+    for (auto &g : e->groups) {
+        if (g.tuned) {
+            launch_sweep(e->P, g.d_runs, g.tile_map(g.pick), (uint32_t)g.runs.size(), g.n_tiles[g.pick], g.cfg,
+                         g.any_glass, e->stream);
+            e->launches += 1;
+            continue;
+        }
+        std::vector<cudaEvent_t> ev(2 * g.candidates.size());
+        for (auto &x : ev) PA_CUDA(cudaEventCreate(&x));
+        for (uint32_t c = 0; c < g.candidates.size(); ++c) {
+            PA_CUDA(cudaEventRecord(ev[2 * c], e->stream));
+            launch_sweep(e->P, g.d_runs, g.tile_map(c), (uint32_t)g.runs.size(), g.n_tiles[c], g.candidates[c],
+                         g.any_glass, e->stream);
+            PA_CUDA(cudaEventRecord(ev[2 * c + 1], e->stream));
+            e->launches += 1;
+        }
+        PA_CUDA(cudaStreamSynchronize(e->stream));
+        PA_CUDA(cudaGetLastError());
+        float best = 0.f;
+        for (uint32_t c = 0; c < g.candidates.size(); ++c) {
+            float ms = 0.f;
+            PA_CUDA(cudaEventElapsedTime(&ms, ev[2 * c], ev[2 * c + 1]));
+            if (c == 0 || ms < best) {
+                best = ms;
+                g.pick = c;
+            }
+        }
+        for (auto &x : ev) cudaEventDestroy(x);
+        g.cfg = g.candidates[g.pick];
+        g.tuned = true;
+        g.tuned_ms = best;
+    }
+    if (!e->q_runs.empty()) {
+        launch_overlap(e->P, e->d_q_runs, (uint32_t)e->q_runs.size(), e->max_Rcap, 0, e->stream);
+        e->launches += 1;
+    }
+    launch_measure(e->P, e->n_runs, 0, e->stream);
+    e->launches += 1;
+    PA_CUDA(cudaGetLastError());
+    return PA_OK;
+}
+
 void enqueue_tick(pa_engine *e)
 {
     timed_launch(e, PA_K_RESAMPLE, [&] { launch_resample(e->P, e->n_runs, e->stream); });
     for (auto &g : e->groups)
         timed_launch(e, PA_K_SWEEP, [&] {
-            launch_sweep(e->P, g.d_runs, (uint32_t)g.runs.size(), g.max_Rcap, g.cfg, g.any_glass, e->stream);
+            launch_sweep(e->P, g.d_runs, g.tile_map(g.pick), (uint32_t)g.runs.size(), g.n_tiles[g.pick], g.cfg,
+                         g.any_glass, e->stream);
         });
     if (!e->q_runs.empty())
         timed_launch(e, PA_K_OVERLAP, [&] {
@@ -202,7 +282,8 @@ pa_status enqueue_init(pa_engine *e)
     if (err) return cuda_fail(err, "reset state");
     e->h2d += sizeof(RunState) * e->n_runs;
     timed_launch(e, PA_K_INIT, [&] { launch_init_couplings(e->P, e->n_runs, e->stream); });
-    timed_launch(e, PA_K_INIT, [&] { launch_init_population(e->P, e->n_runs, e->max_R, e->stream); });
+    timed_launch(e, PA_K_INIT,
+                 [&] { launch_init_population(e->P, e->d_init_tiles, e->n_runs, e->init_tiles, e->max_pw, e->stream); });
     if (!e->q_runs.empty())
         timed_launch(e, PA_K_OVERLAP, [&] {
             launch_overlap(e->P, e->d_q_runs, (uint32_t)e->q_runs.size(), e->max_Rcap, 1, e->stream);
@@ -282,7 +363,7 @@ pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream,
 
 pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, uint32_t flags, pa_engine **out)
 {
-    if (!out || (flags & ~(uint32_t)PA_CREATE_GENERIC_SWEEP)) return PA_ERR_INVALID_ARG;
+    if (!out || (flags & ~(uint32_t)(PA_CREATE_GENERIC_SWEEP | PA_CREATE_NO_AUTOTUNE))) return PA_ERR_INVALID_ARG;
     *out = nullptr;
     pa_status vs = validate(runs, n_runs);
     if (vs != PA_OK) return vs;
@@ -319,6 +400,7 @@ pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stre
         x.Lh = d.L / 2;
         const uint32_t pw = (x.N + 63) / 64;  // words per colour plane
         x.wstride = (2 * pw + 3) / 4 * 4;
+        e->max_pw = pw > e->max_pw ? pw : e->max_pw;
         x.model = d.model;
         x.R = d.R;
         x.R_cap = default_cap(d);
@@ -378,7 +460,9 @@ pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stre
             g = group_of_L.emplace(d.L, e->groups.size()).first;
             SweepGroup sg;
             sg.L = d.L;
-            sg.cfg = sweep_config(d.L, (flags & PA_CREATE_GENERIC_SWEEP) ? 0 : 1);
+            sg.candidates = sweep_candidates(d.L, (flags & PA_CREATE_GENERIC_SWEEP) ? 0 : 1);
+            sg.cfg = sg.candidates[0];
+            sg.tuned = sg.candidates.size() < 2 || (flags & PA_CREATE_NO_AUTOTUNE);
             sg.max_Rcap = 0;
             e->groups.push_back(sg);
         }
@@ -427,10 +511,22 @@ pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stre
     e->P.wt = d_wt;
     e->P.thr = d_thr;
     for (auto &g : e->groups) {
-        TRY(dalloc(e, &g.d_runs, g.runs.size()));
-        if (cudaMemcpyAsync(g.d_runs, g.runs.data(), sizeof(uint32_t) * g.runs.size(), cudaMemcpyHostToDevice,
-                            e->stream) != cudaSuccess)
+        // run indices, then one tile map per candidate shape (each n + 1 entries)
+        TRY(dalloc(e, &g.d_runs, g.runs.size() * (1 + g.candidates.size()) + g.candidates.size()));
+        TRY(upload_tile_maps(e, g));
+    }
+    {
+        std::vector<uint32_t> h(1, 0u);
+        for (uint32_t r = 0; r < n_runs; ++r) {
+            const uint64_t next = (uint64_t)h.back() + (e->rd[r].R + 3) / 4;
+            if (next > 0x7fffffffull) TRY(PA_ERR_INVALID_ARG);
+            h.push_back((uint32_t)next);
+        }
+        e->init_tiles = h.back();
+        TRY(dalloc(e, &e->d_init_tiles, h.size()));
+        if (cudaMemcpy(e->d_init_tiles, h.data(), sizeof(uint32_t) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             TRY(PA_ERR_CUDA);
+        e->h2d += sizeof(uint32_t) * h.size();
     }
     if (!e->q_runs.empty()) {
         TRY(dalloc(e, &e->d_q_runs, e->q_runs.size()));
@@ -477,6 +573,13 @@ pa_status pa_anneal_step(pa_engine *e, uint32_t n_steps, int use_graph)
     if (!e) return PA_ERR_INVALID_ARG;
     if (e->latched != PA_OK) return e->latched;
     if (n_steps == 0) return PA_OK;
+    bool untuned = false;
+    for (auto &g : e->groups) untuned |= !g.tuned;
+    if (untuned) {
+        pa_status s = enqueue_tuning_tick(e);
+        if (s != PA_OK) return s;
+        if (--n_steps == 0) return PA_OK;
+    }
     if (use_graph && !e->profiling) {
         if (!e->graph_exec) {
             PA_CUDA(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
@@ -502,6 +605,18 @@ pa_status pa_sync(pa_engine *e)
 }
 
 uint64_t pa_launch_count(const pa_engine *e) { return e ? e->launches : 0; }
+
+pa_status pa_sweep_shape(const pa_engine *e, uint32_t group, uint32_t *L, uint32_t *words_per_thread,
+                         uint32_t *block, uint32_t *tuned)
+{
+    if (!e || group >= e->groups.size() || !L || !words_per_thread || !block || !tuned) return PA_ERR_INVALID_ARG;
+    const SweepGroup &g = e->groups[group];
+    *L = g.L;
+    *words_per_thread = g.cfg.fast ? g.cfg.WPT : 0;
+    *block = g.cfg.block;
+    *tuned = (g.tuned && g.candidates.size() > 1) ? 1u : 0u;
+    return PA_OK;
+}
 
 pa_status pa_set_profiling(pa_engine *e, int on)
 {

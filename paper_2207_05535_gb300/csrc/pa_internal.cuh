@@ -20,6 +20,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 
 #include "pa.h"
 
@@ -94,11 +95,15 @@ inline uint64_t scratch_words(uint32_t N, uint32_t R_cap)
 
 // Launch wrappers implemented in pa_kernels.cu (all asynchronous on `s`).
 void launch_init_couplings(const Pool &P, uint32_t n_runs, cudaStream_t s);
-void launch_init_population(const Pool &P, uint32_t n_runs, uint32_t max_R, cudaStream_t s);
+// Work lists: tile_off = prefix of per-run tile counts (n + 1 entries).
+void launch_init_population(const Pool &P, const uint32_t *tile_off, uint32_t n_runs, uint32_t n_tiles,
+                            uint32_t max_pw, cudaStream_t s);
 void launch_resample(const Pool &P, uint32_t n_runs, cudaStream_t s);
-SweepCfg sweep_config(uint32_t L, int allow_fast);
-void launch_sweep(const Pool &P, const uint32_t *group_runs, uint32_t n_group_runs, uint32_t max_Rcap,
-                  const SweepCfg &cfg, int any_glass, cudaStream_t s);
+// Launch shapes to try for lattice size L (first = default); one entry unless
+// the bit-sliced kernel applies.
+std::vector<SweepCfg> sweep_candidates(uint32_t L, int allow_fast);
+void launch_sweep(const Pool &P, const uint32_t *group_runs, const uint32_t *tile_off, uint32_t n_group_runs,
+                  uint32_t n_tiles, const SweepCfg &cfg, int any_glass, cudaStream_t s);
 void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, uint32_t max_Rcap, int init,
                     cudaStream_t s);
 void launch_measure(const Pool &P, uint32_t n_runs, int init, cudaStream_t s);

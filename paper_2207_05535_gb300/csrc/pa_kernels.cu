@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "pa_internal.cuh"
 
@@ -190,6 +191,21 @@ __device__ uint32_t block_inclusive_max(uint32_t v, uint32_t *sh)
 
 __device__ __forceinline__ uint32_t get_bit(const uint32_t *w, uint32_t n) { return (w[n >> 5] >> (n & 31)) & 1u; }
 
+// Work list: tile_off[g] = first tile of run slot g (prefix of per-run tile
+// counts, tile_off[n] = total).  Returns the slot holding tile t.
+__device__ __forceinline__ uint32_t locate_slot(const uint32_t *tile_off, uint32_t n, uint32_t t)
+{
+    uint32_t a = 0, b = n;  // invariant: tile_off[a] <= t < tile_off[b]
+    while (b - a > 1) {
+        const uint32_t m = (a + b) >> 1;
+        if (tile_off[m] <= t)
+            a = m;
+        else
+            b = m;
+    }
+    return a;
+}
+
 __device__ __forceinline__ void set_status(const Pool &P, uint32_t run, uint32_t code)
 {
     P.st[run].status = code;
@@ -213,6 +229,38 @@ __device__ __forceinline__ uint32_t spin_bit(const uint32_t *planes, uint32_t PW
 {
     const uint32_t x = n % L, y = n / L, c = (x + y) & 1u, k = n >> 1;
     return (planes[c * PW + (k >> 5)] >> (k & 31)) & 1u;
+}
+
+// Neighbour masks of word w of colour plane c (L a power of two, 8..256), read
+// from the other plane O (HW words): the spin at the same sublattice index,
+// at the index rotated by one within the row (k - 1 on rows with (c + y) even,
+// k + 1 on odd rows), in the row above and in the row below.
+__device__ __forceinline__ void plane_neighbours(const uint32_t *O, uint32_t HW, uint32_t Lh, uint32_t c, uint32_t w,
+                                                 uint32_t &same, uint32_t &rot, uint32_t &up, uint32_t &dn)
+{
+    if (Lh < 32) {  // several rows per word
+        const uint32_t LOW = Lh == 4 ? 0x11111111u : Lh == 8 ? 0x01010101u : 0x00010001u;
+        const uint32_t HIGH = LOW << (Lh - 1);
+        const uint32_t EVEN = Lh == 4 ? 0x0F0F0F0Fu : Lh == 8 ? 0x00FF00FFu : 0x0000FFFFu;  // rows 0, 2, ...
+        const uint32_t o = O[w], op = O[(w - 1) & (HW - 1)], on = O[(w + 1) & (HW - 1)];
+        same = o;
+        up = __funnelshift_l(op, o, Lh);  // bit k <- k - Lh
+        dn = __funnelshift_r(o, on, Lh);  // bit k <- k + Lh
+        const uint32_t rl = ((o << 1) & ~LOW) | ((o >> (Lh - 1)) & LOW);   // bit k <- k - 1 in the row
+        const uint32_t rr = ((o >> 1) & ~HIGH) | ((o << (Lh - 1)) & HIGH); // bit k <- k + 1 in the row
+        rot = c == 0 ? ((rl & EVEN) | (rr & ~EVEN)) : ((rr & EVEN) | (rl & ~EVEN));
+    } else {  // WR words per row
+        const uint32_t WR = Lh >> 5;
+        const uint32_t o = O[w];
+        same = o;
+        up = O[(w - WR) & (HW - 1)];
+        dn = O[(w + WR) & (HW - 1)];
+        const uint32_t y = w / WR, base = y * WR, q = w - base;
+        if (((c + y) & 1u) == 0)
+            rot = (o << 1) | (O[base + ((q - 1) & (WR - 1))] >> 31);
+        else
+            rot = (o >> 1) | (O[base + ((q + 1) & (WR - 1))] << 31);
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -271,44 +319,60 @@ __global__ void init_couplings_kernel(Pool P)
     }
 }
 
-// One warp per replica: uniform spins from Philox, then E and M exactly.
-__global__ void init_population_kernel(Pool P)
+// One warp per replica (4 per CTA, CTAs from the work list over all runs):
+// uniform spins from Philox (one call per four consecutive sites), then E and
+// M exactly.  Power-of-two L uses word-wide neighbour masks for E.
+__global__ void __launch_bounds__(128) init_population_kernel(Pool P, const uint32_t *tile_off, uint32_t n_runs)
 {
-    const uint32_t run = blockIdx.y;
+    extern __shared__ __align__(16) uint32_t sw[];  // per warp: 2 PW plane words
+    const uint32_t run = locate_slot(tile_off, n_runs, blockIdx.x);
     const RunDev rd = P.runs[run];
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j >= rd.R) return;
-    const uint32_t L = rd.L, half = rd.N >> 1, PW = (rd.N + 63) / 64;
-    uint32_t *s = P.spins[0] + rd.spin_off + (uint64_t)j * rd.wstride;
-    for (uint32_t cw = lane; cw < 2 * PW; cw += 32) {
-        const uint32_t c = cw / PW, w = cw - c * PW;
-        uint32_t word = 0;
-        for (uint32_t b = 0; b < 32; ++b) {
-            const uint32_t k = 32 * w + b;
-            if (k >= half) break;
-            const uint32_t n = site_of(L, c, k);
-            const uint4 u = philox4x32_10(n >> 2, j, 0, TAG_INIT << 24, rd.seed, rd.run_id);
-            word |= (pick(u, n & 3u) >> 31) << b;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t j = (blockIdx.x - tile_off[run]) * (blockDim.x >> 5) + warp;
+    if (j >= rd.R) return;  // warp-uniform; no block barrier below
+    const uint32_t L = rd.L, N = rd.N, PW = (N + 63) / 64;
+    uint32_t *pl = sw + warp * 2 * PW;
+    for (uint32_t cw = lane; cw < 2 * PW; cw += 32) pl[cw] = 0;
+    __syncwarp();
+    for (uint32_t g = lane; 4 * g < N; g += 32) {
+        const uint4 u = philox4x32_10(g, j, 0, TAG_INIT << 24, rd.seed, rd.run_id);
+        for (uint32_t q = 0; q < 4; ++q) {
+            const uint32_t n = 4 * g + q;
+            if (n >= N) break;
+            const uint32_t c = ((n % L) + (n / L)) & 1u, k = n >> 1;
+            if (pick(u, q) >> 31) atomicOr(&pl[c * PW + (k >> 5)], 1u << (k & 31));
         }
-        s[cw] = word;
     }
     __syncwarp();
-    const uint32_t *Jr = P.J + rd.J_off, *Jd = Jr + rd.wstride;
+    uint32_t *s = P.spins[0] + rd.spin_off + (uint64_t)j * rd.wstride;
+    for (uint32_t cw = lane; cw < 2 * PW; cw += 32) s[cw] = pl[cw];
     int32_t unsat = 0, up = 0;
-    for (uint32_t n = lane; n < rd.N; n += 32) {
-        const uint32_t x = n % L, y = n / L;
-        const uint32_t b = spin_bit(s, PW, L, n);
-        const uint32_t br = spin_bit(s, PW, L, y * L + (x + 1 == L ? 0 : x + 1));
-        const uint32_t bd = spin_bit(s, PW, L, (y + 1 == L ? 0 : y + 1) * L + x);
-        unsat += (int32_t)((b ^ br ^ get_bit(Jr, n)) + (b ^ bd ^ get_bit(Jd, n)));
-        up += (int32_t)b;
+    for (uint32_t cw = lane; cw < 2 * PW; cw += 32) up += __popc(pl[cw]);
+    const bool pow2 = L >= 8 && (L & (L - 1)) == 0;
+    if (pow2) {
+        const uint32_t *Jp = P.J + rd.J_off + 2 * rd.wstride;  // [c][4][PW] bond masks
+        for (uint32_t w = lane; w < PW; w += 32) {
+            uint32_t same, rot, upn, dn;
+            plane_neighbours(pl + PW, PW, rd.Lh, 0, w, same, rot, upn, dn);
+            const uint32_t S = pl[w];
+            unsat += __popc(S ^ same ^ Jp[w]) + __popc(S ^ rot ^ Jp[PW + w]) + __popc(S ^ upn ^ Jp[2 * PW + w]) +
+                     __popc(S ^ dn ^ Jp[3 * PW + w]);
+        }
+    } else {
+        const uint32_t *Jr = P.J + rd.J_off, *Jd = Jr + rd.wstride;
+        for (uint32_t n = lane; n < N; n += 32) {
+            const uint32_t x = n % L, y = n / L;
+            const uint32_t b = spin_bit(pl, PW, L, n);
+            const uint32_t br = spin_bit(pl, PW, L, y * L + (x + 1 == L ? 0 : x + 1));
+            const uint32_t bd = spin_bit(pl, PW, L, (y + 1 == L ? 0 : y + 1) * L + x);
+            unsat += (int32_t)((b ^ br ^ get_bit(Jr, n)) + (b ^ bd ^ get_bit(Jd, n)));
+        }
     }
     unsat = warp_sum(unsat);
     up = warp_sum(up);
     if (lane == 0) {
-        P.E[0][rd.rep_off + j] = 2 * unsat - 2 * (int32_t)rd.N;  // H = (#unsatisfied) - (#satisfied)
-        P.M[0][rd.rep_off + j] = 2 * up - (int32_t)rd.N;
+        P.E[0][rd.rep_off + j] = 2 * unsat - 2 * (int32_t)N;  // H = (#unsatisfied) - (#satisfied)
+        P.M[0][rd.rep_off + j] = 2 * up - (int32_t)N;
         P.fam[0][rd.rep_off + j] = j;
     }
 }
@@ -474,17 +538,19 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P)
 // "bond mask" plane holds per site the J = -1 bits of its right, left, down
 // and up bonds.
 // --------------------------------------------------------------------------
-__global__ void sweep_kernel(Pool P, const uint32_t *group_runs, SweepCfg cfg)
+__global__ void sweep_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off, uint32_t n_group_runs,
+                             SweepCfg cfg)
 {
     extern __shared__ __align__(16) uint8_t sm[];
-    const uint32_t run = group_runs[blockIdx.y];
+    const uint32_t slot = locate_slot(tile_off, n_group_runs, blockIdx.x);
+    const uint32_t run = group_runs[slot];
     const RunDev rd = P.runs[run];
     const RunState st = P.st[run];
     if (st.status) return;
     const uint32_t i = st.step + 1;
     if (i >= rd.n_beta) return;
     const uint32_t Rn = st.R_new;
-    const uint32_t tile0 = blockIdx.x * cfg.RPC;
+    const uint32_t tile0 = (blockIdx.x - tile_off[slot]) * cfg.RPC;
     if (tile0 >= Rn) return;  // uniform over the CTA
 
     const uint32_t L = rd.L, N = rd.N, Lh = rd.Lh, half = N >> 1, PS = cfg.PS, PW = (N + 63) / 64;
@@ -644,18 +710,20 @@ __device__ __forceinline__ uint4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c3
     return make_uint4(x0, x1, x2, x3);
 }
 
-template <bool SG, int WPT>
-__global__ void __launch_bounds__(256) sweep_pow2_kernel(Pool P, const uint32_t *group_runs, SweepCfg cfg)
+template <bool SG, int WPT, int MAXT>
+__global__ void __launch_bounds__(MAXT) sweep_pow2_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off,
+                                                          uint32_t n_group_runs, SweepCfg cfg)
 {
     extern __shared__ __align__(16) uint32_t smw[];
-    const uint32_t run = group_runs[blockIdx.y];
+    const uint32_t slot = locate_slot(tile_off, n_group_runs, blockIdx.x);
+    const uint32_t run = group_runs[slot];
     const RunDev rd = P.runs[run];
     const RunState st = P.st[run];
     if (st.status) return;
     const uint32_t i = st.step + 1;
     if (i >= rd.n_beta) return;
     const uint32_t Rn = st.R_new;
-    const uint32_t tile0 = blockIdx.x * cfg.RPC;
+    const uint32_t tile0 = (blockIdx.x - tile_off[slot]) * cfg.RPC;
     if (tile0 >= Rn) return;  // uniform over the CTA
 
     const uint32_t TPR = cfg.TPR, HW = TPR * WPT;  // threads per replica, words per plane
@@ -697,12 +765,6 @@ __global__ void __launch_bounds__(256) sweep_pow2_kernel(Pool P, const uint32_t 
 #pragma unroll
                 for (int d = 0; d < 4; ++d) J[q][c][d] = Jp[(c * 4 + d) * HW + tl + q * TPR];
     }
-    // segment masks for rows shorter than a word (Lh = 4, 8, 16)
-    const uint32_t LOW = Lh == 4 ? 0x11111111u : Lh == 8 ? 0x01010101u : 0x00010001u;
-    const uint32_t HIGH = LOW << ((Lh - 1) & 31);
-    const uint32_t EVEN = Lh == 4 ? 0x0F0F0F0Fu : Lh == 8 ? 0x00FF00FFu : 0x0000FFFFu;  // rows 0, 2, ...
-    const uint32_t WR = Lh >> 5;  // words per row when Lh >= 32
-
     const unsigned long long T1 = P.thr[rd.thr_off + 2 * i], T2 = P.thr[rd.thr_off + 2 * i + 1];
     const uint32_t t1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T1;
     const uint32_t t2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T2;
@@ -713,29 +775,8 @@ __global__ void __launch_bounds__(256) sweep_pow2_kernel(Pool P, const uint32_t 
     const uint32_t hi1_0 = __umulhi(0xCD9E8D57u, i), lo1_0 = 0xCD9E8D57u * i;
     if (TPR <= 32) __syncwarp(); else __syncthreads();
 
-    // neighbour masks of plane-c word w, read from plane (c ^ 1)
     auto neighbours = [&](uint32_t c, uint32_t w, uint32_t &same, uint32_t &rot, uint32_t &up, uint32_t &dn) {
-        const uint32_t *O = pl + (c ^ 1u) * HW;
-        if (Lh < 32) {
-            const uint32_t o = O[w], op = O[(w - 1) & (HW - 1)], on = O[(w + 1) & (HW - 1)];
-            same = o;
-            up = __funnelshift_l(op, o, Lh);  // bit k <- k - Lh
-            dn = __funnelshift_r(o, on, Lh);  // bit k <- k + Lh
-            const uint32_t rl = ((o << 1) & ~LOW) | ((o >> (Lh - 1)) & LOW);   // bit k <- k - 1 in the row
-            const uint32_t rr = ((o >> 1) & ~HIGH) | ((o << (Lh - 1)) & HIGH); // bit k <- k + 1 in the row
-            // rows with (c + y) even see the rotated neighbour at k - 1, odd rows at k + 1
-            rot = c == 0 ? ((rl & EVEN) | (rr & ~EVEN)) : ((rr & EVEN) | (rl & ~EVEN));
-        } else {
-            const uint32_t o = O[w];
-            same = o;
-            up = O[(w - WR) & (HW - 1)];
-            dn = O[(w + WR) & (HW - 1)];
-            const uint32_t y = w / WR, base = y * WR, q = w - base;
-            if (((c + y) & 1u) == 0)
-                rot = (o << 1) | (O[base + ((q - 1) & (WR - 1))] >> 31);
-            else
-                rot = (o >> 1) | (O[base + ((q + 1) & (WR - 1))] << 31);
-        }
+        plane_neighbours(pl + (c ^ 1u) * HW, HW, Lh, c, w, same, rot, up, dn);
     };
 
     for (uint32_t t = 0; t < rd.theta; ++t) {
@@ -976,19 +1017,20 @@ __global__ void __launch_bounds__(512) measure_kernel(Pool P, int init)
 
 // --------------------------------------------------------------------------
 // Weighted averages (Sec. IV, Eqs. appropriateWeight / simpleWeight, W_conf,
-// W_F, Wvar_C, Wvar_Chi) in FP64: one thread per group, sequential over steps
-// and runs m = 0..M-1.  w receives the weights [group][step][m].
+// W_F, Wvar_C, Wvar_Chi) in FP64: one warp per group, lanes over the runs m,
+// temperatures in order.  w receives the weights [group][step][m].
 // --------------------------------------------------------------------------
-__global__ void wavg_kernel(const pa_step_record *recs, const unsigned long long *rec_off, uint32_t n_groups,
-                            uint32_t M, uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w)
+__global__ void __launch_bounds__(64) wavg_kernel(const pa_step_record *recs, const unsigned long long *rec_off,
+                                                  uint32_t n_groups, uint32_t M, uint32_t n_steps, uint32_t N,
+                                                  uint32_t kind, pa_wavg *out, double *w)
 {
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_groups) return;
+    const uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (g >= n_groups) return;  // warp-uniform
     const unsigned long long *off = rec_off + (uint64_t)g * M;
     double *wg = w + (uint64_t)g * n_steps * M;
     const double Nd = (double)N;
     // pass 1: log weights lambda(i, m) = ln R_i + (-beta_i F_i) [+ sum_{k<=i} ln(R_{k-1} / R)]
-    for (uint32_t m = 0; m < M; ++m) {
+    for (uint32_t m = lane; m < M; m += 32) {
         const pa_step_record *r = recs + off[m];
         double lsum = 0.0;
         for (uint32_t i = 0; i < n_steps; ++i) {
@@ -996,24 +1038,23 @@ __global__ void wavg_kernel(const pa_step_record *recs, const unsigned long long
             wg[(uint64_t)i * M + m] = log((double)r[i].R) + r[i].minus_betaF + lsum;
         }
     }
-    // pass 2: normalise per temperature and average
+    // pass 2: normalise per temperature and average (each lane touches only its own m)
     double WF = Nd * log(2.0);
     for (uint32_t i = 0; i < n_steps; ++i) {
         double *wi = wg + (uint64_t)i * M;
         double lmax = -INFINITY;
-        for (uint32_t m = 0; m < M; ++m) lmax = wi[m] > lmax ? wi[m] : lmax;
+        for (uint32_t m = lane; m < M; m += 32) lmax = wi[m] > lmax ? wi[m] : lmax;
+        lmax = warp_max(lmax);
         double z = 0.0;
-        for (uint32_t m = 0; m < M; ++m) {
+        for (uint32_t m = lane; m < M; m += 32) {
             wi[m] = exp(wi[m] - lmax);
             z += wi[m];
         }
-        pa_wavg o;
-        o.beta = recs[off[0] + i].beta;
-        o.W_e = o.W_e2 = o.W_m = o.W_m2 = o.W_c = o.W_chi = o.W_absq = o.W_absq_pair = 0.0;
-        o.w_max = 0.0;
-        o.sum_w = 0.0;
-        const double beta = o.beta;
-        for (uint32_t m = 0; m < M; ++m) {
+        z = warp_sum(z);
+        const double beta = recs[off[0] + i].beta;
+        double se = 0.0, se2 = 0.0, sm = 0.0, sm2 = 0.0, sc = 0.0, schi = 0.0, sq = 0.0, sqp = 0.0, sw = 0.0,
+               wmax = 0.0;
+        for (uint32_t m = lane; m < M; m += 32) {
             wi[m] = wi[m] / z;
             const pa_step_record *r = recs + off[m] + i;
             const double Ri = (double)r->R;
@@ -1021,35 +1062,49 @@ __global__ void wavg_kernel(const pa_step_record *recs, const unsigned long long
             const double e2 = (double)r->sumE2 / (Nd * Nd * Ri);
             const double mm = (double)r->sumAbsM / (Nd * Ri);
             const double m2 = (double)r->sumM2 / (Nd * Nd * Ri);
-            const double c = beta * beta * Nd * (e2 - e * e);
-            const double chi = beta * Nd * (m2 - mm * mm);
+            const double c = beta * beta * Nd * (e2 - e * e);  // Eq. c
+            const double chi = beta * Nd * (m2 - mm * mm);     // Eq. chi
             const double wm = wi[m];
-            o.W_e += wm * e;
-            o.W_e2 += wm * e2;
-            o.W_m += wm * mm;
-            o.W_m2 += wm * m2;
-            o.W_c += wm * c;
-            o.W_chi += wm * chi;
-            if (r->n_q) o.W_absq += wm * ((double)r->sum_absq / (Nd * (double)r->n_q));
-            if (r->n_q_pair) o.W_absq_pair += wm * ((double)r->sum_absq_pair / (Nd * (double)r->n_q_pair));
-            o.sum_w += wm;
-            o.w_max = wm > o.w_max ? wm : o.w_max;
+            se += wm * e;
+            se2 += wm * e2;
+            sm += wm * mm;
+            sm2 += wm * m2;
+            sc += wm * c;
+            schi += wm * chi;
+            if (r->n_q) sq += wm * ((double)r->sum_absq / (Nd * (double)r->n_q));
+            if (r->n_q_pair) sqp += wm * ((double)r->sum_absq_pair / (Nd * (double)r->n_q_pair));
+            sw += wm;
+            wmax = wm > wmax ? wm : wmax;
         }
+        pa_wavg o;
+        o.beta = beta;
+        o.W_e = warp_sum(se);
+        o.W_e2 = warp_sum(se2);
+        o.W_m = warp_sum(sm);
+        o.W_m2 = warp_sum(sm2);
+        o.W_c = warp_sum(sc);
+        o.W_chi = warp_sum(schi);
+        o.W_absq = warp_sum(sq);
+        o.W_absq_pair = warp_sum(sqp);
+        o.sum_w = warp_sum(sw);
+        o.w_max = warp_max(wmax);
         o.Wvar_c = beta * beta * Nd * (o.W_e2 - o.W_e * o.W_e);
         o.Wvar_chi = beta * Nd * (o.W_m2 - o.W_m * o.W_m);
-        if (i > 0) {
-            const double *wp = wi - M;  // weights at beta_{i-1}
+        if (i > 0) {  // Eq. W_F: W[Q_i] = sum_m w_{i-1} Q_i, as a log-sum-exp
+            const double *wp = wi - M;
             double lm = -INFINITY;
-            for (uint32_t m = 0; m < M; ++m) {
+            for (uint32_t m = lane; m < M; m += 32) {
                 const double l = log(wp[m]) + recs[off[m] + i].lnQ;
                 lm = l > lm ? l : lm;
             }
+            lm = warp_max(lm);
             double zz = 0.0;
-            for (uint32_t m = 0; m < M; ++m) zz += exp(log(wp[m]) + recs[off[m] + i].lnQ - lm);
+            for (uint32_t m = lane; m < M; m += 32) zz += exp(log(wp[m]) + recs[off[m] + i].lnQ - lm);
+            zz = warp_sum(zz);
             WF = WF + (lm + log(zz));
         }
         o.W_minus_betaF = WF;
-        out[(uint64_t)g * n_steps + i] = o;
+        if (lane == 0) out[(uint64_t)g * n_steps + i] = o;
     }
 }
 
@@ -1089,31 +1144,52 @@ void launch_init_couplings(const Pool &P, uint32_t n_runs, cudaStream_t s)
     init_couplings_kernel<<<n_runs, 256, 0, s>>>(P);
 }
 
-void launch_init_population(const Pool &P, uint32_t n_runs, uint32_t max_R, cudaStream_t s)
+void launch_init_population(const Pool &P, const uint32_t *tile_off, uint32_t n_runs, uint32_t n_tiles,
+                            uint32_t max_pw, cudaStream_t s)
 {
-    dim3 grid((max_R + 3) / 4, n_runs);
-    init_population_kernel<<<grid, 128, 0, s>>>(P);
+    init_population_kernel<<<n_tiles, 128, 4 * 2 * max_pw * sizeof(uint32_t), s>>>(P, tile_off, n_runs);
 }
 
 void launch_resample(const Pool &P, uint32_t n_runs, cudaStream_t s) { resample_kernel<<<n_runs, 512, 0, s>>>(P); }
 
-SweepCfg sweep_config(uint32_t L, int allow_fast)
+// Launch shapes of the bit-sliced kernel: WPT plane words per thread and
+// `block` threads per CTA (a multiple of the threads per replica, HW / WPT).
+SweepCfg sweep_fast_config(uint32_t L, uint32_t WPT, uint32_t block)
 {
     SweepCfg c{};
+    const uint32_t N = L * L, HW = N / 64;
+    c.fast = 1;
+    c.WPT = WPT;
+    c.TPR = HW / WPT;
+    c.block = block;
+    c.RPC = block / c.TPR;
+    c.G = N / 8;
+    c.PS = 0;
+    c.smem = c.RPC * 2 * HW * 4 + 8 * c.RPC;
+    return c;
+}
+
+std::vector<SweepCfg> sweep_candidates(uint32_t L, int allow_fast)
+{
+    std::vector<SweepCfg> v;
     const uint32_t N = L * L;
     const bool pow2 = L >= 8 && L <= 256 && (L & (L - 1)) == 0;
     if (pow2 && allow_fast) {
-        const uint32_t HW = N / 64;  // words per colour plane
-        c.fast = 1;
-        c.WPT = HW > 256 ? HW / 256 : 1;
-        c.TPR = HW / c.WPT;
-        c.block = c.TPR >= 128 ? c.TPR : 128;
-        c.RPC = c.block / c.TPR;
-        c.G = N / 8;
-        c.PS = 0;
-        c.smem = c.RPC * 2 * HW * 4 + 8 * c.RPC;
-        return c;
+        const uint32_t HW = N / 64;
+        if (HW <= 128) {
+            v.push_back(sweep_fast_config(L, 1, 128));
+            v.push_back(sweep_fast_config(L, 1, 256));
+        } else if (HW == 256) {
+            v.push_back(sweep_fast_config(L, 1, 256));
+            v.push_back(sweep_fast_config(L, 2, 128));
+        } else {  // L = 256
+            v.push_back(sweep_fast_config(L, 4, 256));
+            v.push_back(sweep_fast_config(L, 2, 512));
+            v.push_back(sweep_fast_config(L, 1, 1024));
+        }
+        return v;
     }
+    SweepCfg c{};
     c.fast = 0;
     c.WPT = 1;
     c.G = (N + 7) / 8;
@@ -1130,23 +1206,27 @@ SweepCfg sweep_config(uint32_t L, int allow_fast)
     }
     c.PS = 4 * c.G;
     c.smem = c.RPC * 2 * c.PS + 2 * c.PS + 8 * c.RPC;
-    return c;
+    v.push_back(c);
+    return v;
 }
 
-void launch_sweep(const Pool &P, const uint32_t *group_runs, uint32_t n_group_runs, uint32_t max_Rcap,
-                  const SweepCfg &cfg, int any_glass, cudaStream_t s)
+void launch_sweep(const Pool &P, const uint32_t *group_runs, const uint32_t *tile_off, uint32_t n_group_runs,
+                  uint32_t n_tiles, const SweepCfg &cfg, int any_glass, cudaStream_t s)
 {
-    dim3 grid((max_Rcap + cfg.RPC - 1) / cfg.RPC, n_group_runs);
+    const dim3 grid(n_tiles);
+#define PA_SWEEP_FAST(SG, WPT, MAXT) \
+    sweep_pow2_kernel<SG, WPT, MAXT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg)
     if (!cfg.fast)
-        sweep_kernel<<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
-    else if (cfg.WPT == 1 && any_glass)
-        sweep_pow2_kernel<true, 1><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
+        sweep_kernel<<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg);
+    else if (cfg.WPT == 1 && cfg.block <= 256)
+        any_glass ? PA_SWEEP_FAST(true, 1, 256) : PA_SWEEP_FAST(false, 1, 256);
     else if (cfg.WPT == 1)
-        sweep_pow2_kernel<false, 1><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
-    else if (any_glass)
-        sweep_pow2_kernel<true, 4><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
+        any_glass ? PA_SWEEP_FAST(true, 1, 1024) : PA_SWEEP_FAST(false, 1, 1024);
+    else if (cfg.WPT == 2)
+        any_glass ? PA_SWEEP_FAST(true, 2, 512) : PA_SWEEP_FAST(false, 2, 512);
     else
-        sweep_pow2_kernel<false, 4><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, cfg);
+        any_glass ? PA_SWEEP_FAST(true, 4, 256) : PA_SWEEP_FAST(false, 4, 256);
+#undef PA_SWEEP_FAST
 }
 
 void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, uint32_t max_Rcap, int init,
@@ -1166,7 +1246,7 @@ void launch_wavg(const pa_step_record *recs, const unsigned long long *rec_off, 
                  uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w, double *Pq, double *Pqp,
                  cudaStream_t s)
 {
-    wavg_kernel<<<(n_groups + 63) / 64, 64, 0, s>>>(recs, rec_off, n_groups, M, n_steps, N, kind, out, w);
+    wavg_kernel<<<(n_groups + 1) / 2, 64, 0, s>>>(recs, rec_off, n_groups, M, n_steps, N, kind, out, w);
     if (Pq || Pqp) {
         dim3 grid(n_steps, n_groups);
         wavg_q_kernel<<<grid, 256, 0, s>>>(recs, rec_off, qh, qhp, qh_off, M, n_steps, N, w, Pq, Pqp);

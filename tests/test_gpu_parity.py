@@ -212,11 +212,22 @@ def test_bitsliced_and_generic_sweeps_agree(L):
     descs = [W.RunDesc(L, W.FERRO, R, 2, b, seed=3, run_id=0),
              W.RunDesc(L, W.EA_PMJ, R, 2, b, seed=3, run_id=1, disorder_id=9, overlap=W.Q_SHIFT)]
     out = []
-    for flags in (0, _lib.PA_CREATE_GENERIC_SWEEP):
+    for flags in (0, _lib.PA_CREATE_GENERIC_SWEEP, _lib.PA_CREATE_NO_AUTOTUNE):
         with _lib.Engine(descs, flags=flags) as eng:
             eng.run_to_end()
             out.append([(eng.records(k), eng.population(k)) for k in range(2)])
-    for (ra, pa), (rb, pb) in zip(out[0], out[1]):
-        assert np.array_equal(ra, rb)
-        for x, y in zip(pa, pb):
-            assert np.array_equal(np.asarray(x), np.asarray(y))
+    for other in out[1:]:
+        for (ra, pa), (rb, pb) in zip(out[0], other):
+            assert np.array_equal(ra, rb)
+            for x, y in zip(pa, pb):
+                assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_uneven_batch_work_list():
+    """Runs of very different R share each lattice size's work list (one launch
+    per kernel): every run equals its oracle run."""
+    b = W.schedule(1.0, 5)
+    descs = []
+    for k, (L, R) in enumerate([(16, 5), (16, 2000), (16, 37), (32, 3), (32, 500), (8, 1), (8, 1000), (64, 17)]):
+        descs.append(W.RunDesc(L, W.FERRO if k % 2 else W.EA_PMJ, R, 2, b, seed=8, run_id=k, disorder_id=k))
+    run_case(descs)
