@@ -45,6 +45,9 @@ WORKLOADS = {
                     "beta 0->1 in 101 steps, theta=10, one launch per kernel per step over all runs"),
     "ising_L256_R1e5": ("2D Ising FM L=256 periodic, R=1e5, beta 0->0.44 in 201 steps, theta=20, "
                         "M=16 runs, free-energy-weighted averages over the runs"),
+    "serving": ("Poisson stream of PA jobs at 200/s (FM or +-J glass with equal odds, L even uniform in 8..64, "
+                "R log-uniform in 1e3..5e4, 50..300 temperatures, beta_f 1 (FM) / 3 (glass), theta=10), "
+                "continuous batching in one server engine with a 64 GB pool budget"),
 }
 WORKLOAD = WORKLOADS["glass_L16_R5000"]
 # Algorithmic work of one attempted update on the binding unit, the 32-bit
@@ -65,6 +68,7 @@ def parse():
     ap.add_argument("--workload", default="glass_L16_R5000", choices=sorted(WORKLOADS))
     ap.add_argument("--samples", type=int, default=100, help="glass: disorder samples (2 populations each)")
     ap.add_argument("--runs", type=int, default=0, help="ising/uneven: number of runs (0 = the workload's)")
+    ap.add_argument("--window", type=float, default=2.0, help="serving: seconds of arrivals")
     ap.add_argument("--max-temps", type=int, default=0,
                     help="anneal only the first T temperatures of the schedule (0 = all); reported in config")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -78,6 +82,8 @@ def _workload_descs(wl, runs=0):
     from paper_2207_05535_gb300 import workloads as W
     if wl == "glass_L16_R5000":
         return W.glass_L16_R5000()
+    if wl == "serving":
+        return [d for _, d in W.serving_stream(duration=2.0)]
     if wl == "ising_L8_R500":
         return W.ising_L8_R500(M=runs or 20)
     if wl == "uneven_4096":
@@ -104,7 +110,7 @@ def _oracle_job(args):
 
 # bounded oracle samples per workload: (temperatures, population cap)
 ORACLE_SAMPLE = {"glass_L16_R5000": (25, 0), "ising_L8_R500": (51, 0), "uneven_4096": (2, 2000),
-                 "ising_L256_R1e5": (2, 200)}
+                 "ising_L256_R1e5": (2, 200), "serving": (6, 2000)}
 
 
 def oracle_sample(wl="glass_L16_R5000", n_temps=None, procs=None):
@@ -229,8 +235,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # weak scaling: every rank anneals its own batch (disorder samples / runs offset by rank)
     wl = args.workload
+    if wl == "serving":
+        return serving_main(args, rank, world, cpu)
+    # weak scaling: every rank anneals its own batch (disorder samples / runs offset by rank)
     if wl == "glass_L16_R5000":
         descs, M_avg = W.glass_L16_R5000(n_samples=args.samples), 2
     elif wl == "ising_L8_R500":
@@ -244,9 +252,8 @@ def main():
     if args.max_temps:
         for d in descs:
             d.betas = d.betas[:args.max_temps]
-    for d in descs:
-        d.disorder_id += 100000 * rank
-        d.run_id += 200000 * rank
+    from paper_2207_05535_gb300 import replicas
+    descs = replicas.shard(descs, rank)
     n_ticks = max(d.n_beta for d in descs) - 1
     idx = np.arange(len(descs), dtype=np.uint32)
     stream = torch.cuda.Stream()
@@ -285,15 +292,7 @@ def main():
         rec = eng.records(k)
         updates += int(sum(descs[k].theta * descs[k].N * int(r) for r in rec["R"][1:]))
         runs_done += 1
-    upd_all = updates * args.steps
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        u = torch.tensor([float(upd_all)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(u)
-        upd_all = float(u.item())
+    t_max, upd_all = replicas.reduce_timing(ms, updates * args.steps, dist, device="cuda")
     value = upd_all / (t_max * 1e6)
     runs_per_s = world * runs_done * args.steps / (t_max / 1e3)
 
@@ -407,6 +406,60 @@ def main():
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def serving_main(args, rank, world, cpu):
+    """The serving workload: a Poisson stream through one continuous-batching server."""
+    import dataclasses
+    import numpy as np
+    import torch
+    from paper_2207_05535_gb300 import _lib, serve
+    from paper_2207_05535_gb300 import workloads as W
+    stream = torch.cuda.Stream()
+    cfg = serve.config_for_budget(64 << 30)
+    arrivals = W.serving_stream(duration=args.window, seed=11 + 1000 * rank)
+    # warm-up: a short stream (tunes the sweep shapes of the lattice sizes it meets)
+    warm = W.serving_stream(duration=0.2, seed=99)
+    for _ in range(max(1, args.warmup)):
+        srv = serve.Server(cfg, stream.cuda_stream)
+        serve.serve([(0.0, d) for _, d in warm], srv)
+        srv.close()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0"))) if rank == 0 else None
+    torch.cuda.synchronize()
+    srv = serve.Server(cfg, stream.cuda_stream)
+    l0 = _lib.pa_launch_count(srv.h)
+    done, st = serve.serve(arrivals, srv)
+    torch.cuda.synchronize()
+    launches = _lib.pa_launch_count(srv.h) - l0
+    srv.close()
+    clk = clocks.stop() if clocks else None
+    summ = serve.summarize(done, st["wall_s"])
+    # plain form: the first 20 jobs one after another, one engine each
+    plain = None
+    if not args.no_plain:
+        t0 = time.perf_counter()
+        upd = 0
+        for _, d in arrivals[:20]:
+            e = _lib.Engine([dataclasses.replace(d)], stream.cuda_stream)
+            e.run_to_end(False)
+            rec = e.records(0)
+            upd += int(sum(d.theta * d.N * int(r) for r in rec["R"][1:]))
+            e.close()
+        pt = time.perf_counter() - t0
+        plain = {"value": upd / (pt * 1e9), "unit": UNIT, "runs": 20, "runs_per_s": 20 / pt,
+                 "form": "the first 20 jobs one after another, one engine and launch sequence each"}
+    out = {"metric": METRIC, "value": summ["updates_per_ns"], "unit": UNIT, "n_gpus": world, "steps": 1,
+           "warmup": args.warmup, "ms_per_step": 1e3 * st["wall_s"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
+           "config": {"workload": WORKLOADS["serving"], "name": "serving", "window_s": args.window,
+                      "jobs": len(arrivals), "form": "continuous batching (admit/retire between steps)"},
+           "serving": summ, "runs_per_s": summ["jobs_per_s"], "gpu_launches": launches, "clocks": clk,
+           "plain": plain, "cpu_baseline": cpu,
+           "e2e": {"value": summ["updates_per_ns"], "unit": UNIT, "h2d_bytes_per_step": None,
+                   "d2h_bytes_per_step": None, "includes": "wall clock of the whole stream: admissions "
+                   "(descriptor and table uploads), steps, record copies, retirements"}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

@@ -124,6 +124,49 @@ enum { PA_CREATE_GENERIC_SWEEP = 1, PA_CREATE_NO_AUTOTUNE = 2 };
 pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, uint32_t flags,
                        pa_engine **out);
 
+/* ---- Serving: continuous batching of PA jobs ----------------------------
+ * A server engine owns fixed device pools sized by this configuration (all
+ * counts, not bytes; see pa_server_bytes).  Jobs (runs) are admitted and
+ * retired between anneal steps; every pa_anneal_step advances all resident,
+ * unfinished runs by one temperature in shared launches, each at its own
+ * temperature index.  A run's results do not depend on which other runs were
+ * resident (its randomness is keyed by its own seed and ids). */
+typedef struct pa_server_config {
+    uint32_t max_runs;          /* slots */
+    uint32_t reserved;          /* must be 0 */
+    uint64_t replica_capacity;  /* sum over resident runs of R_cap */
+    uint64_t spin_words;        /* sum of R_cap * (2 ceil(L^2/64) rounded up to 4) */
+    uint64_t record_capacity;   /* sum of n_beta */
+    uint64_t qhist_words;       /* sum over overlap runs of n_beta (L^2 + 1) */
+    uint64_t scratch_words;     /* per run about 2 (L^2 + 1) + R_cap / 2 64-bit words */
+    uint64_t coupling_words;    /* per run 2 * spin stride + 8 ceil(L^2/64) */
+    uint64_t table_doubles;     /* cache of weight tables, (L^2 + 1) per distinct (L, dbeta) */
+} pa_server_config;
+
+/* Create an empty server engine (flags as for pa_create_ex).  Errors:
+ * PA_ERR_INVALID_ARG, PA_ERR_OOM, PA_ERR_CUDA. */
+pa_status pa_server_create(const pa_server_config *cfg, void *cuda_stream, uint32_t flags, pa_engine **out);
+
+/* Admit n_runs runs (pair indices relative to this call; a pair is admitted
+ * together) into free slots; *slots_out receives their slot numbers, which
+ * every per-run call takes in place of a run index.  All or nothing: returns
+ * PA_ERR_BUSY (nothing admitted) when slots, pool space or table space are
+ * short.  Their beta_0 populations are drawn with the next enqueued work. */
+pa_status pa_admit(pa_engine *e, const pa_run_desc *runs, uint32_t n_runs, uint32_t *slots_out);
+
+/* Release a slot and its pool ranges (after reading its records).  Waits for
+ * the engine's queued work.  A retired run's partner continues without
+ * two-population overlaps. */
+pa_status pa_retire(pa_engine *e, uint32_t slot);
+
+/* Slots whose runs have reached their last temperature (host bookkeeping, no
+ * synchronisation): writes up to cap slots, *n_out = how many there are. */
+pa_status pa_finished(const pa_engine *e, uint32_t *slots_out, uint32_t cap, uint32_t *n_out);
+
+/* Device state of a slot: temperature index, population size and status
+ * (0 or the pa_status that stopped it).  Synchronises. */
+pa_status pa_run_state(pa_engine *e, uint32_t slot, uint32_t *step, uint32_t *R, uint32_t *status);
+
 /* Return every run of the engine to its beta_0 population (same descriptors,
  * same randomness, so the next anneal repeats the first one bit for bit)
  * without reallocating: clears records, histograms and statuses, redraws the

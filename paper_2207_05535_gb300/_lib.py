@@ -25,6 +25,12 @@ class PAError(RuntimeError):
         super().__init__(f"{what}: {STATUS.get(code, code)}")
 
 
+class pa_server_config(C.Structure):
+    _fields_ = [("max_runs", C.c_uint32), ("reserved", C.c_uint32), ("replica_capacity", C.c_uint64),
+                ("spin_words", C.c_uint64), ("record_capacity", C.c_uint64), ("qhist_words", C.c_uint64),
+                ("scratch_words", C.c_uint64), ("coupling_words", C.c_uint64), ("table_doubles", C.c_uint64)]
+
+
 class pa_run_desc(C.Structure):
     _fields_ = [("L", C.c_uint32), ("model", C.c_uint32), ("R", C.c_uint32), ("R_cap", C.c_uint32),
                 ("theta", C.c_uint32), ("n_beta", C.c_uint32), ("beta", C.POINTER(C.c_double)),
@@ -48,7 +54,8 @@ WAVG_DTYPE = np.dtype([
     ("w_max", "f8"), ("sum_w", "f8"),
 ])
 
-EXPORTS = ["pa_create", "pa_create_ex", "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population",
+EXPORTS = ["pa_create", "pa_create_ex", "pa_server_create", "pa_admit", "pa_retire", "pa_finished", "pa_run_state",
+           "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population",
            "pa_weighted_average_runs", "pa_weighted_average", "pa_weighted_average_noalloc", "pa_launch_count", "pa_set_profiling",
            "pa_kernel_times", "pa_transfer_bytes", "pa_sweep_shape", "pa_destroy", "pa_status_string"]
 KERNEL_KINDS = ["resample", "sweep", "overlap", "measure", "init", "wavg"]
@@ -70,6 +77,11 @@ def load(path: str = LIB_PATH):
         P, u32, vp = C.POINTER, C.c_uint32, C.c_void_p
         lib.pa_create.argtypes = [P(pa_run_desc), u32, vp, P(vp)]
         lib.pa_create_ex.argtypes = [P(pa_run_desc), u32, vp, u32, P(vp)]
+        lib.pa_server_create.argtypes = [P(pa_server_config), vp, u32, P(vp)]
+        lib.pa_admit.argtypes = [vp, P(pa_run_desc), u32, P(u32)]
+        lib.pa_retire.argtypes = [vp, u32]
+        lib.pa_finished.argtypes = [vp, P(u32), u32, P(u32)]
+        lib.pa_run_state.argtypes = [vp, u32, P(u32), P(u32), P(u32)]
         lib.pa_reset.argtypes = [vp]
         lib.pa_anneal_step.argtypes = [vp, u32, C.c_int]
         lib.pa_sync.argtypes = [vp]
@@ -139,6 +151,39 @@ def pa_create_ex(runs, stream=None, flags=0):
     s = C.c_void_p(stream) if stream else None
     _check(lib.pa_create_ex(d, len(runs), s, flags, C.byref(h)), "pa_create_ex")
     return h
+
+
+def pa_server_create(cfg, stream=None, flags=0):
+    h = C.c_void_p()
+    s = C.c_void_p(stream) if stream else None
+    _check(load().pa_server_create(C.byref(cfg), s, flags, C.byref(h)), "pa_server_create")
+    return h
+
+
+def pa_admit(h, runs):
+    """Admit runs (pair indices relative to the list); returns their slots.
+    Raises PAError with code PA_ERR_BUSY (8) when there is no room."""
+    d = make_descs(runs)
+    slots = (C.c_uint32 * len(runs))()
+    _check(load().pa_admit(h, d, len(runs), slots), "pa_admit")
+    return [int(x) for x in slots]
+
+
+def pa_retire(h, slot):
+    _check(load().pa_retire(h, slot), "pa_retire")
+
+
+def pa_finished(h, cap=4096):
+    buf = (C.c_uint32 * cap)()
+    n = C.c_uint32()
+    _check(load().pa_finished(h, buf, cap, C.byref(n)), "pa_finished")
+    return [int(buf[k]) for k in range(min(n.value, cap))]
+
+
+def pa_run_state(h, slot):
+    a, b, c = C.c_uint32(), C.c_uint32(), C.c_uint32()
+    _check(load().pa_run_state(h, slot, C.byref(a), C.byref(b), C.byref(c)), "pa_run_state")
+    return int(a.value), int(b.value), int(c.value)
 
 
 def pa_reset(h):

@@ -1,64 +1,153 @@
 // Host side of the population-annealing engine: the C ABI declared in pa.h.
 //
-// pa_create lays out one device pool for all runs (offsets per run, see
-// pa_internal.cuh), builds the per-step tables on the host (weights
-// exp(-4 n dbeta_i) for the resampling normalisation and the Metropolis
-// thresholds floor(exp(-4 m beta_i) 2^32)), draws the beta_0 populations and
-// measures step 0.  pa_anneal_step enqueues one anneal step per call for all
-// runs: resample (all runs), sweep (one launch per lattice size), overlaps and
-// measurement; the sequence can be captured once as a CUDA graph and
-// replayed because every kernel reads its temperature index from device state.
+// An engine owns fixed device pools (replica slots, spin words, records,
+// overlap histograms, per-run tables, scratch) and a set of resident runs,
+// each at its own offsets (pa_internal.cuh).  Runs enter by admission: the
+// engine carves their ranges from free lists, uploads their descriptor and
+// tables, and with the next enqueued work draws their beta_0 populations and
+// measures step 0.  Every anneal step then advances all resident, unfinished
+// runs by one temperature in shared launches: resample (all runs), sweep (one
+// launch per lattice size over a work list of (run, tile)), overlaps and
+// measurement.  Kernels read each run's temperature index from device state,
+// so runs at different temperatures share launches and one captured graph
+// serves every step while the resident set is unchanged.
+//
+// pa_create sizes the pools to exactly its runs and admits them all (batch
+// form); pa_server_create sizes them from a configuration and runs enter and
+// leave with pa_admit / pa_retire between steps (continuous batching).
+//
+// Host tables: the resampling weights exp(-4 n dbeta) for n = 0..N are built
+// with libm once per distinct (N, dbeta) and shared by every run and step that
+// uses them; the Metropolis thresholds floor(exp(-4 m beta_i) 2^32) per step.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "pa_internal.cuh"
 
 using namespace pa;
 
-struct SweepGroup {
-    uint32_t L;
-    int any_glass = 0;
-    SweepCfg cfg;                     // chosen launch shape
-    std::vector<SweepCfg> candidates; // timed on the first anneal step when more than one
-    bool tuned = false;
-    float tuned_ms = 0.f;
-    uint32_t max_Rcap;
-    std::vector<uint32_t> runs;
-    std::vector<uint32_t> n_tiles;   // per candidate: total tiles (prefix of ceil(R_cap / RPC))
-    uint32_t *d_runs = nullptr;      // run indices, then per candidate its tile map (n + 1 entries)
-    uint32_t pick = 0;               // chosen candidate
-    const uint32_t *tile_map(uint32_t c) const { return d_runs + runs.size() + (size_t)c * (runs.size() + 1); }
+namespace {
+
+// First-fit free list over [0, cap) in arbitrary units.
+struct FreeList {
+    uint64_t cap = 0;
+    std::map<uint64_t, uint64_t> free_;  // offset -> size
+    void init(uint64_t c)
+    {
+        cap = c;
+        free_.clear();
+        if (c) free_[0] = c;
+    }
+    bool alloc(uint64_t n, uint64_t &off)
+    {
+        if (n == 0) {
+            off = 0;
+            return true;
+        }
+        for (auto it = free_.begin(); it != free_.end(); ++it)
+            if (it->second >= n) {
+                off = it->first;
+                const uint64_t rest = it->second - n;
+                free_.erase(it);
+                if (rest) free_[off + n] = rest;
+                return true;
+            }
+        return false;
+    }
+    void release(uint64_t off, uint64_t n)
+    {
+        if (n == 0) return;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
 };
+
+struct Tuning {
+    std::vector<SweepCfg> candidates;
+    uint32_t pick = 0;
+    bool tuned = false;
+    float ms = 0.f;
+};
+
+struct SweepGroup {  // runs of one lattice size among the resident runs
+    uint32_t L = 0;
+    int any_glass = 0;
+    std::vector<uint32_t> runs;
+    uint64_t runs_off = 0;               // in d_meta
+    std::vector<uint64_t> tile_map_off;  // per candidate, in d_meta (n + 1 entries)
+    std::vector<uint32_t> n_tiles;       // per candidate
+};
+
+// Offsets of one run in each pool (units of that pool).
+struct Ranges {
+    uint64_t rep = 0, spin = 0, rec = 0, qh = 0, scr = 0, J = 0, beta = 0, thr = 0, wto = 0;
+};
+
+struct RunHost {  // host view of a resident run
+    bool used = false;
+    pa_run_desc d{};
+    Ranges g;
+    uint32_t steps_done = 0;  // temperature index reached (mirrors the device while no error)
+};
+
+}  // namespace
 
 struct pa_engine {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int device = 0;
-    uint32_t n_runs = 0;
+    uint32_t flags = 0;
+    bool server = false;
+    // slots
+    uint32_t S = 0;
     std::vector<RunDev> rd;
-    std::vector<SweepGroup> groups;
-    std::vector<uint32_t> q_runs;
-    uint32_t *d_q_runs = nullptr;
-    uint32_t *d_init_tiles = nullptr;  // prefix of ceil(R / 4) over all runs
-    uint32_t init_tiles = 0;
-    uint32_t max_pw = 1;  // largest colour-plane word count of any run
-    uint32_t max_Rcap = 0, max_R = 0, max_nbeta = 0;
+    std::vector<RunHost> rh;
+    std::vector<uint32_t> active;   // resident slots, admission order
+    std::vector<uint32_t> pending;  // admitted, beta_0 not drawn yet
+    // pools and their free lists
     Pool P{};
-    std::vector<void *> allocs;
+    RunDev *d_runs = nullptr;
+    double *d_beta = nullptr, *d_wt = nullptr;
+    unsigned long long *d_thr = nullptr, *d_wtoff = nullptr;
+    FreeList fl_rep, fl_spin, fl_rec, fl_qh, fl_scr, fl_J, fl_beta, fl_thr, fl_wto;
+    uint64_t wt_cap = 0, wt_used = 0;
+    std::map<std::pair<uint32_t, uint64_t>, uint64_t> wt_cache;  // (N, dbeta bits) -> offset
+    // device metadata (lists and work lists), rebuilt when the resident set changes
+    uint32_t *d_meta = nullptr;
+    uint64_t meta_cap = 0;
+    std::vector<uint32_t> h_meta;
+    bool dirty = true;
+    uint64_t active_off = 0, q_off = 0, init_runs_off = 0, init_tiles_off = 0, init_q_off = 0;
+    uint32_t init_q_n = 0;
+    std::vector<uint32_t> q_runs;
+    uint32_t init_n = 0, init_tiles = 0;
+    std::vector<SweepGroup> groups;
+    std::map<uint32_t, Tuning> tuning;  // per lattice size
+    uint32_t max_Rcap_active = 0, max_pw = 1;
+    // execution
     uint64_t launches = 0;
-    uint64_t rec_count = 0, qh_count = 0;
-    uint64_t launches_per_tick = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     pa_status latched = PA_OK;
-    // profiling: event pairs per launch, summed by pa_kernel_times
     bool profiling = false;
     std::vector<cudaEvent_t> ev_free;
     struct Timed {
@@ -67,9 +156,9 @@ struct pa_engine {
     };
     std::vector<Timed> timed;
     uint64_t h2d = 0, d2h = 0;
-    // scratch for weighted averages (grown on demand)
     void *wa_buf = nullptr;
     size_t wa_bytes = 0;
+    std::vector<void *> allocs;
 };
 
 namespace {
@@ -81,10 +170,16 @@ pa_status cuda_fail(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? PA_ERR_OOM : PA_ERR_CUDA;
 }
 
-#define PA_CUDA(call)                                             \
-    do {                                                          \
-        cudaError_t _e = (call);                                  \
-        if (_e != cudaSuccess) return cuda_fail(_e, #call);       \
+#define PA_CUDA(call)                                       \
+    do {                                                    \
+        cudaError_t _e = (call);                            \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+    } while (0)
+
+#define PA_TRY(expr)                \
+    do {                            \
+        pa_status _s = (expr);      \
+        if (_s != PA_OK) return _s; \
     } while (0)
 
 template <typename T>
@@ -103,24 +198,43 @@ pa_status dalloc(pa_engine *e, T **p, size_t count)
     return PA_OK;
 }
 
-uint32_t default_cap(const pa_run_desc &d)
+uint32_t cap_of(const pa_run_desc &d)
 {
     if (d.R_cap) return d.R_cap;
     if (d.resample == PA_MULTINOMIAL) return d.R;
     return d.R + 8u * (uint32_t)std::ceil(std::sqrt((double)d.R)) + 64u;
 }
 
+uint32_t plane_words(uint32_t L) { return (L * L + 63) / 64; }
+uint32_t stride_words(uint32_t L) { return (2 * plane_words(L) + 3) / 4 * 4; }
+
+Ranges sizes_of(const pa_run_desc &d)
+{
+    const uint32_t N = d.L * d.L, cap = cap_of(d);
+    Ranges z;
+    z.rep = cap;
+    z.spin = (uint64_t)cap * stride_words(d.L);
+    z.rec = d.n_beta;
+    z.qh = d.overlap ? (uint64_t)d.n_beta * (N + 1) : 0;
+    z.scr = scratch_words(N, cap);
+    z.J = 2ull * stride_words(d.L) + 8ull * plane_words(d.L);
+    z.beta = d.n_beta;
+    z.thr = 2ull * d.n_beta;
+    z.wto = d.n_beta;
+    return z;
+}
+
+// Validate runs[0..n) as one admission (pair indices relative to the batch).
 pa_status validate(const pa_run_desc *runs, uint32_t n)
 {
     if (!runs || n == 0) return PA_ERR_INVALID_ARG;
     for (uint32_t r = 0; r < n; ++r) {
         const pa_run_desc &d = runs[r];
         if (d.L < 4 || d.L > 256 || (d.L & 1u)) return PA_ERR_INVALID_ARG;
-        if (d.model > PA_EA_PMJ || d.resample > PA_MULTINOMIAL || d.overlap > 3u || d.reserved) return PA_ERR_INVALID_ARG;
+        if (d.model > PA_EA_PMJ || d.resample > PA_MULTINOMIAL || d.overlap > 3u || d.reserved)
+            return PA_ERR_INVALID_ARG;
         if (d.R < 1 || d.n_beta < 1 || !d.beta || d.theta > (1u << 22)) return PA_ERR_INVALID_ARG;
-        const uint32_t cap = default_cap(d);
-        if (cap < d.R) return PA_ERR_INVALID_ARG;
-        if (d.resample == PA_MULTINOMIAL && cap < d.R) return PA_ERR_INVALID_ARG;
+        if (cap_of(d) < d.R) return PA_ERR_INVALID_ARG;
         for (uint32_t i = 1; i < d.n_beta; ++i)
             if (!(d.beta[i] >= d.beta[i - 1])) return PA_ERR_INVALID_ARG;
         if (!std::isfinite(d.beta[0]) || !std::isfinite(d.beta[d.n_beta - 1])) return PA_ERR_INVALID_ARG;
@@ -142,11 +256,306 @@ unsigned long long threshold(double beta, int m)
     return (unsigned long long)(p * 4294967296.0);
 }
 
-std::string key_of(const double *b, uint32_t n, uint32_t N)
+pa_status alloc_pools(pa_engine *e, const pa_server_config &c)
 {
-    std::string k(reinterpret_cast<const char *>(&N), sizeof N);
-    k.append(reinterpret_cast<const char *>(b), sizeof(double) * n);
-    return k;
+    e->S = c.max_runs;
+    e->rd.assign(e->S, RunDev{});
+    e->rh.assign(e->S, RunHost{});
+    PA_TRY(dalloc(e, &e->d_runs, e->S));
+    PA_TRY(dalloc(e, &e->P.st, e->S));
+    for (int b = 0; b < 2; ++b) {
+        PA_TRY(dalloc(e, &e->P.spins[b], c.spin_words));
+        PA_TRY(dalloc(e, &e->P.E[b], c.replica_capacity));
+        PA_TRY(dalloc(e, &e->P.M[b], c.replica_capacity));
+        PA_TRY(dalloc(e, &e->P.fam[b], c.replica_capacity));
+        PA_CUDA(cudaMemsetAsync(e->P.spins[b], 0, sizeof(uint32_t) * std::max<uint64_t>(c.spin_words, 1), e->stream));
+    }
+    PA_TRY(dalloc(e, &e->P.parent, c.replica_capacity));
+    PA_TRY(dalloc(e, &e->P.cnt, c.replica_capacity));
+    PA_TRY(dalloc(e, &e->P.rec, c.record_capacity));
+    PA_TRY(dalloc(e, &e->P.qh, c.qhist_words));
+    PA_TRY(dalloc(e, &e->P.qhp, c.qhist_words));
+    PA_TRY(dalloc(e, &e->P.J, c.coupling_words));
+    PA_TRY(dalloc(e, &e->P.scratch, c.scratch_words));
+    PA_TRY(dalloc(e, &e->P.status, 1));
+    PA_TRY(dalloc(e, &e->d_beta, c.record_capacity));
+    PA_TRY(dalloc(e, &e->d_thr, 2 * c.record_capacity));
+    PA_TRY(dalloc(e, &e->d_wtoff, c.record_capacity));
+    PA_TRY(dalloc(e, &e->d_wt, c.table_doubles));
+    e->meta_cap = 9ull * e->S + 3ull * 128 + 1024;
+    PA_TRY(dalloc(e, &e->d_meta, e->meta_cap));
+    PA_CUDA(cudaMemsetAsync(e->P.status, 0, sizeof(uint32_t), e->stream));
+    e->P.runs = e->d_runs;
+    e->P.beta = e->d_beta;
+    e->P.wt = e->d_wt;
+    e->P.wtoff = e->d_wtoff;
+    e->P.thr = e->d_thr;
+    e->fl_rep.init(c.replica_capacity);
+    e->fl_spin.init(c.spin_words);
+    e->fl_rec.init(c.record_capacity);
+    e->fl_qh.init(c.qhist_words);
+    e->fl_scr.init(c.scratch_words);
+    e->fl_J.init(c.coupling_words);
+    e->fl_beta.init(c.record_capacity);
+    e->fl_thr.init(2 * c.record_capacity);
+    e->fl_wto.init(c.record_capacity);
+    e->wt_cap = c.table_doubles;
+    return PA_OK;
+}
+
+// Weight table exp(-4 n dbeta), n = 0..N, from the cache or built now.
+pa_status weight_table(pa_engine *e, uint32_t N, double dbeta, uint64_t &off)
+{
+    uint64_t bits;
+    std::memcpy(&bits, &dbeta, sizeof bits);
+    auto key = std::make_pair(N, bits);
+    auto it = e->wt_cache.find(key);
+    if (it != e->wt_cache.end()) {
+        off = it->second;
+        return PA_OK;
+    }
+    if (e->wt_used + N + 1 > e->wt_cap) return PA_ERR_BUSY;
+    std::vector<double> t(N + 1);
+    for (uint32_t n = 0; n <= N; ++n) t[n] = std::exp(-(double)(4 * n) * dbeta);
+    PA_CUDA(cudaMemcpyAsync(e->d_wt + e->wt_used, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice,
+                            e->stream));
+    PA_CUDA(cudaStreamSynchronize(e->stream));  // t must outlive the copy
+    e->h2d += sizeof(double) * t.size();
+    off = e->wt_used;
+    e->wt_used += N + 1;
+    e->wt_cache.emplace(key, off);
+    return PA_OK;
+}
+
+// Reserve every pool range of one run (all or nothing).
+bool reserve(pa_engine *e, const pa_run_desc &d, Ranges &g)
+{
+    const Ranges z = sizes_of(d);
+    FreeList *fl[9] = {&e->fl_rep, &e->fl_spin, &e->fl_rec, &e->fl_qh, &e->fl_scr,
+                       &e->fl_J, &e->fl_beta, &e->fl_thr, &e->fl_wto};
+    const uint64_t n[9] = {z.rep, z.spin, z.rec, z.qh, z.scr, z.J, z.beta, z.thr, z.wto};
+    uint64_t *o[9] = {&g.rep, &g.spin, &g.rec, &g.qh, &g.scr, &g.J, &g.beta, &g.thr, &g.wto};
+    for (int k = 0; k < 9; ++k)
+        if (!fl[k]->alloc(n[k], *o[k])) {
+            for (int q = 0; q < k; ++q) fl[q]->release(*o[q], n[q]);
+            return false;
+        }
+    return true;
+}
+
+void unreserve(pa_engine *e, const pa_run_desc &d, const Ranges &g)
+{
+    const Ranges z = sizes_of(d);
+    e->fl_rep.release(g.rep, z.rep);
+    e->fl_spin.release(g.spin, z.spin);
+    e->fl_rec.release(g.rec, z.rec);
+    e->fl_qh.release(g.qh, z.qh);
+    e->fl_scr.release(g.scr, z.scr);
+    e->fl_J.release(g.J, z.J);
+    e->fl_beta.release(g.beta, z.beta);
+    e->fl_thr.release(g.thr, z.thr);
+    e->fl_wto.release(g.wto, z.wto);
+}
+
+// Admit runs[0..n): reserve slots and ranges and table references (all or
+// nothing), upload the descriptors and tables; the beta_0 draw is enqueued
+// with the next work.
+pa_status admit(pa_engine *e, const pa_run_desc *runs, uint32_t n, uint32_t *slots)
+{
+    PA_TRY(validate(runs, n));
+    std::vector<uint32_t> got;
+    for (uint32_t s = 0; s < e->S && got.size() < n; ++s)
+        if (!e->rh[s].used) got.push_back(s);
+    if (got.size() < n) return PA_ERR_BUSY;
+    std::vector<Ranges> gs(n);
+    std::vector<std::vector<unsigned long long>> wtos(n);
+    uint32_t k = 0;
+    pa_status st = PA_OK;
+    for (; k < n; ++k) {
+        if (!reserve(e, runs[k], gs[k])) {
+            st = PA_ERR_BUSY;
+            break;
+        }
+        const pa_run_desc &d = runs[k];
+        wtos[k].assign(d.n_beta, 0ull);
+        for (uint32_t i = 1; i < d.n_beta && st == PA_OK; ++i) {
+            uint64_t off = 0;
+            st = weight_table(e, d.L * d.L, d.beta[i] - d.beta[i - 1], off);
+            wtos[k][i] = off;
+        }
+        if (st != PA_OK) {
+            unreserve(e, runs[k], gs[k]);
+            break;
+        }
+    }
+    if (st != PA_OK) {  // roll back the runs reserved so far (cached tables stay)
+        for (uint32_t q = 0; q < k; ++q) unreserve(e, runs[q], gs[q]);
+        return st;
+    }
+    for (uint32_t r = 0; r < n; ++r) {
+        const pa_run_desc &d = runs[r];
+        const uint32_t N = d.L * d.L, s = got[r];
+        const Ranges &g = gs[r];
+        std::vector<unsigned long long> thr(2 * d.n_beta);
+        for (uint32_t i = 0; i < d.n_beta; ++i) {
+            thr[2 * i] = threshold(d.beta[i], 1);
+            thr[2 * i + 1] = threshold(d.beta[i], 2);
+        }
+        RunDev x;
+        std::memset(&x, 0, sizeof x);
+        x.L = d.L;
+        x.N = N;
+        x.Lh = d.L / 2;
+        x.wstride = stride_words(d.L);
+        x.model = d.model;
+        x.R = d.R;
+        x.R_cap = cap_of(d);
+        x.theta = d.theta;
+        x.n_beta = d.n_beta;
+        x.seed = d.seed;
+        x.run_id = d.run_id;
+        x.disorder_id = d.disorder_id;
+        x.resample = d.resample;
+        x.overlap = d.overlap;
+        x.paired = (d.overlap & PA_Q_PAIR) ? (int32_t)got[d.paired] : -1;
+        x.rep_off = g.rep;
+        x.spin_off = g.spin;
+        x.rec_off = g.rec;
+        x.qh_off = g.qh;
+        x.beta_off = g.beta;
+        x.wt_off = g.wto;
+        x.thr_off = g.thr;
+        x.J_off = g.J;
+        x.scr_off = g.scr;
+        x.ln2N = (double)N * std::log(2.0);
+        e->rd[s] = x;
+        RunState rs;
+        rs.step = 0;
+        rs.R_cur = d.R;
+        rs.R_new = d.R;
+        rs.status = 0;
+        rs.lnQ = 0.0;
+        const uint64_t nq = sizes_of(d).qh;
+        cudaError_t err = cudaMemcpyAsync(e->d_runs + s, &e->rd[s], sizeof(RunDev), cudaMemcpyHostToDevice, e->stream);
+        if (!err) err = cudaMemcpyAsync(e->P.st + s, &rs, sizeof rs, cudaMemcpyHostToDevice, e->stream);
+        if (!err)
+            err = cudaMemcpyAsync(e->d_beta + g.beta, d.beta, sizeof(double) * d.n_beta, cudaMemcpyHostToDevice,
+                                  e->stream);
+        if (!err)
+            err = cudaMemcpyAsync(e->d_thr + g.thr, thr.data(), sizeof(unsigned long long) * thr.size(),
+                                  cudaMemcpyHostToDevice, e->stream);
+        if (!err)
+            err = cudaMemcpyAsync(e->d_wtoff + g.wto, wtos[r].data(), sizeof(unsigned long long) * d.n_beta,
+                                  cudaMemcpyHostToDevice, e->stream);
+        if (!err) err = cudaMemsetAsync(e->P.rec + g.rec, 0, sizeof(pa_step_record) * d.n_beta, e->stream);
+        if (!err && nq) err = cudaMemsetAsync(e->P.qh + g.qh, 0, sizeof(uint32_t) * nq, e->stream);
+        if (!err && nq) err = cudaMemsetAsync(e->P.qhp + g.qh, 0, sizeof(uint32_t) * nq, e->stream);
+        if (!err) err = cudaStreamSynchronize(e->stream);  // host buffers must outlive the copies
+        if (err) return cuda_fail(err, "admit upload");
+        e->h2d += sizeof(RunDev) + sizeof rs + sizeof(double) * d.n_beta +
+                  sizeof(unsigned long long) * (thr.size() + d.n_beta);
+        RunHost &h = e->rh[s];
+        h.used = true;
+        h.d = d;
+        h.d.beta = nullptr;  // not kept: the caller owns it
+        h.g = g;
+        h.steps_done = 0;
+        e->active.push_back(s);
+        e->pending.push_back(s);
+        if (slots) slots[r] = s;
+        e->max_pw = std::max(e->max_pw, plane_words(d.L));
+    }
+    e->dirty = true;
+    return PA_OK;
+}
+
+// Rebuild the device lists (resident runs, overlap runs, per-size work lists,
+// the pending-draw list) after the resident set changed.
+pa_status rebuild(pa_engine *e)
+{
+    PA_CUDA(cudaStreamSynchronize(e->stream));  // nothing in flight reads d_meta
+    std::vector<uint32_t> &m = e->h_meta;
+    m.clear();
+    e->active_off = m.size();
+    m.insert(m.end(), e->active.begin(), e->active.end());
+    e->q_runs.clear();
+    e->max_Rcap_active = 0;
+    for (uint32_t s : e->active) {
+        if (e->rd[s].overlap) e->q_runs.push_back(s);
+        e->max_Rcap_active = std::max(e->max_Rcap_active, e->rd[s].R_cap);
+    }
+    e->q_off = m.size();
+    m.insert(m.end(), e->q_runs.begin(), e->q_runs.end());
+    e->groups.clear();
+    std::map<uint32_t, size_t> gi;  // lattice size -> group, in order of first appearance
+    for (uint32_t s : e->active) {
+        const uint32_t L = e->rd[s].L;
+        auto it = gi.find(L);
+        if (it == gi.end()) {
+            it = gi.emplace(L, e->groups.size()).first;
+            SweepGroup g;
+            g.L = L;
+            e->groups.push_back(g);
+            if (!e->tuning.count(L)) {
+                Tuning t;
+                t.candidates = sweep_candidates(L, (e->flags & PA_CREATE_GENERIC_SWEEP) ? 0 : 1);
+                t.tuned = t.candidates.size() < 2 || (e->flags & PA_CREATE_NO_AUTOTUNE);
+                e->tuning[L] = t;
+            }
+        }
+        SweepGroup &g = e->groups[it->second];
+        g.runs.push_back(s);
+        if (e->rd[s].model == PA_EA_PMJ) g.any_glass = 1;
+    }
+    for (auto &g : e->groups) {
+        const Tuning &t = e->tuning[g.L];
+        g.runs_off = m.size();
+        m.insert(m.end(), g.runs.begin(), g.runs.end());
+        for (const SweepCfg &c : t.candidates) {
+            g.tile_map_off.push_back(m.size());
+            uint64_t acc = 0;
+            m.push_back(0u);
+            for (uint32_t s : g.runs) {
+                acc += (e->rd[s].R_cap + c.RPC - 1) / c.RPC;
+                if (acc > 0x7fffffffull) return PA_ERR_INVALID_ARG;  // beyond one launch's grid
+                m.push_back((uint32_t)acc);
+            }
+            g.n_tiles.push_back((uint32_t)acc);
+        }
+    }
+    e->init_runs_off = m.size();
+    m.insert(m.end(), e->pending.begin(), e->pending.end());
+    e->init_tiles_off = m.size();
+    uint64_t acc = 0;
+    m.push_back(0u);
+    for (uint32_t s : e->pending) {  // 4 replicas per CTA
+        acc += (e->rd[s].R + 3) / 4;
+        if (acc > 0x7fffffffull) return PA_ERR_INVALID_ARG;
+        m.push_back((uint32_t)acc);
+    }
+    e->init_n = (uint32_t)e->pending.size();
+    e->init_tiles = (uint32_t)acc;
+    e->init_q_off = m.size();  // pending runs with overlaps: their step-0 overlaps only
+    e->init_q_n = 0;
+    for (uint32_t s : e->pending)
+        if (e->rd[s].overlap) {
+            m.push_back(s);
+            ++e->init_q_n;
+        }
+    if (m.size() > e->meta_cap) return PA_ERR_INVALID_ARG;
+    PA_CUDA(cudaMemcpyAsync(e->d_meta, m.data(), sizeof(uint32_t) * m.size(), cudaMemcpyHostToDevice, e->stream));
+    PA_CUDA(cudaStreamSynchronize(e->stream));
+    e->h2d += sizeof(uint32_t) * m.size();
+    e->dirty = false;
+    if (e->graph_exec) {
+        cudaGraphExecDestroy(e->graph_exec);
+        e->graph_exec = nullptr;
+    }
+    if (e->graph) {
+        cudaGraphDestroy(e->graph);
+        e->graph = nullptr;
+    }
+    return PA_OK;
 }
 
 cudaEvent_t take_event(pa_engine *e)
@@ -165,6 +574,7 @@ cudaEvent_t take_event(pa_engine *e)
 template <typename F>
 void timed_launch(pa_engine *e, int kind, F &&launch)
 {
+    e->launches += 1;
     if (!e->profiling) {
         launch();
         return;
@@ -176,123 +586,114 @@ void timed_launch(pa_engine *e, int kind, F &&launch)
     e->timed.push_back(t);
 }
 
-pa_status upload_tile_maps(pa_engine *e, SweepGroup &g)
+const uint32_t *meta(pa_engine *e, uint64_t off) { return e->d_meta + off; }
+
+void launch_group_sweep(pa_engine *e, const SweepGroup &g, uint32_t c)
 {
-    std::vector<uint32_t> h(g.runs);
-    g.n_tiles.clear();
-    for (const SweepCfg &c : g.candidates) {
-        uint64_t acc = 0;
-        h.push_back(0u);
-        for (uint32_t r : g.runs) {
-            acc += (e->rd[r].R_cap + c.RPC - 1) / c.RPC;
-            if (acc > 0x7fffffffull) return PA_ERR_INVALID_ARG;  // beyond one launch's grid
-            h.push_back((uint32_t)acc);
-        }
-        g.n_tiles.push_back((uint32_t)acc);
-    }
-    cudaError_t err = cudaMemcpy(g.d_runs, h.data(), sizeof(uint32_t) * h.size(), cudaMemcpyHostToDevice);
-    if (err != cudaSuccess) return cuda_fail(err, "tile maps");
-    e->h2d += sizeof(uint32_t) * h.size();
-    return PA_OK;
+    const Tuning &t = e->tuning[g.L];
+    launch_sweep(e->P, meta(e, g.runs_off), meta(e, g.tile_map_off[c]), (uint32_t)g.runs.size(), g.n_tiles[c],
+                 t.candidates[c], g.any_glass, e->stream);
 }
 
-// One eager anneal step that times every candidate sweep shape of the groups
-// not tuned yet on the real data and keeps the fastest.  Each candidate reads
-// the same parents and writes the same children, so running several is
-// harmless; the last launch leaves the children in place.
-pa_status enqueue_tuning_tick(pa_engine *e)
+// beta_0 draws of the pending runs (Sec. II.B step (i)) and their step-0 measurement.
+pa_status enqueue_pending(pa_engine *e)
 {
-    launch_resample(e->P, e->n_runs, e->stream);
-    e->launches += 1;
-    for (auto &g : e->groups) {
-        if (g.tuned) {
-            launch_sweep(e->P, g.d_runs, g.tile_map(g.pick), (uint32_t)g.runs.size(), g.n_tiles[g.pick], g.cfg,
-                         g.any_glass, e->stream);
-            e->launches += 1;
-            continue;
-        }
-        std::vector<cudaEvent_t> ev(2 * g.candidates.size());
-        for (auto &x : ev) PA_CUDA(cudaEventCreate(&x));
-        for (uint32_t c = 0; c < g.candidates.size(); ++c) {
-            PA_CUDA(cudaEventRecord(ev[2 * c], e->stream));
-            launch_sweep(e->P, g.d_runs, g.tile_map(c), (uint32_t)g.runs.size(), g.n_tiles[c], g.candidates[c],
-                         g.any_glass, e->stream);
-            PA_CUDA(cudaEventRecord(ev[2 * c + 1], e->stream));
-            e->launches += 1;
-        }
-        PA_CUDA(cudaStreamSynchronize(e->stream));
-        PA_CUDA(cudaGetLastError());
-        float best = 0.f;
-        for (uint32_t c = 0; c < g.candidates.size(); ++c) {
-            float ms = 0.f;
-            PA_CUDA(cudaEventElapsedTime(&ms, ev[2 * c], ev[2 * c + 1]));
-            if (c == 0 || ms < best) {
-                best = ms;
-                g.pick = c;
-            }
-        }
-        for (auto &x : ev) cudaEventDestroy(x);
-        g.cfg = g.candidates[g.pick];
-        g.tuned = true;
-        g.tuned_ms = best;
-    }
-    if (!e->q_runs.empty()) {
-        launch_overlap(e->P, e->d_q_runs, (uint32_t)e->q_runs.size(), e->max_Rcap, 0, e->stream);
-        e->launches += 1;
-    }
-    launch_measure(e->P, e->n_runs, 0, e->stream);
-    e->launches += 1;
+    if (e->pending.empty()) return PA_OK;
+    const uint32_t *runs = meta(e, e->init_runs_off);
+    timed_launch(e, PA_K_INIT, [&] { launch_init_couplings(e->P, runs, e->init_n, e->stream); });
+    timed_launch(e, PA_K_INIT, [&] {
+        launch_init_population(e->P, meta(e, e->init_tiles_off), runs, e->init_n, e->init_tiles, e->max_pw,
+                               e->stream);
+    });
+    if (e->init_q_n)  // step-0 overlaps of the pending runs (pairs are admitted together)
+        timed_launch(e, PA_K_OVERLAP, [&] {
+            launch_overlap(e->P, meta(e, e->init_q_off), e->init_q_n, e->max_Rcap_active, 1, e->stream);
+        });
+    timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, runs, e->init_n, 1, e->stream); });
+    e->pending.clear();
+    e->dirty = true;  // the pending list is consumed
     PA_CUDA(cudaGetLastError());
     return PA_OK;
 }
 
 void enqueue_tick(pa_engine *e)
 {
-    timed_launch(e, PA_K_RESAMPLE, [&] { launch_resample(e->P, e->n_runs, e->stream); });
-    for (auto &g : e->groups)
-        timed_launch(e, PA_K_SWEEP, [&] {
-            launch_sweep(e->P, g.d_runs, g.tile_map(g.pick), (uint32_t)g.runs.size(), g.n_tiles[g.pick], g.cfg,
-                         g.any_glass, e->stream);
-        });
+    const uint32_t *act = meta(e, e->active_off);
+    const uint32_t na = (uint32_t)e->active.size();
+    timed_launch(e, PA_K_RESAMPLE, [&] { launch_resample(e->P, act, na, e->stream); });
+    for (auto &g : e->groups) timed_launch(e, PA_K_SWEEP, [&] { launch_group_sweep(e, g, e->tuning[g.L].pick); });
     if (!e->q_runs.empty())
         timed_launch(e, PA_K_OVERLAP, [&] {
-            launch_overlap(e->P, e->d_q_runs, (uint32_t)e->q_runs.size(), e->max_Rcap, 0, e->stream);
+            launch_overlap(e->P, meta(e, e->q_off), (uint32_t)e->q_runs.size(), e->max_Rcap_active, 0, e->stream);
         });
-    timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, e->n_runs, 0, e->stream); });
+    timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, act, na, 0, e->stream); });
 }
 
-// beta_0: couplings, uniform populations, step-0 measurement (Sec. II.B step (i)).
-pa_status enqueue_init(pa_engine *e)
+// One eager step that first times every candidate sweep shape of the lattice
+// sizes not tuned yet on the real data and keeps the fastest.  Each candidate
+// reads the same parents and writes the same children, so running several is
+// harmless; the last launch leaves the children in place.
+pa_status enqueue_tuning_tick(pa_engine *e)
 {
-    std::vector<RunState> h_st(e->n_runs);
-    for (uint32_t r = 0; r < e->n_runs; ++r) {
-        h_st[r].step = 0;
-        h_st[r].R_cur = e->rd[r].R;
-        h_st[r].R_new = e->rd[r].R;
-        h_st[r].status = 0;
-        h_st[r].lnQ = 0.0;
+    const uint32_t *act = meta(e, e->active_off);
+    const uint32_t na = (uint32_t)e->active.size();
+    timed_launch(e, PA_K_RESAMPLE, [&] { launch_resample(e->P, act, na, e->stream); });
+    for (auto &g : e->groups) {
+        Tuning &t = e->tuning[g.L];
+        if (t.tuned) {
+            timed_launch(e, PA_K_SWEEP, [&] { launch_group_sweep(e, g, t.pick); });
+            continue;
+        }
+        std::vector<cudaEvent_t> ev(2 * t.candidates.size());
+        for (auto &x : ev) PA_CUDA(cudaEventCreate(&x));
+        for (uint32_t c = 0; c < t.candidates.size(); ++c) {
+            PA_CUDA(cudaEventRecord(ev[2 * c], e->stream));
+            launch_group_sweep(e, g, c);
+            PA_CUDA(cudaEventRecord(ev[2 * c + 1], e->stream));
+            e->launches += 1;
+        }
+        PA_CUDA(cudaStreamSynchronize(e->stream));
+        PA_CUDA(cudaGetLastError());
+        float best = 0.f;
+        for (uint32_t c = 0; c < t.candidates.size(); ++c) {
+            float ms = 0.f;
+            PA_CUDA(cudaEventElapsedTime(&ms, ev[2 * c], ev[2 * c + 1]));
+            if (c == 0 || ms < best) {
+                best = ms;
+                t.pick = c;
+            }
+        }
+        for (auto &x : ev) cudaEventDestroy(x);
+        t.tuned = true;
+        t.ms = best;
     }
-    cudaError_t err = cudaMemcpyAsync(e->P.st, h_st.data(), sizeof(RunState) * e->n_runs, cudaMemcpyHostToDevice,
-                                      e->stream);
-    if (!err) err = cudaMemsetAsync(e->P.rec, 0, sizeof(pa_step_record) * (e->rec_count ? e->rec_count : 1), e->stream);
-    if (!err) err = cudaMemsetAsync(e->P.qh, 0, sizeof(uint32_t) * (e->qh_count ? e->qh_count : 1), e->stream);
-    if (!err) err = cudaMemsetAsync(e->P.qhp, 0, sizeof(uint32_t) * (e->qh_count ? e->qh_count : 1), e->stream);
-    if (!err) err = cudaMemsetAsync(e->P.status, 0, sizeof(uint32_t), e->stream);
-    if (!err) err = cudaStreamSynchronize(e->stream);  // h_st must outlive the copy
-    if (err) return cuda_fail(err, "reset state");
-    e->h2d += sizeof(RunState) * e->n_runs;
-    timed_launch(e, PA_K_INIT, [&] { launch_init_couplings(e->P, e->n_runs, e->stream); });
-    timed_launch(e, PA_K_INIT,
-                 [&] { launch_init_population(e->P, e->d_init_tiles, e->n_runs, e->init_tiles, e->max_pw, e->stream); });
     if (!e->q_runs.empty())
         timed_launch(e, PA_K_OVERLAP, [&] {
-            launch_overlap(e->P, e->d_q_runs, (uint32_t)e->q_runs.size(), e->max_Rcap, 1, e->stream);
+            launch_overlap(e->P, meta(e, e->q_off), (uint32_t)e->q_runs.size(), e->max_Rcap_active, 0, e->stream);
         });
-    timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, e->n_runs, 1, e->stream); });
-    e->launches += 3 + (e->q_runs.empty() ? 0 : 1);
-    e->latched = PA_OK;
-    err = cudaGetLastError();
-    return err ? cuda_fail(err, "init launch") : PA_OK;
+    timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, act, na, 0, e->stream); });
+    PA_CUDA(cudaGetLastError());
+    return PA_OK;
+}
+
+// Bring the device lists up to date and draw pending populations.
+pa_status prepare(pa_engine *e)
+{
+    if (e->dirty) PA_TRY(rebuild(e));
+    if (!e->pending.empty()) {
+        PA_TRY(enqueue_pending(e));
+        PA_TRY(rebuild(e));  // drop the consumed pending list
+    }
+    return PA_OK;
+}
+
+void advance_host_steps(pa_engine *e, uint32_t n)
+{
+    for (uint32_t s : e->active) {
+        RunHost &h = e->rh[s];
+        const uint32_t last = h.d.n_beta - 1;
+        h.steps_done = std::min<uint32_t>(last, h.steps_done + n);
+    }
 }
 
 // Synchronise for a read: CUDA errors only (a run that stopped is readable).
@@ -317,6 +718,29 @@ pa_status latch_device_status(pa_engine *e)
     }
     return e->latched;
 }
+
+pa_status engine_new(void *cuda_stream, uint32_t flags, pa_engine **out)
+{
+    if (flags & ~(uint32_t)(PA_CREATE_GENERIC_SWEEP | PA_CREATE_NO_AUTOTUNE)) return PA_ERR_INVALID_ARG;
+    PA_CUDA(prepare_kernels());
+    pa_engine *e = new (std::nothrow) pa_engine();
+    if (!e) return PA_ERR_OOM;
+    e->flags = flags;
+    if (cuda_stream) {
+        e->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        cudaError_t err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+        if (err != cudaSuccess) {
+            delete e;
+            return cuda_fail(err, "cudaStreamCreate");
+        }
+        e->own_stream = true;
+    }
+    *out = e;
+    return PA_OK;
+}
+
+bool slot_ok(const pa_engine *e, uint32_t s) { return e && s < e->S && e->rh[s].used; }
 
 }  // namespace
 
@@ -363,242 +787,182 @@ pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream,
 
 pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, uint32_t flags, pa_engine **out)
 {
-    if (!out || (flags & ~(uint32_t)(PA_CREATE_GENERIC_SWEEP | PA_CREATE_NO_AUTOTUNE))) return PA_ERR_INVALID_ARG;
+    if (!out) return PA_ERR_INVALID_ARG;
     *out = nullptr;
-    pa_status vs = validate(runs, n_runs);
-    if (vs != PA_OK) return vs;
-    PA_CUDA(prepare_kernels());
-
-    pa_engine *e = new (std::nothrow) pa_engine();
-    if (!e) return PA_ERR_OOM;
-    cudaGetDevice(&e->device);
-    if (cuda_stream) {
-        e->stream = static_cast<cudaStream_t>(cuda_stream);
-    } else {
-        cudaError_t err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
-        if (err != cudaSuccess) {
-            delete e;
-            return cuda_fail(err, "cudaStreamCreate");
-        }
-        e->own_stream = true;
-    }
-    e->n_runs = n_runs;
-    e->rd.resize(n_runs);
-
-    // ---- layout
-    uint64_t rep = 0, spinw = 0, rec = 0, qh = 0, J = 0, scr = 0;
-    std::map<std::string, uint64_t> beta_tab, wt_tab, thr_tab;
-    std::vector<double> h_beta, h_wt;
-    std::vector<unsigned long long> h_thr;
-    std::map<uint32_t, size_t> group_of_L;
+    PA_TRY(validate(runs, n_runs));
+    // pools sized exactly for these runs; tables for their distinct (N, dbeta)
+    pa_server_config c{};
+    c.max_runs = n_runs;
+    std::map<std::pair<uint32_t, uint64_t>, int> keys;
     for (uint32_t r = 0; r < n_runs; ++r) {
-        const pa_run_desc &d = runs[r];
-        RunDev &x = e->rd[r];
-        std::memset(&x, 0, sizeof x);
-        x.L = d.L;
-        x.N = d.L * d.L;
-        x.Lh = d.L / 2;
-        const uint32_t pw = (x.N + 63) / 64;  // words per colour plane
-        x.wstride = (2 * pw + 3) / 4 * 4;
-        e->max_pw = pw > e->max_pw ? pw : e->max_pw;
-        x.model = d.model;
-        x.R = d.R;
-        x.R_cap = default_cap(d);
-        x.theta = d.theta;
-        x.n_beta = d.n_beta;
-        x.seed = d.seed;
-        x.run_id = d.run_id;
-        x.disorder_id = d.disorder_id;
-        x.resample = d.resample;
-        x.overlap = d.overlap;
-        x.paired = (d.overlap & PA_Q_PAIR) ? d.paired : -1;
-        x.rep_off = rep;
-        rep += x.R_cap;
-        x.spin_off = spinw;
-        spinw += (uint64_t)x.R_cap * x.wstride;
-        x.rec_off = rec;
-        rec += d.n_beta;
-        x.qh_off = qh;
-        if (d.overlap) qh += (uint64_t)d.n_beta * (x.N + 1);
-        x.J_off = J;
-        J += 2ull * x.wstride + 8ull * pw;
-        x.scr_off = scr;
-        scr += scratch_words(x.N, x.R_cap);
-        x.ln2N = (double)x.N * std::log(2.0);
-        // schedule and tables, shared by runs with equal (N, schedule)
-        std::string kb = key_of(d.beta, d.n_beta, 0);
-        auto itb = beta_tab.find(kb);
-        if (itb == beta_tab.end()) {
-            itb = beta_tab.emplace(kb, h_beta.size()).first;
-            h_beta.insert(h_beta.end(), d.beta, d.beta + d.n_beta);
-            thr_tab[kb] = h_thr.size();
-            for (uint32_t i = 0; i < d.n_beta; ++i) {
-                h_thr.push_back(threshold(d.beta[i], 1));
-                h_thr.push_back(threshold(d.beta[i], 2));
-            }
+        const Ranges z = sizes_of(runs[r]);
+        c.replica_capacity += z.rep;
+        c.spin_words += z.spin;
+        c.record_capacity += z.rec;
+        c.qhist_words += z.qh;
+        c.scratch_words += z.scr;
+        c.coupling_words += z.J;
+        const uint32_t N = runs[r].L * runs[r].L;
+        for (uint32_t i = 1; i < runs[r].n_beta; ++i) {
+            const double db = runs[r].beta[i] - runs[r].beta[i - 1];
+            uint64_t bits;
+            std::memcpy(&bits, &db, sizeof bits);
+            if (keys.emplace(std::make_pair(N, bits), 0).second) c.table_doubles += N + 1;
         }
-        x.beta_off = itb->second;
-        x.thr_off = thr_tab[kb];
-        std::string kw = key_of(d.beta, d.n_beta, x.N);
-        auto itw = wt_tab.find(kw);
-        if (itw == wt_tab.end()) {
-            itw = wt_tab.emplace(kw, h_wt.size()).first;
-            const uint32_t n1 = x.N + 1;
-            size_t base = h_wt.size();
-            h_wt.resize(base + (size_t)d.n_beta * n1, 0.0);
-            for (uint32_t i = 1; i < d.n_beta; ++i) {
-                const double dbeta = d.beta[i] - d.beta[i - 1];
-                for (uint32_t n = 0; n < n1; ++n) h_wt[base + (size_t)i * n1 + n] = std::exp(-(double)(4 * n) * dbeta);
-            }
-        }
-        x.wt_off = itw->second;
-        e->max_Rcap = x.R_cap > e->max_Rcap ? x.R_cap : e->max_Rcap;
-        e->max_R = x.R > e->max_R ? x.R : e->max_R;
-        e->max_nbeta = d.n_beta > e->max_nbeta ? d.n_beta : e->max_nbeta;
-        auto g = group_of_L.find(d.L);
-        if (g == group_of_L.end()) {
-            g = group_of_L.emplace(d.L, e->groups.size()).first;
-            SweepGroup sg;
-            sg.L = d.L;
-            sg.candidates = sweep_candidates(d.L, (flags & PA_CREATE_GENERIC_SWEEP) ? 0 : 1);
-            sg.cfg = sg.candidates[0];
-            sg.tuned = sg.candidates.size() < 2 || (flags & PA_CREATE_NO_AUTOTUNE);
-            sg.max_Rcap = 0;
-            e->groups.push_back(sg);
-        }
-        SweepGroup &sg = e->groups[g->second];
-        sg.runs.push_back(r);
-        if (d.model == PA_EA_PMJ) sg.any_glass = 1;
-        sg.max_Rcap = x.R_cap > sg.max_Rcap ? x.R_cap : sg.max_Rcap;
-        if (d.overlap) e->q_runs.push_back(r);
     }
-
-    // ---- allocation
-    pa_status s = PA_OK;
-    RunDev *d_runs = nullptr;
-    unsigned long long *d_thr = nullptr;
-    double *d_beta = nullptr, *d_wt = nullptr;
-    uint32_t wmax = 0;
-    for (auto &x : e->rd) wmax = x.wstride > wmax ? x.wstride : wmax;
-    uint64_t spin_words = 0;
-    for (auto &x : e->rd) spin_words += (uint64_t)x.R_cap * x.wstride;
-#define TRY(expr)                      \
-    do {                               \
-        s = (expr);                    \
-        if (s != PA_OK) goto fail;     \
-    } while (0)
-    TRY(dalloc(e, &d_runs, n_runs));
-    TRY(dalloc(e, &e->P.st, n_runs));
-    for (int b = 0; b < 2; ++b) {
-        TRY(dalloc(e, &e->P.spins[b], spin_words));
-        TRY(dalloc(e, &e->P.E[b], rep));
-        TRY(dalloc(e, &e->P.M[b], rep));
-        TRY(dalloc(e, &e->P.fam[b], rep));
+    pa_engine *e = nullptr;
+    PA_TRY(engine_new(cuda_stream, flags, &e));
+    pa_status s = alloc_pools(e, c);
+    if (s == PA_OK) s = admit(e, runs, n_runs, nullptr);
+    if (s == PA_OK) s = prepare(e);
+    if (s != PA_OK) {
+        pa_destroy(e);
+        return s;
     }
-    TRY(dalloc(e, &e->P.parent, rep));
-    TRY(dalloc(e, &e->P.cnt, rep));
-    TRY(dalloc(e, &e->P.rec, rec));
-    TRY(dalloc(e, &e->P.qh, qh));
-    TRY(dalloc(e, &e->P.qhp, qh));
-    TRY(dalloc(e, &d_beta, h_beta.size()));
-    TRY(dalloc(e, &d_wt, h_wt.size()));
-    TRY(dalloc(e, &d_thr, h_thr.size()));
-    TRY(dalloc(e, &e->P.J, J));
-    TRY(dalloc(e, &e->P.scratch, scr));
-    TRY(dalloc(e, &e->P.status, 1));
-    e->P.runs = d_runs;
-    e->P.beta = d_beta;
-    e->P.wt = d_wt;
-    e->P.thr = d_thr;
-    for (auto &g : e->groups) {
-        // run indices, then one tile map per candidate shape (each n + 1 entries)
-        TRY(dalloc(e, &g.d_runs, g.runs.size() * (1 + g.candidates.size()) + g.candidates.size()));
-        TRY(upload_tile_maps(e, g));
-    }
-    {
-        std::vector<uint32_t> h(1, 0u);
-        for (uint32_t r = 0; r < n_runs; ++r) {
-            const uint64_t next = (uint64_t)h.back() + (e->rd[r].R + 3) / 4;
-            if (next > 0x7fffffffull) TRY(PA_ERR_INVALID_ARG);
-            h.push_back((uint32_t)next);
-        }
-        e->init_tiles = h.back();
-        TRY(dalloc(e, &e->d_init_tiles, h.size()));
-        if (cudaMemcpy(e->d_init_tiles, h.data(), sizeof(uint32_t) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-            TRY(PA_ERR_CUDA);
-        e->h2d += sizeof(uint32_t) * h.size();
-    }
-    if (!e->q_runs.empty()) {
-        TRY(dalloc(e, &e->d_q_runs, e->q_runs.size()));
-        if (cudaMemcpyAsync(e->d_q_runs, e->q_runs.data(), sizeof(uint32_t) * e->q_runs.size(),
-                            cudaMemcpyHostToDevice, e->stream) != cudaSuccess)
-            TRY(PA_ERR_CUDA);
-    }
-    {
-        cudaError_t err = cudaSuccess;
-        err = err ? err : cudaMemcpyAsync(d_runs, e->rd.data(), sizeof(RunDev) * n_runs, cudaMemcpyHostToDevice, e->stream);
-        err = err ? err : cudaMemcpyAsync(d_beta, h_beta.data(), sizeof(double) * h_beta.size(), cudaMemcpyHostToDevice, e->stream);
-        err = err ? err : cudaMemcpyAsync(d_wt, h_wt.data(), sizeof(double) * h_wt.size(), cudaMemcpyHostToDevice, e->stream);
-        err = err ? err : cudaMemcpyAsync(d_thr, h_thr.data(), sizeof(unsigned long long) * h_thr.size(), cudaMemcpyHostToDevice, e->stream);
-        for (int b = 0; b < 2 && err == cudaSuccess; ++b)
-            err = cudaMemsetAsync(e->P.spins[b], 0, sizeof(uint32_t) * (spin_words ? spin_words : 1), e->stream);
-        if (err != cudaSuccess) TRY(cuda_fail(err, "upload"));
-        e->h2d += sizeof(RunDev) * n_runs + sizeof(double) * (h_beta.size() + h_wt.size()) +
-                  sizeof(unsigned long long) * h_thr.size();
-        // host tables must outlive the asynchronous copies
-        err = cudaStreamSynchronize(e->stream);
-        if (err != cudaSuccess) TRY(cuda_fail(err, "upload sync"));
-    }
-    e->rec_count = rec;
-    e->qh_count = qh;
-    e->launches_per_tick = 2 + e->groups.size() + (e->q_runs.empty() ? 0 : 1);
-    TRY(enqueue_init(e));
     *out = e;
     return PA_OK;
-fail:
-#undef TRY
-    pa_destroy(e);
-    return s;
+}
+
+pa_status pa_server_create(const pa_server_config *cfg, void *cuda_stream, uint32_t flags, pa_engine **out)
+{
+    if (!out || !cfg || cfg->max_runs == 0 || cfg->max_runs > (1u << 20)) return PA_ERR_INVALID_ARG;
+    *out = nullptr;
+    pa_engine *e = nullptr;
+    PA_TRY(engine_new(cuda_stream, flags, &e));
+    e->server = true;
+    pa_status s = alloc_pools(e, *cfg);
+    if (s != PA_OK) {
+        pa_destroy(e);
+        return s;
+    }
+    *out = e;
+    return PA_OK;
+}
+
+pa_status pa_admit(pa_engine *e, const pa_run_desc *runs, uint32_t n_runs, uint32_t *slots_out)
+{
+    if (!e || !slots_out) return PA_ERR_INVALID_ARG;
+    if (e->latched != PA_OK) return e->latched;
+    return admit(e, runs, n_runs, slots_out);
+}
+
+pa_status pa_retire(pa_engine *e, uint32_t slot)
+{
+    if (!slot_ok(e, slot)) return PA_ERR_INVALID_ARG;
+    PA_CUDA(cudaStreamSynchronize(e->stream));  // no queued work may still use its ranges
+    const int32_t partner = e->rd[slot].paired;
+    if (partner >= 0 && slot_ok(e, (uint32_t)partner) && e->rd[(uint32_t)partner].paired == (int32_t)slot) {
+        // the partner keeps running without two-population overlaps
+        RunDev &p = e->rd[(uint32_t)partner];
+        p.paired = -1;
+        p.overlap &= ~(uint32_t)PA_Q_PAIR;
+        PA_CUDA(cudaMemcpyAsync(e->d_runs + partner, &p, sizeof(RunDev), cudaMemcpyHostToDevice, e->stream));
+        PA_CUDA(cudaStreamSynchronize(e->stream));
+    }
+    unreserve(e, e->rh[slot].d, e->rh[slot].g);
+    e->rh[slot] = RunHost{};
+    e->active.erase(std::remove(e->active.begin(), e->active.end(), slot), e->active.end());
+    e->pending.erase(std::remove(e->pending.begin(), e->pending.end(), slot), e->pending.end());
+    e->dirty = true;
+    return PA_OK;
+}
+
+pa_status pa_run_state(pa_engine *e, uint32_t slot, uint32_t *step, uint32_t *R, uint32_t *status)
+{
+    if (!slot_ok(e, slot)) return PA_ERR_INVALID_ARG;
+    PA_TRY(prepare(e));
+    RunState st;
+    PA_CUDA(cudaMemcpyAsync(&st, e->P.st + slot, sizeof st, cudaMemcpyDeviceToHost, e->stream));
+    PA_CUDA(cudaStreamSynchronize(e->stream));
+    if (step) *step = st.step;
+    if (R) *R = st.R_cur;
+    if (status) *status = st.status;
+    return PA_OK;
+}
+
+pa_status pa_finished(const pa_engine *e, uint32_t *slots_out, uint32_t cap, uint32_t *n_out)
+{
+    if (!e || !n_out) return PA_ERR_INVALID_ARG;
+    uint32_t n = 0;
+    for (uint32_t s : e->active) {
+        const RunHost &h = e->rh[s];
+        if (h.steps_done + 1 >= h.d.n_beta) {
+            if (slots_out && n < cap) slots_out[n] = s;
+            ++n;
+        }
+    }
+    *n_out = n;
+    return PA_OK;
 }
 
 pa_status pa_reset(pa_engine *e)
 {
     if (!e) return PA_ERR_INVALID_ARG;
     PA_CUDA(cudaStreamSynchronize(e->stream));
-    return enqueue_init(e);
+    std::vector<RunState> st(e->active.size());
+    for (size_t k = 0; k < e->active.size(); ++k) {
+        const uint32_t s = e->active[k];
+        const RunDev &x = e->rd[s];
+        st[k].step = 0;
+        st[k].R_cur = x.R;
+        st[k].R_new = x.R;
+        st[k].status = 0;
+        st[k].lnQ = 0.0;
+        PA_CUDA(cudaMemcpyAsync(e->P.st + s, &st[k], sizeof(RunState), cudaMemcpyHostToDevice, e->stream));
+        PA_CUDA(cudaMemsetAsync(e->P.rec + x.rec_off, 0, sizeof(pa_step_record) * x.n_beta, e->stream));
+        if (x.overlap) {
+            const uint64_t nq = (uint64_t)x.n_beta * (x.N + 1);
+            PA_CUDA(cudaMemsetAsync(e->P.qh + x.qh_off, 0, sizeof(uint32_t) * nq, e->stream));
+            PA_CUDA(cudaMemsetAsync(e->P.qhp + x.qh_off, 0, sizeof(uint32_t) * nq, e->stream));
+        }
+        e->rh[s].steps_done = 0;
+        if (std::find(e->pending.begin(), e->pending.end(), s) == e->pending.end()) e->pending.push_back(s);
+    }
+    PA_CUDA(cudaMemsetAsync(e->P.status, 0, sizeof(uint32_t), e->stream));
+    PA_CUDA(cudaStreamSynchronize(e->stream));  // st must outlive the copies
+    e->latched = PA_OK;
+    e->h2d += sizeof(RunState) * e->active.size();
+    e->dirty = true;
+    return prepare(e);
 }
 
 pa_status pa_anneal_step(pa_engine *e, uint32_t n_steps, int use_graph)
 {
     if (!e) return PA_ERR_INVALID_ARG;
     if (e->latched != PA_OK) return e->latched;
-    if (n_steps == 0) return PA_OK;
+    PA_TRY(prepare(e));
+    if (n_steps == 0 || e->active.empty()) return PA_OK;
     bool untuned = false;
-    for (auto &g : e->groups) untuned |= !g.tuned;
+    for (auto &g : e->groups) untuned |= !e->tuning[g.L].tuned;
     if (untuned) {
-        pa_status s = enqueue_tuning_tick(e);
-        if (s != PA_OK) return s;
+        PA_TRY(enqueue_tuning_tick(e));
+        advance_host_steps(e, 1);
         if (--n_steps == 0) return PA_OK;
     }
     if (use_graph && !e->profiling) {
         if (!e->graph_exec) {
+            const uint64_t l0 = e->launches;
             PA_CUDA(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
             enqueue_tick(e);
             PA_CUDA(cudaStreamEndCapture(e->stream, &e->graph));
             PA_CUDA(cudaGraphInstantiate(&e->graph_exec, e->graph, 0));
+            e->launches = l0;  // capturing launched nothing
         }
+        const uint64_t per_tick = 2 + e->groups.size() + (e->q_runs.empty() ? 0 : 1);
         for (uint32_t k = 0; k < n_steps; ++k) PA_CUDA(cudaGraphLaunch(e->graph_exec, e->stream));
+        e->launches += per_tick * n_steps;
     } else {
         for (uint32_t k = 0; k < n_steps; ++k) enqueue_tick(e);
         PA_CUDA(cudaGetLastError());
     }
-    e->launches += e->launches_per_tick * n_steps;
+    advance_host_steps(e, n_steps);
     return PA_OK;
 }
 
 pa_status pa_sync(pa_engine *e)
 {
     if (!e) return PA_ERR_INVALID_ARG;
+    PA_TRY(prepare(e));
     PA_CUDA(cudaStreamSynchronize(e->stream));
     PA_CUDA(cudaGetLastError());
     return latch_device_status(e);
@@ -611,10 +975,12 @@ pa_status pa_sweep_shape(const pa_engine *e, uint32_t group, uint32_t *L, uint32
 {
     if (!e || group >= e->groups.size() || !L || !words_per_thread || !block || !tuned) return PA_ERR_INVALID_ARG;
     const SweepGroup &g = e->groups[group];
+    const Tuning &t = e->tuning.at(g.L);
+    const SweepCfg &c = t.candidates[t.pick];
     *L = g.L;
-    *words_per_thread = g.cfg.fast ? g.cfg.WPT : 0;
-    *block = g.cfg.block;
-    *tuned = (g.tuned && g.candidates.size() > 1) ? 1u : 0u;
+    *words_per_thread = c.fast ? c.WPT : 0;
+    *block = c.block;
+    *tuned = (t.tuned && t.candidates.size() > 1) ? 1u : 0u;
     return PA_OK;
 }
 
@@ -656,9 +1022,10 @@ pa_status pa_transfer_bytes(const pa_engine *e, uint64_t *h2d, uint64_t *d2h)
 pa_status pa_records(pa_engine *e, uint32_t run, pa_step_record *host_out, uint32_t *host_qhist,
                      uint32_t *host_qhist_pair)
 {
-    if (!e || run >= e->n_runs || !host_out) return PA_ERR_INVALID_ARG;
+    if (!slot_ok(e, run) || !host_out) return PA_ERR_INVALID_ARG;
     const RunDev &x = e->rd[run];
     if ((host_qhist || host_qhist_pair) && !x.overlap) return PA_ERR_INVALID_ARG;
+    PA_TRY(prepare(e));
     PA_CUDA(cudaMemcpyAsync(host_out, e->P.rec + x.rec_off, sizeof(pa_step_record) * x.n_beta,
                             cudaMemcpyDeviceToHost, e->stream));
     const size_t nq = (size_t)x.n_beta * (x.N + 1);
@@ -674,9 +1041,10 @@ pa_status pa_records(pa_engine *e, uint32_t run, pa_step_record *host_out, uint3
 pa_status pa_measure(pa_engine *e, uint32_t run, uint32_t step, pa_step_record *host_out, uint32_t *host_qhist,
                      uint32_t *host_qhist_pair)
 {
-    if (!e || run >= e->n_runs || !host_out) return PA_ERR_INVALID_ARG;
+    if (!slot_ok(e, run) || !host_out) return PA_ERR_INVALID_ARG;
     const RunDev &x = e->rd[run];
     if (step >= x.n_beta) return PA_ERR_INVALID_ARG;
+    PA_TRY(prepare(e));
     if ((host_qhist || host_qhist_pair) && !x.overlap) return PA_ERR_INVALID_ARG;
     PA_CUDA(cudaMemcpyAsync(host_out, e->P.rec + x.rec_off + step, sizeof(pa_step_record), cudaMemcpyDeviceToHost,
                             e->stream));
@@ -693,7 +1061,8 @@ pa_status pa_measure(pa_engine *e, uint32_t run, uint32_t step, pa_step_record *
 pa_status pa_population(pa_engine *e, uint32_t run, int8_t *host_spins, int32_t *host_E, int32_t *host_M,
                         uint32_t *host_fam, uint32_t *R_out, uint32_t *step_out)
 {
-    if (!e || run >= e->n_runs) return PA_ERR_INVALID_ARG;
+    if (!slot_ok(e, run)) return PA_ERR_INVALID_ARG;
+    PA_TRY(prepare(e));
     const RunDev &x = e->rd[run];
     RunState st;
     PA_CUDA(cudaMemcpyAsync(&st, e->P.st + run, sizeof st, cudaMemcpyDeviceToHost, e->stream));
@@ -745,11 +1114,13 @@ pa_status pa_weighted_average_runs(pa_engine *e, const uint32_t *run_idx, uint32
                                    uint32_t weight_kind, pa_wavg *host_out, double *host_Pq, double *host_Pq_pair)
 {
     if (!e || !run_idx || !n_groups || !M || !host_out || weight_kind > PA_WEIGHT_SIMPLE) return PA_ERR_INVALID_ARG;
-    const RunDev &r0 = e->rd[run_idx[0] < e->n_runs ? run_idx[0] : 0];
+    if (!slot_ok(e, run_idx[0])) return PA_ERR_INVALID_ARG;
+    PA_TRY(prepare(e));
+    const RunDev &r0 = e->rd[run_idx[0]];
     const uint32_t n_steps = r0.n_beta, N = r0.N;
     std::vector<unsigned long long> rec_off((size_t)n_groups * M), qh_off((size_t)n_groups * M);
     for (size_t k = 0; k < rec_off.size(); ++k) {
-        if (run_idx[k] >= e->n_runs) return PA_ERR_INVALID_ARG;
+        if (!slot_ok(e, run_idx[k])) return PA_ERR_INVALID_ARG;
         const RunDev &x = e->rd[run_idx[k]];
         if (x.n_beta != n_steps || x.N != N) return PA_ERR_INVALID_ARG;
         if ((host_Pq || host_Pq_pair) && !x.overlap) return PA_ERR_INVALID_ARG;

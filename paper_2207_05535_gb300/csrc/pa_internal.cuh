@@ -10,8 +10,10 @@
 //   parent, cnt          [sum R_cap]        parent map of the children, copy numbers r_j
 //   rec                  [sum n_beta]       per-temperature records (pa_step_record)
 //   qh, qhp              [sum n_beta (N+1)] overlap histograms over d (shift / pair)
-//   beta, wt, thr                           schedule, exp(-4 n dbeta_i) per step, Metropolis
-//                                           thresholds per step (shared by equal schedules)
+//   beta, thr                               schedule and Metropolis thresholds per step
+//   wt, wtoff                               weight tables exp(-4 n dbeta) shared by every run
+//                                           and step with the same (N, dbeta); wtoff[wt_off + i]
+//                                           = offset of step i's table in wt
 //   J                    per run: site-order "J = -1" bits of right / down bonds
 //                        (2 wstride words), then per colour plane word the four bond
 //                        masks (same, rotated, up, down neighbour) [2][4][PW]
@@ -67,7 +69,8 @@ struct Pool {
     uint32_t *qh;
     uint32_t *qhp;
     const double *beta;
-    const double *wt;
+    const double *wt;                  // weight tables exp(-4 n dbeta), (N + 1) doubles each
+    const unsigned long long *wtoff;   // per run and step: offset of its table in wt
     const unsigned long long *thr;
     uint32_t *J;
     unsigned long long *scratch;
@@ -94,11 +97,12 @@ inline uint64_t scratch_words(uint32_t N, uint32_t R_cap)
 }
 
 // Launch wrappers implemented in pa_kernels.cu (all asynchronous on `s`).
-void launch_init_couplings(const Pool &P, uint32_t n_runs, cudaStream_t s);
+// `runs`: indices of the runs to process (NULL: runs 0..n_runs-1).
+void launch_init_couplings(const Pool &P, const uint32_t *runs, uint32_t n_runs, cudaStream_t s);
 // Work lists: tile_off = prefix of per-run tile counts (n + 1 entries).
-void launch_init_population(const Pool &P, const uint32_t *tile_off, uint32_t n_runs, uint32_t n_tiles,
-                            uint32_t max_pw, cudaStream_t s);
-void launch_resample(const Pool &P, uint32_t n_runs, cudaStream_t s);
+void launch_init_population(const Pool &P, const uint32_t *tile_off, const uint32_t *runs, uint32_t n_runs,
+                            uint32_t n_tiles, uint32_t max_pw, cudaStream_t s);
+void launch_resample(const Pool &P, const uint32_t *runs, uint32_t n_runs, cudaStream_t s);
 // Launch shapes to try for lattice size L (first = default); one entry unless
 // the bit-sliced kernel applies.
 std::vector<SweepCfg> sweep_candidates(uint32_t L, int allow_fast);
@@ -106,7 +110,7 @@ void launch_sweep(const Pool &P, const uint32_t *group_runs, const uint32_t *til
                   uint32_t n_tiles, const SweepCfg &cfg, int any_glass, cudaStream_t s);
 void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, uint32_t max_Rcap, int init,
                     cudaStream_t s);
-void launch_measure(const Pool &P, uint32_t n_runs, int init, cudaStream_t s);
+void launch_measure(const Pool &P, const uint32_t *runs, uint32_t n_runs, int init, cudaStream_t s);
 void launch_wavg(const pa_step_record *recs, const unsigned long long *rec_off, const uint32_t *qh,
                  const uint32_t *qhp, const unsigned long long *qh_off, uint32_t n_groups, uint32_t M,
                  uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w, double *Pq, double *Pqp,

@@ -270,9 +270,9 @@ __device__ __forceinline__ void plane_neighbours(const uint32_t *O, uint32_t HW,
 // four bond masks of its sites: bond to the same-index neighbour, to the
 // rotated neighbour (index k -+ 1 within the row), up and down.
 // --------------------------------------------------------------------------
-__global__ void init_couplings_kernel(Pool P)
+__global__ void init_couplings_kernel(Pool P, const uint32_t *runs)
 {
-    const RunDev rd = P.runs[blockIdx.x];
+    const RunDev rd = P.runs[runs ? runs[blockIdx.x] : blockIdx.x];
     const uint32_t SW = rd.wstride;          // site-order words (>= ceil(N/32))
     const uint32_t PW = (rd.N + 63) / 64;    // plane words
     uint32_t *Jr = P.J + rd.J_off, *Jd = Jr + SW, *Jp = Jd + SW;  // Jp: [c][4][PW]
@@ -322,13 +322,14 @@ __global__ void init_couplings_kernel(Pool P)
 // One warp per replica (4 per CTA, CTAs from the work list over all runs):
 // uniform spins from Philox (one call per four consecutive sites), then E and
 // M exactly.  Power-of-two L uses word-wide neighbour masks for E.
-__global__ void __launch_bounds__(128) init_population_kernel(Pool P, const uint32_t *tile_off, uint32_t n_runs)
+__global__ void __launch_bounds__(128)
+    init_population_kernel(Pool P, const uint32_t *tile_off, const uint32_t *runs, uint32_t n_runs)
 {
     extern __shared__ __align__(16) uint32_t sw[];  // per warp: 2 PW plane words
-    const uint32_t run = locate_slot(tile_off, n_runs, blockIdx.x);
-    const RunDev rd = P.runs[run];
+    const uint32_t slot = locate_slot(tile_off, n_runs, blockIdx.x);
+    const RunDev rd = P.runs[runs ? runs[slot] : slot];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t j = (blockIdx.x - tile_off[run]) * (blockDim.x >> 5) + warp;
+    const uint32_t j = (blockIdx.x - tile_off[slot]) * (blockDim.x >> 5) + warp;
     if (j >= rd.R) return;  // warp-uniform; no block barrier below
     const uint32_t L = rd.L, N = rd.N, PW = (N + 63) / 64;
     uint32_t *pl = sw + warp * 2 * PW;
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(128) init_population_kernel(Pool P, const uint
     }
     __syncwarp();
     uint32_t *s = P.spins[0] + rd.spin_off + (uint64_t)j * rd.wstride;
-    for (uint32_t cw = lane; cw < 2 * PW; cw += 32) s[cw] = pl[cw];
+    for (uint32_t cw = lane; cw < rd.wstride; cw += 32) s[cw] = cw < 2 * PW ? pl[cw] : 0u;  // padding cleared
     int32_t unsat = 0, up = 0;
     for (uint32_t cw = lane; cw < 2 * PW; cw += 32) up += __popc(pl[cw]);
     const bool pow2 = L >= 8 && (L & (L - 1)) == 0;
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(128) init_population_kernel(Pool P, const uint
 // --------------------------------------------------------------------------
 // Resampling (Sec. II.B steps (ii)-(iii), Eqs. tauBoltz and QBoltz).
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) resample_kernel(Pool P)
+__global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *runs)
 {
     __shared__ uint32_t sh_hist[SMEM_BINS];
     __shared__ int32_t sh_i[32];
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P)
     __shared__ double sh_S;
     __shared__ uint32_t sh_carry;
 
-    const uint32_t run = blockIdx.x;
+    const uint32_t run = runs ? runs[blockIdx.x] : blockIdx.x;
     const RunDev rd = P.runs[run];
     RunState *st = &P.st[run];
     if (st->status) return;
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P)
     __syncthreads();
 
     const double dbeta = P.beta[rd.beta_off + i] - P.beta[rd.beta_off + i - 1];
-    const double *w = P.wt + rd.wt_off + (uint64_t)i * n1;  // w[n] = exp(-4 n dbeta)
+    const double *w = P.wt + P.wtoff[rd.wt_off + i];  // w[n] = exp(-4 n dbeta_i), shared table
     const bool multi = rd.resample == PA_MULTINOMIAL;
     if (tid == 0) {
         // S = sum_j exp(-dbeta (E_j - E_min)), level by level in ascending order
@@ -538,8 +539,9 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P)
 // "bond mask" plane holds per site the J = -1 bits of its right, left, down
 // and up bonds.
 // --------------------------------------------------------------------------
-__global__ void sweep_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off, uint32_t n_group_runs,
-                             SweepCfg cfg)
+template <bool HOIST, int MAXT>
+__global__ void __launch_bounds__(MAXT) sweep_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off,
+                                                     uint32_t n_group_runs, SweepCfg cfg)
 {
     extern __shared__ __align__(16) uint8_t sm[];
     const uint32_t slot = locate_slot(tile_off, n_group_runs, blockIdx.x);
@@ -596,6 +598,60 @@ __global__ void sweep_kernel(Pool P, const uint32_t *group_runs, const uint32_t 
 
     const unsigned long long T1 = P.thr[rd.thr_off + 2 * i], T2 = P.thr[rd.thr_off + 2 * i + 1];
     int32_t dE = 0, dM = 0;
+    if (HOIST) {
+        // One Philox group per thread (blocks of at most 512 threads): the neighbour indices and bond
+        // bits of its four sites per colour are computed once, outside the sweeps.
+        const uint32_t g = tl;
+        const bool has = active && g < cfg.G;
+        uint32_t nrl[2][4], ndu[2][4];  // packed 16-bit indices in the other plane: right|left, down|up
+        uint32_t jbits = 0;             // 4 bond bits per site, site (c, q) at bit 16 c + 4 q
+        uint32_t nval[2] = {0, 0};
+#pragma unroll
+        for (uint32_t c = 0; c < 2; ++c)
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q) {
+                nrl[c][q] = ndu[c][q] = 0;
+                const uint32_t k = 4 * g + q;
+                if (!has || k >= half) continue;
+                const uint32_t y = k / Lh, xp = k - y * Lh;
+                const uint32_t x = 2 * xp + ((c + y) & 1u);
+                const uint32_t xr = x + 1 == L ? 0 : x + 1, xl = x == 0 ? L - 1 : x - 1;
+                const uint32_t yd = y + 1 == L ? 0 : y + 1, yu = y == 0 ? L - 1 : y - 1;
+                nrl[c][q] = (y * Lh + (xr >> 1)) | ((y * Lh + (xl >> 1)) << 16);
+                ndu[c][q] = (yd * Lh + xp) | ((yu * Lh + xp) << 16);
+                jbits |= (uint32_t)jm[c * PS + k] << (16 * c + 4 * q);
+                nval[c] = q + 1;
+            }
+        for (uint32_t t = 0; t < rd.theta; ++t) {
+#pragma unroll
+            for (uint32_t c = 0; c < 2; ++c) {
+                if (has) {
+                    uint8_t *mine = planes + c * PS;
+                    const uint8_t *other = planes + (c ^ 1u) * PS;
+                    const uint4 u = philox4x32_10(g, child, i, (TAG_SWEEP << 24) | (t << 1) | c, rd.seed, rd.run_id);
+#pragma unroll
+                    for (uint32_t q = 0; q < 4; ++q) {
+                        if (q >= nval[c]) break;
+                        const uint32_t k = 4 * g + q;
+                        const uint32_t jb = (jbits >> (16 * c + 4 * q)) & 15u;
+                        const uint32_t s = mine[k];
+                        const uint32_t unsat = (s ^ other[nrl[c][q] & 0xffffu] ^ (jb & 1u)) +
+                                               (s ^ other[nrl[c][q] >> 16] ^ ((jb >> 1) & 1u)) +
+                                               (s ^ other[ndu[c][q] & 0xffffu] ^ ((jb >> 2) & 1u)) +
+                                               (s ^ other[ndu[c][q] >> 16] ^ (jb >> 3));
+                        const bool accept =
+                            unsat >= 2u || (unsigned long long)pick(u, q) < (unsat == 1u ? T1 : T2);
+                        if (accept) {
+                            mine[k] = (uint8_t)(s ^ 1u);
+                            dE += 8 - 4 * (int32_t)unsat;
+                            dM += 2 - 4 * (int32_t)s;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    } else
     for (uint32_t t = 0; t < rd.theta; ++t) {
         for (uint32_t c = 0; c < 2; ++c) {
             if (active) {
@@ -869,6 +925,7 @@ __global__ void overlap_kernel(Pool P, const uint32_t *q_runs, int init)
     const uint32_t R = init ? rd.R : st.R_new;
     const uint32_t buf = i & 1u;
     const uint32_t N = rd.N, ws = rd.wstride;
+    const uint32_t nw = 2 * ((N + 63) / 64);  // plane words; the stride's padding is never compared
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     pa_step_record *rec = P.rec + rd.rec_off + i;
 
@@ -877,13 +934,10 @@ __global__ void overlap_kernel(Pool P, const uint32_t *q_runs, int init)
         if (blockIdx.x * blockDim.x < h) {
             long long v = 0;
             if (p < h) {
-                const uint4 *a = reinterpret_cast<const uint4 *>(P.spins[buf] + rd.spin_off + (uint64_t)p * ws);
-                const uint4 *b = reinterpret_cast<const uint4 *>(P.spins[buf] + rd.spin_off + (uint64_t)(p + h) * ws);
+                const uint32_t *a = P.spins[buf] + rd.spin_off + (uint64_t)p * ws;
+                const uint32_t *b = P.spins[buf] + rd.spin_off + (uint64_t)(p + h) * ws;
                 uint32_t d = 0;
-                for (uint32_t q = 0; q < ws / 4; ++q) {
-                    const uint4 x = a[q], y = b[q];
-                    d += __popc(x.x ^ y.x) + __popc(x.y ^ y.y) + __popc(x.z ^ y.z) + __popc(x.w ^ y.w);
-                }
+                for (uint32_t q = 0; q < nw; ++q) d += __popc(a[q] ^ b[q]);  // the two colour planes only
                 atomicAdd(&P.qh[rd.qh_off + (uint64_t)i * (N + 1) + d], 1u);
                 const long long qn = (long long)N - 2 * (long long)d;
                 v = qn < 0 ? -qn : qn;
@@ -905,13 +959,10 @@ __global__ void overlap_kernel(Pool P, const uint32_t *q_runs, int init)
         if (blockIdx.x * blockDim.x < n) {
             long long v = 0;
             if (p < n) {
-                const uint4 *a = reinterpret_cast<const uint4 *>(P.spins[buf] + rd.spin_off + (uint64_t)p * ws);
-                const uint4 *b = reinterpret_cast<const uint4 *>(P.spins[buf] + rb.spin_off + (uint64_t)p * ws);
+                const uint32_t *a = P.spins[buf] + rd.spin_off + (uint64_t)p * ws;
+                const uint32_t *b = P.spins[buf] + rb.spin_off + (uint64_t)p * ws;
                 uint32_t d = 0;
-                for (uint32_t q = 0; q < ws / 4; ++q) {
-                    const uint4 x = a[q], y = b[q];
-                    d += __popc(x.x ^ y.x) + __popc(x.y ^ y.y) + __popc(x.z ^ y.z) + __popc(x.w ^ y.w);
-                }
+                for (uint32_t q = 0; q < nw; ++q) d += __popc(a[q] ^ b[q]);
                 atomicAdd(&P.qhp[rd.qh_off + (uint64_t)i * (N + 1) + d], 1u);
                 atomicAdd(&P.qhp[rb.qh_off + (uint64_t)i * (N + 1) + d], 1u);
                 const long long qn = (long long)N - 2 * (long long)d;
@@ -935,12 +986,12 @@ __global__ void overlap_kernel(Pool P, const uint32_t *q_runs, int init)
 // Measurement (Sec. III.B, Eqs. e, m, c, chi through exact integer sums;
 // Eq. F running sum; Eq. rho_t through family run lengths).  Finishes the step.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) measure_kernel(Pool P, int init)
+__global__ void __launch_bounds__(512) measure_kernel(Pool P, const uint32_t *runs, int init)
 {
     __shared__ long long sh_l[32];
     __shared__ uint32_t sh_u[33];
     __shared__ uint32_t sh_carry;
-    const uint32_t run = blockIdx.x;
+    const uint32_t run = runs ? runs[blockIdx.x] : blockIdx.x;
     const RunDev rd = P.runs[run];
     RunState *st = &P.st[run];
     if (st->status) return;
@@ -1135,22 +1186,28 @@ __global__ void wavg_q_kernel(const pa_step_record *recs, const unsigned long lo
 // ------------------------------------------------------------------ launchers
 cudaError_t prepare_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_kernel<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     return e;
 }
 
-void launch_init_couplings(const Pool &P, uint32_t n_runs, cudaStream_t s)
+void launch_init_couplings(const Pool &P, const uint32_t *runs, uint32_t n_runs, cudaStream_t s)
 {
-    init_couplings_kernel<<<n_runs, 256, 0, s>>>(P);
+    init_couplings_kernel<<<n_runs, 256, 0, s>>>(P, runs);
 }
 
-void launch_init_population(const Pool &P, const uint32_t *tile_off, uint32_t n_runs, uint32_t n_tiles,
-                            uint32_t max_pw, cudaStream_t s)
+void launch_init_population(const Pool &P, const uint32_t *tile_off, const uint32_t *runs, uint32_t n_runs,
+                            uint32_t n_tiles, uint32_t max_pw, cudaStream_t s)
 {
-    init_population_kernel<<<n_tiles, 128, 4 * 2 * max_pw * sizeof(uint32_t), s>>>(P, tile_off, n_runs);
+    init_population_kernel<<<n_tiles, 128, 4 * 2 * max_pw * sizeof(uint32_t), s>>>(P, tile_off, runs, n_runs);
 }
 
-void launch_resample(const Pool &P, uint32_t n_runs, cudaStream_t s) { resample_kernel<<<n_runs, 512, 0, s>>>(P); }
+void launch_resample(const Pool &P, const uint32_t *runs, uint32_t n_runs, cudaStream_t s)
+{
+    resample_kernel<<<n_runs, 512, 0, s>>>(P, runs);
+}
 
 // Launch shapes of the bit-sliced kernel: WPT plane words per thread and
 // `block` threads per CTA (a multiple of the threads per replica, HW / WPT).
@@ -1216,8 +1273,10 @@ void launch_sweep(const Pool &P, const uint32_t *group_runs, const uint32_t *til
     const dim3 grid(n_tiles);
 #define PA_SWEEP_FAST(SG, WPT, MAXT) \
     sweep_pow2_kernel<SG, WPT, MAXT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg)
-    if (!cfg.fast)
-        sweep_kernel<<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg);
+    if (!cfg.fast && cfg.G <= cfg.TPR && cfg.block <= 512)
+        sweep_kernel<true, 512><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg);
+    else if (!cfg.fast)
+        sweep_kernel<false, 1024><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg);
     else if (cfg.WPT == 1 && cfg.block <= 256)
         any_glass ? PA_SWEEP_FAST(true, 1, 256) : PA_SWEEP_FAST(false, 1, 256);
     else if (cfg.WPT == 1)
@@ -1236,9 +1295,9 @@ void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, ui
     overlap_kernel<<<grid, 256, 0, s>>>(P, q_runs, init);
 }
 
-void launch_measure(const Pool &P, uint32_t n_runs, int init, cudaStream_t s)
+void launch_measure(const Pool &P, const uint32_t *runs, uint32_t n_runs, int init, cudaStream_t s)
 {
-    measure_kernel<<<n_runs, 512, 0, s>>>(P, init);
+    measure_kernel<<<n_runs, 512, 0, s>>>(P, runs, init);
 }
 
 void launch_wavg(const pa_step_record *recs, const unsigned long long *rec_off, const uint32_t *qh,
