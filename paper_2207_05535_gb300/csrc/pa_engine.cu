@@ -205,7 +205,7 @@ uint32_t cap_of(const pa_run_desc &d)
     return d.R + 8u * (uint32_t)std::ceil(std::sqrt((double)d.R)) + 64u;
 }
 
-uint32_t plane_words(uint32_t L) { return (L * L + 63) / 64; }
+uint32_t plane_words(uint32_t L) { return plane_words_of(L); }
 uint32_t stride_words(uint32_t L) { return (2 * plane_words(L) + 3) / 4 * 4; }
 
 Ranges sizes_of(const pa_run_desc &d)
@@ -418,6 +418,8 @@ pa_status admit(pa_engine *e, const pa_run_desc *runs, uint32_t n, uint32_t *slo
         x.resample = d.resample;
         x.overlap = d.overlap;
         x.paired = (d.overlap & PA_Q_PAIR) ? (int32_t)got[d.paired] : -1;
+        x.pitch = row_pitch(d.L);
+        x.pw = plane_words(d.L);
         x.rep_off = g.rep;
         x.spin_off = g.spin;
         x.rec_off = g.rec;
@@ -1075,12 +1077,11 @@ pa_status pa_population(pa_engine *e, uint32_t run, int8_t *host_spins, int32_t 
         PA_CUDA(cudaMemcpyAsync(words.data(), e->P.spins[b] + x.spin_off, sizeof(uint32_t) * words.size(),
                                 cudaMemcpyDeviceToHost, e->stream));
         PA_CUDA(cudaStreamSynchronize(e->stream));
-        const uint32_t pw = (x.N + 63) / 64;
         for (uint32_t j = 0; j < R; ++j)
             for (uint32_t n = 0; n < x.N; ++n) {
-                const uint32_t c = ((n % x.L) + (n / x.L)) & 1u, k = n >> 1;
-                const uint32_t word = words[(size_t)j * x.wstride + c * pw + (k >> 5)];
-                host_spins[(size_t)j * x.N + n] = ((word >> (k & 31)) & 1u) ? (int8_t)1 : (int8_t)-1;
+                const uint32_t xx = n % x.L, y = n / x.L, c = (xx + y) & 1u, pos = y * x.pitch + (xx >> 1);
+                const uint32_t word = words[(size_t)j * x.wstride + c * x.pw + (pos >> 5)];
+                host_spins[(size_t)j * x.N + n] = ((word >> (pos & 31)) & 1u) ? (int8_t)1 : (int8_t)-1;
             }
     }
     if (host_E && R)

@@ -3,9 +3,10 @@
 // Device memory layout (one pool per engine, every run at its own offsets):
 //   spins[b]  uint32 [sum R_cap wstride]    replica j of a run at word spin_off + j wstride:
 //                                           colour plane 0 in words [0, PW), plane 1 in
-//                                           [PW, 2 PW), PW = ceil(N/64); site n = y L + x has
-//                                           colour (x + y) & 1 and index k = n >> 1 (bit k & 31
-//                                           of word k >> 5); bit 1 = spin +1; buffer b = step & 1
+//                                           [PW, 2 PW); site n = y L + x has colour (x + y) & 1
+//                                           and sits in row y of its plane at bit position
+//                                           y * pitch + (x >> 1) (rows padded to the pitch,
+//                                           padding bits 0); bit 1 = spin +1; buffer b = step & 1
 //   E[b], M[b], fam[b]   [sum R_cap]        energy, magnetisation, beta_0 ancestor
 //   parent, cnt          [sum R_cap]        parent map of the children, copy numbers r_j
 //   rec                  [sum n_beta]       per-temperature records (pa_step_record)
@@ -41,6 +42,8 @@ struct RunDev {
     uint32_t n_beta, seed, run_id, disorder_id;
     uint32_t resample, overlap;
     int32_t paired;
+    uint32_t pitch;  // bits per row in a colour plane (>= L/2; see row_pitch)
+    uint32_t pw;     // words per colour plane = ceil(L pitch / 32)
     uint32_t pad0;
     uint64_t rep_off;   // first replica slot (E, M, fam, parent, cnt)
     uint64_t spin_off;  // first spin word (runs of different L have different wstride)
@@ -79,7 +82,7 @@ struct Pool {
 
 // Sweep launch shape for one lattice size.
 struct SweepCfg {
-    uint32_t fast;   // 1: bit-sliced kernel (L a power of two, 8..256)
+    uint32_t fast;   // 0: byte planes; 1: bit-sliced (L/2 a power of two); 2: bit-sliced, padded rows
     uint32_t block;  // threads per CTA
     uint32_t TPR;    // threads per replica (power of two; fast kernel: words per plane)
     uint32_t RPC;    // replicas per CTA
@@ -88,6 +91,22 @@ struct SweepCfg {
     uint32_t smem;   // dynamic shared memory bytes
     uint32_t WPT;    // fast kernel: plane words per thread
 };
+
+// Row pitch of a colour plane: L/2 when that is a power of two; else the
+// smallest power of two >= L/2 that makes L * pitch a multiple of 32 (rows then
+// tile 32-bit words, so the bit-sliced sweep applies) for L/2 < 32, and L/2
+// rounded up to a multiple of 32 beyond.
+inline uint32_t row_pitch(uint32_t L)
+{
+    const uint32_t Lh = L / 2;
+    if ((Lh & (Lh - 1)) == 0) return Lh;
+    if (Lh < 32)
+        for (uint32_t P = 4; P <= 32; P <<= 1)
+            if (P >= Lh && (L * P) % 32 == 0) return P;
+    return (Lh + 31) / 32 * 32;
+}
+
+inline uint32_t plane_words_of(uint32_t L) { return (L * row_pitch(L) + 31) / 32; }
 
 // Scratch words (64-bit) of one run.
 inline uint64_t scratch_words(uint32_t N, uint32_t R_cap)

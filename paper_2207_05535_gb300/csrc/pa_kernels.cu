@@ -213,22 +213,19 @@ __device__ __forceinline__ void set_status(const Pool &P, uint32_t run, uint32_t
 }
 
 // --------------------------------------------------------------------------
-// Spin layout of a replica (HBM and the fast sweep's shared memory): two
-// colour planes, plane c holding the sites of colour c = (x + y) & 1 in
-// sublattice order k = n >> 1 (n = y L + x), bit k & 31 of word k >> 5, bit 1 =
-// spin +1.  Plane 0 occupies words [0, PW), plane 1 words [PW, 2 PW), PW =
-// ceil(N / 64).  Site of (c, k): y = k / (L/2), x = 2 (k mod L/2) + ((c + y) & 1).
+// Spin layout of a replica (HBM and the bit-sliced sweeps' shared memory): two
+// colour planes, plane c holding the sites of colour c = (x + y) & 1, row y of
+// the plane at bit positions [y P, y P + L/2) with P = rd.pitch >= L/2 (padding
+// bits 0), position y P + (x >> 1) for site n = y L + x; bit pos & 31 of word
+// pos >> 5, bit 1 = spin +1.  Plane 0 occupies words [0, PW), plane 1
+// [PW, 2 PW), PW = rd.pw.  Philox counters use the compact sublattice index
+// k = n >> 1 = y L/2 + (x >> 1) whatever the pitch.
 // --------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t site_of(uint32_t L, uint32_t c, uint32_t k)
+__device__ __forceinline__ uint32_t spin_bit(const uint32_t *planes, uint32_t PW, uint32_t L, uint32_t pitch,
+                                             uint32_t n)
 {
-    const uint32_t Lh = L >> 1, y = k / Lh, xp = k - y * Lh;
-    return y * L + 2 * xp + ((c + y) & 1u);
-}
-
-__device__ __forceinline__ uint32_t spin_bit(const uint32_t *planes, uint32_t PW, uint32_t L, uint32_t n)
-{
-    const uint32_t x = n % L, y = n / L, c = (x + y) & 1u, k = n >> 1;
-    return (planes[c * PW + (k >> 5)] >> (k & 31)) & 1u;
+    const uint32_t x = n % L, y = n / L, c = (x + y) & 1u, pos = y * pitch + (x >> 1);
+    return (planes[c * PW + (pos >> 5)] >> (pos & 31)) & 1u;
 }
 
 // Neighbour masks of word w of colour plane c (L a power of two, 8..256), read
@@ -274,7 +271,7 @@ __global__ void init_couplings_kernel(Pool P, const uint32_t *runs)
 {
     const RunDev rd = P.runs[runs ? runs[blockIdx.x] : blockIdx.x];
     const uint32_t SW = rd.wstride;          // site-order words (>= ceil(N/32))
-    const uint32_t PW = (rd.N + 63) / 64;    // plane words
+    const uint32_t PW = rd.pw;               // plane words
     uint32_t *Jr = P.J + rd.J_off, *Jd = Jr + SW, *Jp = Jd + SW;  // Jp: [c][4][PW]
     for (uint32_t w = threadIdx.x; w < SW; w += blockDim.x) {
         uint32_t wr = 0, wd = 0;
@@ -295,14 +292,14 @@ __global__ void init_couplings_kernel(Pool P, const uint32_t *runs)
         Jd[w] = wd;
     }
     __syncthreads();
-    const uint32_t L = rd.L, half = rd.N >> 1;
+    const uint32_t L = rd.L, Lh = rd.Lh, Pt = rd.pitch;
     for (uint32_t cw = threadIdx.x; cw < 2 * PW; cw += blockDim.x) {
         const uint32_t c = cw / PW, w = cw - c * PW;
         uint32_t js = 0, jr = 0, ju = 0, jd = 0;
         for (uint32_t b = 0; b < 32; ++b) {
-            const uint32_t k = 32 * w + b;
-            if (k >= half) break;
-            const uint32_t n = site_of(L, c, k), x = n % L, y = n / L;
+            const uint32_t pos = 32 * w + b, y = pos / Pt, xp = pos - y * Pt;
+            if (y >= L || xp >= Lh) continue;  // row padding
+            const uint32_t x = 2 * xp + ((c + y) & 1u), n = y * L + x;
             const uint32_t p = (c + y) & 1u;
             const uint32_t right = get_bit(Jr, n), left = get_bit(Jr, y * L + (x == 0 ? L - 1 : x - 1));
             const uint32_t down = get_bit(Jd, n), up = get_bit(Jd, (y == 0 ? L - 1 : y - 1) * L + x);
@@ -331,7 +328,7 @@ __global__ void __launch_bounds__(128)
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t j = (blockIdx.x - tile_off[slot]) * (blockDim.x >> 5) + warp;
     if (j >= rd.R) return;  // warp-uniform; no block barrier below
-    const uint32_t L = rd.L, N = rd.N, PW = (N + 63) / 64;
+    const uint32_t L = rd.L, N = rd.N, PW = rd.pw, Pt = rd.pitch;
     uint32_t *pl = sw + warp * 2 * PW;
     for (uint32_t cw = lane; cw < 2 * PW; cw += 32) pl[cw] = 0;
     __syncwarp();
@@ -340,8 +337,8 @@ __global__ void __launch_bounds__(128)
         for (uint32_t q = 0; q < 4; ++q) {
             const uint32_t n = 4 * g + q;
             if (n >= N) break;
-            const uint32_t c = ((n % L) + (n / L)) & 1u, k = n >> 1;
-            if (pick(u, q) >> 31) atomicOr(&pl[c * PW + (k >> 5)], 1u << (k & 31));
+            const uint32_t x = n % L, y = n / L, c = (x + y) & 1u, pos = y * Pt + (x >> 1);
+            if (pick(u, q) >> 31) atomicOr(&pl[c * PW + (pos >> 5)], 1u << (pos & 31));
         }
     }
     __syncwarp();
@@ -349,7 +346,7 @@ __global__ void __launch_bounds__(128)
     for (uint32_t cw = lane; cw < rd.wstride; cw += 32) s[cw] = cw < 2 * PW ? pl[cw] : 0u;  // padding cleared
     int32_t unsat = 0, up = 0;
     for (uint32_t cw = lane; cw < 2 * PW; cw += 32) up += __popc(pl[cw]);
-    const bool pow2 = L >= 8 && (L & (L - 1)) == 0;
+    const bool pow2 = L >= 8 && Pt == rd.Lh;  // L/2 a power of two: rows fill the words
     if (pow2) {
         const uint32_t *Jp = P.J + rd.J_off + 2 * rd.wstride;  // [c][4][PW] bond masks
         for (uint32_t w = lane; w < PW; w += 32) {
@@ -363,9 +360,9 @@ __global__ void __launch_bounds__(128)
         const uint32_t *Jr = P.J + rd.J_off, *Jd = Jr + rd.wstride;
         for (uint32_t n = lane; n < N; n += 32) {
             const uint32_t x = n % L, y = n / L;
-            const uint32_t b = spin_bit(pl, PW, L, n);
-            const uint32_t br = spin_bit(pl, PW, L, y * L + (x + 1 == L ? 0 : x + 1));
-            const uint32_t bd = spin_bit(pl, PW, L, (y + 1 == L ? 0 : y + 1) * L + x);
+            const uint32_t b = spin_bit(pl, PW, L, Pt, n);
+            const uint32_t br = spin_bit(pl, PW, L, Pt, y * L + (x + 1 == L ? 0 : x + 1));
+            const uint32_t bd = spin_bit(pl, PW, L, Pt, (y + 1 == L ? 0 : y + 1) * L + x);
             unsat += (int32_t)((b ^ br ^ get_bit(Jr, n)) + (b ^ bd ^ get_bit(Jd, n)));
         }
     }
@@ -555,7 +552,7 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(Pool P, const uint32_t *gro
     const uint32_t tile0 = (blockIdx.x - tile_off[slot]) * cfg.RPC;
     if (tile0 >= Rn) return;  // uniform over the CTA
 
-    const uint32_t L = rd.L, N = rd.N, Lh = rd.Lh, half = N >> 1, PS = cfg.PS, PW = (N + 63) / 64;
+    const uint32_t L = rd.L, N = rd.N, Lh = rd.Lh, half = N >> 1, PS = cfg.PS, PW = rd.pw, Pt = rd.pitch;
     const uint32_t rloc = threadIdx.x / cfg.TPR, tl = threadIdx.x % cfg.TPR;
     const uint32_t child = tile0 + rloc;
     const bool active = rloc < cfg.RPC && child < Rn;
@@ -588,9 +585,9 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(Pool P, const uint32_t *gro
             const uint32_t c = cw / PW, w = cw - c * PW;
             const uint32_t word = src[cw];
             for (uint32_t b = 0; b < 32; ++b) {
-                const uint32_t k = 32 * w + b;
-                if (k >= half) break;
-                planes[c * PS + k] = (uint8_t)((word >> b) & 1u);
+                const uint32_t pos = 32 * w + b, y = pos / Pt, xp = pos - y * Pt;
+                if (y >= L || xp >= Lh) continue;  // row padding
+                planes[c * PS + y * Lh + xp] = (uint8_t)((word >> b) & 1u);
             }
         }
     }
@@ -695,9 +692,9 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(Pool P, const uint32_t *gro
             const uint32_t c = cw / PW, w = cw - c * PW;
             uint32_t word = 0;
             for (uint32_t b = 0; b < 32; ++b) {
-                const uint32_t k = 32 * w + b;
-                if (k >= half) break;
-                word |= (uint32_t)planes[c * PS + k] << b;
+                const uint32_t pos = 32 * w + b, y = pos / Pt, xp = pos - y * Pt;
+                if (y >= L || xp >= Lh) continue;  // row padding stays 0
+                word |= (uint32_t)planes[c * PS + y * Lh + xp] << b;
             }
             dst[cw] = word;
         }
@@ -911,6 +908,155 @@ __global__ void __launch_bounds__(MAXT) sweep_pow2_kernel(Pool P, const uint32_t
 }
 
 // --------------------------------------------------------------------------
+// Bit-sliced sweep for even L whose half-width L/2 is not a power of two but
+// at most 31 (Sec. V.A.1): rows of a colour plane are padded to a pitch P in
+// {4, 8, 16, 32} with L P a multiple of 32, so rows tile 32-bit words exactly
+// as in the power-of-two kernel; padding bits are masked out of every flip
+// and popcount and stay 0.  Each thread owns one plane word (32 / P rows); its
+// sites are the compact sublattice indices [kb, kb + (32 / P) L/2), drawn from
+// the same Philox counters as every other path (the groups at either end of
+// the range are shared with the neighbouring words and drawn by both), and
+// each comparison bit is placed at its padded position.
+// --------------------------------------------------------------------------
+template <bool SG>
+__global__ void __launch_bounds__(256) sweep_pad_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off,
+                                                        uint32_t n_group_runs, SweepCfg cfg)
+{
+    extern __shared__ __align__(16) uint32_t smw[];
+    const uint32_t slot = locate_slot(tile_off, n_group_runs, blockIdx.x);
+    const uint32_t run = group_runs[slot];
+    const RunDev rd = P.runs[run];
+    const RunState st = P.st[run];
+    if (st.status) return;
+    const uint32_t i = st.step + 1;
+    if (i >= rd.n_beta) return;
+    const uint32_t Rn = st.R_new;
+    const uint32_t tile0 = (blockIdx.x - tile_off[slot]) * cfg.RPC;
+    if (tile0 >= Rn) return;  // uniform over the CTA
+
+    const uint32_t HW = cfg.TPR;  // words per plane = threads per replica
+    const uint32_t Lh = rd.Lh, Pt = rd.pitch, N = rd.N;
+    const uint32_t rloc = threadIdx.x / HW, w = threadIdx.x - rloc * HW;
+    const uint32_t child = tile0 + rloc;
+    const bool active = child < Rn;
+    uint32_t *pl = smw + rloc * 2 * HW;
+    int32_t *acc = reinterpret_cast<int32_t *>(smw + cfg.RPC * 2 * HW);
+    if (threadIdx.x < 2 * cfg.RPC) acc[threadIdx.x] = 0;
+
+    const uint32_t ob = (i - 1) & 1u, nbuf = i & 1u;
+    uint32_t own[2] = {0u, 0u}, parent = 0;
+    if (active) {
+        parent = P.parent[rd.rep_off + child];
+        const uint32_t *src = P.spins[ob] + rd.spin_off + (uint64_t)parent * rd.wstride;
+        own[0] = src[w];
+        own[1] = src[HW + w];
+    }
+    pl[w] = own[0];
+    pl[HW + w] = own[1];
+    uint32_t J[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    if (SG) {
+        const uint32_t *Jp = P.J + rd.J_off + 2 * rd.wstride;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int d = 0; d < 4; ++d) J[c][d] = Jp[(c * 4 + d) * HW + w];
+    }
+    // word geometry
+    const bool sub = Pt < 32;  // several rows per word
+    const uint32_t RW = sub ? 32 / Pt : 1u, y0 = w * RW;
+    const uint32_t wp = (w + HW - 1) % HW, wn = (w + 1) % HW;
+    const uint32_t LOW = !sub ? 1u : Pt == 4 ? 0x11111111u : Pt == 8 ? 0x01010101u : 0x00010001u;
+    const uint32_t HIGH = LOW << (Lh - 1);
+    const uint32_t EVEN = Pt == 4 ? 0x0F0F0F0Fu : Pt == 8 ? 0x00FF00FFu : 0x0000FFFFu;  // rows 0, 2, ... (sub)
+    const uint32_t VMASK = LOW * ((1u << Lh) - 1u);                                      // Lh < 32 here
+    const uint32_t kb = y0 * Lh, kend = kb + RW * Lh;                                     // compact sites of the word
+
+    const unsigned long long T1 = P.thr[rd.thr_off + 2 * i], T2 = P.thr[rd.thr_off + 2 * i + 1];
+    const uint32_t t1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T1;
+    const uint32_t t2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T2;
+    const uint32_t all1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : 0u;
+    const uint32_t all2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : 0u;
+    PhiloxKeys K;
+    philox_keys(K, rd.seed, rd.run_id);
+    const uint32_t hi1_0 = __umulhi(0xCD9E8D57u, i), lo1_0 = 0xCD9E8D57u * i;
+    __syncthreads();
+
+    auto neighbours = [&](uint32_t c, uint32_t &same, uint32_t &rot, uint32_t &up, uint32_t &dn) {
+        const uint32_t *O = pl + (c ^ 1u) * HW;
+        const uint32_t o = O[w];
+        same = o;
+        const uint32_t rl = ((o << 1) & ~LOW) | ((o >> (Lh - 1)) & LOW);   // xp <- xp - 1 in the row
+        const uint32_t rr = ((o >> 1) & ~HIGH) | ((o << (Lh - 1)) & HIGH); // xp <- xp + 1 in the row
+        if (sub) {
+            up = __funnelshift_l(O[wp], o, Pt);  // row above: position - P
+            dn = __funnelshift_r(o, O[wn], Pt);  // row below: position + P
+            rot = c == 0 ? ((rl & EVEN) | (rr & ~EVEN)) : ((rr & EVEN) | (rl & ~EVEN));
+        } else {
+            up = O[wp];
+            dn = O[wn];
+            rot = ((c + y0) & 1u) == 0 ? rl : rr;
+        }
+    };
+
+    for (uint32_t t = 0; t < rd.theta; ++t) {
+#pragma unroll
+        for (uint32_t c = 0; c < 2; ++c) {
+            if (active) {
+                uint32_t same, rot, up, dn;
+                neighbours(c, same, rot, up, dn);
+                const uint32_t S = own[c];
+                const uint32_t x1 = S ^ same ^ J[c][0], x2 = S ^ rot ^ J[c][1];
+                const uint32_t x3 = S ^ up ^ J[c][2], x4 = S ^ dn ^ J[c][3];
+                const uint32_t a = x1 ^ x2, b = x1 & x2, e = x3 ^ x4, f = x3 & x4;
+                const uint32_t c0 = a ^ e, ge2 = b | f | (a & e);
+                const uint32_t ctr3 = (TAG_SWEEP << 24) | (t << 1) | c;
+                uint32_t B1 = 0, B2 = 0, r = 0, xp = 0;  // (r, xp): row and column of the next site
+                for (uint32_t g = kb >> 2; 4 * g < kend; ++g) {
+                    const uint4 u = philox_rk(g, child, ctr3, hi1_0, lo1_0, K);
+#pragma unroll
+                    for (uint32_t q = 0; q < 4; ++q) {
+                        const uint32_t k = 4 * g + q;
+                        if (k < kb || k >= kend) continue;
+                        const uint32_t pos = r * Pt + xp, v = pick(u, q);
+                        B1 |= (uint32_t)(v < t1) << pos;
+                        B2 |= (uint32_t)(v < t2) << pos;
+                        if (++xp == Lh) {
+                            xp = 0;
+                            ++r;
+                        }
+                    }
+                }
+                const uint32_t flip = (ge2 | (c0 & (B1 | all1)) | B2 | all2) & VMASK;
+                own[c] = S ^ flip;
+                pl[c * HW + w] = own[c];
+            }
+            __syncthreads();
+        }
+    }
+
+    // child: planes, E from the final lattice (every bond touches one colour-0 site), M
+    if (active) {
+        uint32_t *dst = P.spins[nbuf] + rd.spin_off + (uint64_t)child * rd.wstride;
+        dst[w] = own[0];
+        dst[HW + w] = own[1];
+        uint32_t same, rot, up, dn;
+        neighbours(0, same, rot, up, dn);
+        const uint32_t S = own[0];
+        const int32_t unsat = __popc((S ^ same ^ J[0][0]) & VMASK) + __popc((S ^ rot ^ J[0][1]) & VMASK) +
+                              __popc((S ^ up ^ J[0][2]) & VMASK) + __popc((S ^ dn ^ J[0][3]) & VMASK);
+        atomicAdd(&acc[2 * rloc], unsat);
+        atomicAdd(&acc[2 * rloc + 1], __popc(own[0]) + __popc(own[1]));
+    }
+    __syncthreads();
+    if (active && w == 0) {
+        const uint64_t pc = rd.rep_off + parent, cc = rd.rep_off + child;
+        P.E[nbuf][cc] = 2 * acc[2 * rloc] - 2 * (int32_t)N;
+        P.M[nbuf][cc] = 2 * acc[2 * rloc + 1] - (int32_t)N;
+        P.fam[nbuf][cc] = P.fam[ob][pc];
+    }
+}
+
+// --------------------------------------------------------------------------
 // Overlaps (Sec. III.D): d = popcount(s XOR s') over the packed spins.
 // --------------------------------------------------------------------------
 __global__ void overlap_kernel(Pool P, const uint32_t *q_runs, int init)
@@ -925,7 +1071,7 @@ __global__ void overlap_kernel(Pool P, const uint32_t *q_runs, int init)
     const uint32_t R = init ? rd.R : st.R_new;
     const uint32_t buf = i & 1u;
     const uint32_t N = rd.N, ws = rd.wstride;
-    const uint32_t nw = 2 * ((N + 63) / 64);  // plane words; the stride's padding is never compared
+    const uint32_t nw = 2 * rd.pw;  // plane words; the stride's padding is never compared
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     pa_step_record *rec = P.rec + rd.rec_off + i;
 
@@ -1246,6 +1392,23 @@ std::vector<SweepCfg> sweep_candidates(uint32_t L, int allow_fast)
         }
         return v;
     }
+    const uint32_t Pt = row_pitch(L);
+    if (allow_fast && L >= 6 && Pt <= 32 && Pt != L / 2) {  // padded rows
+        const uint32_t HW = L * Pt / 32;
+        for (uint32_t target : {128u, 256u}) {
+            SweepCfg c{};
+            c.fast = 2;
+            c.WPT = 1;
+            c.TPR = HW;
+            c.RPC = target / HW > 0 ? target / HW : 1;
+            c.block = c.RPC * HW;
+            c.G = (N + 7) / 8;
+            c.PS = 0;
+            c.smem = c.RPC * 2 * HW * 4 + 8 * c.RPC;
+            v.push_back(c);
+        }
+        return v;
+    }
     SweepCfg c{};
     c.fast = 0;
     c.WPT = 1;
@@ -1273,7 +1436,12 @@ void launch_sweep(const Pool &P, const uint32_t *group_runs, const uint32_t *til
     const dim3 grid(n_tiles);
 #define PA_SWEEP_FAST(SG, WPT, MAXT) \
     sweep_pow2_kernel<SG, WPT, MAXT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg)
-    if (!cfg.fast && cfg.G <= cfg.TPR && cfg.block <= 512)
+    if (cfg.fast == 2) {
+        if (any_glass)
+            sweep_pad_kernel<true><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg);
+        else
+            sweep_pad_kernel<false><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg);
+    } else if (!cfg.fast && cfg.G <= cfg.TPR && cfg.block <= 512)
         sweep_kernel<true, 512><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg);
     else if (!cfg.fast)
         sweep_kernel<false, 1024><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg);

@@ -203,10 +203,11 @@ def test_glass_L16_R5000_full_size_sampled_runs():
             assert np.all(rec["status"] == 0) and np.all(rec["R"] > 4000)
 
 
-@pytest.mark.parametrize("L", [8, 16, 32, 64, 128, 256])
+@pytest.mark.parametrize("L", [6, 8, 10, 12, 14, 16, 18, 30, 32, 46, 62, 64, 128, 256])
 def test_bitsliced_and_generic_sweeps_agree(L):
-    """The bit-sliced kernel (powers of two) and the byte-plane kernel flip the
-    same spins: whole anneals agree bit for bit for the ferromagnet and the glass."""
+    """The bit-sliced kernels (L/2 a power of two, or rows padded to a pitch)
+    and the byte-plane kernel flip the same spins: whole anneals agree bit for
+    bit for the ferromagnet and the glass."""
     R = max(4, 20000 // (L * L) * 8)
     b = W.schedule(1.5, 5)
     descs = [W.RunDesc(L, W.FERRO, R, 2, b, seed=3, run_id=0),
