@@ -56,6 +56,9 @@ WORKLOAD = WORKLOADS["glass_L16_R5000"]
 # slots per call, 10 per update.  The multiplier retires 64 multiply-add lanes
 # per clock per SM.
 ALGO_MULADD_PER_UPDATE = 10.0
+# DRAM bytes per sweep launch from one ncu capture (profiles/sweep_pow2_glass_L16_R5000.md),
+# valid only for the kernel source it was taken on.
+SWEEP_TRAFFIC = {"kernels_sha256_16": "1731982756b93843", "workload": "glass_L16_R5000", "bytes_per_launch": 44.954624e6}
 MULADD_LANES_PER_SM = 64
 
 
@@ -171,6 +174,16 @@ class Clocks:
         reasons = sorted({names[j] for r in rows for j in range(4) if r[3 + j].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def sweep_traffic(wl):
+    """Measured DRAM bytes per sweep launch, or None when the kernels changed since."""
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2207_05535_gb300", "csrc", "pa_kernels.cu"), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    if sha == SWEEP_TRAFFIC["kernels_sha256_16"] and wl == SWEEP_TRAFFIC["workload"]:
+        return SWEEP_TRAFFIC["bytes_per_launch"]
+    return None
 
 
 def peaks():
@@ -384,7 +397,7 @@ def main():
             "runs_per_s": runs_per_s,
             "roofline": {"bound": "alu", "kernel": "sweep_pow2_kernel", "achieved": achieved_tops,
                          "peak": peak_tops, "unit": "Tmuladd/s", "frac": achieved_tops / peak_tops,
-                         "traffic": None,
+                         "traffic": sweep_traffic(wl),
                          "basis": f"{ALGO_MULADD_PER_UPDATE:g} integer multiply-add slots per attempted update "
                                   f"(Philox4x32-10: 40 per call, 4 updates per call); peak = 152 SMs x "
                                   f"{MULADD_LANES_PER_SM} lanes x {sm_mhz:g} MHz, clock from MEASURED_PEAKS.json "
