@@ -37,6 +37,9 @@ namespace pa {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+#ifndef PA_PACK_MODE
+#define PA_PACK_MODE 2  // packing of the comparison bits: 0 add/add, 1 or/or, 2 or/add (fastest), 3 add/or
+#endif
 constexpr uint32_t SMEM_BINS = 4096;
 
 __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
@@ -847,15 +850,25 @@ __global__ void __launch_bounds__(MAXT) sweep_pow2_kernel(Pool P, const uint32_t
                     const uint32_t x3 = S ^ up ^ J[q][c][2], x4 = S ^ dn ^ J[q][c][3];
                     const uint32_t a = x1 ^ x2, b = x1 & x2, e = x3 ^ x4, f = x3 & x4;
                     const uint32_t c0 = a ^ e, ge2 = b | f | (a & e);
-                    // bits of distinct sites never collide, so the packing can add
+                    // bits of distinct sites never collide, so the packing can add or or
                     uint32_t B1 = 0, B2 = 0;
 #pragma unroll
                     for (uint32_t g = 0; g < 8; ++g) {
                         const uint4 u = philox_rk(8 * w + g, child, ctr3, hi1_0, lo1_0, K);
+#if PA_PACK_MODE == 1 || PA_PACK_MODE == 2
+                        B1 |= ((uint32_t)(u.x < t1) << (4 * g)) | ((uint32_t)(u.y < t1) << (4 * g + 1)) |
+                              ((uint32_t)(u.z < t1) << (4 * g + 2)) | ((uint32_t)(u.w < t1) << (4 * g + 3));
+#else
                         B1 += ((uint32_t)(u.x < t1) << (4 * g)) + ((uint32_t)(u.y < t1) << (4 * g + 1)) +
                               ((uint32_t)(u.z < t1) << (4 * g + 2)) + ((uint32_t)(u.w < t1) << (4 * g + 3));
+#endif
+#if PA_PACK_MODE == 1 || PA_PACK_MODE == 3
+                        B2 |= ((uint32_t)(u.x < t2) << (4 * g)) | ((uint32_t)(u.y < t2) << (4 * g + 1)) |
+                              ((uint32_t)(u.z < t2) << (4 * g + 2)) | ((uint32_t)(u.w < t2) << (4 * g + 3));
+#else
                         B2 += ((uint32_t)(u.x < t2) << (4 * g)) + ((uint32_t)(u.y < t2) << (4 * g + 1)) +
                               ((uint32_t)(u.z < t2) << (4 * g + 2)) + ((uint32_t)(u.w < t2) << (4 * g + 3));
+#endif
                     }
                     const uint32_t flip = ge2 | (c0 & (B1 | all1)) | B2 | all2;
                     own[q][c] = S ^ flip;
