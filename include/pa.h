@@ -89,6 +89,13 @@ typedef struct pa_step_record {
     uint32_t n_q_pair;    /* number of pairs with the partner, min(R_i, R_i') */
     uint32_t N;           /* number of spins */
     uint32_t status;      /* 0, or the pa_status that stopped this run */
+    /* Higher powers for the central-moment and Binder estimators (Sec. IV.E):
+     * exact sums as 128-bit two's-complement integers, word 0 the low 64 bits
+     * (a single H_j^4 exceeds int64 at L = 256). */
+    uint64_t sumE3[2];    /* sum_j H_j^3 */
+    uint64_t sumE4[2];    /* sum_j H_j^4 */
+    uint64_t sumAbsM3[2]; /* sum_j |M_j|^3 */
+    uint64_t sumM4[2];    /* sum_j M_j^4 */
 } pa_step_record;
 
 /* Weighted averages at one temperature over M runs (Sec. IV). */
@@ -101,6 +108,13 @@ typedef struct pa_wavg {
     double W_absq, W_absq_pair;  /* Eq. W_conf applied to |q| */
     double w_max;                /* largest weight */
     double sum_w;                /* sum of the weights */
+    double W_e3, W_e4, W_m3, W_m4; /* Eq. W_conf applied to e^3, e^4, |m|^3, m^4 */
+    double Wk3_e, Wk4_e;         /* Eq. W_k: central moments of order 3 and 4 of e,
+                                    sum_l C(k,l) (-1)^(k-l) W[e]^(k-l) W[e^l], W[e^0] = 1 */
+    double Wk3_m, Wk4_m;         /* the same for |m| */
+    double W_U4;                 /* Binder cumulant from weighted moments, 1 - W[m^4] / (3 W[m^2]^2) */
+    double W_U4_conf;            /* Eq. W_conf applied to each run's 1 - m^4 / (3 (m^2)^2); NaN when a
+                                    run's population has M = 0 in every replica */
 } pa_wavg;
 
 typedef struct pa_engine pa_engine;

@@ -8,9 +8,11 @@ from .oracle import (  # noqa: F401
     OracleRun,
     build,
     bruteforce,
+    bruteforce_moments,
     couplings,
     dos_transfer,
     energy,
+    i128,
     kaufman_lnZ,
     load,
     metropolis_threshold,

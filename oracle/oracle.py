@@ -48,6 +48,7 @@ RECORD_DTYPE = np.dtype([
     ("sum_c2", "i8"), ("sum_absq", "i8"), ("sum_absq_pair", "i8"),
     ("R", "u4"), ("R_target", "u4"), ("n_fam", "u4"), ("max_fam", "u4"),
     ("n_q", "u4"), ("n_q_pair", "u4"), ("N", "u4"), ("status", "u4"),
+    ("sumE3", "u8", (2,)), ("sumE4", "u8", (2,)), ("sumAbsM3", "u8", (2,)), ("sumM4", "u8", (2,)),
 ])
 
 WAVG_DTYPE = np.dtype([
@@ -55,7 +56,16 @@ WAVG_DTYPE = np.dtype([
     ("Wvar_c", "f8"), ("Wvar_chi", "f8"), ("W_c", "f8"), ("W_chi", "f8"),
     ("W_minus_betaF", "f8"), ("W_absq", "f8"), ("W_absq_pair", "f8"),
     ("w_max", "f8"), ("sum_w", "f8"),
+    ("W_e3", "f8"), ("W_e4", "f8"), ("W_m3", "f8"), ("W_m4", "f8"),
+    ("Wk3_e", "f8"), ("Wk4_e", "f8"), ("Wk3_m", "f8"), ("Wk4_m", "f8"),
+    ("W_U4", "f8"), ("W_U4_conf", "f8"),
 ])
+
+
+def i128(w):
+    """A record's 128-bit sum (two uint64 words, low first, two's complement) as a Python int."""
+    v = int(w[0]) | int(w[1]) << 64
+    return v - (1 << 128) if v >> 127 else v
 
 
 def _p(a, ct):
@@ -110,6 +120,8 @@ def load():
         lib.or_bruteforce.argtypes = [u32, P(C.c_int8), P(C.c_int8), f64, P(f64), P(f64), P(f64), P(f64),
                                       P(f64), P(f64)]
         lib.or_bruteforce.restype = C.c_int
+        lib.or_bruteforce_moments.argtypes = [u32, P(C.c_int8), P(C.c_int8), f64, P(f64)]
+        lib.or_bruteforce_moments.restype = C.c_int
         lib.or_kaufman_lnZ.argtypes = [u32, f64]
         lib.or_kaufman_lnZ.restype = f64
         lib.or_dos_transfer.argtypes = [u32, P(C.c_int8), P(C.c_int8), P(C.c_uint64), P(C.c_uint64)]
@@ -178,6 +190,18 @@ def bruteforce(L, Jr, Jd, beta):
         raise ValueError("bruteforce: lattice too large")
     lnZ, e, c, m, chi = (o.value for o in out)
     return dict(lnZ=lnZ, e=e, c=c, absm=m, chi=chi, pE=pE)
+
+
+def bruteforce_moments(L, Jr, Jd, beta):
+    """Exact <e^k> and <|m|^k>, k = 1..4, by enumeration (N <= 24): two arrays of 4."""
+    lib = load()
+    out = np.zeros(8, dtype=np.float64)
+    rc = lib.or_bruteforce_moments(L, _p(np.ascontiguousarray(Jr, np.int8), C.c_int8),
+                                   _p(np.ascontiguousarray(Jd, np.int8), C.c_int8), float(beta),
+                                   _p(out, C.c_double))
+    if rc != 0:
+        raise ValueError("bruteforce_moments: lattice too large")
+    return out[:4], out[4:]
 
 
 def kaufman_lnZ(L, K):

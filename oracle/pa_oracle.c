@@ -14,7 +14,8 @@
  *   - the overlap q and index-shift pairs of Sec. III.D,
  *   - the mean-square family size rho_t of Sec. V.A.4 (Eq. rho_t),
  *   - the weighted averages of Sec. IV (Eqs. appropriateWeight, simpleWeight,
- *     W_conf, W_F, Wvar_C, Wvar_Chi, W_conf_q),
+ *     W_conf, W_F, Wvar_C, Wvar_Chi, W_conf_q), and the central-moment estimators
+ *     W_k of Sec. IV.E for k = 3, 4 with the Binder cumulant built the same way,
  * plus exact reference solvers used only to pin this oracle: brute-force
  * enumeration, Kaufman's finite-lattice partition function (Sec. V.A.3 names it as
  * the exact FM reference) and a transfer-matrix density of states.
@@ -121,7 +122,26 @@ typedef struct {
     uint32_t n_q, n_q_pair;
     uint32_t N;
     uint32_t status;
+    /* Sec. IV.E central moments need higher powers: exact sums as 128-bit two's
+     * complement integers, word 0 the low 64 bits (sum_j H_j^4 exceeds int64
+     * once L reaches 256). */
+    uint64_t sumE3[2];     /* sum_j H_j^3 */
+    uint64_t sumE4[2];     /* sum_j H_j^4 */
+    uint64_t sumAbsM3[2];  /* sum_j |M_j|^3 */
+    uint64_t sumM4[2];     /* sum_j M_j^4 */
 } or_record;
+
+static void put_i128(uint64_t w[2], __int128 v)
+{
+    unsigned __int128 u = (unsigned __int128)v;
+    w[0] = (uint64_t)u;
+    w[1] = (uint64_t)(u >> 64);
+}
+
+static __int128 get_i128(const uint64_t w[2])
+{
+    return (__int128)(((unsigned __int128)w[1] << 64) | (unsigned __int128)w[0]);
+}
 
 typedef struct {
     or_desc d;
@@ -266,13 +286,24 @@ static void measure(or_run *a, uint32_t step)
     rc->R_target = a->d.R;
     rc->N = N;
     rc->sumE = rc->sumE2 = rc->sumAbsM = rc->sumM2 = 0;
+    __int128 sE3 = 0, sE4 = 0, sAM3 = 0, sM4 = 0;
     for (uint32_t j = 0; j < R; ++j) {
         int64_t e = a->E[j], m = a->M[j];
+        int64_t am = m < 0 ? -m : m;
         rc->sumE += e;
         rc->sumE2 += e * e;
-        rc->sumAbsM += m < 0 ? -m : m;
+        rc->sumAbsM += am;
         rc->sumM2 += m * m;
+        __int128 E = e, A = am;
+        sE3 += E * E * E;
+        sE4 += E * E * E * E;
+        sAM3 += A * A * A;
+        sM4 += A * A * A * A;
     }
+    put_i128(rc->sumE3, sE3);
+    put_i128(rc->sumE4, sE4);
+    put_i128(rc->sumAbsM3, sAM3);
+    put_i128(rc->sumM4, sM4);
     /* families: runs of equal ancestor id (copies are placed contiguously) */
     rc->sum_c2 = 0;
     rc->n_fam = 0;
@@ -602,7 +633,29 @@ typedef struct {
     double W_absq, W_absq_pair;      /* Eq. W_conf applied to |q| */
     double w_max;                    /* largest weight */
     double sum_w;                    /* sum of the weights (1 up to rounding) */
+    double W_e3, W_e4, W_m3, W_m4;   /* Eq. W_conf applied to e^3, e^4, |m|^3, m^4 */
+    double Wk3_e, Wk4_e;             /* Eq. W_k, k = 3, 4, for O = e */
+    double Wk3_m, Wk4_m;             /* Eq. W_k, k = 3, 4, for O = |m| */
+    double W_U4;                     /* Binder cumulant 1 - W[m^4] / (3 W[m^2]^2) */
+    double W_U4_conf;                /* Eq. W_conf applied to each run's 1 - m^4 / (3 (m^2)^2) */
 } or_wavg;
+
+/* Eq. W_k (Sec. IV.E): the k-th central moment from the weighted raw moments
+ * Wl[l] = W[O^l], l = 0..k, Wl[0] = 1 (mu'_0 = 1), by the binomial expansion
+ *   sum_{l=0}^{k} C(k, l) (-1)^{k-l} W[O]^{k-l} W[O^l],  terms in order l = 0..k. */
+static double central_moment(int k, const double *Wl)
+{
+    double sum = 0.0;
+    for (int l = 0; l <= k; ++l) {
+        double binom = 1.0;
+        for (int t = 0; t < l; ++t) binom = binom * (double)(k - t) / (double)(t + 1);
+        double pw = 1.0;
+        for (int t = 0; t < k - l; ++t) pw = pw * Wl[1];
+        double sign = ((k - l) & 1) ? -1.0 : 1.0;
+        sum = sum + sign * binom * pw * Wl[l];
+    }
+    return sum;
+}
 
 static double log_weight(const or_record *recs, uint32_t n_steps, uint32_t m, uint32_t i, uint32_t kind)
 {
@@ -663,6 +716,15 @@ int or_weighted_average(const or_record *recs, const uint32_t *qh, const uint32_
             o->W_m2 += w[m] * m2;
             o->W_c += w[m] * c;
             o->W_chi += w[m] * chi;
+            double e3 = (double)get_i128(r->sumE3) / (Nd * Nd * Nd * Ri);
+            double e4 = (double)get_i128(r->sumE4) / (Nd * Nd * Nd * Nd * Ri);
+            double m3 = (double)get_i128(r->sumAbsM3) / (Nd * Nd * Nd * Ri);
+            double m4 = (double)get_i128(r->sumM4) / (Nd * Nd * Nd * Nd * Ri);
+            o->W_e3 += w[m] * e3;
+            o->W_e4 += w[m] * e4;
+            o->W_m3 += w[m] * m3;
+            o->W_m4 += w[m] * m4;
+            o->W_U4_conf += w[m] * (1.0 - m4 / (3.0 * m2 * m2)); /* NaN if a run has M = 0 throughout */
             if (r->n_q) o->W_absq += w[m] * ((double)r->sum_absq / (Nd * (double)r->n_q));
             if (r->n_q_pair) o->W_absq_pair += w[m] * ((double)r->sum_absq_pair / (Nd * (double)r->n_q_pair));
             o->sum_w += w[m];
@@ -670,6 +732,15 @@ int or_weighted_average(const or_record *recs, const uint32_t *qh, const uint32_
         }
         o->Wvar_c = beta * beta * Nd * (o->W_e2 - o->W_e * o->W_e);
         o->Wvar_chi = beta * Nd * (o->W_m2 - o->W_m * o->W_m);
+        {
+            double We[5] = {1.0, o->W_e, o->W_e2, o->W_e3, o->W_e4};
+            double Wm[5] = {1.0, o->W_m, o->W_m2, o->W_m3, o->W_m4};
+            o->Wk3_e = central_moment(3, We);
+            o->Wk4_e = central_moment(4, We);
+            o->Wk3_m = central_moment(3, Wm);
+            o->Wk4_m = central_moment(4, Wm);
+            o->W_U4 = 1.0 - o->W_m4 / (3.0 * o->W_m2 * o->W_m2);
+        }
         /* Eq. W_F: -beta_i W[F_i] = sum_{k<=i} ln W[Q_k] + ln Z(0), W[Q_k] = sum_m w_{k-1} Q_k */
         if (i > 0) {
             double lm = -INFINITY;
@@ -760,6 +831,44 @@ int or_bruteforce(uint32_t L, const int8_t *Jr, const int8_t *Jd, double beta, d
     if (pE && pl)
         for (uint32_t n = 0; n <= N; ++n) pE[n] = (double)(pl[n] / Z);
     free(pl);
+    return OR_OK;
+}
+
+/* Brute-force enumeration of the Boltzmann moments that the central-moment and
+ * Binder estimators of Sec. IV.E target: out[k-1] = <e^k>, out[3+k] = <|m|^k>
+ * for k = 1..4 (e = H/N, m = M/N), in long double.  N <= 24. */
+int or_bruteforce_moments(uint32_t L, const int8_t *Jr, const int8_t *Jd, double beta, double out[8])
+{
+    uint32_t N = L * L;
+    if (N > 24) return OR_ERR_INVALID;
+    int8_t s[24];
+    int64_t Elo = INT64_MAX;
+    for (uint64_t st = 0; st < ((uint64_t)1 << N); ++st) {
+        for (uint32_t i = 0; i < N; ++i) s[i] = (st >> i) & 1u ? 1 : -1;
+        int64_t E = or_energy(L, s, Jr, Jd);
+        if (E < Elo) Elo = E;
+    }
+    long double Z = 0, se[4] = {0, 0, 0, 0}, sm[4] = {0, 0, 0, 0};
+    long double Nl = (long double)N;
+    for (uint64_t st = 0; st < ((uint64_t)1 << N); ++st) {
+        for (uint32_t i = 0; i < N; ++i) s[i] = (st >> i) & 1u ? 1 : -1;
+        int64_t E = or_energy(L, s, Jr, Jd);
+        int64_t Mg = or_magnetisation(N, s);
+        long double b = expl(-(long double)beta * (long double)(E - Elo));
+        long double e = (long double)E / Nl, am = (long double)(Mg < 0 ? -Mg : Mg) / Nl;
+        long double pe = 1, pm = 1;
+        Z += b;
+        for (int k = 0; k < 4; ++k) {
+            pe *= e;
+            pm *= am;
+            se[k] += b * pe;
+            sm[k] += b * pm;
+        }
+    }
+    for (int k = 0; k < 4; ++k) {
+        out[k] = (double)(se[k] / Z);
+        out[4 + k] = (double)(sm[k] / Z);
+    }
     return OR_OK;
 }
 

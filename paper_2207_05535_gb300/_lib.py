@@ -45,6 +45,7 @@ RECORD_DTYPE = np.dtype([
     ("sum_c2", "i8"), ("sum_absq", "i8"), ("sum_absq_pair", "i8"),
     ("R", "u4"), ("R_target", "u4"), ("n_fam", "u4"), ("max_fam", "u4"),
     ("n_q", "u4"), ("n_q_pair", "u4"), ("N", "u4"), ("status", "u4"),
+    ("sumE3", "u8", (2,)), ("sumE4", "u8", (2,)), ("sumAbsM3", "u8", (2,)), ("sumM4", "u8", (2,)),
 ])
 
 WAVG_DTYPE = np.dtype([
@@ -52,6 +53,9 @@ WAVG_DTYPE = np.dtype([
     ("Wvar_c", "f8"), ("Wvar_chi", "f8"), ("W_c", "f8"), ("W_chi", "f8"),
     ("W_minus_betaF", "f8"), ("W_absq", "f8"), ("W_absq_pair", "f8"),
     ("w_max", "f8"), ("sum_w", "f8"),
+    ("W_e3", "f8"), ("W_e4", "f8"), ("W_m3", "f8"), ("W_m4", "f8"),
+    ("Wk3_e", "f8"), ("Wk4_e", "f8"), ("Wk3_m", "f8"), ("Wk4_m", "f8"),
+    ("W_U4", "f8"), ("W_U4_conf", "f8"),
 ])
 
 EXPORTS = ["pa_create", "pa_create_ex", "pa_server_create", "pa_admit", "pa_retire", "pa_finished", "pa_run_state",

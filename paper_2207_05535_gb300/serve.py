@@ -29,7 +29,7 @@ def config_for_budget(budget_bytes: int, max_runs: int = 4096, max_L: int = 64, 
     words_per_replica = 2 * math.ceil(mean_L2 / 64) + 2       # spin stride incl. rounding
     bytes_per_replica = 2 * 4 * words_per_replica + 6 * 4 + 2 * 4 + 4  # spins x2, E/M/fam x2, parent, cnt, scratch
     N_max = max_L * max_L
-    per_run_fixed = (112 * max_n_beta + 8 * 2 * (N_max + 1) + 4 * (2 * (2 * math.ceil(N_max / 64) + 4)
+    per_run_fixed = (176 * max_n_beta + 8 * 2 * (N_max + 1) + 4 * (2 * (2 * math.ceil(N_max / 64) + 4)
                      + 8 * math.ceil(N_max / 64)) + 8 * 4 * max_n_beta)
     rest = budget_bytes - table_bytes - max_runs * per_run_fixed
     if rest <= 0:
