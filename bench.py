@@ -58,7 +58,7 @@ WORKLOAD = WORKLOADS["glass_L16_R5000"]
 ALGO_MULADD_PER_UPDATE = 10.0
 # DRAM bytes per sweep launch from one ncu capture (profiles/sweep_pow2_glass_L16_R5000.md),
 # valid only for the kernel source it was taken on.
-SWEEP_TRAFFIC = {"kernels_sha256_16": "1731982756b93843", "workload": "glass_L16_R5000", "bytes_per_launch": 44.954624e6}
+SWEEP_TRAFFIC = {"sweep_source_sha256_16": "1705e80b5cd49b74", "workload": "glass_L16_R5000", "bytes_per_launch": 45.043456e6}
 MULADD_LANES_PER_SM = 64
 
 
@@ -176,12 +176,22 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def sweep_traffic(wl):
-    """Measured DRAM bytes per sweep launch, or None when the kernels changed since."""
+def sweep_source_sha():
+    """Hash of the source the sweep kernels compile from: the shared header and
+    the part of the kernel file before the overlap and measurement kernels."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2207_05535_gb300", "csrc", "pa_kernels.cu"), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    if sha == SWEEP_TRAFFIC["kernels_sha256_16"] and wl == SWEEP_TRAFFIC["workload"]:
+    csrc = os.path.join(ROOT, "paper_2207_05535_gb300", "csrc")
+    with open(os.path.join(csrc, "pa_internal.cuh"), "rb") as f:
+        head = f.read()
+    with open(os.path.join(csrc, "pa_kernels.cu"), "rb") as f:
+        body = f.read()
+    cut = body.find(b"// Overlaps (Sec. III.D)")
+    return hashlib.sha256(head + body[:cut]).hexdigest()[:16]
+
+
+def sweep_traffic(wl):
+    """Measured DRAM bytes per sweep launch, or None when the sweep source changed since."""
+    if sweep_source_sha() == SWEEP_TRAFFIC["sweep_source_sha256_16"] and wl == SWEEP_TRAFFIC["workload"]:
         return SWEEP_TRAFFIC["bytes_per_launch"]
     return None
 

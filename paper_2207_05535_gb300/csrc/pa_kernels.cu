@@ -12,7 +12,7 @@
 //                    thresholds (Sec. V.A.1), packed and written back
 //   overlap_kernel   XOR + popcount overlaps of index-shift pairs j <-> j+floor(R/2)
 //                    and of pairs with a partner population (Sec. III.D)
-//   measure_kernel   integer reductions of E, E^2, |M|, M^2, family statistics
+//   measure_kernel   integer reductions of E^k, |M|^k (k <= 4; 128-bit for k >= 3), family statistics
 //                    (Eq. rho_t) and the free-energy running sum (Eq. F)
 // Nothing here allocates memory; no spin-wait exists in any kernel.
 //
@@ -1145,11 +1145,55 @@ __global__ void overlap_kernel(Pool P, const uint32_t *q_runs, int init)
 // Measurement (Sec. III.B, Eqs. e, m, c, chi through exact integer sums;
 // Eq. F running sum; Eq. rho_t through family run lengths).  Finishes the step.
 // --------------------------------------------------------------------------
+// 128-bit two's-complement integer, lo the low 64 bits: exact sums of the
+// third and fourth powers of energies and magnetisations (Sec. IV.E).
+struct I128 {
+    unsigned long long lo;
+    long long hi;
+};
+
+__device__ __forceinline__ void add128(I128 &a, unsigned long long lo, long long hi)
+{
+    const unsigned long long s = a.lo + lo;
+    a.hi += hi + (s < lo ? 1ll : 0ll);
+    a.lo = s;
+}
+
+__device__ __forceinline__ void add128_signed(I128 &a, long long v) { add128(a, (unsigned long long)v, v >> 63); }
+
+// a += v * v for 0 <= v < 2^63 (full 128-bit product)
+__device__ __forceinline__ void add128_square(I128 &a, unsigned long long v)
+{
+    add128(a, v * v, (long long)__umul64hi(v, v));
+}
+
+// Per-warp partial results of the measurement: moment sums and the family
+// run statistics of one contiguous chunk of replicas.
+struct MeasurePart {
+    long long sE, sE2, sAM, sM2, c2;
+    I128 sE3, sE4, sAM3, sM4;
+    uint32_t nfam, cmax, lead, trail, len;
+};
+
+__device__ __forceinline__ I128 warp_sum128(I128 v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long lo = __shfl_xor_sync(FULL, v.lo, o);
+        const long long hi = __shfl_xor_sync(FULL, v.hi, o);
+        add128(v, lo, hi);
+    }
+    return v;
+}
+
+// Each warp takes a contiguous chunk of the R_i replicas.  Families are
+// contiguous runs of equal ancestor id; inside a chunk a warp-wide inclusive
+// max-scan of run starts gives every replica its run start (the chunk's first
+// replica is treated as a start), and thread 0 then joins the runs that cross
+// chunk boundaries: pieces a and b of one family counted as a^2 + b^2 gain 2ab.
 __global__ void __launch_bounds__(512) measure_kernel(Pool P, const uint32_t *runs, int init)
 {
-    __shared__ long long sh_l[32];
-    __shared__ uint32_t sh_u[33];
-    __shared__ uint32_t sh_carry;
+    __shared__ MeasurePart part[16];  // launched with 512 threads: 16 warps
     const uint32_t run = runs ? runs[blockIdx.x] : blockIdx.x;
     const RunDev rd = P.runs[run];
     RunState *st = &P.st[run];
@@ -1161,68 +1205,148 @@ __global__ void __launch_bounds__(512) measure_kernel(Pool P, const uint32_t *ru
     const int32_t *E = P.E[b] + rd.rep_off;
     const int32_t *M = P.M[b] + rd.rep_off;
     const uint32_t *fam = P.fam[b] + rd.rep_off;
-    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t chunk = (R + nw - 1) / nw;
+    const uint32_t lo = min(R, wid * chunk), hi = min(R, lo + chunk);
 
-    long long sE = 0, sE2 = 0, sAM = 0, sM2 = 0;
-    for (uint32_t j = tid; j < R; j += nt) {
-        const long long e = E[j], m = M[j];
-        sE += e;
-        sE2 += e * e;
-        sAM += m < 0 ? -m : m;
-        sM2 += m * m;
-    }
-    sE = block_sum(sE, sh_l);
-    sE2 = block_sum(sE2, sh_l);
-    sAM = block_sum(sAM, sh_l);
-    sM2 = block_sum(sM2, sh_l);
-
-    // families are contiguous: start(j) = last index <= j where the ancestor changes
-    long long c2 = 0;
-    uint32_t nfam = 0, cmax = 0;
-    if (tid == 0) sh_carry = 0;
-    __syncthreads();
-    for (uint32_t base = 0; base < R; base += nt) {
-        const uint32_t j = base + tid;
-        const bool ok = j < R;
-        const bool flag = ok && (j == 0 || fam[j] != fam[j - 1]);
-        uint32_t sj = block_inclusive_max(flag ? j : 0u, sh_u);
-        const uint32_t carry = sh_carry;
-        sj = sj > carry ? sj : carry;
+    long long sE = 0, sE2 = 0, sAM = 0, sM2 = 0, c2 = 0;
+    I128 sE3 = {0ull, 0ll}, sE4 = {0ull, 0ll}, sAM3 = {0ull, 0ll}, sM4 = {0ull, 0ll};
+    uint32_t nfam = 0, cmax = 0, first = hi, open = lo;
+    for (uint32_t base = lo; base < hi; base += 32) {
+        const uint32_t j = base + lane;
+        const bool ok = j < hi;
+        bool start = false, forced = false;
         if (ok) {
-            const uint32_t len = j - sj + 1;
-            c2 += 2 * (long long)(j - sj) + 1;  // sum over a family of (2r + 1) = size^2
-            nfam += flag ? 1u : 0u;
-            cmax = len > cmax ? len : cmax;
+            const long long e = E[j], m = M[j];
+            const long long am = m < 0 ? -m : m;
+            const long long e2 = e * e, m2 = m * m;  // |E| <= 2N = 2^17, |M| <= 2^16
+            sE += e;
+            sE2 += e2;
+            sAM += am;
+            sM2 += m2;
+            add128_signed(sE3, e2 * e);
+            add128_square(sE4, (unsigned long long)e2);
+            add128_signed(sAM3, m2 * am);
+            add128_square(sM4, (unsigned long long)m2);
+            start = j == 0 || fam[j] != fam[j - 1];
+            forced = start || j == lo;
         }
-        __syncthreads();
-        if (tid == nt - 1) sh_carry = sj;
-        __syncthreads();
+        uint32_t sj = forced ? j : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, sj, o);
+            if ((int)lane >= o) sj = y > sj ? y : sj;
+        }
+        sj = sj > open ? sj : open;
+        if (ok) {
+            c2 += 2 * (long long)(j - sj) + 1;  // sum over a run of (2r + 1) = length^2
+            nfam += start ? 1u : 0u;
+            cmax = j - sj + 1 > cmax ? j - sj + 1 : cmax;
+            first = start && j < first ? j : first;
+        }
+        open = __shfl_sync(FULL, sj, 31);
     }
-    c2 = block_sum(c2, sh_l);
-    nfam = (uint32_t)block_sum((long long)nfam, sh_l);
-    cmax = (uint32_t)block_max((long long)cmax, sh_l, 0ll);
+    MeasurePart w;
+    w.sE = warp_sum(sE);
+    w.sE2 = warp_sum(sE2);
+    w.sAM = warp_sum(sAM);
+    w.sM2 = warp_sum(sM2);
+    w.c2 = warp_sum(c2);
+    w.sE3 = warp_sum128(sE3);
+    w.sE4 = warp_sum128(sE4);
+    w.sAM3 = warp_sum128(sAM3);
+    w.sM4 = warp_sum128(sM4);
+    w.nfam = warp_sum(nfam);
+    w.cmax = warp_max(cmax);
+    w.lead = warp_min(first) - lo;  // replicas continuing the previous chunk's family
+    w.trail = hi - open;            // length of the chunk's last run
+    w.len = hi - lo;
+    if (lane == 0) part[wid] = w;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
 
-    if (tid == 0) {
-        pa_step_record *rec = P.rec + rd.rec_off + i;
-        const double lnQ = init ? 0.0 : st->lnQ;
-        rec->beta = P.beta[rd.beta_off + i];
-        rec->lnQ = lnQ;
-        rec->minus_betaF = init ? rd.ln2N : P.rec[rd.rec_off + i - 1].minus_betaF + lnQ;
-        rec->sumE = sE;
-        rec->sumE2 = sE2;
-        rec->sumAbsM = sAM;
-        rec->sumM2 = sM2;
-        rec->sum_c2 = c2;
-        rec->R = R;
-        rec->R_target = rd.R;
-        rec->n_fam = nfam;
-        rec->max_fam = cmax;
-        rec->N = rd.N;
-        rec->status = 0;
-        st->step = i;
-        st->R_cur = R;
-        st->R_new = R;
+    MeasurePart t = part[0];
+    uint32_t run_open = t.trail;
+    for (uint32_t k = 1; k < nw; ++k) {
+        const MeasurePart &q = part[k];
+        if (q.len == 0) continue;
+        t.sE += q.sE;
+        t.sE2 += q.sE2;
+        t.sAM += q.sAM;
+        t.sM2 += q.sM2;
+        t.c2 += q.c2;
+        add128(t.sE3, q.sE3.lo, q.sE3.hi);
+        add128(t.sE4, q.sE4.lo, q.sE4.hi);
+        add128(t.sAM3, q.sAM3.lo, q.sAM3.hi);
+        add128(t.sM4, q.sM4.lo, q.sM4.hi);
+        t.nfam += q.nfam;
+        t.cmax = q.cmax > t.cmax ? q.cmax : t.cmax;
+        if (q.lead > 0) {  // the family open at the end of the previous chunks continues
+            t.c2 += 2 * (long long)run_open * q.lead;
+            const uint32_t merged = run_open + q.lead;
+            t.cmax = merged > t.cmax ? merged : t.cmax;
+            run_open = q.lead == q.len ? merged : q.trail;
+        } else {
+            run_open = q.trail;
+        }
     }
+
+    pa_step_record *rec = P.rec + rd.rec_off + i;
+    const double lnQ = init ? 0.0 : st->lnQ;
+    rec->beta = P.beta[rd.beta_off + i];
+    rec->lnQ = lnQ;
+    rec->minus_betaF = init ? rd.ln2N : P.rec[rd.rec_off + i - 1].minus_betaF + lnQ;
+    rec->sumE = t.sE;
+    rec->sumE2 = t.sE2;
+    rec->sumAbsM = t.sAM;
+    rec->sumM2 = t.sM2;
+    rec->sum_c2 = t.c2;
+    rec->sumE3[0] = t.sE3.lo;
+    rec->sumE3[1] = (unsigned long long)t.sE3.hi;
+    rec->sumE4[0] = t.sE4.lo;
+    rec->sumE4[1] = (unsigned long long)t.sE4.hi;
+    rec->sumAbsM3[0] = t.sAM3.lo;
+    rec->sumAbsM3[1] = (unsigned long long)t.sAM3.hi;
+    rec->sumM4[0] = t.sM4.lo;
+    rec->sumM4[1] = (unsigned long long)t.sM4.hi;
+    rec->R = R;
+    rec->R_target = rd.R;
+    rec->n_fam = t.nfam;
+    rec->max_fam = t.cmax;
+    rec->N = rd.N;
+    rec->status = 0;
+    st->step = i;
+    st->R_cur = R;
+    st->R_new = R;
+}
+
+// A record's 128-bit sum as a double: sign and magnitude, then hi 2^64 + lo
+// (hi < 2^53, so at most two roundings).
+__device__ __forceinline__ double i128_to_double(const uint64_t *w)
+{
+    unsigned long long lo = w[0], hi = w[1];
+    const bool neg = (long long)hi < 0;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    const double v = (double)hi * 18446744073709551616.0 + (double)lo;
+    return neg ? -v : v;
+}
+
+// Eq. W_k (Sec. IV.E): k-th central moment from weighted raw moments
+// raw[l] = W[O^l] (raw[0] = 1) by the binomial expansion, terms l = 0..k.
+__device__ __forceinline__ double central_from_raw(int k, const double *raw)
+{
+    double acc = 0.0, binom = 1.0;
+    for (int l = 0; l <= k; ++l) {
+        double p = 1.0;
+        for (int t = l; t < k; ++t) p = p * raw[1];
+        const double term = binom * p * raw[l];
+        acc = acc + (((k - l) & 1) ? -term : term);
+        binom = binom * (double)(k - l) / (double)(l + 1);
+    }
+    return acc;
 }
 
 // --------------------------------------------------------------------------
@@ -1263,7 +1387,8 @@ __global__ void __launch_bounds__(64) wavg_kernel(const pa_step_record *recs, co
         z = warp_sum(z);
         const double beta = recs[off[0] + i].beta;
         double se = 0.0, se2 = 0.0, sm = 0.0, sm2 = 0.0, sc = 0.0, schi = 0.0, sq = 0.0, sqp = 0.0, sw = 0.0,
-               wmax = 0.0;
+               wmax = 0.0, se3 = 0.0, se4 = 0.0, sm3 = 0.0, sm4 = 0.0, su4 = 0.0;
+        const double N3 = Nd * Nd * Nd, N4 = N3 * Nd;
         for (uint32_t m = lane; m < M; m += 32) {
             wi[m] = wi[m] / z;
             const pa_step_record *r = recs + off[m] + i;
@@ -1283,6 +1408,15 @@ __global__ void __launch_bounds__(64) wavg_kernel(const pa_step_record *recs, co
             schi += wm * chi;
             if (r->n_q) sq += wm * ((double)r->sum_absq / (Nd * (double)r->n_q));
             if (r->n_q_pair) sqp += wm * ((double)r->sum_absq_pair / (Nd * (double)r->n_q_pair));
+            const double e3 = i128_to_double(r->sumE3) / (N3 * Ri);
+            const double e4 = i128_to_double(r->sumE4) / (N4 * Ri);
+            const double m3 = i128_to_double(r->sumAbsM3) / (N3 * Ri);
+            const double m4 = i128_to_double(r->sumM4) / (N4 * Ri);
+            se3 += wm * e3;
+            se4 += wm * e4;
+            sm3 += wm * m3;
+            sm4 += wm * m4;
+            su4 += wm * (1.0 - m4 / (3.0 * m2 * m2));  // per-run Binder cumulant
             sw += wm;
             wmax = wm > wmax ? wm : wmax;
         }
@@ -1300,6 +1434,20 @@ __global__ void __launch_bounds__(64) wavg_kernel(const pa_step_record *recs, co
         o.w_max = warp_max(wmax);
         o.Wvar_c = beta * beta * Nd * (o.W_e2 - o.W_e * o.W_e);
         o.Wvar_chi = beta * Nd * (o.W_m2 - o.W_m * o.W_m);
+        o.W_e3 = warp_sum(se3);
+        o.W_e4 = warp_sum(se4);
+        o.W_m3 = warp_sum(sm3);
+        o.W_m4 = warp_sum(sm4);
+        o.W_U4_conf = warp_sum(su4);
+        {
+            const double re[5] = {1.0, o.W_e, o.W_e2, o.W_e3, o.W_e4};
+            const double rm[5] = {1.0, o.W_m, o.W_m2, o.W_m3, o.W_m4};
+            o.Wk3_e = central_from_raw(3, re);
+            o.Wk4_e = central_from_raw(4, re);
+            o.Wk3_m = central_from_raw(3, rm);
+            o.Wk4_m = central_from_raw(4, rm);
+            o.W_U4 = 1.0 - o.W_m4 / (3.0 * o.W_m2 * o.W_m2);
+        }
         if (i > 0) {  // Eq. W_F: W[Q_i] = sum_m w_{i-1} Q_i, as a log-sum-exp
             const double *wp = wi - M;
             double lm = -INFINITY;

@@ -11,7 +11,7 @@ import pytest
 import oracle as O
 from paper_2207_05535_gb300 import _lib
 from paper_2207_05535_gb300 import workloads as W
-from tests.helpers import compare_records, oracle_runs
+from tests.helpers import compare_records, oracle_runs, wavg_close
 
 pytestmark = pytest.mark.gpu
 
@@ -143,13 +143,7 @@ def test_capacity_overflow_is_reported_not_written():
 
 # ------------------------------------------------------------------ weighted averages
 def _wavg_close(g, o):
-    for f in _lib.WAVG_DTYPE.names:
-        scale = np.maximum(np.abs(o[f]), 1e-300)
-        if f in ("Wvar_c", "Wvar_chi", "W_c", "W_chi"):
-            # differences of O(1) terms: relative to the terms combined
-            scale = np.maximum(scale, np.abs(o["beta"]) ** 2 * 64 * (np.abs(o["W_e2"]) + np.abs(o["W_m2"])) + 1e-300)
-        err = np.abs(g[f] - o[f]) / scale
-        assert np.all(err <= 1e-12), (f, err.max())
+    wavg_close(g, o, _lib.WAVG_DTYPE.names)
 
 
 def test_weighted_averages_from_host_records():

@@ -64,7 +64,8 @@ def test_server_results_equal_alone_and_oracle():
         o = O.OracleRun.from_desc(d)
         o.run_to_end()
         orec = o.records()
-        for f in ("sumE", "sumE2", "sumAbsM", "sumM2", "sum_c2", "sum_absq", "R", "n_fam", "max_fam", "n_q"):
+        for f in ("sumE", "sumE2", "sumAbsM", "sumM2", "sumE3", "sumE4", "sumAbsM3", "sumM4", "sum_c2", "sum_absq", "R",
+                  "n_fam", "max_fam", "n_q"):
             assert np.array_equal(got[k][f], orec[f]), (k, f)
         assert np.allclose(got[k]["minus_betaF"], orec["minus_betaF"], rtol=1e-12, atol=0)
 
