@@ -52,13 +52,21 @@ enum { PA_NEAREST = 0, PA_MULTINOMIAL = 1 };   /* resampling of Sec. II.B step (
 enum { PA_Q_NONE = 0, PA_Q_SHIFT = 1, PA_Q_PAIR = 2 }; /* overlap pairs of Sec. III.D (bit flags) */
 enum { PA_WEIGHT_FULL = 0, PA_WEIGHT_SIMPLE = 1 };     /* Eq. appropriateWeight / Eq. simpleWeight */
 
+/* theta = PA_THETA_INF: the theta -> infinity limit of Sec. V.B.  Step (iv)'s
+ * Metropolis sweeps are replaced by simple sampling of the exact energy
+ * distribution P_beta(E) = g(E) exp(-beta E) / Z(beta) from the density of
+ * states the descriptor supplies (log_g); every replica gets a fresh energy at
+ * each temperature (and at beta_0).  Spins are not represented (all -1 in
+ * pa_population) and M = 0; overlaps are not available. */
+#define PA_THETA_INF 0xFFFFFFFFu
+
 /* One PA run (Sec. II.B): caller-owned, copied by pa_create. */
 typedef struct pa_run_desc {
     uint32_t L;           /* linear lattice size, even, 4 <= L <= 256; N = L*L sites, periodic */
     uint32_t model;       /* PA_FERRO or PA_EA_PMJ */
     uint32_t R;           /* target population size R (Sec. II.B step (i)), >= 1 */
     uint32_t R_cap;       /* capacity (>= R); 0 = R + 8 ceil(sqrt R) + 64 (R for multinomial) */
-    uint32_t theta;       /* Metropolis sweeps per temperature (Sec. V.A.1) */
+    uint32_t theta;       /* Metropolis sweeps per temperature (Sec. V.A.1), <= 2^22, or PA_THETA_INF */
     uint32_t n_beta;      /* number of temperatures, >= 1 */
     const double *beta;   /* host, n_beta entries, non-decreasing; beta[0] = 0 gives absolute F */
     uint32_t seed;        /* Philox key word 0 */
@@ -68,6 +76,9 @@ typedef struct pa_run_desc {
     uint32_t overlap;     /* PA_Q_* flags */
     int32_t paired;       /* with PA_Q_PAIR: index (in this pa_create call) of the partner run, else -1 */
     uint32_t reserved;    /* must be 0 */
+    const double *log_g;  /* theta = PA_THETA_INF: host, 2N+1 entries, ln g(E) of the exact density of
+                             states at E = 2u - 2N, u = 0..2N (-INFINITY where g(E) = 0; no NaN or
+                             +INFINITY); read at admission.  Ignored (may be NULL) otherwise. */
 } pa_run_desc;
 
 /* Per-temperature record of one run (Sec. III.B-D, Eq. rho_t).  Integer sums

@@ -21,4 +21,5 @@ from .oracle import (  # noqa: F401
     weighted_average,
     RECORD_DTYPE,
     WAVG_DTYPE,
+    THETA_INF,
 )

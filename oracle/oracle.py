@@ -39,7 +39,10 @@ class Desc(C.Structure):
     _fields_ = [("L", C.c_uint32), ("model", C.c_uint32), ("R", C.c_uint32), ("R_cap", C.c_uint32),
                 ("theta", C.c_uint32), ("n_beta", C.c_uint32), ("beta", C.POINTER(C.c_double)),
                 ("seed", C.c_uint32), ("run_id", C.c_uint32), ("disorder_id", C.c_uint32),
-                ("resample", C.c_uint32), ("overlap", C.c_uint32)]
+                ("resample", C.c_uint32), ("overlap", C.c_uint32), ("log_g", C.POINTER(C.c_double))]
+
+
+THETA_INF = 0xFFFFFFFF  # theta = infinity: energies drawn from the exact distribution (needs log_g)
 
 
 RECORD_DTYPE = np.dtype([
@@ -225,13 +228,15 @@ def dos_transfer(L, Jr, Jd):
 class OracleRun:
     """One PA run of the oracle (steps (i)-(vi) of Sec. II.B)."""
 
-    def __init__(self, L, model, R, R_cap, theta, betas, seed, run_id, disorder_id, resample=0, overlap=0):
+    def __init__(self, L, model, R, R_cap, theta, betas, seed, run_id, disorder_id, resample=0, overlap=0,
+                 log_g=None):
         self.lib = load()
         self.betas = np.ascontiguousarray(betas, dtype=np.float64)
         self.L, self.N = L, L * L
         self.n_beta = len(self.betas)
+        self.log_g = None if log_g is None else np.ascontiguousarray(log_g, dtype=np.float64)
         d = Desc(L, model, R, R_cap, theta, self.n_beta, _p(self.betas, C.c_double), seed, run_id, disorder_id,
-                 resample, overlap)
+                 resample, overlap, _p(self.log_g, C.c_double))
         st = C.c_int(0)
         self.h = self.lib.or_create(C.byref(d), C.byref(st))
         if not self.h:
@@ -240,7 +245,7 @@ class OracleRun:
     @classmethod
     def from_desc(cls, desc):
         return cls(desc.L, desc.model, desc.R, desc.R_cap, desc.theta, desc.betas, desc.seed, desc.run_id,
-                   desc.disorder_id, desc.resample, desc.overlap)
+                   desc.disorder_id, desc.resample, desc.overlap, getattr(desc, "log_g", None))
 
     def __del__(self):
         h = getattr(self, "h", None)

@@ -32,6 +32,8 @@
  *   multinomial draw d             : ctr (d, 0, step, MULTINOMIAL<<24),     words 0,1 (level), 2 (member)
  *   Metropolis at site with sublattice index k, child j, sweep t, colour c:
  *                                    ctr (k>>2, j, step, SWEEP<<24 | t<<1 | c), word k&3
+ *   energy draw of replica j (theta = infinity, Sec. V.B):
+ *                                    ctr (j, 0, step, DOS<<24),               words 0,1
  * Build with -ffp-contract=off: no fused multiply-add anywhere in the FP64 paths.
  */
 #include <math.h>
@@ -44,6 +46,8 @@
 #define OR_TAG_RESAMPLE 3u
 #define OR_TAG_MULTINOMIAL 4u
 #define OR_TAG_DISORDER 5u
+#define OR_TAG_DOS 6u
+#define OR_THETA_INF 0xFFFFFFFFu /* theta = infinity: simple sampling of the exact energy distribution */
 
 #define OR_OK 0
 #define OR_ERR_INVALID 1
@@ -105,6 +109,7 @@ typedef struct {
     uint32_t seed, run_id, disorder_id;
     uint32_t resample;     /* 0 = nearest integer, 1 = multinomial */
     uint32_t overlap;      /* bit 0: index-shift q; bit 1: q against a paired run */
+    const double *log_g;   /* theta = OR_THETA_INF: ln g(E) at E = 2u - 2N, u = 0..2N (-INFINITY where g = 0) */
 } or_desc;
 
 /* Per-temperature record (one per step i = 0..n_beta-1). */
@@ -385,10 +390,76 @@ static void free_run(or_run *a)
 
 void or_destroy(or_run *a) { free_run(a); }
 
+/* ------------------------------------------------------------------------- */
+/* theta = infinity (Sec. V.B): step (iv) replaced by simple sampling of the  */
+/* exact energy distribution P_beta(E) = g(E) exp(-beta E) / Z(beta).         */
+/* ------------------------------------------------------------------------- */
+/* Cumulative weights over the levels u = 0..2N (E = 2u - 2N) in ascending order,
+ *   C[u] = sum_{v <= u} exp(ln g(v) - beta E(v) - c),  c = max_v (ln g(v) - beta E(v)),
+ * with exp(-inf) = 0 where g = 0.  Returns the last level with a positive weight. */
+static uint32_t dos_cdf(const or_run *a, double beta, double *C)
+{
+    uint32_t U = 2 * a->N;
+    double c = -INFINITY;
+    for (uint32_t u = 0; u <= U; ++u)
+        if (a->d.log_g[u] > -INFINITY) {
+            double l = a->d.log_g[u] - beta * (double)(2 * (int64_t)u - 2 * (int64_t)a->N);
+            if (l > c) c = l;
+        }
+    double acc = 0.0;
+    uint32_t last = 0;
+    for (uint32_t u = 0; u <= U; ++u) {
+        double p = 0.0;
+        if (a->d.log_g[u] > -INFINITY) {
+            double l = a->d.log_g[u] - beta * (double)(2 * (int64_t)u - 2 * (int64_t)a->N);
+            p = exp(l - c);
+        }
+        acc = acc + p;
+        C[u] = acc;
+        if (p > 0.0) last = u;
+    }
+    return last;
+}
+
+/* One energy from P_beta: the first level u with x < C[u], x a 53-bit uniform
+ * (words 0 and 1 of the replica's draw) times C[2N]; the last positive level if x
+ * rounds up to C[2N]. */
+static int32_t dos_draw(const or_run *a, const double *C, uint32_t last, uint32_t step, uint32_t j)
+{
+    uint32_t U = 2 * a->N;
+    uint32_t ctr[4] = {j, 0, step, OR_TAG_DOS << 24}, key[2] = {a->d.seed, a->d.run_id}, o[4];
+    or_philox4x32_10(ctr, key, o);
+    uint64_t u53 = ((uint64_t)(o[0] >> 5) << 26) | (uint64_t)(o[1] >> 6);
+    double x = (double)u53 * (1.0 / 9007199254740992.0) * C[U];
+    uint32_t lev = last;
+    for (uint32_t u = 0; u <= U; ++u)
+        if (x < C[u]) {
+            lev = u;
+            break;
+        }
+    return (int32_t)(2 * (int64_t)lev - 2 * (int64_t)a->N);
+}
+
+/* Fresh energies for replicas 0..R-1 at beta_step; their spins are not
+ * represented (left at -1) and M = 0. */
+static int dos_resample_energies(or_run *a, uint32_t step, uint32_t R)
+{
+    double *C = (double *)malloc(sizeof(double) * (2 * a->N + 1));
+    if (!C) return OR_ERR_OOM;
+    uint32_t last = dos_cdf(a, a->beta[step], C);
+    for (uint32_t j = 0; j < R; ++j) {
+        a->E[j] = dos_draw(a, C, last, step, j);
+        a->M[j] = 0;
+    }
+    free(C);
+    return OR_OK;
+}
+
 or_run *or_create(const or_desc *d, int *status)
 {
     *status = OR_ERR_INVALID;
     if (d->L < 4 || (d->L & 1u) || d->R < 1 || d->R_cap < d->R || d->n_beta < 1 || !d->beta) return NULL;
+    if (d->theta == OR_THETA_INF && (!d->log_g || d->overlap)) return NULL;
     for (uint32_t i = 1; i < d->n_beta; ++i)
         if (!(d->beta[i] >= d->beta[i - 1])) return NULL;
     or_run *a = (or_run *)calloc(1, sizeof(or_run));
@@ -424,7 +495,18 @@ or_run *or_create(const or_desc *d, int *status)
     memcpy(a->beta, d->beta, sizeof(double) * d->n_beta);
     a->d.beta = a->beta;
     or_couplings(a->L, d->model, d->seed, d->disorder_id, a->Jr, a->Jd);
-    for (uint32_t j = 0; j < d->R; ++j) {
+    if (d->theta == OR_THETA_INF) {
+        /* beta_0 = 0 population as energies drawn from g(E) / 2^N */
+        memset(a->s, -1, (size_t)C * N);
+        memset(a->s_tmp, -1, (size_t)C * N);
+        if (dos_resample_energies(a, 0, d->R) != OR_OK) {
+            free_run(a);
+            *status = OR_ERR_OOM;
+            return NULL;
+        }
+        for (uint32_t j = 0; j < d->R; ++j) a->fam[j] = j;
+    }
+    for (uint32_t j = 0; j < d->R && d->theta != OR_THETA_INF; ++j) {
         int8_t *s = a->s + (size_t)j * N;
         for (uint32_t i = 0; i < N; ++i) {
             uint32_t w = philox_word(d->seed, d->run_id, i >> 2, j, 0, OR_TAG_INIT << 24, i & 3);
@@ -583,8 +665,13 @@ int or_step(or_run *a)
     a->R_cur = Rnew;
     a->step = i;
 
-    /* Step (iv): theta Metropolis sweeps at beta_i for every replica */
-    for (uint32_t j = 0; j < Rnew; ++j) sweep_replica(a, j, i);
+    /* Step (iv): theta Metropolis sweeps at beta_i for every replica, or at
+     * theta = infinity fresh energies from the exact distribution at beta_i */
+    if (a->d.theta == OR_THETA_INF) {
+        if (dos_resample_energies(a, i, Rnew) != OR_OK) return OR_ERR_OOM;
+    } else {
+        for (uint32_t j = 0; j < Rnew; ++j) sweep_replica(a, j, i);
+    }
 
     /* Step (v): measurements at beta_i */
     a->rec[i].lnQ = lnQ;

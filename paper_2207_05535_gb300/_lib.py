@@ -36,7 +36,7 @@ class pa_run_desc(C.Structure):
                 ("theta", C.c_uint32), ("n_beta", C.c_uint32), ("beta", C.POINTER(C.c_double)),
                 ("seed", C.c_uint32), ("run_id", C.c_uint32), ("disorder_id", C.c_uint32),
                 ("resample", C.c_uint32), ("overlap", C.c_uint32), ("paired", C.c_int32),
-                ("reserved", C.c_uint32)]
+                ("reserved", C.c_uint32), ("log_g", C.POINTER(C.c_double))]
 
 
 RECORD_DTYPE = np.dtype([
@@ -127,9 +127,11 @@ def make_descs(runs):
     keep = []
     for k, r in enumerate(runs):
         b = np.ascontiguousarray(r.betas, dtype=np.float64)
-        keep.append(b)
+        g = None if r.log_g is None else np.ascontiguousarray(r.log_g, dtype=np.float64)
+        keep += [b, g]
         arr[k] = pa_run_desc(r.L, r.model, r.R, r.R_cap, r.theta, len(b), _p(b, C.c_double), r.seed, r.run_id,
-                             r.disorder_id, r.resample, r.overlap, r.paired if r.overlap & W.Q_PAIR else -1, 0)
+                             r.disorder_id, r.resample, r.overlap, r.paired if r.overlap & W.Q_PAIR else -1, 0,
+                             _p(g, C.c_double))
     arr._keep = keep
     return arr
 

@@ -23,6 +23,7 @@ MULTINOMIAL = 1
 Q_NONE = 0
 Q_SHIFT = 1
 Q_PAIR = 2
+THETA_INF = 0xFFFFFFFF  # theta -> infinity: energies drawn from the exact density of states (Sec. V.B)
 
 
 def schedule(beta_f: float, n: int) -> np.ndarray:
@@ -53,6 +54,7 @@ class RunDesc:
     overlap: int = Q_NONE
     paired: int = -1          # index (within the same batch) of the paired population
     R_cap: int = 0
+    log_g: np.ndarray | None = None  # theta = THETA_INF: ln g(E) at E = 2u - 2N, u = 0..2N
 
     def __post_init__(self):
         self.betas = np.ascontiguousarray(self.betas, dtype=np.float64)
@@ -68,7 +70,10 @@ class RunDesc:
         return len(self.betas)
 
     def updates(self) -> int:
-        """Nominal attempted spin updates of the whole anneal (theta N R per step)."""
+        """Nominal attempted spin updates of the whole anneal (theta N R per step;
+        none for theta = THETA_INF, where energies are drawn instead)."""
+        if self.theta == THETA_INF:
+            return 0
         return self.theta * self.N * self.R * (self.n_beta - 1)
 
 

@@ -46,10 +46,10 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "pa.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(pa_run_desc), sizeof(pa_step_record), sizeof(pa_wavg),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(pa_run_desc), sizeof(pa_step_record), sizeof(pa_wavg),
          offsetof(pa_step_record, R), offsetof(pa_step_record, status), offsetof(pa_wavg, W_minus_betaF),
          offsetof(pa_step_record, sumE3), offsetof(pa_step_record, sumM4), offsetof(pa_wavg, W_e3),
-         offsetof(pa_wavg, W_U4_conf));
+         offsetof(pa_wavg, W_U4_conf), offsetof(pa_run_desc, log_g));
   return 0;
 }
 ''')
@@ -66,6 +66,7 @@ int main(void) {
     assert vals[7] == _lib.RECORD_DTYPE.fields["sumM4"][1]
     assert vals[8] == _lib.WAVG_DTYPE.fields["W_e3"][1]
     assert vals[9] == _lib.WAVG_DTYPE.fields["W_U4_conf"][1]
+    assert vals[10] == _lib.pa_run_desc.log_g.offset
 
 
 def test_status_strings(lib):
