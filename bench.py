@@ -43,6 +43,9 @@ WORKLOADS = {
                       "resampling, M=20 runs from seed 1, free-energy-weighted averages over the 20 runs"),
     "uneven_4096": ("4096 independent 2D Ising FM runs, L drawn from {16,32,64,128}, R from {1e3,1e4,5e4} by seed, "
                     "beta 0->1 in 101 steps, theta=10, one launch per kernel per step over all runs"),
+    "ferro_L8_theta_inf": ("2D Ising FM L=8 periodic, theta = infinity (energies drawn from the exact density of "
+                           "states, Sec. V.B), R=2e4, beta 0->0.6 in 61 steps, nearest-integer resampling, 200 runs, "
+                           "free-energy-weighted averages over groups of 20 runs"),
     "ising_L256_R1e5": ("2D Ising FM L=256 periodic, R=1e5, beta 0->0.44 in 201 steps, theta=20, "
                         "M=16 runs, free-energy-weighted averages over the runs"),
     "serving": ("Poisson stream of PA jobs at 200/s (FM or +-J glass with equal odds, L even uniform in 8..64, "
@@ -56,9 +59,23 @@ WORKLOAD = WORKLOADS["glass_L16_R5000"]
 # slots per call, 10 per update.  The multiplier retires 64 multiply-add lanes
 # per clock per SM.
 ALGO_MULADD_PER_UPDATE = 10.0
+ALGO_MULADD_PER_DRAW = 40.0  # theta = infinity: one Philox4x32-10 call per energy draw
+INF_WORKLOADS = {"ferro_L8_theta_inf"}
+METRIC_INF = "energy draws/ns of theta = infinity PA (Sec. V.B) at oracle-exact"
+UNIT_INF = "energy draws/ns"
+
+
+def metric_unit(wl):
+    return (METRIC_INF, UNIT_INF) if wl in INF_WORKLOADS else (METRIC, UNIT)
+
+
+def work_units(d, R):
+    """Work of one temperature at population R: attempted spin updates (theta N R),
+    or R energy draws for theta = infinity runs."""
+    return R if d.theta == 0xFFFFFFFF else d.theta * d.N * R
 # DRAM bytes per sweep launch from one ncu capture (profiles/sweep_pow2_glass_L16_R5000.md),
 # valid only for the kernel source it was taken on.
-SWEEP_TRAFFIC = {"sweep_source_sha256_16": "1705e80b5cd49b74", "workload": "glass_L16_R5000", "bytes_per_launch": 45.043456e6}
+SWEEP_TRAFFIC = {"sweep_source_sha256_16": "fcf6082c6bd700e1", "workload": "glass_L16_R5000", "bytes_per_launch": 44.072448e6}
 MULADD_LANES_PER_SM = 64
 
 
@@ -91,29 +108,32 @@ def _workload_descs(wl, runs=0):
         return W.ising_L8_R500(M=runs or 20)
     if wl == "uneven_4096":
         return W.batched_uneven(n_runs=runs or 4096)
+    if wl == "ferro_L8_theta_inf":
+        from paper_2207_05535_gb300 import dos
+        return W.ferro_theta_inf(dos.log_dos(8), M=runs or 200)
     return W.ising_L256_R1e5(M=runs or 16)
 
 
 def _oracle_job(args):
-    wl, k, n_temps, r_max = args
+    descs, n_temps, r_max = args
     sys.path.insert(0, ROOT)
     import dataclasses
     import oracle as O
-    d = _workload_descs(wl)[k]
-    if r_max and d.R > r_max:
-        d = dataclasses.replace(d, R=r_max, R_cap=0)
-    r = O.OracleRun.from_desc(d)
     t0 = time.perf_counter()
     upd = 0
-    for i in range(1, n_temps):
-        assert r.step() == 0
-        upd += d.theta * d.N * int(r.record(i)["R"])
+    for d in descs:  # runs one after another in this process
+        if r_max and d.R > r_max:
+            d = dataclasses.replace(d, R=r_max, R_cap=0)
+        r = O.OracleRun.from_desc(d)
+        for i in range(1, n_temps):
+            assert r.step() == 0
+            upd += work_units(d, int(r.record(i)["R"]))
     return upd, time.perf_counter() - t0
 
 
-# bounded oracle samples per workload: (temperatures, population cap)
-ORACLE_SAMPLE = {"glass_L16_R5000": (25, 0), "ising_L8_R500": (51, 0), "uneven_4096": (2, 2000),
-                 "ising_L256_R1e5": (2, 200), "serving": (6, 2000)}
+# bounded oracle samples per workload: (temperatures, population cap, runs per process)
+ORACLE_SAMPLE = {"glass_L16_R5000": (25, 0, 1), "ising_L8_R500": (51, 0, 1), "uneven_4096": (2, 2000, 1),
+                 "ising_L256_R1e5": (2, 200, 1), "serving": (6, 2000, 1), "ferro_L8_theta_inf": (61, 0, 12)}
 
 
 def oracle_sample(wl="glass_L16_R5000", n_temps=None, procs=None):
@@ -121,21 +141,23 @@ def oracle_sample(wl="glass_L16_R5000", n_temps=None, procs=None):
     of the workload (population capped for the largest workloads) through its
     first n_temps temperatures."""
     procs = procs or os.cpu_count() or 1
-    nt, r_max = ORACLE_SAMPLE[wl]
+    nt, r_max, reps = ORACLE_SAMPLE[wl]
     n_temps = n_temps or nt
-    n_runs = len(_workload_descs(wl))
+    descs = _workload_descs(wl)
     import oracle
     oracle.build()
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(procs) as pool:
-        res = pool.map(_oracle_job, [(wl, k % n_runs, n_temps, r_max) for k in range(procs)])
+        res = pool.map(_oracle_job, [([descs[(k * reps + q) % len(descs)] for q in range(reps)], n_temps, r_max)
+                                     for k in range(procs)])
     wall = time.perf_counter() - t0
     upd = sum(u for u, _ in res)
     cap = f", populations capped at R={r_max}" if r_max else ""
-    return {"value": upd / (wall * 1e9), "unit": UNIT, "cores": procs, "kind": "oracle",
-            "sample": f"{procs} runs of the workload (one per process) through their first {n_temps} "
-                      f"temperatures{cap} ({upd:.3e} attempted updates, {wall:.1f} s wall)"}
+    unit = metric_unit(wl)[1]
+    return {"value": upd / (wall * 1e9), "unit": unit, "cores": procs, "kind": "oracle",
+            "sample": f"{procs * reps} runs of the workload ({reps} per process) through their first {n_temps} "
+                      f"temperatures{cap} ({upd:.3e} {unit.split('/')[0]}, {wall:.1f} s wall)"}
 
 
 # ---------------------------------------------------------------- clocks
@@ -215,7 +237,7 @@ def main():
         if rank != 0:
             return
         W_, K = args.warmup, args.steps
-        nt, _ = ORACLE_SAMPLE[args.workload]
+        nt = ORACLE_SAMPLE[args.workload][0]
         for _ in range(W_):
             oracle_sample(args.workload, n_temps=2)
         vals, tot = [], 0.0
@@ -226,13 +248,16 @@ def main():
             vals.append(s["value"])
         v = statistics.median(vals)
         print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
+            "impl": "reference", "metric": metric_unit(args.workload)[0], "value": v,
+            "unit": metric_unit(args.workload)[1], "n_gpus": args.gpus, "steps": K,
             "warmup": W_, "ms_per_step": 1e3 * tot / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
                        "sample": "bounded oracle sample per step"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": s["cores"], "kind": "oracle", "sample": s["sample"]},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+            "cpu_baseline": {"value": v, "unit": metric_unit(args.workload)[1], "cores": s["cores"], "kind": "oracle",
+                             "sample": s["sample"]},
+            "e2e": {"value": v, "unit": metric_unit(args.workload)[1], "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}), flush=True)
         return
 
     # CPU baseline first: a spawn pool, before any CUDA context exists
@@ -269,6 +294,8 @@ def main():
         M_avg = len(descs)
     elif wl == "uneven_4096":
         descs, M_avg = W.batched_uneven(n_runs=args.runs or 4096), 0
+    elif wl == "ferro_L8_theta_inf":
+        descs, M_avg = _workload_descs(wl, args.runs), 20
     else:
         descs = W.ising_L256_R1e5(M=args.runs or 16)
         M_avg = len(descs)
@@ -313,7 +340,7 @@ def main():
     runs_done = 0
     for k in range(len(descs)):
         rec = eng.records(k)
-        updates += int(sum(descs[k].theta * descs[k].N * int(r) for r in rec["R"][1:]))
+        updates += int(sum(work_units(descs[k], int(r)) for r in rec["R"][1:]))
         runs_done += 1
     t_max, upd_all = replicas.reduce_timing(ms, updates * args.steps, dist, device="cuda")
     value = upd_all / (t_max * 1e6)
@@ -335,7 +362,10 @@ def main():
     pk, pk_kind = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak_tops = 152 * MULADD_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # integer multiply-add slots, T/s
-    achieved_tops = updates * ALGO_MULADD_PER_UPDATE / (sweep_ms / args.steps * 1e-3) / 1e12
+    inf = wl in INF_WORKLOADS
+    slots = ALGO_MULADD_PER_DRAW if inf else ALGO_MULADD_PER_UPDATE
+    achieved_tops = updates * slots / (sweep_ms / args.steps * 1e-3) / 1e12
+    metric, unit = metric_unit(wl)
     total_kernel_ms = sum(t for t, _ in kt_tot.values())
 
     # ---- plain form: one run per engine, all on one stream (one run per launch)
@@ -364,11 +394,11 @@ def main():
         for u, e in zip(units, engines):
             for k, d_ in enumerate(u):
                 rec = e.records(k)
-                pupd += int(sum(d_.theta * d_.N * int(r) for r in rec["R"][1:]))
+                pupd += int(sum(work_units(d_, int(r)) for r in rec["R"][1:]))
                 nruns += 1
         for e in engines:
             e.close()
-        plain = {"value": pupd / (pms * 1e6), "unit": UNIT, "runs": nruns, "runs_per_s": nruns / (pms / 1e3),
+        plain = {"value": pupd / (pms * 1e6), "unit": unit, "runs": nruns, "runs_per_s": nruns / (pms / 1e3),
                  "form": "one run (glass: one disorder sample of two populations) per engine and per launch, "
                          "no graph, one stream"}
 
@@ -390,26 +420,30 @@ def main():
             e.close()
             es.append(time.perf_counter() - t0)
             h2d, d2h = a_, b_
-        e2e = {"value": updates * world / (statistics.median(es) * 1e9), "unit": UNIT,
+        e2e = {"value": updates * world / (statistics.median(es) * 1e9), "unit": unit,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "includes": "pa_create (allocation, table upload, beta_0 draw) + anneal + weighted averages + "
                            "all records copied to host + pa_destroy"}
 
     if rank == 0:
         out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[wl], "name": wl, "runs_per_gpu": len(descs), "temperatures": n_ticks + 1,
-                       "attempted_updates_per_step": updates, "l2": "flushed between steps (256 MB write)",
+                       ("energy_draws_per_step" if inf else "attempted_updates_per_step"): updates,
+                       "l2": "flushed between steps (256 MB write)",
                        "form": "batched: all runs in one launch per kernel, anneal captured as a CUDA graph",
                        "parallelism": f"replicas x{world} (independent runs per GPU)"},
             "runs_per_s": runs_per_s,
-            "roofline": {"bound": "alu", "kernel": "sweep_pow2_kernel", "achieved": achieved_tops,
+            "roofline": {"bound": "alu", "kernel": "dos_sample_kernel" if inf else "sweep_pow2_kernel",
+                         "achieved": achieved_tops,
                          "peak": peak_tops, "unit": "Tmuladd/s", "frac": achieved_tops / peak_tops,
                          "traffic": sweep_traffic(wl),
-                         "basis": f"{ALGO_MULADD_PER_UPDATE:g} integer multiply-add slots per attempted update "
-                                  f"(Philox4x32-10: 40 per call, 4 updates per call); peak = 152 SMs x "
+                         "basis": (f"{ALGO_MULADD_PER_DRAW:g} integer multiply-add slots per energy draw "
+                                   f"(one Philox4x32-10 call)" if inf else
+                                   f"{ALGO_MULADD_PER_UPDATE:g} integer multiply-add slots per attempted update "
+                                   f"(Philox4x32-10: 40 per call, 4 updates per call)") + "; peak = 152 SMs x "
                                   f"{MULADD_LANES_PER_SM} lanes x {sm_mhz:g} MHz, clock from MEASURED_PEAKS.json "
                                   f"({pk_kind})",
                          "updates_per_ns_sweep_only": updates / (sweep_ms / args.steps * 1e-3) / 1e9,

@@ -3,7 +3,9 @@
     python -m paper_2207_05535_gb300.build
 
 The translation units compile in parallel; no cmake.  FMA contraction is off
-(-fmad=false) so the FP64 resampling arithmetic rounds exactly as written.
+in device code (-fmad=false) and in host code (-ffp-contract=off: the host
+builds the FP64 tables that decide integers, and aarch64 compilers contract
+a - b * c by default) so the FP64 arithmetic rounds exactly as written.
 """
 from __future__ import annotations
 
@@ -32,8 +34,8 @@ def nvcc() -> str:
 
 
 def _flags(extra=()):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-                   "-I", CSRC, *extra]
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler",
+                   "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC, *extra]
 
 
 def _stale(outp, deps):

@@ -131,6 +131,7 @@ struct pa_engine {
     FreeList fl_rep, fl_spin, fl_rec, fl_qh, fl_scr, fl_J, fl_beta, fl_thr, fl_wto;
     uint64_t wt_cap = 0, wt_used = 0;
     std::map<std::pair<uint32_t, uint64_t>, uint64_t> wt_cache;  // (N, dbeta bits) -> offset
+    std::map<std::vector<double>, uint64_t> dos_cache;            // (ln g, schedule, N) -> offset
     // device metadata (lists and work lists), rebuilt when the resident set changes
     uint32_t *d_meta = nullptr;
     uint64_t meta_cap = 0;
@@ -140,6 +141,9 @@ struct pa_engine {
     uint32_t init_q_n = 0;
     std::vector<uint32_t> q_runs;
     uint32_t init_n = 0, init_tiles = 0;
+    std::vector<uint32_t> inf_runs;  // resident theta = PA_THETA_INF runs
+    uint64_t inf_off = 0, init_inf_off = 0;
+    uint32_t inf_maxR = 0, init_inf_n = 0, init_inf_maxR = 0;
     std::vector<SweepGroup> groups;
     std::map<uint32_t, Tuning> tuning;  // per lattice size
     uint32_t max_Rcap_active = 0, max_pw = 1;
@@ -233,7 +237,19 @@ pa_status validate(const pa_run_desc *runs, uint32_t n)
         if (d.L < 4 || d.L > 256 || (d.L & 1u)) return PA_ERR_INVALID_ARG;
         if (d.model > PA_EA_PMJ || d.resample > PA_MULTINOMIAL || d.overlap > 3u || d.reserved)
             return PA_ERR_INVALID_ARG;
-        if (d.R < 1 || d.n_beta < 1 || !d.beta || d.theta > (1u << 22)) return PA_ERR_INVALID_ARG;
+        if (d.R < 1 || d.n_beta < 1 || !d.beta) return PA_ERR_INVALID_ARG;
+        if (d.theta == PA_THETA_INF) {  // needs a density of states; no configurations, so no overlaps
+            if (!d.log_g || d.overlap) return PA_ERR_INVALID_ARG;
+            bool any = false;
+            for (uint32_t u = 0; u <= 2 * d.L * d.L; ++u) {
+                const double v = d.log_g[u];
+                if (std::isnan(v) || v == INFINITY) return PA_ERR_INVALID_ARG;
+                any = any || v > -INFINITY;
+            }
+            if (!any) return PA_ERR_INVALID_ARG;
+        } else if (d.theta > (1u << 22)) {
+            return PA_ERR_INVALID_ARG;
+        }
         if (cap_of(d) < d.R) return PA_ERR_INVALID_ARG;
         for (uint32_t i = 1; i < d.n_beta; ++i)
             if (!(d.beta[i] >= d.beta[i - 1])) return PA_ERR_INVALID_ARG;
@@ -282,7 +298,7 @@ pa_status alloc_pools(pa_engine *e, const pa_server_config &c)
     PA_TRY(dalloc(e, &e->d_thr, 2 * c.record_capacity));
     PA_TRY(dalloc(e, &e->d_wtoff, c.record_capacity));
     PA_TRY(dalloc(e, &e->d_wt, c.table_doubles));
-    e->meta_cap = 9ull * e->S + 3ull * 128 + 1024;
+    e->meta_cap = 11ull * e->S + 3ull * 128 + 1024;
     PA_TRY(dalloc(e, &e->d_meta, e->meta_cap));
     PA_CUDA(cudaMemsetAsync(e->P.status, 0, sizeof(uint32_t), e->stream));
     e->P.runs = e->d_runs;
@@ -324,6 +340,57 @@ pa_status weight_table(pa_engine *e, uint32_t N, double dbeta, uint64_t &off)
     off = e->wt_used;
     e->wt_used += N + 1;
     e->wt_cache.emplace(key, off);
+    return PA_OK;
+}
+
+// theta = PA_THETA_INF: per step i the cumulative weights of the exact energy
+// distribution over the levels u = 0..2N (E = 2u - 2N), ascending,
+//   C[u] = sum_{v<=u} exp(ln g(v) - beta_i E(v) - c),  c = max_v (ln g(v) - beta_i E(v)),
+// then the last level with a positive weight; (2N + 2) doubles per step, built
+// with libm on the host and shared by runs with the same (ln g, schedule).
+pa_status dos_table(pa_engine *e, const pa_run_desc &d, uint64_t &off)
+{
+    const uint32_t N = d.L * d.L, U = 2 * N;
+    std::vector<double> key(d.log_g, d.log_g + U + 1);
+    key.insert(key.end(), d.beta, d.beta + d.n_beta);
+    key.push_back((double)N);
+    auto it = e->dos_cache.find(key);
+    if (it != e->dos_cache.end()) {
+        off = it->second;
+        return PA_OK;
+    }
+    const uint64_t n = (uint64_t)d.n_beta * (U + 2);
+    if (e->wt_used + n > e->wt_cap) return PA_ERR_BUSY;
+    std::vector<double> t(n);
+    for (uint32_t i = 0; i < d.n_beta; ++i) {
+        double *C = t.data() + (uint64_t)i * (U + 2);
+        const double beta = d.beta[i];
+        double c = -INFINITY;
+        for (uint32_t u = 0; u <= U; ++u)
+            if (d.log_g[u] > -INFINITY) {
+                const double l = d.log_g[u] - beta * (double)(2 * (int64_t)u - 2 * (int64_t)N);
+                if (l > c) c = l;
+            }
+        double acc = 0.0;
+        uint32_t last = 0;
+        for (uint32_t u = 0; u <= U; ++u) {
+            double p = 0.0;
+            if (d.log_g[u] > -INFINITY) {
+                const double l = d.log_g[u] - beta * (double)(2 * (int64_t)u - 2 * (int64_t)N);
+                p = std::exp(l - c);
+            }
+            acc = acc + p;
+            C[u] = acc;
+            if (p > 0.0) last = u;
+        }
+        C[U + 1] = (double)last;
+    }
+    PA_CUDA(cudaMemcpyAsync(e->d_wt + e->wt_used, t.data(), sizeof(double) * n, cudaMemcpyHostToDevice, e->stream));
+    PA_CUDA(cudaStreamSynchronize(e->stream));  // t must outlive the copy
+    e->h2d += sizeof(double) * n;
+    off = e->wt_used;
+    e->wt_used += n;
+    e->dos_cache.emplace(std::move(key), off);
     return PA_OK;
 }
 
@@ -369,6 +436,7 @@ pa_status admit(pa_engine *e, const pa_run_desc *runs, uint32_t n, uint32_t *slo
     if (got.size() < n) return PA_ERR_BUSY;
     std::vector<Ranges> gs(n);
     std::vector<std::vector<unsigned long long>> wtos(n);
+    std::vector<uint64_t> dos_offs(n, 0);
     uint32_t k = 0;
     pa_status st = PA_OK;
     for (; k < n; ++k) {
@@ -383,6 +451,7 @@ pa_status admit(pa_engine *e, const pa_run_desc *runs, uint32_t n, uint32_t *slo
             st = weight_table(e, d.L * d.L, d.beta[i] - d.beta[i - 1], off);
             wtos[k][i] = off;
         }
+        if (st == PA_OK && d.theta == PA_THETA_INF) st = dos_table(e, d, dos_offs[k]);
         if (st != PA_OK) {
             unreserve(e, runs[k], gs[k]);
             break;
@@ -430,6 +499,7 @@ pa_status admit(pa_engine *e, const pa_run_desc *runs, uint32_t n, uint32_t *slo
         x.J_off = g.J;
         x.scr_off = g.scr;
         x.ln2N = (double)N * std::log(2.0);
+        x.dos_off = dos_offs[r];
         e->rd[s] = x;
         RunState rs;
         rs.step = 0;
@@ -460,6 +530,7 @@ pa_status admit(pa_engine *e, const pa_run_desc *runs, uint32_t n, uint32_t *slo
         h.used = true;
         h.d = d;
         h.d.beta = nullptr;  // not kept: the caller owns it
+        h.d.log_g = nullptr;
         h.g = g;
         h.steps_done = 0;
         e->active.push_back(s);
@@ -490,7 +561,14 @@ pa_status rebuild(pa_engine *e)
     m.insert(m.end(), e->q_runs.begin(), e->q_runs.end());
     e->groups.clear();
     std::map<uint32_t, size_t> gi;  // lattice size -> group, in order of first appearance
+    e->inf_runs.clear();
+    e->inf_maxR = 0;
     for (uint32_t s : e->active) {
+        if (e->rd[s].theta == PA_THETA_INF) {  // sampled from the density of states, no sweep
+            e->inf_runs.push_back(s);
+            e->inf_maxR = std::max(e->inf_maxR, e->rd[s].R_cap);
+            continue;
+        }
         const uint32_t L = e->rd[s].L;
         auto it = gi.find(L);
         if (it == gi.end()) {
@@ -525,18 +603,29 @@ pa_status rebuild(pa_engine *e)
             g.n_tiles.push_back((uint32_t)acc);
         }
     }
+    e->inf_off = m.size();
+    m.insert(m.end(), e->inf_runs.begin(), e->inf_runs.end());
     e->init_runs_off = m.size();
     m.insert(m.end(), e->pending.begin(), e->pending.end());
     e->init_tiles_off = m.size();
     uint64_t acc = 0;
     m.push_back(0u);
-    for (uint32_t s : e->pending) {  // 4 replicas per CTA
-        acc += (e->rd[s].R + 3) / 4;
+    for (uint32_t s : e->pending) {  // 4 replicas per CTA; none for theta = PA_THETA_INF runs
+        acc += e->rd[s].theta == PA_THETA_INF ? 0u : (e->rd[s].R + 3) / 4;
         if (acc > 0x7fffffffull) return PA_ERR_INVALID_ARG;
         m.push_back((uint32_t)acc);
     }
     e->init_n = (uint32_t)e->pending.size();
     e->init_tiles = (uint32_t)acc;
+    e->init_inf_off = m.size();
+    e->init_inf_n = 0;
+    e->init_inf_maxR = 0;
+    for (uint32_t s : e->pending)
+        if (e->rd[s].theta == PA_THETA_INF) {
+            m.push_back(s);
+            ++e->init_inf_n;
+            e->init_inf_maxR = std::max(e->init_inf_maxR, e->rd[s].R);
+        }
     e->init_q_off = m.size();  // pending runs with overlaps: their step-0 overlaps only
     e->init_q_n = 0;
     for (uint32_t s : e->pending)
@@ -603,10 +692,15 @@ pa_status enqueue_pending(pa_engine *e)
     if (e->pending.empty()) return PA_OK;
     const uint32_t *runs = meta(e, e->init_runs_off);
     timed_launch(e, PA_K_INIT, [&] { launch_init_couplings(e->P, runs, e->init_n, e->stream); });
-    timed_launch(e, PA_K_INIT, [&] {
-        launch_init_population(e->P, meta(e, e->init_tiles_off), runs, e->init_n, e->init_tiles, e->max_pw,
-                               e->stream);
-    });
+    if (e->init_tiles)
+        timed_launch(e, PA_K_INIT, [&] {
+            launch_init_population(e->P, meta(e, e->init_tiles_off), runs, e->init_n, e->init_tiles, e->max_pw,
+                                   e->stream);
+        });
+    if (e->init_inf_n)
+        timed_launch(e, PA_K_INIT, [&] {
+            launch_dos_sample(e->P, meta(e, e->init_inf_off), e->init_inf_n, e->init_inf_maxR, 1, e->stream);
+        });
     if (e->init_q_n)  // step-0 overlaps of the pending runs (pairs are admitted together)
         timed_launch(e, PA_K_OVERLAP, [&] {
             launch_overlap(e->P, meta(e, e->init_q_off), e->init_q_n, e->max_Rcap_active, 1, e->stream);
@@ -618,12 +712,22 @@ pa_status enqueue_pending(pa_engine *e)
     return PA_OK;
 }
 
+// Fresh energies for the theta = PA_THETA_INF runs (in place of their sweeps).
+void enqueue_dos_sample(pa_engine *e)
+{
+    if (e->inf_runs.empty()) return;
+    timed_launch(e, PA_K_SWEEP, [&] {
+        launch_dos_sample(e->P, meta(e, e->inf_off), (uint32_t)e->inf_runs.size(), e->inf_maxR, 0, e->stream);
+    });
+}
+
 void enqueue_tick(pa_engine *e)
 {
     const uint32_t *act = meta(e, e->active_off);
     const uint32_t na = (uint32_t)e->active.size();
     timed_launch(e, PA_K_RESAMPLE, [&] { launch_resample(e->P, act, na, e->stream); });
     for (auto &g : e->groups) timed_launch(e, PA_K_SWEEP, [&] { launch_group_sweep(e, g, e->tuning[g.L].pick); });
+    enqueue_dos_sample(e);
     if (!e->q_runs.empty())
         timed_launch(e, PA_K_OVERLAP, [&] {
             launch_overlap(e->P, meta(e, e->q_off), (uint32_t)e->q_runs.size(), e->max_Rcap_active, 0, e->stream);
@@ -669,6 +773,7 @@ pa_status enqueue_tuning_tick(pa_engine *e)
         t.tuned = true;
         t.ms = best;
     }
+    enqueue_dos_sample(e);
     if (!e->q_runs.empty())
         timed_launch(e, PA_K_OVERLAP, [&] {
             launch_overlap(e->P, meta(e, e->q_off), (uint32_t)e->q_runs.size(), e->max_Rcap_active, 0, e->stream);
@@ -796,6 +901,7 @@ pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stre
     pa_server_config c{};
     c.max_runs = n_runs;
     std::map<std::pair<uint32_t, uint64_t>, int> keys;
+    std::map<std::vector<double>, int> dos_keys;
     for (uint32_t r = 0; r < n_runs; ++r) {
         const Ranges z = sizes_of(runs[r]);
         c.replica_capacity += z.rep;
@@ -810,6 +916,12 @@ pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stre
             uint64_t bits;
             std::memcpy(&bits, &db, sizeof bits);
             if (keys.emplace(std::make_pair(N, bits), 0).second) c.table_doubles += N + 1;
+        }
+        if (runs[r].theta == PA_THETA_INF) {
+            std::vector<double> key(runs[r].log_g, runs[r].log_g + 2 * N + 1);
+            key.insert(key.end(), runs[r].beta, runs[r].beta + runs[r].n_beta);
+            key.push_back((double)N);
+            if (dos_keys.emplace(std::move(key), 0).second) c.table_doubles += (uint64_t)runs[r].n_beta * (2 * N + 2);
         }
     }
     pa_engine *e = nullptr;

@@ -14,7 +14,11 @@
 //   beta, thr                               schedule and Metropolis thresholds per step
 //   wt, wtoff                               weight tables exp(-4 n dbeta) shared by every run
 //                                           and step with the same (N, dbeta); wtoff[wt_off + i]
-//                                           = offset of step i's table in wt
+//                                           = offset of step i's table in wt.  Runs with
+//                                           theta = PA_THETA_INF also keep per step the
+//                                           cumulative level weights of P_beta_i over
+//                                           u = 0..2N and, in entry 2N + 1, the last level
+//                                           with a positive weight (as a double)
 //   J                    per run: site-order "J = -1" bits of right / down bonds
 //                        (2 wstride words), then per colour plane word the four bond
 //                        masks (same, rotated, up, down neighbour) [2][4][PW]
@@ -29,7 +33,8 @@
 
 namespace pa {
 
-constexpr uint32_t TAG_INIT = 1u, TAG_SWEEP = 2u, TAG_RESAMPLE = 3u, TAG_MULTINOMIAL = 4u, TAG_DISORDER = 5u;
+constexpr uint32_t TAG_INIT = 1u, TAG_SWEEP = 2u, TAG_RESAMPLE = 3u, TAG_MULTINOMIAL = 4u, TAG_DISORDER = 5u,
+                   TAG_DOS = 6u;
 
 // status bits in the engine-wide device status word
 constexpr uint32_t ST_CAPACITY = 1u << PA_ERR_CAPACITY;
@@ -49,6 +54,7 @@ struct RunDev {
     uint64_t spin_off;  // first spin word (runs of different L have different wstride)
     uint64_t rec_off, qh_off, beta_off, wt_off, thr_off, J_off, scr_off;
     double ln2N;  // N ln 2 = ln Z(beta_0 = 0)
+    uint64_t dos_off;  // theta = PA_THETA_INF: step i's energy CDF at wt[dos_off + i (2N + 2)]
 };
 
 struct RunState {
@@ -130,6 +136,10 @@ void launch_sweep(const Pool &P, const uint32_t *group_runs, const uint32_t *til
 void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, uint32_t max_Rcap, int init,
                     cudaStream_t s);
 void launch_measure(const Pool &P, const uint32_t *runs, uint32_t n_runs, int init, cudaStream_t s);
+// theta = PA_THETA_INF runs: fresh energies from the exact distribution for
+// the population of the step in flight (init: the beta_0 population).
+void launch_dos_sample(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_R, int init,
+                       cudaStream_t s);
 void launch_wavg(const pa_step_record *recs, const unsigned long long *rec_off, const uint32_t *qh,
                  const uint32_t *qhp, const unsigned long long *qh_off, uint32_t n_groups, uint32_t M,
                  uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w, double *Pq, double *Pqp,

@@ -1142,6 +1142,45 @@ __global__ void overlap_kernel(Pool P, const uint32_t *q_runs, int init)
 }
 
 // --------------------------------------------------------------------------
+// theta = infinity (Sec. V.B): step (iv) replaced by simple sampling of the
+// exact energy distribution.  One thread per child: a 53-bit uniform from
+// Philox (words 0, 1), x = u * C[2N], the first level u with x < C[u] by
+// binary search over the host-built cumulative weights (the last positive
+// level if x rounds up to C[2N]); E = 2u - 2N, M = 0, family from the parent,
+// spin planes cleared (configurations are not represented).
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) dos_sample_kernel(Pool P, const uint32_t *runs, int init)
+{
+    const uint32_t run = runs[blockIdx.y];
+    const RunDev rd = P.runs[run];
+    const RunState *st = &P.st[run];
+    if (st->status) return;
+    const uint32_t i = init ? 0u : st->step + 1;
+    if (i >= rd.n_beta) return;
+    const uint32_t R = init ? rd.R : st->R_new;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= R) return;
+    const uint32_t U = 2 * rd.N, b = i & 1u;
+    const double *C = P.wt + rd.dos_off + (uint64_t)i * (U + 2);
+    const uint4 o = philox4x32_10(k, 0u, i, TAG_DOS << 24, rd.seed, rd.run_id);
+    const unsigned long long u53 = ((unsigned long long)(o.x >> 5) << 26) | (unsigned long long)(o.y >> 6);
+    const double x = __dmul_rn(__dmul_rn((double)u53, 1.0 / 9007199254740992.0), C[U]);
+    uint32_t lo = 0, hi = U + 1;  // first u with x < C[u]
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (x < C[mid]) hi = mid;
+        else lo = mid + 1;
+    }
+    const uint32_t lev = lo <= U ? lo : (uint32_t)C[U + 1];
+    const uint64_t slot = rd.rep_off + k;
+    P.E[b][slot] = (int32_t)(2 * (int64_t)lev - 2 * (int64_t)rd.N);
+    P.M[b][slot] = 0;
+    P.fam[b][slot] = init ? k : P.fam[b ^ 1u][rd.rep_off + P.parent[slot]];
+    uint32_t *dst = P.spins[b] + rd.spin_off + (uint64_t)k * rd.wstride;
+    for (uint32_t w = 0; w < rd.wstride; ++w) dst[w] = 0u;
+}
+
+// --------------------------------------------------------------------------
 // Measurement (Sec. III.B, Eqs. e, m, c, chi through exact integer sums;
 // Eq. F running sum; Eq. rho_t through family run lengths).  Finishes the step.
 // --------------------------------------------------------------------------
@@ -1509,6 +1548,13 @@ void launch_init_population(const Pool &P, const uint32_t *tile_off, const uint3
                             uint32_t n_tiles, uint32_t max_pw, cudaStream_t s)
 {
     init_population_kernel<<<n_tiles, 128, 4 * 2 * max_pw * sizeof(uint32_t), s>>>(P, tile_off, runs, n_runs);
+}
+
+void launch_dos_sample(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_R, int init,
+                       cudaStream_t s)
+{
+    if (n_runs == 0 || max_R == 0) return;
+    dos_sample_kernel<<<dim3((max_R + 255) / 256, n_runs), 256, 0, s>>>(P, runs, init);
 }
 
 void launch_resample(const Pool &P, const uint32_t *runs, uint32_t n_runs, cudaStream_t s)

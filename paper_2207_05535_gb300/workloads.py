@@ -122,6 +122,14 @@ def ising_L256_R1e5(M=16, R=100000, n=201):
     return ferro_runs(L=256, R=R, theta=20, beta_f=0.44, n=n, M=M, seed=1)
 
 
+def ferro_theta_inf(log_g, L=8, R=20000, beta_f=0.6, n=61, M=200, seed=1, resample=NEAREST):
+    """theta = infinity ferromagnet runs (Sec. V.B): at every temperature each
+    replica's energy is drawn from the exact distribution of the density of states
+    log_g (ln g at E = 2u - 2N, u = 0..2N) instead of Metropolis sweeps."""
+    b = schedule(beta_f, n)
+    return [RunDesc(L, FERRO, R, THETA_INF, b, seed, m, 0, resample, log_g=log_g) for m in range(M)]
+
+
 def serving_stream(rate=200.0, duration=10.0, seed=11, Lmin=8, Lmax=64, Rmin=1000, Rmax=50000, nmin=50,
                    nmax=300, theta=10):
     """Poisson arrivals of PA jobs: FM or glass with equal odds, L even uniform in

@@ -77,6 +77,9 @@ def test_status_strings(lib):
 @pytest.mark.parametrize("bad", [
     dict(L=7), dict(L=2), dict(L=258), dict(R=0), dict(R_cap=10, R=20), dict(model=3), dict(resample=5),
     dict(betas=np.array([0.0, 0.5, 0.4])), dict(betas=np.array([])), dict(overlap=8),
+    dict(theta=W.THETA_INF), dict(theta=W.THETA_INF, log_g=np.zeros(129), overlap=1),
+    dict(theta=W.THETA_INF, log_g=np.full(129, -np.inf)), dict(theta=W.THETA_INF, log_g=np.full(129, np.nan)),
+    dict(theta=(1 << 22) + 1),
 ])
 def test_invalid_descriptors_rejected_before_any_device_work(lib, bad):
     args = dict(L=8, model=W.FERRO, R=16, theta=1, betas=np.array([0.0, 0.1]))
