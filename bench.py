@@ -75,7 +75,7 @@ def work_units(d, R):
     return R if d.theta == 0xFFFFFFFF else d.theta * d.N * R
 # DRAM bytes per sweep launch from one ncu capture (profiles/sweep_pow2_glass_L16_R5000.md),
 # valid only for the kernel source it was taken on.
-SWEEP_TRAFFIC = {"sweep_source_sha256_16": "fcf6082c6bd700e1", "workload": "glass_L16_R5000", "bytes_per_launch": 44.072448e6}
+SWEEP_TRAFFIC = {"sweep_source_sha256_16": "22e464d70b729340", "workload": "glass_L16_R5000", "bytes_per_launch": 44.1728e6}
 MULADD_LANES_PER_SM = 64
 
 
@@ -89,6 +89,7 @@ def parse():
     ap.add_argument("--samples", type=int, default=100, help="glass: disorder samples (2 populations each)")
     ap.add_argument("--runs", type=int, default=0, help="ising/uneven: number of runs (0 = the workload's)")
     ap.add_argument("--window", type=float, default=2.0, help="serving: seconds of arrivals")
+    ap.add_argument("--wang", action="store_true", help="also measure Wang pairing overlaps (Sec. III.D)")
     ap.add_argument("--max-temps", type=int, default=0,
                     help="anneal only the first T temperatures of the schedule (0 = all); reported in config")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -302,6 +303,9 @@ def main():
     if args.max_temps:
         for d in descs:
             d.betas = d.betas[:args.max_temps]
+    if args.wang:  # add Wang et al.'s pairing (Sec. III.D) to every run's overlap measurements
+        for d in descs:
+            d.overlap |= W.Q_WANG
     from paper_2207_05535_gb300 import replicas
     descs = replicas.shard(descs, rank)
     n_ticks = max(d.n_beta for d in descs) - 1
@@ -430,7 +434,7 @@ def main():
             "metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[wl], "name": wl, "runs_per_gpu": len(descs), "temperatures": n_ticks + 1,
+            "config": {"workload": WORKLOADS[wl] + ("; plus Wang pairing overlaps" if args.wang else ""), "name": wl, "runs_per_gpu": len(descs), "temperatures": n_ticks + 1,
                        ("energy_draws_per_step" if inf else "attempted_updates_per_step"): updates,
                        "l2": "flushed between steps (256 MB write)",
                        "form": "batched: all runs in one launch per kernel, anneal captured as a CUDA graph",

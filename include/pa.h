@@ -49,7 +49,12 @@ typedef enum {
 
 enum { PA_FERRO = 0, PA_EA_PMJ = 1 };          /* Eq. H_ferro (J = 1), Eq. H_SG (J = +-1) */
 enum { PA_NEAREST = 0, PA_MULTINOMIAL = 1 };   /* resampling of Sec. II.B step (iii) / Sec. IV.C */
-enum { PA_Q_NONE = 0, PA_Q_SHIFT = 1, PA_Q_PAIR = 2 }; /* overlap pairs of Sec. III.D (bit flags) */
+/* Overlap pairs of Sec. III.D (bit flags): index shift j <-> j + floor(R_i/2);
+ * j <-> j with the paired population; Wang et al.'s pairing (k, pi*_k) from random
+ * permutations with a random search pattern, no pair within one family (needs
+ * R_cap <= PA_WANG_MAX_RCAP; skipped at a step where no such pairing is found). */
+enum { PA_Q_NONE = 0, PA_Q_SHIFT = 1, PA_Q_PAIR = 2, PA_Q_WANG = 4 };
+#define PA_WANG_MAX_RCAP 8192u
 enum { PA_WEIGHT_FULL = 0, PA_WEIGHT_SIMPLE = 1 };     /* Eq. appropriateWeight / Eq. simpleWeight */
 
 /* theta = PA_THETA_INF: the theta -> infinity limit of Sec. V.B.  Step (iv)'s
@@ -107,6 +112,9 @@ typedef struct pa_step_record {
     uint64_t sumE4[2];    /* sum_j H_j^4 */
     uint64_t sumAbsM3[2]; /* sum_j |M_j|^3 */
     uint64_t sumM4[2];    /* sum_j M_j^4 */
+    int64_t sum_absq_wang; /* sum over the Wang pairs (k, pi*_k), k < R_i, of |N - 2 d| */
+    uint32_t n_q_wang;    /* R_i, or 0 when no pairing without a shared family was found */
+    uint32_t wang_swaps;  /* transpositions made by the pairing search */
 } pa_step_record;
 
 /* Weighted averages at one temperature over M runs (Sec. IV). */
@@ -126,6 +134,7 @@ typedef struct pa_wavg {
     double W_U4;                 /* Binder cumulant from weighted moments, 1 - W[m^4] / (3 W[m^2]^2) */
     double W_U4_conf;            /* Eq. W_conf applied to each run's 1 - m^4 / (3 (m^2)^2); NaN when a
                                     run's population has M = 0 in every replica */
+    double W_absq_wang;          /* Eq. W_conf applied to |q| over the Wang pairs */
 } pa_wavg;
 
 typedef struct pa_engine pa_engine;
@@ -211,14 +220,14 @@ pa_status pa_sync(pa_engine *e);
 /* Copy the records of run `run` (index in pa_create order) for steps
  * 0..n_beta-1 into host_out[n_beta] (steps not reached yet are zero), and the
  * overlap histograms over d = 0..N (d = Hamming distance, q = 1 - 2d/N) into
- * host_qhist[n_beta][N+1] / host_qhist_pair[n_beta][N+1] when non-NULL.
- * Synchronises. */
+ * host_qhist[n_beta][N+1] / host_qhist_pair[n_beta][N+1] / host_qhist_wang[n_beta][N+1]
+ * (index shift, paired population, Wang pairs) when non-NULL.  Synchronises. */
 pa_status pa_records(pa_engine *e, uint32_t run, pa_step_record *host_out, uint32_t *host_qhist,
-                     uint32_t *host_qhist_pair);
+                     uint32_t *host_qhist_pair, uint32_t *host_qhist_wang);
 
 /* Copy one record (and optional histograms, N+1 entries each). Synchronises. */
 pa_status pa_measure(pa_engine *e, uint32_t run, uint32_t step, pa_step_record *host_out, uint32_t *host_qhist,
-                     uint32_t *host_qhist_pair);
+                     uint32_t *host_qhist_pair, uint32_t *host_qhist_wang);
 
 /* Copy the current population of run `run`: host_spins[R_i][N] as int8 +-1
  * (site n = y*L + x), energies, magnetisations and family ids (index of the
@@ -230,19 +239,21 @@ pa_status pa_population(pa_engine *e, uint32_t run, int8_t *host_spins, int32_t 
 /* Weighted averages (Sec. IV) over groups of runs resident in the engine:
  * group g holds runs run_idx[g*M .. g*M+M-1] (same N and n_beta).  Writes
  * host_out[g][n_beta] and, when non-NULL, the weighted overlap distributions
- * host_Pq[g][n_beta][N+1] / host_Pq_pair (Eq. W_conf_q).  weight_kind is
+ * host_Pq[g][n_beta][N+1] / host_Pq_pair / host_Pq_wang (Eq. W_conf_q).  weight_kind is
  * PA_WEIGHT_FULL or PA_WEIGHT_SIMPLE.  Runs in FP64 on the device.  Synchronises. */
 pa_status pa_weighted_average_runs(pa_engine *e, const uint32_t *run_idx, uint32_t n_groups, uint32_t M,
                                    uint32_t weight_kind, pa_wavg *host_out, double *host_Pq,
-                                   double *host_Pq_pair);
+                                   double *host_Pq_pair, double *host_Pq_wang);
 
 /* Weighted averages from host records: recs[m*n_steps + i] for M runs of N spins,
- * optional histograms qhist[(m*n_steps + i)*(N+1) + d].  Writes out[n_steps] and
- * Pq / Pq_pair [n_steps][N+1] when non-NULL.  Computes on the device of the
- * current CUDA context (stream: cudaStream_t or NULL); blocking. */
+ * optional histograms qhist[(m*n_steps + i)*(N+1) + d] (likewise qhist_pair,
+ * qhist_wang).  Writes out[n_steps] and Pq / Pq_pair / Pq_wang [n_steps][N+1]
+ * when non-NULL.  Computes on the device of the current CUDA context (stream:
+ * cudaStream_t or NULL); blocking. */
 pa_status pa_weighted_average(const pa_step_record *recs, const uint32_t *qhist, const uint32_t *qhist_pair,
-                              uint32_t M, uint32_t n_steps, uint32_t N, uint32_t weight_kind, pa_wavg *out,
-                              double *Pq, double *Pq_pair, void *cuda_stream);
+                              const uint32_t *qhist_wang, uint32_t M, uint32_t n_steps, uint32_t N,
+                              uint32_t weight_kind, pa_wavg *out, double *Pq, double *Pq_pair, double *Pq_wang,
+                              void *cuda_stream);
 
 /* Limits of pa_weighted_average_noalloc's fixed scratch. */
 #define PA_NOALLOC_MAX_RUNS 4096u      /* M */

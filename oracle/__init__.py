@@ -13,6 +13,7 @@ from .oracle import (  # noqa: F401
     dos_transfer,
     energy,
     i128,
+    wang_pairing,
     kaufman_lnZ,
     load,
     metropolis_threshold,

@@ -52,6 +52,7 @@ RECORD_DTYPE = np.dtype([
     ("R", "u4"), ("R_target", "u4"), ("n_fam", "u4"), ("max_fam", "u4"),
     ("n_q", "u4"), ("n_q_pair", "u4"), ("N", "u4"), ("status", "u4"),
     ("sumE3", "u8", (2,)), ("sumE4", "u8", (2,)), ("sumAbsM3", "u8", (2,)), ("sumM4", "u8", (2,)),
+    ("sum_absq_wang", "i8"), ("n_q_wang", "u4"), ("wang_swaps", "u4"),
 ])
 
 WAVG_DTYPE = np.dtype([
@@ -61,7 +62,7 @@ WAVG_DTYPE = np.dtype([
     ("w_max", "f8"), ("sum_w", "f8"),
     ("W_e3", "f8"), ("W_e4", "f8"), ("W_m3", "f8"), ("W_m4", "f8"),
     ("Wk3_e", "f8"), ("Wk4_e", "f8"), ("Wk3_m", "f8"), ("Wk4_m", "f8"),
-    ("W_U4", "f8"), ("W_U4_conf", "f8"),
+    ("W_U4", "f8"), ("W_U4_conf", "f8"), ("W_absq_wang", "f8"),
 ])
 
 
@@ -109,7 +110,7 @@ def load():
         lib.or_current_R.restype = u32
         lib.or_get_record.argtypes = [C.c_void_p, u32, C.c_void_p]
         lib.or_get_record.restype = None
-        lib.or_get_qhist.argtypes = [C.c_void_p, u32, P(u32), P(u32)]
+        lib.or_get_qhist.argtypes = [C.c_void_p, u32, P(u32), P(u32), P(u32)]
         lib.or_get_qhist.restype = None
         lib.or_get_counts.argtypes = [C.c_void_p, P(u32), u32]
         lib.or_get_counts.restype = None
@@ -117,14 +118,16 @@ def load():
         lib.or_get_population.restype = None
         lib.or_get_couplings.argtypes = [C.c_void_p, P(C.c_int8), P(C.c_int8)]
         lib.or_get_couplings.restype = None
-        lib.or_weighted_average.argtypes = [C.c_void_p, P(u32), P(u32), u32, u32, u32, u32, C.c_void_p,
-                                            P(f64), P(f64), P(f64)]
+        lib.or_weighted_average.argtypes = [C.c_void_p, P(u32), P(u32), P(u32), u32, u32, u32, u32, C.c_void_p,
+                                            P(f64), P(f64), P(f64), P(f64)]
         lib.or_weighted_average.restype = C.c_int
         lib.or_bruteforce.argtypes = [u32, P(C.c_int8), P(C.c_int8), f64, P(f64), P(f64), P(f64), P(f64),
                                       P(f64), P(f64)]
         lib.or_bruteforce.restype = C.c_int
         lib.or_bruteforce_moments.argtypes = [u32, P(C.c_int8), P(C.c_int8), f64, P(f64)]
         lib.or_bruteforce_moments.restype = C.c_int
+        lib.or_wang_pairing.argtypes = [u32, u32, u32, u32, P(u32), P(u32), P(u32)]
+        lib.or_wang_pairing.restype = C.c_int
         lib.or_kaufman_lnZ.argtypes = [u32, f64]
         lib.or_kaufman_lnZ.restype = f64
         lib.or_dos_transfer.argtypes = [u32, P(C.c_int8), P(C.c_int8), P(C.c_uint64), P(C.c_uint64)]
@@ -193,6 +196,16 @@ def bruteforce(L, Jr, Jd, beta):
         raise ValueError("bruteforce: lattice too large")
     lnZ, e, c, m, chi = (o.value for o in out)
     return dict(lnZ=lnZ, e=e, c=c, absm=m, chi=chi, pE=pE)
+
+
+def wang_pairing(seed, run_id, step, fam):
+    """Wang pairing of replicas with families fam (Sec. III.D): (pi* or None, swaps)."""
+    lib = load()
+    f = np.ascontiguousarray(fam, dtype=np.uint32)
+    pi = np.zeros(max(1, len(f)), dtype=np.uint32)
+    sw = C.c_uint32(0)
+    ok = lib.or_wang_pairing(seed, run_id, step, len(f), _p(f, C.c_uint32), _p(pi, C.c_uint32), C.byref(sw))
+    return (pi[:len(f)] if ok else None), int(sw.value)
 
 
 def bruteforce_moments(L, Jr, Jd, beta):
@@ -280,8 +293,14 @@ class OracleRun:
     def qhist(self, step):
         a = np.zeros(self.N + 1, dtype=np.uint32)
         b = np.zeros(self.N + 1, dtype=np.uint32)
-        self.lib.or_get_qhist(self.h, step, _p(a, C.c_uint32), _p(b, C.c_uint32))
+        self.lib.or_get_qhist(self.h, step, _p(a, C.c_uint32), _p(b, C.c_uint32), None)
         return a, b
+
+    def qhist_wang(self, step):
+        """Histogram over d of the Wang pairs at this step (zeros if none were measured)."""
+        w = np.zeros(self.N + 1, dtype=np.uint32)
+        self.lib.or_get_qhist(self.h, step, None, None, _p(w, C.c_uint32))
+        return w
 
     def counts(self, n):
         r = np.zeros(n, dtype=np.uint32)
@@ -311,21 +330,24 @@ class OracleRun:
                 raise RuntimeError(f"or_step failed ({rc})")
 
 
-def weighted_average(recs, N, kind=0, qh=None, qh_pair=None, return_weights=False):
-    """recs: array [M, n_steps] of RECORD_DTYPE; qh: uint32 [M, n_steps, N+1]."""
+def weighted_average(recs, N, kind=0, qh=None, qh_pair=None, return_weights=False, qh_wang=None):
+    """recs: array [M, n_steps] of RECORD_DTYPE; qh, qh_pair, qh_wang: uint32 [M, n_steps, N+1].
+    Returns (out, Pq, Pq_pair), then Pq_wang if qh_wang is given, then the weights if asked."""
     lib = load()
     recs = np.ascontiguousarray(recs, dtype=RECORD_DTYPE)
     M, n = recs.shape
     out = np.zeros(n, dtype=WAVG_DTYPE)
     Pq = np.zeros((n, N + 1)) if qh is not None else None
     Pp = np.zeros((n, N + 1)) if qh_pair is not None else None
+    Pw = np.zeros((n, N + 1)) if qh_wang is not None else None
     qh = np.ascontiguousarray(qh, dtype=np.uint32) if qh is not None else None
     qh_pair = np.ascontiguousarray(qh_pair, dtype=np.uint32) if qh_pair is not None else None
+    qh_wang = np.ascontiguousarray(qh_wang, dtype=np.uint32) if qh_wang is not None else None
     w = np.zeros((n, M)) if return_weights else None
-    rc = lib.or_weighted_average(recs.ctypes.data, _p(qh, C.c_uint32), _p(qh_pair, C.c_uint32), M, n, N, kind,
-                                 out.ctypes.data, _p(Pq, C.c_double), _p(Pp, C.c_double), _p(w, C.c_double))
+    rc = lib.or_weighted_average(recs.ctypes.data, _p(qh, C.c_uint32), _p(qh_pair, C.c_uint32),
+                                 _p(qh_wang, C.c_uint32), M, n, N, kind, out.ctypes.data, _p(Pq, C.c_double),
+                                 _p(Pp, C.c_double), _p(Pw, C.c_double), _p(w, C.c_double))
     if rc:
         raise ValueError(f"or_weighted_average failed ({rc})")
-    if return_weights:
-        return out, Pq, Pp, w
-    return out, Pq, Pp
+    res = (out, Pq, Pp) + ((Pw,) if qh_wang is not None else ()) + ((w,) if return_weights else ())
+    return res

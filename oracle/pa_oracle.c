@@ -34,6 +34,8 @@
  *                                    ctr (k>>2, j, step, SWEEP<<24 | t<<1 | c), word k&3
  *   energy draw of replica j (theta = infinity, Sec. V.B):
  *                                    ctr (j, 0, step, DOS<<24),               words 0,1
+ *   permutation keys of replica j (Wang pairing, Sec. III.D):
+ *                                    ctr (j, 0, step, WANG<<24),              words 0,1 (pi), 2,3 (sigma)
  * Build with -ffp-contract=off: no fused multiply-add anywhere in the FP64 paths.
  */
 #include <math.h>
@@ -47,6 +49,8 @@
 #define OR_TAG_MULTINOMIAL 4u
 #define OR_TAG_DISORDER 5u
 #define OR_TAG_DOS 6u
+#define OR_TAG_WANG 7u
+#define OR_WANG_IDX_BITS 13u     /* Wang pairing: R_cap <= 2^13 */
 #define OR_THETA_INF 0xFFFFFFFFu /* theta = infinity: simple sampling of the exact energy distribution */
 
 #define OR_OK 0
@@ -108,7 +112,7 @@ typedef struct {
     const double *beta;    /* schedule, non-decreasing */
     uint32_t seed, run_id, disorder_id;
     uint32_t resample;     /* 0 = nearest integer, 1 = multinomial */
-    uint32_t overlap;      /* bit 0: index-shift q; bit 1: q against a paired run */
+    uint32_t overlap;      /* bit 0: index-shift q; bit 1: q against a paired run; bit 2: Wang pairing */
     const double *log_g;   /* theta = OR_THETA_INF: ln g(E) at E = 2u - 2N, u = 0..2N (-INFINITY where g = 0) */
 } or_desc;
 
@@ -134,6 +138,9 @@ typedef struct {
     uint64_t sumE4[2];     /* sum_j H_j^4 */
     uint64_t sumAbsM3[2];  /* sum_j |M_j|^3 */
     uint64_t sumM4[2];     /* sum_j M_j^4 */
+    int64_t sum_absq_wang; /* sum over the R_i Wang pairs (k, pi*_k) of |N - 2 d| */
+    uint32_t n_q_wang;     /* R_i, or 0 when no pairing without a shared family was found */
+    uint32_t wang_swaps;   /* transpositions made by the pairing search */
 } or_record;
 
 static void put_i128(uint64_t w[2], __int128 v)
@@ -164,6 +171,7 @@ typedef struct {
     or_record *rec;        /* [n_beta] */
     uint32_t *qhist;       /* [n_beta][N+1] index-shift overlap histogram over d */
     uint32_t *qhist_pair;  /* [n_beta][N+1] */
+    uint32_t *qhist_wang;  /* [n_beta][N+1] Wang-pairing overlap histogram */
 } or_run;
 
 /* ------------------------------------------------------------------------- */
@@ -282,6 +290,73 @@ static uint32_t hamming(const int8_t *a, const int8_t *b, uint32_t N)
     return d;
 }
 
+/* Independent pairings from permutations (Sec. III.D, the method of Wang et al.
+ * with the random search pattern sigma).  A random permutation of 0..R-1 lists
+ * the replica indices j in ascending order of 64-bit keys drawn per replica, the
+ * low 13 bits of each key replaced by j (so no two keys tie). */
+static int cmp_u64(const void *x, const void *y)
+{
+    uint64_t u = *(const uint64_t *)x, v = *(const uint64_t *)y;
+    return u < v ? -1 : u > v ? 1 : 0;
+}
+
+static void wang_permutation(uint32_t seed, uint32_t run_id, uint32_t step, uint32_t R, int which, uint32_t *out,
+                             uint64_t *tmp)
+{
+    const uint64_t mask = ((uint64_t)1 << OR_WANG_IDX_BITS) - 1;
+    for (uint32_t j = 0; j < R; ++j) {
+        uint32_t ctr[4] = {j, 0, step, OR_TAG_WANG << 24}, key[2] = {seed, run_id}, o[4];
+        or_philox4x32_10(ctr, key, o);
+        uint64_t k = which ? ((uint64_t)o[2] << 32 | o[3]) : ((uint64_t)o[0] << 32 | o[1]);
+        tmp[j] = (k & ~mask) | j;
+    }
+    qsort(tmp, R, sizeof(uint64_t), cmp_u64);
+    for (uint32_t k = 0; k < R; ++k) out[k] = (uint32_t)(tmp[k] & mask);
+}
+
+/* Starting from a random permutation pi, visit the positions k = sigma_0,
+ * sigma_1, ... (sigma a second random permutation); where replica k and pi_k
+ * share a family, try the positions p = sigma_{i+1}, sigma_{i+2}, ... (indices
+ * mod R) until pi_p is not in k's family and pi_k is not in p's family, then
+ * swap pi_k and pi_p.  A swap leaves both positions without a shared family and
+ * changes no other, so one pass suffices.  Returns 1 with pi = pi*, or 0 if a
+ * search tried all R - 1 positions in vain (possible once a family holds more
+ * than R/2 replicas); *swaps counts the swaps made.  f: family of each replica;
+ * the keys come from (seed, run_id) at temperature index `step`. */
+int or_wang_pairing(uint32_t seed, uint32_t run_id, uint32_t step, uint32_t R, const uint32_t *f, uint32_t *pi,
+                    uint32_t *swaps)
+{
+    if (R > (1u << OR_WANG_IDX_BITS)) return 0;
+    uint32_t *sigma = (uint32_t *)malloc(sizeof(uint32_t) * R);
+    uint64_t *tmp = (uint64_t *)malloc(sizeof(uint64_t) * R);
+    int ok = sigma && tmp;
+    *swaps = 0;
+    if (ok) {
+        wang_permutation(seed, run_id, step, R, 0, pi, tmp);
+        wang_permutation(seed, run_id, step, R, 1, sigma, tmp);
+        for (uint32_t i = 0; i < R && ok; ++i) {
+            uint32_t k = sigma[i];
+            if (f[pi[k]] != f[k]) continue;
+            int found = 0;
+            for (uint32_t l = 1; l < R; ++l) {
+                uint32_t p = sigma[(i + l) % R];
+                if (f[pi[p]] != f[k] && f[pi[k]] != f[p]) {
+                    uint32_t t = pi[k];
+                    pi[k] = pi[p];
+                    pi[p] = t;
+                    *swaps += 1;
+                    found = 1;
+                    break;
+                }
+            }
+            ok = found;
+        }
+    }
+    free(sigma);
+    free(tmp);
+    return ok;
+}
+
 static void measure(or_run *a, uint32_t step)
 {
     or_record *rc = &a->rec[step];
@@ -338,6 +413,25 @@ static void measure(or_run *a, uint32_t step)
         }
         rc->n_q = h;
     }
+    /* Wang pairs (k, pi*_k), k = 0..R-1: every replica used twice */
+    rc->n_q_wang = 0;
+    rc->sum_absq_wang = 0;
+    rc->wang_swaps = 0;
+    if (a->d.overlap & 4u) {
+        uint32_t *hist = a->qhist_wang + (size_t)step * (N + 1);
+        memset(hist, 0, sizeof(uint32_t) * (N + 1));
+        uint32_t *pi = (uint32_t *)malloc(sizeof(uint32_t) * (R ? R : 1));
+        if (pi && or_wang_pairing(a->d.seed, a->d.run_id, step, R, a->fam, pi, &rc->wang_swaps)) {
+            for (uint32_t k = 0; k < R; ++k) {
+                uint32_t dd = hamming(a->s + (size_t)k * N, a->s + (size_t)pi[k] * N, N);
+                hist[dd] += 1;
+                int64_t qn = (int64_t)N - 2 * (int64_t)dd;
+                rc->sum_absq_wang += qn < 0 ? -qn : qn;
+            }
+            rc->n_q_wang = R;
+        }
+        free(pi);
+    }
 }
 
 /* Overlaps between two independent populations of the same disorder sample:
@@ -385,6 +479,7 @@ static void free_run(or_run *a)
     free(a->rec);
     free(a->qhist);
     free(a->qhist_pair);
+    free(a->qhist_wang);
     free(a);
 }
 
@@ -460,6 +555,7 @@ or_run *or_create(const or_desc *d, int *status)
     *status = OR_ERR_INVALID;
     if (d->L < 4 || (d->L & 1u) || d->R < 1 || d->R_cap < d->R || d->n_beta < 1 || !d->beta) return NULL;
     if (d->theta == OR_THETA_INF && (!d->log_g || d->overlap)) return NULL;
+    if ((d->overlap & 4u) && d->R_cap > (1u << OR_WANG_IDX_BITS)) return NULL;
     for (uint32_t i = 1; i < d->n_beta; ++i)
         if (!(d->beta[i] >= d->beta[i - 1])) return NULL;
     or_run *a = (or_run *)calloc(1, sizeof(or_run));
@@ -486,8 +582,10 @@ or_run *or_create(const or_desc *d, int *status)
     a->rec = (or_record *)calloc(d->n_beta, sizeof(or_record));
     a->qhist = (uint32_t *)calloc((size_t)d->n_beta * (N + 1), sizeof(uint32_t));
     a->qhist_pair = (uint32_t *)calloc((size_t)d->n_beta * (N + 1), sizeof(uint32_t));
+    a->qhist_wang = (uint32_t *)calloc((size_t)d->n_beta * (N + 1), sizeof(uint32_t));
     if (!a->beta || !a->s || !a->s_tmp || !a->E || !a->M || !a->E_tmp || !a->M_tmp || !a->fam ||
-        !a->fam_tmp || !a->r || !a->Jr || !a->Jd || !a->rec || !a->qhist || !a->qhist_pair) {
+        !a->fam_tmp || !a->r || !a->Jr || !a->Jd || !a->rec || !a->qhist || !a->qhist_pair ||
+        !a->qhist_wang) {
         free_run(a);
         *status = OR_ERR_OOM;
         return NULL;
@@ -684,11 +782,12 @@ int or_step(or_run *a)
 uint32_t or_current_step(const or_run *a) { return a->step; }
 uint32_t or_current_R(const or_run *a) { return a->R_cur; }
 void or_get_record(const or_run *a, uint32_t step, or_record *out) { *out = a->rec[step]; }
-void or_get_qhist(const or_run *a, uint32_t step, uint32_t *out, uint32_t *out_pair)
+void or_get_qhist(const or_run *a, uint32_t step, uint32_t *out, uint32_t *out_pair, uint32_t *out_wang)
 {
     size_t n = a->N + 1;
     if (out) memcpy(out, a->qhist + (size_t)step * n, sizeof(uint32_t) * n);
     if (out_pair) memcpy(out_pair, a->qhist_pair + (size_t)step * n, sizeof(uint32_t) * n);
+    if (out_wang) memcpy(out_wang, a->qhist_wang + (size_t)step * n, sizeof(uint32_t) * n);
 }
 void or_get_counts(const or_run *a, uint32_t *r, uint32_t n) { memcpy(r, a->r, sizeof(uint32_t) * n); }
 void or_get_population(const or_run *a, int8_t *s, int32_t *E, int32_t *M, uint32_t *fam)
@@ -707,7 +806,8 @@ void or_get_couplings(const or_run *a, int8_t *Jr, int8_t *Jd)
 
 /* ------------------------------------------------------------------------- */
 /* Weighted averages over M independent runs, Sec. IV.                        */
-/* recs[m * n_steps + i], qh[(m * n_steps + i) * (N+1)] (optional).           */
+/* recs[m * n_steps + i], qh[(m * n_steps + i) * (N+1)] (optional; likewise  */
+/* qh_pair and qh_wang, with Pq, Pq_pair, Pq_wang [n_steps][N+1] out).        */
 /* kind 0: free-energy weight w (Eq. appropriateWeight);                      */
 /* kind 1: simplified weight (Eq. simpleWeight, read with beta = beta_i).     */
 /* ------------------------------------------------------------------------- */
@@ -725,6 +825,7 @@ typedef struct {
     double Wk3_m, Wk4_m;             /* Eq. W_k, k = 3, 4, for O = |m| */
     double W_U4;                     /* Binder cumulant 1 - W[m^4] / (3 W[m^2]^2) */
     double W_U4_conf;                /* Eq. W_conf applied to each run's 1 - m^4 / (3 (m^2)^2) */
+    double W_absq_wang;              /* Eq. W_conf applied to |q| over the Wang pairs */
 } or_wavg;
 
 /* Eq. W_k (Sec. IV.E): the k-th central moment from the weighted raw moments
@@ -753,9 +854,9 @@ static double log_weight(const or_record *recs, uint32_t n_steps, uint32_t m, ui
     return lam;
 }
 
-int or_weighted_average(const or_record *recs, const uint32_t *qh, const uint32_t *qh_pair, uint32_t M,
-                        uint32_t n_steps, uint32_t N, uint32_t kind, or_wavg *out, double *Pq, double *Pq_pair,
-                        double *w_out /* [n_steps][M] or NULL */)
+int or_weighted_average(const or_record *recs, const uint32_t *qh, const uint32_t *qh_pair, const uint32_t *qh_wang,
+                        uint32_t M, uint32_t n_steps, uint32_t N, uint32_t kind, or_wavg *out, double *Pq,
+                        double *Pq_pair, double *Pq_wang, double *w_out /* [n_steps][M] or NULL */)
 {
     if (M == 0 || n_steps == 0 || N == 0 || kind > 1) return OR_ERR_INVALID;
     double *w = (double *)malloc(sizeof(double) * M);
@@ -814,6 +915,7 @@ int or_weighted_average(const or_record *recs, const uint32_t *qh, const uint32_
             o->W_U4_conf += w[m] * (1.0 - m4 / (3.0 * m2 * m2)); /* NaN if a run has M = 0 throughout */
             if (r->n_q) o->W_absq += w[m] * ((double)r->sum_absq / (Nd * (double)r->n_q));
             if (r->n_q_pair) o->W_absq_pair += w[m] * ((double)r->sum_absq_pair / (Nd * (double)r->n_q_pair));
+            if (r->n_q_wang) o->W_absq_wang += w[m] * ((double)r->sum_absq_wang / (Nd * (double)r->n_q_wang));
             o->sum_w += w[m];
             if (w[m] > o->w_max) o->w_max = w[m];
         }
@@ -859,6 +961,16 @@ int or_weighted_average(const or_record *recs, const uint32_t *qh, const uint32_
                 if (!r->n_q_pair) continue;
                 const uint32_t *hq = qh_pair + ((size_t)m * n_steps + i) * (N + 1);
                 for (uint32_t dd = 0; dd <= N; ++dd) P[dd] += w[m] * ((double)hq[dd] / (double)r->n_q_pair);
+            }
+        }
+        if (Pq_wang && qh_wang) {
+            double *P = Pq_wang + (size_t)i * (N + 1);
+            for (uint32_t dd = 0; dd <= N; ++dd) P[dd] = 0.0;
+            for (uint32_t m = 0; m < M; ++m) {
+                const or_record *r = &recs[(size_t)m * n_steps + i];
+                if (!r->n_q_wang) continue;
+                const uint32_t *hq = qh_wang + ((size_t)m * n_steps + i) * (N + 1);
+                for (uint32_t dd = 0; dd <= N; ++dd) P[dd] += w[m] * ((double)hq[dd] / (double)r->n_q_wang);
             }
         }
         for (uint32_t m = 0; m < M; ++m) wprev[m] = w[m];

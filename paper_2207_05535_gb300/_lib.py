@@ -46,6 +46,7 @@ RECORD_DTYPE = np.dtype([
     ("R", "u4"), ("R_target", "u4"), ("n_fam", "u4"), ("max_fam", "u4"),
     ("n_q", "u4"), ("n_q_pair", "u4"), ("N", "u4"), ("status", "u4"),
     ("sumE3", "u8", (2,)), ("sumE4", "u8", (2,)), ("sumAbsM3", "u8", (2,)), ("sumM4", "u8", (2,)),
+    ("sum_absq_wang", "i8"), ("n_q_wang", "u4"), ("wang_swaps", "u4"),
 ])
 
 WAVG_DTYPE = np.dtype([
@@ -55,7 +56,7 @@ WAVG_DTYPE = np.dtype([
     ("w_max", "f8"), ("sum_w", "f8"),
     ("W_e3", "f8"), ("W_e4", "f8"), ("W_m3", "f8"), ("W_m4", "f8"),
     ("Wk3_e", "f8"), ("Wk4_e", "f8"), ("Wk3_m", "f8"), ("Wk4_m", "f8"),
-    ("W_U4", "f8"), ("W_U4_conf", "f8"),
+    ("W_U4", "f8"), ("W_U4_conf", "f8"), ("W_absq_wang", "f8"),
 ])
 
 EXPORTS = ["pa_create", "pa_create_ex", "pa_server_create", "pa_admit", "pa_retire", "pa_finished", "pa_run_state",
@@ -89,12 +90,13 @@ def load(path: str = LIB_PATH):
         lib.pa_reset.argtypes = [vp]
         lib.pa_anneal_step.argtypes = [vp, u32, C.c_int]
         lib.pa_sync.argtypes = [vp]
-        lib.pa_records.argtypes = [vp, u32, vp, P(u32), P(u32)]
-        lib.pa_measure.argtypes = [vp, u32, u32, vp, P(u32), P(u32)]
+        lib.pa_records.argtypes = [vp, u32, vp, P(u32), P(u32), P(u32)]
+        lib.pa_measure.argtypes = [vp, u32, u32, vp, P(u32), P(u32), P(u32)]
         lib.pa_population.argtypes = [vp, u32, P(C.c_int8), P(C.c_int32), P(C.c_int32), P(u32), P(u32), P(u32)]
-        lib.pa_weighted_average_runs.argtypes = [vp, P(u32), u32, u32, u32, vp, P(C.c_double), P(C.c_double)]
-        lib.pa_weighted_average.argtypes = [vp, P(u32), P(u32), u32, u32, u32, u32, vp, P(C.c_double),
-                                            P(C.c_double), vp]
+        lib.pa_weighted_average_runs.argtypes = [vp, P(u32), u32, u32, u32, vp, P(C.c_double), P(C.c_double),
+                                                 P(C.c_double)]
+        lib.pa_weighted_average.argtypes = [vp, P(u32), P(u32), P(u32), u32, u32, u32, u32, vp, P(C.c_double),
+                                            P(C.c_double), P(C.c_double), vp]
         lib.pa_weighted_average_noalloc.argtypes = [vp, u32, u32, u32, u32, vp, vp]
         lib.pa_launch_count.argtypes = [vp]
         lib.pa_launch_count.restype = C.c_uint64
@@ -205,18 +207,23 @@ def pa_sync(h):
     _check(rc, "pa_sync")
 
 
-def pa_records(h, run, n_beta, N=None, qhist=False):
+def pa_records(h, run, n_beta, N=None, qhist=False, wang=False):
+    """Records [n_beta]; with qhist also the index-shift and pair histograms
+    (rec, qa, qb); with wang the Wang-pair histograms are appended."""
     lib = load()
     rec = np.zeros(n_beta, dtype=RECORD_DTYPE)
     qa = np.zeros((n_beta, N + 1), dtype=np.uint32) if qhist else None
     qb = np.zeros((n_beta, N + 1), dtype=np.uint32) if qhist else None
-    _check(lib.pa_records(h, run, rec.ctypes.data, _p(qa, C.c_uint32), _p(qb, C.c_uint32)), "pa_records")
-    return (rec, qa, qb) if qhist else rec
+    qw = np.zeros((n_beta, N + 1), dtype=np.uint32) if wang else None
+    _check(lib.pa_records(h, run, rec.ctypes.data, _p(qa, C.c_uint32), _p(qb, C.c_uint32), _p(qw, C.c_uint32)),
+           "pa_records")
+    out = (rec,) + ((qa, qb) if qhist else ()) + ((qw,) if wang else ())
+    return out if len(out) > 1 else rec
 
 
 def pa_measure(h, run, step):
     rec = np.zeros(1, dtype=RECORD_DTYPE)
-    _check(load().pa_measure(h, run, step, rec.ctypes.data, None, None), "pa_measure")
+    _check(load().pa_measure(h, run, step, rec.ctypes.data, None, None, None), "pa_measure")
     return rec[0]
 
 
@@ -233,30 +240,38 @@ def pa_population(h, run, R_cap, N):
     return s[:n], E[:n], M[:n], fam[:n], step.value
 
 
-def pa_weighted_average_runs(h, run_idx, M, n_steps, N, kind=0, q=False):
+def pa_weighted_average_runs(h, run_idx, M, n_steps, N, kind=0, q=False, wang=False):
+    """out [G][n_steps]; with q also (Pq, Pq_pair); with wang Pq_wang is appended."""
     idx = np.ascontiguousarray(run_idx, dtype=np.uint32).reshape(-1)
     G = len(idx) // M
     out = np.zeros((G, n_steps), dtype=WAVG_DTYPE)
     Pq = np.zeros((G, n_steps, N + 1)) if q else None
     Pp = np.zeros((G, n_steps, N + 1)) if q else None
+    Pw = np.zeros((G, n_steps, N + 1)) if wang else None
     _check(load().pa_weighted_average_runs(h, _p(idx, C.c_uint32), G, M, kind, out.ctypes.data,
-                                           _p(Pq, C.c_double), _p(Pp, C.c_double)), "pa_weighted_average_runs")
-    return (out, Pq, Pp) if q else out
+                                           _p(Pq, C.c_double), _p(Pp, C.c_double), _p(Pw, C.c_double)),
+           "pa_weighted_average_runs")
+    res = (out,) + ((Pq, Pp) if q else ()) + ((Pw,) if wang else ())
+    return res if len(res) > 1 else out
 
 
-def pa_weighted_average(recs, N, kind=0, qh=None, qh_pair=None, stream=None):
+def pa_weighted_average(recs, N, kind=0, qh=None, qh_pair=None, stream=None, qh_wang=None):
+    """(out, Pq, Pq_pair), with Pq_wang appended when qh_wang is given."""
     recs = np.ascontiguousarray(recs, dtype=RECORD_DTYPE)
     M, n = recs.shape
     out = np.zeros(n, dtype=WAVG_DTYPE)
     qh = np.ascontiguousarray(qh, dtype=np.uint32) if qh is not None else None
     qh_pair = np.ascontiguousarray(qh_pair, dtype=np.uint32) if qh_pair is not None else None
+    qh_wang = np.ascontiguousarray(qh_wang, dtype=np.uint32) if qh_wang is not None else None
     Pq = np.zeros((n, N + 1)) if qh is not None else None
     Pp = np.zeros((n, N + 1)) if qh_pair is not None else None
+    Pw = np.zeros((n, N + 1)) if qh_wang is not None else None
     s = C.c_void_p(stream) if stream else None
-    _check(load().pa_weighted_average(recs.ctypes.data, _p(qh, C.c_uint32), _p(qh_pair, C.c_uint32), M, n, N, kind,
-                                      out.ctypes.data, _p(Pq, C.c_double), _p(Pp, C.c_double), s),
+    _check(load().pa_weighted_average(recs.ctypes.data, _p(qh, C.c_uint32), _p(qh_pair, C.c_uint32),
+                                      _p(qh_wang, C.c_uint32), M, n, N, kind, out.ctypes.data, _p(Pq, C.c_double),
+                                      _p(Pp, C.c_double), _p(Pw, C.c_double), s),
            "pa_weighted_average")
-    return out, Pq, Pp
+    return (out, Pq, Pp) + ((Pw,) if qh_wang is not None else ())
 
 
 def pa_launch_count(h):
@@ -340,17 +355,17 @@ class Engine:
     def sync(self):
         pa_sync(self.h)
 
-    def records(self, run, qhist=False):
+    def records(self, run, qhist=False, wang=False):
         r = self.runs[run]
-        return pa_records(self.h, run, r.n_beta, r.N, qhist)
+        return pa_records(self.h, run, r.n_beta, r.N, qhist, wang)
 
     def population(self, run):
         r = self.runs[run]
         return pa_population(self.h, run, r.R_cap, r.N)
 
-    def weighted_average(self, run_idx, M, kind=0, q=False):
+    def weighted_average(self, run_idx, M, kind=0, q=False, wang=False):
         r = self.runs[int(np.asarray(run_idx).reshape(-1)[0])]
-        return pa_weighted_average_runs(self.h, run_idx, M, r.n_beta, r.N, kind, q)
+        return pa_weighted_average_runs(self.h, run_idx, M, r.n_beta, r.N, kind, q, wang)
 
     @property
     def launches(self):

@@ -142,6 +142,9 @@ struct pa_engine {
     std::vector<uint32_t> q_runs;
     uint32_t init_n = 0, init_tiles = 0;
     std::vector<uint32_t> inf_runs;  // resident theta = PA_THETA_INF runs
+    std::vector<uint32_t> wang_runs;  // resident runs with PA_Q_WANG
+    uint64_t wang_off = 0, init_wang_off = 0;
+    uint32_t wang_maxcap = 0, init_wang_n = 0, init_wang_maxcap = 0;
     uint64_t inf_off = 0, init_inf_off = 0;
     uint32_t inf_maxR = 0, init_inf_n = 0, init_inf_maxR = 0;
     std::vector<SweepGroup> groups;
@@ -235,8 +238,9 @@ pa_status validate(const pa_run_desc *runs, uint32_t n)
     for (uint32_t r = 0; r < n; ++r) {
         const pa_run_desc &d = runs[r];
         if (d.L < 4 || d.L > 256 || (d.L & 1u)) return PA_ERR_INVALID_ARG;
-        if (d.model > PA_EA_PMJ || d.resample > PA_MULTINOMIAL || d.overlap > 3u || d.reserved)
+        if (d.model > PA_EA_PMJ || d.resample > PA_MULTINOMIAL || d.overlap > 7u || d.reserved)
             return PA_ERR_INVALID_ARG;
+        if ((d.overlap & PA_Q_WANG) && cap_of(d) > PA_WANG_MAX_RCAP) return PA_ERR_INVALID_ARG;
         if (d.R < 1 || d.n_beta < 1 || !d.beta) return PA_ERR_INVALID_ARG;
         if (d.theta == PA_THETA_INF) {  // needs a density of states; no configurations, so no overlaps
             if (!d.log_g || d.overlap) return PA_ERR_INVALID_ARG;
@@ -291,6 +295,7 @@ pa_status alloc_pools(pa_engine *e, const pa_server_config &c)
     PA_TRY(dalloc(e, &e->P.rec, c.record_capacity));
     PA_TRY(dalloc(e, &e->P.qh, c.qhist_words));
     PA_TRY(dalloc(e, &e->P.qhp, c.qhist_words));
+    PA_TRY(dalloc(e, &e->P.qhw, c.qhist_words));
     PA_TRY(dalloc(e, &e->P.J, c.coupling_words));
     PA_TRY(dalloc(e, &e->P.scratch, c.scratch_words));
     PA_TRY(dalloc(e, &e->P.status, 1));
@@ -298,7 +303,7 @@ pa_status alloc_pools(pa_engine *e, const pa_server_config &c)
     PA_TRY(dalloc(e, &e->d_thr, 2 * c.record_capacity));
     PA_TRY(dalloc(e, &e->d_wtoff, c.record_capacity));
     PA_TRY(dalloc(e, &e->d_wt, c.table_doubles));
-    e->meta_cap = 11ull * e->S + 3ull * 128 + 1024;
+    e->meta_cap = 13ull * e->S + 3ull * 128 + 1024;
     PA_TRY(dalloc(e, &e->d_meta, e->meta_cap));
     PA_CUDA(cudaMemsetAsync(e->P.status, 0, sizeof(uint32_t), e->stream));
     e->P.runs = e->d_runs;
@@ -522,6 +527,7 @@ pa_status admit(pa_engine *e, const pa_run_desc *runs, uint32_t n, uint32_t *slo
         if (!err) err = cudaMemsetAsync(e->P.rec + g.rec, 0, sizeof(pa_step_record) * d.n_beta, e->stream);
         if (!err && nq) err = cudaMemsetAsync(e->P.qh + g.qh, 0, sizeof(uint32_t) * nq, e->stream);
         if (!err && nq) err = cudaMemsetAsync(e->P.qhp + g.qh, 0, sizeof(uint32_t) * nq, e->stream);
+        if (!err && nq) err = cudaMemsetAsync(e->P.qhw + g.qh, 0, sizeof(uint32_t) * nq, e->stream);
         if (!err) err = cudaStreamSynchronize(e->stream);  // host buffers must outlive the copies
         if (err) return cuda_fail(err, "admit upload");
         e->h2d += sizeof(RunDev) + sizeof rs + sizeof(double) * d.n_beta +
@@ -559,6 +565,15 @@ pa_status rebuild(pa_engine *e)
     }
     e->q_off = m.size();
     m.insert(m.end(), e->q_runs.begin(), e->q_runs.end());
+    e->wang_runs.clear();
+    e->wang_maxcap = 0;
+    for (uint32_t s : e->active)
+        if (e->rd[s].overlap & PA_Q_WANG) {
+            e->wang_runs.push_back(s);
+            e->wang_maxcap = std::max(e->wang_maxcap, e->rd[s].R_cap);
+        }
+    e->wang_off = m.size();
+    m.insert(m.end(), e->wang_runs.begin(), e->wang_runs.end());
     e->groups.clear();
     std::map<uint32_t, size_t> gi;  // lattice size -> group, in order of first appearance
     e->inf_runs.clear();
@@ -625,6 +640,15 @@ pa_status rebuild(pa_engine *e)
             m.push_back(s);
             ++e->init_inf_n;
             e->init_inf_maxR = std::max(e->init_inf_maxR, e->rd[s].R);
+        }
+    e->init_wang_off = m.size();
+    e->init_wang_n = 0;
+    e->init_wang_maxcap = 0;
+    for (uint32_t s : e->pending)
+        if (e->rd[s].overlap & PA_Q_WANG) {
+            m.push_back(s);
+            ++e->init_wang_n;
+            e->init_wang_maxcap = std::max(e->init_wang_maxcap, e->rd[s].R_cap);
         }
     e->init_q_off = m.size();  // pending runs with overlaps: their step-0 overlaps only
     e->init_q_n = 0;
@@ -705,11 +729,24 @@ pa_status enqueue_pending(pa_engine *e)
         timed_launch(e, PA_K_OVERLAP, [&] {
             launch_overlap(e->P, meta(e, e->init_q_off), e->init_q_n, e->max_Rcap_active, 1, e->stream);
         });
+    if (e->init_wang_n)
+        timed_launch(e, PA_K_OVERLAP, [&] {
+            launch_wang(e->P, meta(e, e->init_wang_off), e->init_wang_n, e->init_wang_maxcap, 1, e->stream);
+        });
     timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, runs, e->init_n, 1, e->stream); });
     e->pending.clear();
     e->dirty = true;  // the pending list is consumed
     PA_CUDA(cudaGetLastError());
     return PA_OK;
+}
+
+// Wang pairings of the runs that measure them (after the sweeps, like the overlaps).
+void enqueue_wang(pa_engine *e)
+{
+    if (e->wang_runs.empty()) return;
+    timed_launch(e, PA_K_OVERLAP, [&] {
+        launch_wang(e->P, meta(e, e->wang_off), (uint32_t)e->wang_runs.size(), e->wang_maxcap, 0, e->stream);
+    });
 }
 
 // Fresh energies for the theta = PA_THETA_INF runs (in place of their sweeps).
@@ -732,6 +769,7 @@ void enqueue_tick(pa_engine *e)
         timed_launch(e, PA_K_OVERLAP, [&] {
             launch_overlap(e->P, meta(e, e->q_off), (uint32_t)e->q_runs.size(), e->max_Rcap_active, 0, e->stream);
         });
+    enqueue_wang(e);
     timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, act, na, 0, e->stream); });
 }
 
@@ -778,6 +816,7 @@ pa_status enqueue_tuning_tick(pa_engine *e)
         timed_launch(e, PA_K_OVERLAP, [&] {
             launch_overlap(e->P, meta(e, e->q_off), (uint32_t)e->q_runs.size(), e->max_Rcap_active, 0, e->stream);
         });
+    enqueue_wang(e);
     timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, act, na, 0, e->stream); });
     PA_CUDA(cudaGetLastError());
     return PA_OK;
@@ -1028,6 +1067,7 @@ pa_status pa_reset(pa_engine *e)
             const uint64_t nq = (uint64_t)x.n_beta * (x.N + 1);
             PA_CUDA(cudaMemsetAsync(e->P.qh + x.qh_off, 0, sizeof(uint32_t) * nq, e->stream));
             PA_CUDA(cudaMemsetAsync(e->P.qhp + x.qh_off, 0, sizeof(uint32_t) * nq, e->stream));
+            PA_CUDA(cudaMemsetAsync(e->P.qhw + x.qh_off, 0, sizeof(uint32_t) * nq, e->stream));
         }
         e->rh[s].steps_done = 0;
         if (std::find(e->pending.begin(), e->pending.end(), s) == e->pending.end()) e->pending.push_back(s);
@@ -1134,32 +1174,36 @@ pa_status pa_transfer_bytes(const pa_engine *e, uint64_t *h2d, uint64_t *d2h)
 }
 
 pa_status pa_records(pa_engine *e, uint32_t run, pa_step_record *host_out, uint32_t *host_qhist,
-                     uint32_t *host_qhist_pair)
+                     uint32_t *host_qhist_pair, uint32_t *host_qhist_wang)
 {
     if (!slot_ok(e, run) || !host_out) return PA_ERR_INVALID_ARG;
     const RunDev &x = e->rd[run];
-    if ((host_qhist || host_qhist_pair) && !x.overlap) return PA_ERR_INVALID_ARG;
+    if ((host_qhist || host_qhist_pair || host_qhist_wang) && !x.overlap) return PA_ERR_INVALID_ARG;
     PA_TRY(prepare(e));
     PA_CUDA(cudaMemcpyAsync(host_out, e->P.rec + x.rec_off, sizeof(pa_step_record) * x.n_beta,
                             cudaMemcpyDeviceToHost, e->stream));
     const size_t nq = (size_t)x.n_beta * (x.N + 1);
-    e->d2h += sizeof(pa_step_record) * x.n_beta + sizeof(uint32_t) * nq * ((host_qhist ? 1 : 0) + (host_qhist_pair ? 1 : 0));
+    e->d2h += sizeof(pa_step_record) * x.n_beta +
+              sizeof(uint32_t) * nq * ((host_qhist ? 1 : 0) + (host_qhist_pair ? 1 : 0) + (host_qhist_wang ? 1 : 0));
     if (host_qhist)
         PA_CUDA(cudaMemcpyAsync(host_qhist, e->P.qh + x.qh_off, sizeof(uint32_t) * nq, cudaMemcpyDeviceToHost, e->stream));
     if (host_qhist_pair)
         PA_CUDA(cudaMemcpyAsync(host_qhist_pair, e->P.qhp + x.qh_off, sizeof(uint32_t) * nq, cudaMemcpyDeviceToHost,
                                 e->stream));
+    if (host_qhist_wang)
+        PA_CUDA(cudaMemcpyAsync(host_qhist_wang, e->P.qhw + x.qh_off, sizeof(uint32_t) * nq, cudaMemcpyDeviceToHost,
+                                e->stream));
     return sync_read(e);
 }
 
 pa_status pa_measure(pa_engine *e, uint32_t run, uint32_t step, pa_step_record *host_out, uint32_t *host_qhist,
-                     uint32_t *host_qhist_pair)
+                     uint32_t *host_qhist_pair, uint32_t *host_qhist_wang)
 {
     if (!slot_ok(e, run) || !host_out) return PA_ERR_INVALID_ARG;
     const RunDev &x = e->rd[run];
     if (step >= x.n_beta) return PA_ERR_INVALID_ARG;
     PA_TRY(prepare(e));
-    if ((host_qhist || host_qhist_pair) && !x.overlap) return PA_ERR_INVALID_ARG;
+    if ((host_qhist || host_qhist_pair || host_qhist_wang) && !x.overlap) return PA_ERR_INVALID_ARG;
     PA_CUDA(cudaMemcpyAsync(host_out, e->P.rec + x.rec_off + step, sizeof(pa_step_record), cudaMemcpyDeviceToHost,
                             e->stream));
     const size_t n1 = x.N + 1;
@@ -1168,6 +1212,9 @@ pa_status pa_measure(pa_engine *e, uint32_t run, uint32_t step, pa_step_record *
                                 cudaMemcpyDeviceToHost, e->stream));
     if (host_qhist_pair)
         PA_CUDA(cudaMemcpyAsync(host_qhist_pair, e->P.qhp + x.qh_off + step * n1, sizeof(uint32_t) * n1,
+                                cudaMemcpyDeviceToHost, e->stream));
+    if (host_qhist_wang)
+        PA_CUDA(cudaMemcpyAsync(host_qhist_wang, e->P.qhw + x.qh_off + step * n1, sizeof(uint32_t) * n1,
                                 cudaMemcpyDeviceToHost, e->stream));
     return sync_read(e);
 }
@@ -1224,7 +1271,8 @@ static pa_status ensure_wa(pa_engine *e, size_t bytes)
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 pa_status pa_weighted_average_runs(pa_engine *e, const uint32_t *run_idx, uint32_t n_groups, uint32_t M,
-                                   uint32_t weight_kind, pa_wavg *host_out, double *host_Pq, double *host_Pq_pair)
+                                   uint32_t weight_kind, pa_wavg *host_out, double *host_Pq, double *host_Pq_pair,
+                                   double *host_Pq_wang)
 {
     if (!e || !run_idx || !n_groups || !M || !host_out || weight_kind > PA_WEIGHT_SIMPLE) return PA_ERR_INVALID_ARG;
     if (!slot_ok(e, run_idx[0])) return PA_ERR_INVALID_ARG;
@@ -1236,7 +1284,7 @@ pa_status pa_weighted_average_runs(pa_engine *e, const uint32_t *run_idx, uint32
         if (!slot_ok(e, run_idx[k])) return PA_ERR_INVALID_ARG;
         const RunDev &x = e->rd[run_idx[k]];
         if (x.n_beta != n_steps || x.N != N) return PA_ERR_INVALID_ARG;
-        if ((host_Pq || host_Pq_pair) && !x.overlap) return PA_ERR_INVALID_ARG;
+        if ((host_Pq || host_Pq_pair || host_Pq_wang) && !x.overlap) return PA_ERR_INVALID_ARG;
         rec_off[k] = x.rec_off;
         qh_off[k] = x.qh_off;
     }
@@ -1246,7 +1294,8 @@ pa_status pa_weighted_average_runs(pa_engine *e, const uint32_t *run_idx, uint32
     const size_t b_out = b_qoff + align256(sizeof(pa_wavg) * n_groups * n_steps);
     const size_t b_w = b_out + align256(sizeof(double) * n_groups * n_steps * M);
     const size_t b_pq = b_w + align256(host_Pq ? sizeof(double) * nP : 0);
-    const size_t total = b_pq + align256(host_Pq_pair ? sizeof(double) * nP : 0);
+    const size_t b_pqp = b_pq + align256(host_Pq_pair ? sizeof(double) * nP : 0);
+    const size_t total = b_pqp + align256(host_Pq_wang ? sizeof(double) * nP : 0);
     pa_status s = ensure_wa(e, total);
     if (s != PA_OK) return s;
     char *base = static_cast<char *>(e->wa_buf);
@@ -1256,40 +1305,47 @@ pa_status pa_weighted_average_runs(pa_engine *e, const uint32_t *run_idx, uint32
     auto *d_w = reinterpret_cast<double *>(base + b_out);
     double *d_pq = host_Pq ? reinterpret_cast<double *>(base + b_w) : nullptr;
     double *d_pqp = host_Pq_pair ? reinterpret_cast<double *>(base + b_pq) : nullptr;
+    double *d_pqw = host_Pq_wang ? reinterpret_cast<double *>(base + b_pqp) : nullptr;
     PA_CUDA(cudaMemcpyAsync(d_roff, rec_off.data(), sizeof(unsigned long long) * nGM, cudaMemcpyHostToDevice, e->stream));
     PA_CUDA(cudaMemcpyAsync(d_qoff, qh_off.data(), sizeof(unsigned long long) * nGM, cudaMemcpyHostToDevice, e->stream));
     timed_launch(e, PA_K_WAVG, [&] {
-        launch_wavg(e->P.rec, d_roff, e->P.qh, e->P.qhp, d_qoff, n_groups, M, n_steps, N, weight_kind, d_out, d_w,
-                    d_pq, d_pqp, e->stream);
+        launch_wavg_wang(e->P.rec, d_roff, e->P.qh, e->P.qhp, e->P.qhw, d_qoff, n_groups, M, n_steps, N, weight_kind,
+                         d_out, d_w, d_pq, d_pqp, d_pqw, e->stream);
     });
-    e->launches += 1 + ((d_pq || d_pqp) ? 1 : 0);
+    e->launches += 1 + ((d_pq || d_pqp || d_pqw) ? 1 : 0);
     e->h2d += 2 * sizeof(unsigned long long) * nGM;
-    e->d2h += sizeof(pa_wavg) * n_groups * n_steps + sizeof(double) * nP * ((host_Pq ? 1 : 0) + (host_Pq_pair ? 1 : 0));
+    e->d2h += sizeof(pa_wavg) * n_groups * n_steps +
+              sizeof(double) * nP * ((host_Pq ? 1 : 0) + (host_Pq_pair ? 1 : 0) + (host_Pq_wang ? 1 : 0));
     PA_CUDA(cudaGetLastError());
     PA_CUDA(cudaMemcpyAsync(host_out, d_out, sizeof(pa_wavg) * n_groups * n_steps, cudaMemcpyDeviceToHost, e->stream));
     if (host_Pq) PA_CUDA(cudaMemcpyAsync(host_Pq, d_pq, sizeof(double) * nP, cudaMemcpyDeviceToHost, e->stream));
     if (host_Pq_pair)
         PA_CUDA(cudaMemcpyAsync(host_Pq_pair, d_pqp, sizeof(double) * nP, cudaMemcpyDeviceToHost, e->stream));
+    if (host_Pq_wang)
+        PA_CUDA(cudaMemcpyAsync(host_Pq_wang, d_pqw, sizeof(double) * nP, cudaMemcpyDeviceToHost, e->stream));
     return pa_sync(e);
 }
 
 pa_status pa_weighted_average(const pa_step_record *recs, const uint32_t *qhist, const uint32_t *qhist_pair,
-                              uint32_t M, uint32_t n_steps, uint32_t N, uint32_t weight_kind, pa_wavg *out,
-                              double *Pq, double *Pq_pair, void *cuda_stream)
+                              const uint32_t *qhist_wang, uint32_t M, uint32_t n_steps, uint32_t N,
+                              uint32_t weight_kind, pa_wavg *out, double *Pq, double *Pq_pair, double *Pq_wang,
+                              void *cuda_stream)
 {
     if (!recs || !M || !n_steps || !N || !out || weight_kind > PA_WEIGHT_SIMPLE) return PA_ERR_INVALID_ARG;
-    if ((Pq && !qhist) || (Pq_pair && !qhist_pair)) return PA_ERR_INVALID_ARG;
+    if ((Pq && !qhist) || (Pq_pair && !qhist_pair) || (Pq_wang && !qhist_wang)) return PA_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const size_t nr = (size_t)M * n_steps, nq = nr * (N + 1), nP = (size_t)n_steps * (N + 1);
     const size_t b_rec = align256(sizeof(pa_step_record) * nr);
     const size_t b_qh = b_rec + align256(qhist ? sizeof(uint32_t) * nq : 0);
     const size_t b_qhp = b_qh + align256(qhist_pair ? sizeof(uint32_t) * nq : 0);
-    const size_t b_off = b_qhp + align256(sizeof(unsigned long long) * M);
+    const size_t b_qhw = b_qhp + align256(qhist_wang ? sizeof(uint32_t) * nq : 0);
+    const size_t b_off = b_qhw + align256(sizeof(unsigned long long) * M);
     const size_t b_qoff = b_off + align256(sizeof(unsigned long long) * M);
     const size_t b_out = b_qoff + align256(sizeof(pa_wavg) * n_steps);
     const size_t b_w = b_out + align256(sizeof(double) * n_steps * M);
     const size_t b_pq = b_w + align256(Pq ? sizeof(double) * nP : 0);
-    const size_t total = b_pq + align256(Pq_pair ? sizeof(double) * nP : 0);
+    const size_t b_pqp = b_pq + align256(Pq_pair ? sizeof(double) * nP : 0);
+    const size_t total = b_pqp + align256(Pq_wang ? sizeof(double) * nP : 0);
     char *base = nullptr;
     cudaError_t err = cudaMalloc(&base, total);
     if (err != cudaSuccess) {
@@ -1305,24 +1361,30 @@ pa_status pa_weighted_average(const pa_step_record *recs, const uint32_t *qhist,
     auto *d_rec = reinterpret_cast<pa_step_record *>(base);
     auto *d_qh = qhist ? reinterpret_cast<uint32_t *>(base + b_rec) : nullptr;
     auto *d_qhp = qhist_pair ? reinterpret_cast<uint32_t *>(base + b_qh) : nullptr;
-    auto *d_roff = reinterpret_cast<unsigned long long *>(base + b_qhp);
+    auto *d_qhw = qhist_wang ? reinterpret_cast<uint32_t *>(base + b_qhp) : nullptr;
+    auto *d_roff = reinterpret_cast<unsigned long long *>(base + b_qhw);
     auto *d_qoff = reinterpret_cast<unsigned long long *>(base + b_off);
     auto *d_out = reinterpret_cast<pa_wavg *>(base + b_qoff);
     auto *d_w = reinterpret_cast<double *>(base + b_out);
     double *d_pq = Pq ? reinterpret_cast<double *>(base + b_w) : nullptr;
     double *d_pqp = Pq_pair ? reinterpret_cast<double *>(base + b_pq) : nullptr;
+    double *d_pqw = Pq_wang ? reinterpret_cast<double *>(base + b_pqp) : nullptr;
     do {
         if ((err = cudaMemcpyAsync(d_rec, recs, sizeof(pa_step_record) * nr, cudaMemcpyHostToDevice, st))) break;
         if (qhist && (err = cudaMemcpyAsync(d_qh, qhist, sizeof(uint32_t) * nq, cudaMemcpyHostToDevice, st))) break;
         if (qhist_pair && (err = cudaMemcpyAsync(d_qhp, qhist_pair, sizeof(uint32_t) * nq, cudaMemcpyHostToDevice, st)))
             break;
+        if (qhist_wang && (err = cudaMemcpyAsync(d_qhw, qhist_wang, sizeof(uint32_t) * nq, cudaMemcpyHostToDevice, st)))
+            break;
         if ((err = cudaMemcpyAsync(d_roff, roff.data(), sizeof(unsigned long long) * M, cudaMemcpyHostToDevice, st))) break;
         if ((err = cudaMemcpyAsync(d_qoff, qoff.data(), sizeof(unsigned long long) * M, cudaMemcpyHostToDevice, st))) break;
-        launch_wavg(d_rec, d_roff, d_qh, d_qhp, d_qoff, 1, M, n_steps, N, weight_kind, d_out, d_w, d_pq, d_pqp, st);
+        launch_wavg_wang(d_rec, d_roff, d_qh, d_qhp, d_qhw, d_qoff, 1, M, n_steps, N, weight_kind, d_out, d_w, d_pq,
+                         d_pqp, d_pqw, st);
         if ((err = cudaGetLastError())) break;
         if ((err = cudaMemcpyAsync(out, d_out, sizeof(pa_wavg) * n_steps, cudaMemcpyDeviceToHost, st))) break;
         if (Pq && (err = cudaMemcpyAsync(Pq, d_pq, sizeof(double) * nP, cudaMemcpyDeviceToHost, st))) break;
         if (Pq_pair && (err = cudaMemcpyAsync(Pq_pair, d_pqp, sizeof(double) * nP, cudaMemcpyDeviceToHost, st))) break;
+        if (Pq_wang && (err = cudaMemcpyAsync(Pq_wang, d_pqw, sizeof(double) * nP, cudaMemcpyDeviceToHost, st))) break;
         err = cudaStreamSynchronize(st);
     } while (0);
     if (err != cudaSuccess) s = cuda_fail(err, "pa_weighted_average");

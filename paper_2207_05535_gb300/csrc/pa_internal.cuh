@@ -10,7 +10,7 @@
 //   E[b], M[b], fam[b]   [sum R_cap]        energy, magnetisation, beta_0 ancestor
 //   parent, cnt          [sum R_cap]        parent map of the children, copy numbers r_j
 //   rec                  [sum n_beta]       per-temperature records (pa_step_record)
-//   qh, qhp              [sum n_beta (N+1)] overlap histograms over d (shift / pair)
+//   qh, qhp, qhw         [sum n_beta (N+1)] overlap histograms over d (shift / pair / Wang)
 //   beta, thr                               schedule and Metropolis thresholds per step
 //   wt, wtoff                               weight tables exp(-4 n dbeta) shared by every run
 //                                           and step with the same (N, dbeta); wtoff[wt_off + i]
@@ -34,7 +34,8 @@
 namespace pa {
 
 constexpr uint32_t TAG_INIT = 1u, TAG_SWEEP = 2u, TAG_RESAMPLE = 3u, TAG_MULTINOMIAL = 4u, TAG_DISORDER = 5u,
-                   TAG_DOS = 6u;
+                   TAG_DOS = 6u, TAG_WANG = 7u;
+constexpr uint32_t WANG_IDX_BITS = 13u;  // PA_WANG_MAX_RCAP = 2^13
 
 // status bits in the engine-wide device status word
 constexpr uint32_t ST_CAPACITY = 1u << PA_ERR_CAPACITY;
@@ -77,6 +78,7 @@ struct Pool {
     pa_step_record *rec;
     uint32_t *qh;
     uint32_t *qhp;
+    uint32_t *qhw;
     const double *beta;
     const double *wt;                  // weight tables exp(-4 n dbeta), (N + 1) doubles each
     const unsigned long long *wtoff;   // per run and step: offset of its table in wt
@@ -140,6 +142,14 @@ void launch_measure(const Pool &P, const uint32_t *runs, uint32_t n_runs, int in
 // the population of the step in flight (init: the beta_0 population).
 void launch_dos_sample(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_R, int init,
                        cudaStream_t s);
+// Wang et al.'s pairing and its overlaps for the runs in `runs` (init: step 0);
+// max_Rcap: the largest R_cap among them (sets the shared memory).
+void launch_wang(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap, int init, cudaStream_t s);
+size_t wang_smem_bytes(uint32_t max_Rcap);
+void launch_wavg_wang(const pa_step_record *recs, const unsigned long long *rec_off, const uint32_t *qh,
+                      const uint32_t *qhp, const uint32_t *qhw, const unsigned long long *qh_off, uint32_t n_groups,
+                      uint32_t M, uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w, double *Pq,
+                      double *Pqp, double *Pqw, cudaStream_t s);
 void launch_wavg(const pa_step_record *recs, const unsigned long long *rec_off, const uint32_t *qh,
                  const uint32_t *qhp, const unsigned long long *qh_off, uint32_t n_groups, uint32_t M,
                  uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w, double *Pq, double *Pqp,

@@ -1142,6 +1142,158 @@ __global__ void overlap_kernel(Pool P, const uint32_t *q_runs, int init)
 }
 
 // --------------------------------------------------------------------------
+// Independent pairings from permutations (Sec. III.D, Wang et al., with the
+// random search pattern sigma).  One CTA per run, everything in shared memory:
+//   1. pi and sigma: replica indices in ascending order of per-replica 64-bit
+//      Philox keys whose low 13 bits are replaced by the index (bitonic sort);
+//   2. warp 0 visits positions k = sigma_0, sigma_1, ...; where replica k and
+//      pi_k share a family it tests the positions sigma_{i+1}, sigma_{i+2}, ...
+//      (mod R) 32 at a time with a ballot and swaps pi_k with the first pi_p
+//      outside k's family whose position p is outside pi_k's family.  A swap
+//      fixes both positions and breaks no other, so one pass in sigma order
+//      equals the serial algorithm; a search that exhausts its R - 1 positions
+//      skips the measurement at this step;
+//   3. every thread takes pairs (k, pi*_k): Hamming distance of the colour
+//      planes, histogram, sum |N - 2d|.
+// --------------------------------------------------------------------------
+__device__ void bitonic_sort_u64(unsigned long long *a, uint32_t n)  // n a power of two, ascending
+{
+    for (uint32_t size = 2; size <= n; size <<= 1)
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t t = threadIdx.x; t < n / 2; t += blockDim.x) {
+                const uint32_t lo = 2 * stride * (t / stride) + (t % stride), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long x = a[lo], y = a[hi];
+                if ((x > y) == up) {
+                    a[lo] = y;
+                    a[hi] = x;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__global__ void __launch_bounds__(1024) wang_kernel(Pool P, const uint32_t *runs, int init, uint32_t n2,
+                                                    uint32_t cap)
+{
+    extern __shared__ __align__(16) unsigned long long wsm[];
+    __shared__ long long sh_l[32];
+    __shared__ uint32_t s_ok, s_swaps;
+    const uint32_t run = runs[blockIdx.x];
+    const RunDev rd = P.runs[run];
+    const RunState st = P.st[run];
+    if (st.status) return;
+    const uint32_t i = init ? 0u : st.step + 1;
+    if (i >= rd.n_beta) return;
+    const uint32_t R = init ? rd.R : st.R_new;
+    const uint32_t b = i & 1u, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31u;
+    unsigned long long *key = wsm;                                // [n2] sort keys, then the families
+    uint32_t *fam = reinterpret_cast<uint32_t *>(wsm);            // [cap], over the keys once sorted
+    uint32_t *pi = reinterpret_cast<uint32_t *>(wsm + n2);        // [cap]
+    uint32_t *sg = pi + cap;                                      // [cap]
+    const unsigned long long mask = (1ull << WANG_IDX_BITS) - 1;
+    uint32_t nr = 2;
+    while (nr < R) nr <<= 1;
+    for (int which = 0; which < 2; ++which) {
+        for (uint32_t j = tid; j < nr; j += nt) {
+            unsigned long long k = ~0ull;  // padding sorts last, ties broken by index
+            if (j < R) {
+                const uint4 o = philox4x32_10(j, 0u, i, TAG_WANG << 24, rd.seed, rd.run_id);
+                k = which ? ((unsigned long long)o.z << 32 | o.w) : ((unsigned long long)o.x << 32 | o.y);
+            }
+            key[j] = (k & ~mask) | j;
+        }
+        __syncthreads();
+        bitonic_sort_u64(key, nr);
+        uint32_t *dst = which ? sg : pi;
+        for (uint32_t k = tid; k < R; k += nt) dst[k] = (uint32_t)(key[k] & mask);
+        __syncthreads();
+    }
+    for (uint32_t j = tid; j < R; j += nt) fam[j] = P.fam[b][rd.rep_off + j];
+    __syncthreads();
+    if (tid < 32) {
+        uint32_t swaps = 0;
+        bool ok = true;
+        for (uint32_t base = 0; base < R && ok; base += 32) {
+            int last = -1;
+            for (;;) {  // mismatches of this chunk in sigma order; at most 32 rounds
+                const uint32_t ii = base + lane;
+                bool mis = false;
+                if (ii < R && (int)lane > last) {
+                    const uint32_t k = sg[ii];
+                    mis = fam[pi[k]] == fam[k];
+                }
+                const unsigned bal = __ballot_sync(FULL, mis);
+                if (!bal) break;
+                const int t = __ffs(bal) - 1;
+                const uint32_t i0 = base + t, k = sg[i0];
+                const uint32_t fk = fam[k], fpk = fam[pi[k]];
+                uint32_t found = 0xFFFFFFFFu;
+                for (uint32_t l0 = 1; l0 < R; l0 += 32) {  // at most R - 1 positions
+                    const uint32_t l = l0 + lane;
+                    bool c = false;
+                    uint32_t p = 0;
+                    if (l < R) {
+                        uint32_t q = i0 + l;
+                        if (q >= R) q -= R;
+                        p = sg[q];
+                        c = fam[pi[p]] != fk && fpk != fam[p];
+                    }
+                    const unsigned bc = __ballot_sync(FULL, c);
+                    if (bc) {
+                        found = __shfl_sync(FULL, p, __ffs(bc) - 1);
+                        break;
+                    }
+                }
+                if (found == 0xFFFFFFFFu) {
+                    ok = false;
+                    break;
+                }
+                if (lane == 0) {
+                    const uint32_t tmp = pi[k];
+                    pi[k] = pi[found];
+                    pi[found] = tmp;
+                }
+                __syncwarp();
+                ++swaps;
+                last = t;
+            }
+        }
+        if (lane == 0) {
+            s_ok = ok ? 1u : 0u;
+            s_swaps = swaps;
+        }
+    }
+    __syncthreads();
+    pa_step_record *rec = P.rec + rd.rec_off + i;
+    if (!s_ok) {
+        if (tid == 0) {
+            rec->n_q_wang = 0;
+            rec->sum_absq_wang = 0;
+            rec->wang_swaps = s_swaps;
+        }
+        return;  // uniform over the CTA
+    }
+    const uint32_t N = rd.N, ws = rd.wstride, nw = 2 * rd.pw;
+    const uint32_t *S = P.spins[b] + rd.spin_off;
+    long long v = 0;
+    for (uint32_t k = tid; k < R; k += nt) {
+        const uint32_t *x = S + (uint64_t)k * ws, *y = S + (uint64_t)pi[k] * ws;
+        uint32_t d = 0;
+        for (uint32_t q = 0; q < nw; ++q) d += __popc(x[q] ^ y[q]);
+        atomicAdd(&P.qhw[rd.qh_off + (uint64_t)i * (N + 1) + d], 1u);
+        const long long qn = (long long)N - 2 * (long long)d;
+        v += qn < 0 ? -qn : qn;
+    }
+    v = block_sum(v, sh_l);
+    if (tid == 0) {
+        rec->sum_absq_wang = v;
+        rec->n_q_wang = R;
+        rec->wang_swaps = s_swaps;
+    }
+}
+
+// --------------------------------------------------------------------------
 // theta = infinity (Sec. V.B): step (iv) replaced by simple sampling of the
 // exact energy distribution.  One thread per child: a 53-bit uniform from
 // Philox (words 0, 1), x = u * C[2N], the first level u with x < C[u] by
@@ -1426,7 +1578,7 @@ __global__ void __launch_bounds__(64) wavg_kernel(const pa_step_record *recs, co
         z = warp_sum(z);
         const double beta = recs[off[0] + i].beta;
         double se = 0.0, se2 = 0.0, sm = 0.0, sm2 = 0.0, sc = 0.0, schi = 0.0, sq = 0.0, sqp = 0.0, sw = 0.0,
-               wmax = 0.0, se3 = 0.0, se4 = 0.0, sm3 = 0.0, sm4 = 0.0, su4 = 0.0;
+               wmax = 0.0, se3 = 0.0, se4 = 0.0, sm3 = 0.0, sm4 = 0.0, su4 = 0.0, sqw = 0.0;
         const double N3 = Nd * Nd * Nd, N4 = N3 * Nd;
         for (uint32_t m = lane; m < M; m += 32) {
             wi[m] = wi[m] / z;
@@ -1447,6 +1599,7 @@ __global__ void __launch_bounds__(64) wavg_kernel(const pa_step_record *recs, co
             schi += wm * chi;
             if (r->n_q) sq += wm * ((double)r->sum_absq / (Nd * (double)r->n_q));
             if (r->n_q_pair) sqp += wm * ((double)r->sum_absq_pair / (Nd * (double)r->n_q_pair));
+            if (r->n_q_wang) sqw += wm * ((double)r->sum_absq_wang / (Nd * (double)r->n_q_wang));
             const double e3 = i128_to_double(r->sumE3) / (N3 * Ri);
             const double e4 = i128_to_double(r->sumE4) / (N4 * Ri);
             const double m3 = i128_to_double(r->sumAbsM3) / (N3 * Ri);
@@ -1478,6 +1631,7 @@ __global__ void __launch_bounds__(64) wavg_kernel(const pa_step_record *recs, co
         o.W_m3 = warp_sum(sm3);
         o.W_m4 = warp_sum(sm4);
         o.W_U4_conf = warp_sum(su4);
+        o.W_absq_wang = warp_sum(sqw);
         {
             const double re[5] = {1.0, o.W_e, o.W_e2, o.W_e3, o.W_e4};
             const double rm[5] = {1.0, o.W_m, o.W_m2, o.W_m3, o.W_m4};
@@ -1507,23 +1661,25 @@ __global__ void __launch_bounds__(64) wavg_kernel(const pa_step_record *recs, co
 
 // Weighted overlap distributions (Eq. W_conf_q): grid (steps, groups).
 __global__ void wavg_q_kernel(const pa_step_record *recs, const unsigned long long *rec_off, const uint32_t *qh,
-                              const uint32_t *qhp, const unsigned long long *qh_off, uint32_t M, uint32_t n_steps,
-                              uint32_t N, const double *w, double *Pq, double *Pqp)
+                              const uint32_t *qhp, const uint32_t *qhw, const unsigned long long *qh_off, uint32_t M,
+                              uint32_t n_steps, uint32_t N, const double *w, double *Pq, double *Pqp, double *Pqw)
 {
     const uint32_t i = blockIdx.x, g = blockIdx.y;
     const double *wi = w + ((uint64_t)g * n_steps + i) * M;
     const unsigned long long *ro = rec_off + (uint64_t)g * M, *qo = qh_off + (uint64_t)g * M;
     for (uint32_t d = threadIdx.x; d <= N; d += blockDim.x) {
-        double a = 0.0, b = 0.0;
+        double a = 0.0, b = 0.0, c = 0.0;
         for (uint32_t m = 0; m < M; ++m) {
             const pa_step_record *r = recs + ro[m] + i;
             const uint64_t q = qo[m] + (uint64_t)i * (N + 1) + d;
             if (Pq && r->n_q) a += wi[m] * ((double)qh[q] / (double)r->n_q);
             if (Pqp && r->n_q_pair) b += wi[m] * ((double)qhp[q] / (double)r->n_q_pair);
+            if (Pqw && r->n_q_wang) c += wi[m] * ((double)qhw[q] / (double)r->n_q_wang);
         }
         const uint64_t o = ((uint64_t)g * n_steps + i) * (N + 1) + d;
         if (Pq) Pq[o] = a;
         if (Pqp) Pqp[o] = b;
+        if (Pqw) Pqw[o] = c;
     }
 }
 
@@ -1536,6 +1692,8 @@ cudaError_t prepare_kernels()
                                          200 * 1024);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sweep_kernel<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)  // Wang pairing with R_cap up to 8192: 160 KB
+        e = cudaFuncSetAttribute(wang_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     return e;
 }
 
@@ -1675,16 +1833,47 @@ void launch_measure(const Pool &P, const uint32_t *runs, uint32_t n_runs, int in
     measure_kernel<<<n_runs, 512, 0, s>>>(P, runs, init);
 }
 
+void launch_wavg_wang(const pa_step_record *recs, const unsigned long long *rec_off, const uint32_t *qh,
+                      const uint32_t *qhp, const uint32_t *qhw, const unsigned long long *qh_off, uint32_t n_groups,
+                      uint32_t M, uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w, double *Pq,
+                      double *Pqp, double *Pqw, cudaStream_t s)
+{
+    wavg_kernel<<<(n_groups + 1) / 2, 64, 0, s>>>(recs, rec_off, n_groups, M, n_steps, N, kind, out, w);
+    if (Pq || Pqp || Pqw) {
+        dim3 grid(n_steps, n_groups);
+        wavg_q_kernel<<<grid, 256, 0, s>>>(recs, rec_off, qh, qhp, qhw, qh_off, M, n_steps, N, w, Pq, Pqp, Pqw);
+    }
+}
+
 void launch_wavg(const pa_step_record *recs, const unsigned long long *rec_off, const uint32_t *qh,
                  const uint32_t *qhp, const unsigned long long *qh_off, uint32_t n_groups, uint32_t M,
                  uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w, double *Pq, double *Pqp,
                  cudaStream_t s)
 {
-    wavg_kernel<<<(n_groups + 1) / 2, 64, 0, s>>>(recs, rec_off, n_groups, M, n_steps, N, kind, out, w);
-    if (Pq || Pqp) {
-        dim3 grid(n_steps, n_groups);
-        wavg_q_kernel<<<grid, 256, 0, s>>>(recs, rec_off, qh, qhp, qh_off, M, n_steps, N, w, Pq, Pqp);
-    }
+    launch_wavg_wang(recs, rec_off, qh, qhp, nullptr, qh_off, n_groups, M, n_steps, N, kind, out, w, Pq, Pqp, nullptr,
+                     s);
+}
+
+static uint32_t wang_n2(uint32_t max_Rcap)
+{
+    uint32_t n2 = 32;
+    while (n2 < max_Rcap) n2 <<= 1;
+    return n2;
+}
+
+// keys (8 n2 bytes, reused for the families) + pi and sigma (4 R_cap bytes each):
+// about 110 KB at R_cap = 5630, so two CTAs fit on an SM
+size_t wang_smem_bytes(uint32_t max_Rcap)
+{
+    const uint32_t cap = (max_Rcap + 3) / 4 * 4;
+    return (size_t)wang_n2(max_Rcap) * 8 + (size_t)cap * 8;
+}
+
+void launch_wang(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap, int init, cudaStream_t s)
+{
+    if (n_runs == 0) return;
+    const uint32_t n2 = wang_n2(max_Rcap), cap = (max_Rcap + 3) / 4 * 4;
+    wang_kernel<<<n_runs, 1024, wang_smem_bytes(max_Rcap), s>>>(P, runs, init, n2, cap);
 }
 
 }  // namespace pa

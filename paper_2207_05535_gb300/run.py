@@ -1,7 +1,7 @@
 """Run a synthetic batch of population-annealing runs on the GPU and print its
 throughput.
 
-    python -m paper_2207_05535_gb300.run --L 30 --runs 40 --R 10000 --temps 8 [--model fm|glass|mixed]
+    python -m paper_2207_05535_gb300.run --L 30 --runs 40 --R 10000 --temps 8 [--model fm|glass|mixed] [--wang]
 
 Runs are independent (run_id = 0..runs-1, disorder_id = run_id), theta sweeps
 per temperature, beta from 0 to --beta-f in --temps equidistant steps.
@@ -27,10 +27,12 @@ def main(argv=None):
     ap.add_argument("--model", default="mixed", choices=["fm", "glass", "mixed"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--generic", action="store_true", help="byte-plane sweep kernel for every size")
+    ap.add_argument("--wang", action="store_true", help="measure overlaps of Wang pairs (Sec. III.D)")
     a = ap.parse_args(argv)
     build.build()
     model = {"fm": lambda k: W.FERRO, "glass": lambda k: W.EA_PMJ, "mixed": lambda k: k % 2}[a.model]
-    descs = [W.RunDesc(a.L, model(k), a.R, a.theta, W.schedule(a.beta_f, a.temps), run_id=k, disorder_id=k)
+    descs = [W.RunDesc(a.L, model(k), a.R, a.theta, W.schedule(a.beta_f, a.temps), run_id=k, disorder_id=k,
+                       overlap=W.Q_WANG if a.wang else W.Q_NONE)
              for k in range(a.runs)]
     flags = (_lib.PA_CREATE_NO_AUTOTUNE if a.no_autotune else 0) | (_lib.PA_CREATE_GENERIC_SWEEP if a.generic else 0)
     t0 = time.perf_counter()

@@ -23,6 +23,7 @@ MULTINOMIAL = 1
 Q_NONE = 0
 Q_SHIFT = 1
 Q_PAIR = 2
+Q_WANG = 4
 THETA_INF = 0xFFFFFFFF  # theta -> infinity: energies drawn from the exact density of states (Sec. V.B)
 
 

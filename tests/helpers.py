@@ -36,7 +36,8 @@ def oracle_runs(descs, idx=None):
 def compare_records(gpu, ora, rtol=1e-12):
     """Integers bit-exact; ln Q and -beta F within rtol (relative, floor 1)."""
     int_fields = ["sumE", "sumE2", "sumAbsM", "sumM2", "sum_c2", "sum_absq", "sum_absq_pair", "R", "R_target",
-                  "n_fam", "max_fam", "n_q", "n_q_pair", "N", "status", "sumE3", "sumE4", "sumAbsM3", "sumM4"]
+                  "n_fam", "max_fam", "n_q", "n_q_pair", "N", "status", "sumE3", "sumE4", "sumAbsM3", "sumM4",
+                  "sum_absq_wang", "n_q_wang", "wang_swaps"]
     for f in int_fields:
         assert np.array_equal(gpu[f], ora[f]), (f, np.nonzero(gpu[f] != ora[f])[0][:5])
     assert np.array_equal(gpu["beta"], ora["beta"])

@@ -79,7 +79,7 @@ def test_status_strings(lib):
     dict(betas=np.array([0.0, 0.5, 0.4])), dict(betas=np.array([])), dict(overlap=8),
     dict(theta=W.THETA_INF), dict(theta=W.THETA_INF, log_g=np.zeros(129), overlap=1),
     dict(theta=W.THETA_INF, log_g=np.full(129, -np.inf)), dict(theta=W.THETA_INF, log_g=np.full(129, np.nan)),
-    dict(theta=(1 << 22) + 1),
+    dict(theta=(1 << 22) + 1), dict(overlap=W.Q_WANG, R=9000), dict(overlap=W.Q_WANG, R=8000, R_cap=8193),
 ])
 def test_invalid_descriptors_rejected_before_any_device_work(lib, bad):
     args = dict(L=8, model=W.FERRO, R=16, theta=1, betas=np.array([0.0, 0.1]))
@@ -109,3 +109,15 @@ def test_oracle_and_engine_records_share_the_abi_layout():
     import oracle as O
     assert O.RECORD_DTYPE == _lib.RECORD_DTYPE
     assert O.WAVG_DTYPE == _lib.WAVG_DTYPE
+
+
+def test_binding_argument_counts_match_the_header(lib):
+    """Every declaration in pa.h has as many parameters as its ctypes binding."""
+    with open(os.path.join(ROOT, "include", "pa.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    decls = {m.group(1): m.group(2) for m in re.finditer(r"\b(pa_\w+)\s*\(([^;{]*?)\)\s*;", text)}
+    for name in _lib.EXPORTS:
+        assert name in decls, name
+        params = [p for p in decls[name].split(",") if p.strip() and p.strip() != "void"]
+        assert len(getattr(lib, name).argtypes) == len(params), name
