@@ -236,6 +236,13 @@ pa_status pa_measure(pa_engine *e, uint32_t run, uint32_t step, pa_step_record *
 pa_status pa_population(pa_engine *e, uint32_t run, int8_t *host_spins, int32_t *host_E, int32_t *host_M,
                         uint32_t *host_fam, uint32_t *R_out, uint32_t *step_out);
 
+/* The same for replicas first .. first+count-1 only (clipped to R_i): the
+ * outputs hold min(count, R_i - first) entries (spins [that][N]).  For sampling
+ * replicas of populations too large to copy whole.  Synchronises. */
+pa_status pa_population_slice(pa_engine *e, uint32_t run, uint32_t first, uint32_t count, int8_t *host_spins,
+                              int32_t *host_E, int32_t *host_M, uint32_t *host_fam, uint32_t *R_out,
+                              uint32_t *step_out);
+
 /* Weighted averages (Sec. IV) over groups of runs resident in the engine:
  * group g holds runs run_idx[g*M .. g*M+M-1] (same N and n_beta).  Writes
  * host_out[g][n_beta] and, when non-NULL, the weighted overlap distributions

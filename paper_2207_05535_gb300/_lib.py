@@ -60,7 +60,7 @@ WAVG_DTYPE = np.dtype([
 ])
 
 EXPORTS = ["pa_create", "pa_create_ex", "pa_server_create", "pa_admit", "pa_retire", "pa_finished", "pa_run_state",
-           "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population",
+           "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population", "pa_population_slice",
            "pa_weighted_average_runs", "pa_weighted_average", "pa_weighted_average_noalloc", "pa_launch_count", "pa_set_profiling",
            "pa_kernel_times", "pa_transfer_bytes", "pa_sweep_shape", "pa_destroy", "pa_status_string"]
 KERNEL_KINDS = ["resample", "sweep", "overlap", "measure", "init", "wavg"]
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
         lib.pa_records.argtypes = [vp, u32, vp, P(u32), P(u32), P(u32)]
         lib.pa_measure.argtypes = [vp, u32, u32, vp, P(u32), P(u32), P(u32)]
         lib.pa_population.argtypes = [vp, u32, P(C.c_int8), P(C.c_int32), P(C.c_int32), P(u32), P(u32), P(u32)]
+        lib.pa_population_slice.argtypes = [vp, u32, u32, u32, P(C.c_int8), P(C.c_int32), P(C.c_int32), P(u32),
+                                            P(u32), P(u32)]
         lib.pa_weighted_average_runs.argtypes = [vp, P(u32), u32, u32, u32, vp, P(C.c_double), P(C.c_double),
                                                  P(C.c_double)]
         lib.pa_weighted_average.argtypes = [vp, P(u32), P(u32), P(u32), u32, u32, u32, u32, vp, P(C.c_double),
@@ -238,6 +240,20 @@ def pa_population(h, run, R_cap, N):
                                 C.byref(R), C.byref(step)), "pa_population")
     n = R.value
     return s[:n], E[:n], M[:n], fam[:n], step.value
+
+
+def pa_population_slice(h, run, first, count, N, spins=True):
+    """Replicas first..first+count-1 of the current population: (spins or None, E, M, fam, R_i, step)."""
+    s = np.zeros((count, N), dtype=np.int8) if spins else None
+    E = np.zeros(count, dtype=np.int32)
+    M = np.zeros(count, dtype=np.int32)
+    fam = np.zeros(count, dtype=np.uint32)
+    R = C.c_uint32()
+    step = C.c_uint32()
+    _check(load().pa_population_slice(h, run, first, count, _p(s, C.c_int8), _p(E, C.c_int32), _p(M, C.c_int32),
+                                      _p(fam, C.c_uint32), C.byref(R), C.byref(step)), "pa_population_slice")
+    n = max(0, min(count, R.value - min(first, R.value)))
+    return (s[:n] if spins else None), E[:n], M[:n], fam[:n], R.value, step.value
 
 
 def pa_weighted_average_runs(h, run_idx, M, n_steps, N, kind=0, q=False, wang=False):

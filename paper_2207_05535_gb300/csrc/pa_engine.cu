@@ -1219,8 +1219,9 @@ pa_status pa_measure(pa_engine *e, uint32_t run, uint32_t step, pa_step_record *
     return sync_read(e);
 }
 
-pa_status pa_population(pa_engine *e, uint32_t run, int8_t *host_spins, int32_t *host_E, int32_t *host_M,
-                        uint32_t *host_fam, uint32_t *R_out, uint32_t *step_out)
+pa_status pa_population_slice(pa_engine *e, uint32_t run, uint32_t first, uint32_t count, int8_t *host_spins,
+                              int32_t *host_E, int32_t *host_M, uint32_t *host_fam, uint32_t *R_out,
+                              uint32_t *step_out)
 {
     if (!slot_ok(e, run)) return PA_ERR_INVALID_ARG;
     PA_TRY(prepare(e));
@@ -1231,26 +1232,36 @@ pa_status pa_population(pa_engine *e, uint32_t run, int8_t *host_spins, int32_t 
     const uint32_t b = st.step & 1u, R = st.R_cur;
     if (R_out) *R_out = R;
     if (step_out) *step_out = st.step;
-    if (host_spins && R) {
-        std::vector<uint32_t> words((size_t)R * x.wstride);
-        PA_CUDA(cudaMemcpyAsync(words.data(), e->P.spins[b] + x.spin_off, sizeof(uint32_t) * words.size(),
-                                cudaMemcpyDeviceToHost, e->stream));
+    const uint32_t lo = std::min(first, R), n = std::min<uint64_t>(count, (uint64_t)R - lo);
+    if (host_spins && n) {
+        std::vector<uint32_t> words((size_t)n * x.wstride);
+        PA_CUDA(cudaMemcpyAsync(words.data(), e->P.spins[b] + x.spin_off + (uint64_t)lo * x.wstride,
+                                sizeof(uint32_t) * words.size(), cudaMemcpyDeviceToHost, e->stream));
         PA_CUDA(cudaStreamSynchronize(e->stream));
-        for (uint32_t j = 0; j < R; ++j)
-            for (uint32_t n = 0; n < x.N; ++n) {
-                const uint32_t xx = n % x.L, y = n / x.L, c = (xx + y) & 1u, pos = y * x.pitch + (xx >> 1);
+        e->d2h += sizeof(uint32_t) * words.size();
+        for (uint32_t j = 0; j < n; ++j)
+            for (uint32_t q = 0; q < x.N; ++q) {
+                const uint32_t xx = q % x.L, y = q / x.L, c = (xx + y) & 1u, pos = y * x.pitch + (xx >> 1);
                 const uint32_t word = words[(size_t)j * x.wstride + c * x.pw + (pos >> 5)];
-                host_spins[(size_t)j * x.N + n] = ((word >> (pos & 31)) & 1u) ? (int8_t)1 : (int8_t)-1;
+                host_spins[(size_t)j * x.N + q] = ((word >> (pos & 31)) & 1u) ? (int8_t)1 : (int8_t)-1;
             }
     }
-    if (host_E && R)
-        PA_CUDA(cudaMemcpyAsync(host_E, e->P.E[b] + x.rep_off, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, e->stream));
-    if (host_M && R)
-        PA_CUDA(cudaMemcpyAsync(host_M, e->P.M[b] + x.rep_off, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, e->stream));
-    if (host_fam && R)
-        PA_CUDA(cudaMemcpyAsync(host_fam, e->P.fam[b] + x.rep_off, sizeof(uint32_t) * R, cudaMemcpyDeviceToHost,
+    if (host_E && n)
+        PA_CUDA(cudaMemcpyAsync(host_E, e->P.E[b] + x.rep_off + lo, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
                                 e->stream));
+    if (host_M && n)
+        PA_CUDA(cudaMemcpyAsync(host_M, e->P.M[b] + x.rep_off + lo, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
+                                e->stream));
+    if (host_fam && n)
+        PA_CUDA(cudaMemcpyAsync(host_fam, e->P.fam[b] + x.rep_off + lo, sizeof(uint32_t) * n,
+                                cudaMemcpyDeviceToHost, e->stream));
     return sync_read(e);
+}
+
+pa_status pa_population(pa_engine *e, uint32_t run, int8_t *host_spins, int32_t *host_E, int32_t *host_M,
+                        uint32_t *host_fam, uint32_t *R_out, uint32_t *step_out)
+{
+    return pa_population_slice(e, run, 0u, 0xFFFFFFFFu, host_spins, host_E, host_M, host_fam, R_out, step_out);
 }
 
 static pa_status ensure_wa(pa_engine *e, size_t bytes)
