@@ -69,6 +69,18 @@ def metric_unit(wl):
     return (METRIC_INF, UNIT_INF) if wl in INF_WORKLOADS else (METRIC, UNIT)
 
 
+def plane_words(L):
+    """Words of one colour plane of a replica (rows padded to the engine's row pitch)."""
+    Lh = L // 2
+    if Lh & (Lh - 1) == 0:
+        pitch = Lh
+    elif Lh < 32:
+        pitch = next(P for P in (4, 8, 16, 32) if P >= Lh and (L * P) % 32 == 0)
+    else:
+        pitch = (Lh + 31) // 32 * 32
+    return (L * pitch + 31) // 32
+
+
 def work_units(d, R):
     """Work of one temperature at population R: attempted spin updates (theta N R),
     or R energy draws for theta = infinity runs."""
@@ -371,6 +383,22 @@ def main():
     achieved_tops = updates * slots / (sweep_ms / args.steps * 1e-3) / 1e12
     metric, unit = metric_unit(wl)
     total_kernel_ms = sum(t for t, _ in kt_tot.values())
+    # overlap kernels (a10): HBM-bound; algorithmic bytes = both replicas' colour planes per pair
+    ov_ms = kt_tot.get("overlap", (0.0, 0))[0] / args.steps
+    ov_bytes = 0
+    for k, d in enumerate(descs):
+        if d.overlap:
+            rec = eng.records(k)
+            per_replica = 2 * plane_words(d.L) * 4
+            ov_bytes += int(np.sum(2 * rec["n_q"].astype(np.int64) + rec["n_q_pair"] + 2 * rec["n_q_wang"])) * per_replica
+    roof_ov = None
+    if ov_ms > 0 and ov_bytes:
+        ach = ov_bytes / (ov_ms * 1e-3) / 1e9
+        roof_ov = {"bound": "hbm", "kernel": "overlap_kernel" + (" + wang_kernel" if args.wang else ""),
+                   "achieved": ach, "peak": float(pk.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+                   "frac": ach / float(pk.get("hbm_gbs", 6800.0)), "bytes_per_step": ov_bytes,
+                   "basis": "2 replicas x 2 colour planes read per overlap pair; peak = HBM copy bandwidth from "
+                            f"MEASURED_PEAKS.json ({pk_kind})"}
 
     # ---- plain form: one run per engine, all on one stream (one run per launch)
     plain = None
@@ -453,6 +481,7 @@ def main():
                          "updates_per_ns_sweep_only": updates / (sweep_ms / args.steps * 1e-3) / 1e9,
                          "sweep_ms_per_step": sweep_ms / args.steps,
                          "sweep_share_of_kernel_time": sweep_ms / total_kernel_ms if total_kernel_ms else None},
+            "roofline_overlap": roof_ov,
             "kernel_ms_per_step": {k: t / args.steps for k, (t, n) in kt_tot.items()},
             "sweep_shapes": [{"L": L_, "words_per_thread": w_, "block": b_, "autotuned": bool(t_)}
                              for (L_, w_, b_, t_) in _lib.pa_sweep_shapes(eng.h)],

@@ -1072,9 +1072,30 @@ __global__ void __launch_bounds__(256) sweep_pad_kernel(Pool P, const uint32_t *
 // --------------------------------------------------------------------------
 // Overlaps (Sec. III.D): d = popcount(s XOR s') over the packed spins.
 // --------------------------------------------------------------------------
-__global__ void overlap_kernel(Pool P, const uint32_t *q_runs, int init)
+// Hamming distance of two replicas' colour planes (nw words; 16-byte loads
+// when nw is a multiple of 4: replica slots are 16-byte aligned).
+__device__ __forceinline__ uint32_t plane_distance(const uint32_t *a, const uint32_t *b, uint32_t nw)
+{
+    uint32_t d = 0;
+    if ((nw & 3u) == 0) {
+        const uint4 *a4 = reinterpret_cast<const uint4 *>(a), *b4 = reinterpret_cast<const uint4 *>(b);
+        for (uint32_t q = 0; q < nw / 4; ++q) {
+            const uint4 x = a4[q], y = b4[q];
+            d += __popc(x.x ^ y.x) + __popc(x.y ^ y.y) + __popc(x.z ^ y.z) + __popc(x.w ^ y.w);
+        }
+    } else {
+        for (uint32_t q = 0; q < nw; ++q) d += __popc(a[q] ^ b[q]);
+    }
+    return d;
+}
+
+// Histograms up to this many bins are accumulated in shared memory per CTA.
+constexpr uint32_t OVERLAP_SMEM_BINS = 4097;  // L <= 64
+
+__global__ void __launch_bounds__(256) overlap_kernel(Pool P, const uint32_t *q_runs, int init)
 {
     __shared__ long long sh_l[32];
+    __shared__ uint32_t hs[2][OVERLAP_SMEM_BINS];
     const uint32_t run = q_runs[blockIdx.y];
     const RunDev rd = P.runs[run];
     const RunState st = P.st[run];
@@ -1086,56 +1107,84 @@ __global__ void overlap_kernel(Pool P, const uint32_t *q_runs, int init)
     const uint32_t N = rd.N, ws = rd.wstride;
     const uint32_t nw = 2 * rd.pw;  // plane words; the stride's padding is never compared
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool smem_hist = N + 1 <= OVERLAP_SMEM_BINS;
     pa_step_record *rec = P.rec + rd.rec_off + i;
+    const uint32_t *S = P.spins[buf] + rd.spin_off;
 
-    if (rd.overlap & PA_Q_SHIFT) {
-        const uint32_t h = R / 2;
-        if (blockIdx.x * blockDim.x < h) {
-            long long v = 0;
-            if (p < h) {
-                const uint32_t *a = P.spins[buf] + rd.spin_off + (uint64_t)p * ws;
-                const uint32_t *b = P.spins[buf] + rd.spin_off + (uint64_t)(p + h) * ws;
-                uint32_t d = 0;
-                for (uint32_t q = 0; q < nw; ++q) d += __popc(a[q] ^ b[q]);  // the two colour planes only
-                atomicAdd(&P.qh[rd.qh_off + (uint64_t)i * (N + 1) + d], 1u);
-                const long long qn = (long long)N - 2 * (long long)d;
-                v = qn < 0 ? -qn : qn;
-            }
-            v = block_sum(v, sh_l);
-            if (threadIdx.x == 0) {
-                atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_absq), (unsigned long long)v);
-                if (blockIdx.x == 0) rec->n_q = h;
+    const bool shift = (rd.overlap & PA_Q_SHIFT) && blockIdx.x * blockDim.x < R / 2;
+    int32_t pr = -1;
+    uint32_t n_pair = 0;
+    const uint32_t *Sb = nullptr;
+    uint32_t *hb = nullptr;
+    pa_step_record *rb_rec = nullptr;
+    if ((rd.overlap & PA_Q_PAIR) && rd.paired > (int32_t)run) {
+        const RunDev rb = P.runs[(uint32_t)rd.paired];
+        const RunState sb = P.st[(uint32_t)rd.paired];
+        if (!sb.status) {
+            const uint32_t Rb = init ? rb.R : sb.R_new;
+            n_pair = R < Rb ? R : Rb;
+            if (blockIdx.x * blockDim.x < n_pair) {
+                pr = rd.paired;
+                Sb = P.spins[buf] + rb.spin_off;
+                hb = P.qhp + rb.qh_off + (uint64_t)i * (N + 1);
+                rb_rec = P.rec + rb.rec_off + i;
             }
         }
     }
-    if ((rd.overlap & PA_Q_PAIR) && rd.paired > (int32_t)run) {
-        const uint32_t pr = (uint32_t)rd.paired;
-        const RunDev rb = P.runs[pr];
-        const RunState sb = P.st[pr];
-        if (sb.status) return;
-        const uint32_t Rb = init ? rb.R : sb.R_new;
-        const uint32_t n = R < Rb ? R : Rb;
-        if (blockIdx.x * blockDim.x < n) {
-            long long v = 0;
-            if (p < n) {
-                const uint32_t *a = P.spins[buf] + rd.spin_off + (uint64_t)p * ws;
-                const uint32_t *b = P.spins[buf] + rb.spin_off + (uint64_t)p * ws;
-                uint32_t d = 0;
-                for (uint32_t q = 0; q < nw; ++q) d += __popc(a[q] ^ b[q]);
-                atomicAdd(&P.qhp[rd.qh_off + (uint64_t)i * (N + 1) + d], 1u);
-                atomicAdd(&P.qhp[rb.qh_off + (uint64_t)i * (N + 1) + d], 1u);
-                const long long qn = (long long)N - 2 * (long long)d;
-                v = qn < 0 ? -qn : qn;
+    if (!shift && pr < 0) return;  // uniform over the CTA
+    if (smem_hist) {
+        for (uint32_t d = threadIdx.x; d <= N; d += blockDim.x) {
+            hs[0][d] = 0;
+            hs[1][d] = 0;
+        }
+        __syncthreads();
+    }
+    uint32_t *ha = P.qh + rd.qh_off + (uint64_t)i * (N + 1);
+    uint32_t *hp = P.qhp + rd.qh_off + (uint64_t)i * (N + 1);
+    long long v = 0, vp = 0;
+    if (shift) {
+        const uint32_t h = R / 2;
+        if (p < h) {
+            const uint32_t d = plane_distance(S + (uint64_t)p * ws, S + (uint64_t)(p + h) * ws, nw);
+            if (smem_hist) atomicAdd(&hs[0][d], 1u);
+            else atomicAdd(&ha[d], 1u);
+            const long long qn = (long long)N - 2 * (long long)d;
+            v = qn < 0 ? -qn : qn;
+        }
+    }
+    if (pr >= 0 && p < n_pair) {
+        const uint32_t d = plane_distance(S + (uint64_t)p * ws, Sb + (uint64_t)p * ws, nw);
+        if (smem_hist) {
+            atomicAdd(&hs[1][d], 1u);
+        } else {
+            atomicAdd(&hp[d], 1u);
+            atomicAdd(&hb[d], 1u);
+        }
+        const long long qn = (long long)N - 2 * (long long)d;
+        vp = qn < 0 ? -qn : qn;
+    }
+    v = block_sum(v, sh_l);
+    vp = block_sum(vp, sh_l);
+    if (smem_hist) {  // one global add per non-empty bin of this CTA
+        for (uint32_t d = threadIdx.x; d <= N; d += blockDim.x) {
+            if (hs[0][d]) atomicAdd(&ha[d], hs[0][d]);
+            if (hs[1][d]) {
+                atomicAdd(&hp[d], hs[1][d]);
+                atomicAdd(&hb[d], hs[1][d]);
             }
-            v = block_sum(v, sh_l);
-            if (threadIdx.x == 0) {
-                pa_step_record *rb_rec = P.rec + rb.rec_off + i;
-                atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_absq_pair), (unsigned long long)v);
-                atomicAdd(reinterpret_cast<unsigned long long *>(&rb_rec->sum_absq_pair), (unsigned long long)v);
-                if (blockIdx.x == 0) {
-                    rec->n_q_pair = n;
-                    rb_rec->n_q_pair = n;
-                }
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (shift) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_absq), (unsigned long long)v);
+            if (blockIdx.x == 0) rec->n_q = R / 2;
+        }
+        if (pr >= 0) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&rec->sum_absq_pair), (unsigned long long)vp);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&rb_rec->sum_absq_pair), (unsigned long long)vp);
+            if (blockIdx.x == 0) {
+                rec->n_q_pair = n_pair;
+                rb_rec->n_q_pair = n_pair;
             }
         }
     }
