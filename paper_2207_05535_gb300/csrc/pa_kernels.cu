@@ -493,32 +493,71 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *r
         }
         __syncthreads();
     } else {
-        // nearest-integer resampling: r_j = floor(tau) + [u < tau - floor(tau)], tau = R w[n_j] / S
-        for (uint32_t j = tid; j < Rprev; j += nt) {
-            const double tau = __ddiv_rn(__dmul_rn((double)rd.R, w[(uint32_t)(E[j] - Emin) >> 2]), S);
+        // nearest-integer resampling: r_j = floor(tau) + [u 2^-32 < tau - floor(tau)], tau = R w[n_j] / S.
+        // tau depends on the level only: per level the floor (over the histogram, no longer
+        // needed) and the integer threshold ceil(frac 2^32), since u 2^-32 < frac <=> u < frac 2^32
+        // exactly (scaling by 2^32 is exact and u is an integer).
+        unsigned long long *thr = reinterpret_cast<unsigned long long *>(cdf);
+        for (uint32_t n = tid; n < nb; n += nt) {
+            const double tau = __ddiv_rn(__dmul_rn((double)rd.R, w[n]), S);
             const double fl = floor(tau);
-            const uint32_t u = philox4x32_10(j, 0, i, TAG_RESAMPLE << 24, rd.seed, rd.run_id).x;
-            const double uf = __dmul_rn((double)u, 2.3283064365386962890625e-10);
-            cnt[j] = (uint32_t)fl + (uf < __dsub_rn(tau, fl) ? 1u : 0u);
+            h[n] = (uint32_t)fl;
+            thr[n] = (unsigned long long)ceil(__dmul_rn(__dsub_rn(tau, fl), 4294967296.0));
         }
         __syncthreads();
     }
 
-    // exclusive scan of the copy numbers and the parent map (contiguous families)
-    if (tid == 0) sh_carry = 0;
-    __syncthreads();
+    // copy numbers (nearest-integer: drawn here), their exclusive scan and the parent map
+    // (contiguous families).  Each warp takes a contiguous chunk of the replicas; one
+    // barrier joins the chunks.
     uint32_t *parent = P.parent + rd.rep_off;
-    for (uint32_t base = 0; base < Rprev; base += nt) {
-        const uint32_t j = base + tid;
-        const uint32_t r = j < Rprev ? cnt[j] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan(r, sh_u, tot);
-        const uint32_t o = sh_carry + ex;
+    const uint32_t lane = tid & 31u, wid = tid >> 5, nwarp = nt >> 5;
+    const uint32_t chunk = (Rprev + nwarp - 1) / nwarp;
+    const uint32_t c_lo = min(Rprev, wid * chunk), c_hi = min(Rprev, c_lo + chunk);
+    const unsigned long long *thr = reinterpret_cast<const unsigned long long *>(cdf);
+    uint32_t wsum = 0;
+    for (uint32_t base = c_lo; base < c_hi; base += 32) {
+        const uint32_t j = base + lane;
+        uint32_t r = 0;
+        if (j < c_hi) {
+            if (multi) {
+                r = cnt[j];
+            } else {
+                const uint32_t n = (uint32_t)(E[j] - Emin) >> 2;
+                const uint32_t u = philox4x32_10(j, 0, i, TAG_RESAMPLE << 24, rd.seed, rd.run_id).x;
+                r = h[n] + ((unsigned long long)u < thr[n] ? 1u : 0u);
+                cnt[j] = r;
+            }
+        }
+        wsum += r;
+    }
+    wsum = warp_sum(wsum);
+    if (lane == 0) sh_u[wid] = wsum;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t acc = 0;
+        for (uint32_t k = 0; k < nwarp; ++k) {
+            const uint32_t v = sh_u[k];
+            sh_u[k] = acc;
+            acc += v;
+        }
+        sh_carry = acc;
+    }
+    __syncthreads();
+    uint32_t carry = sh_u[wid];
+    for (uint32_t base = c_lo; base < c_hi; base += 32) {
+        const uint32_t j = base + lane;
+        const uint32_t r = j < c_hi ? cnt[j] : 0u;
+        uint32_t x = r;  // inclusive scan over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        const uint32_t o = carry + x - r;
         for (uint32_t c = 0; c < r; ++c)
             if (o + c < rd.R_cap) parent[o + c] = j;
-        __syncthreads();
-        if (tid == 0) sh_carry += tot;
-        __syncthreads();
+        carry += __shfl_sync(FULL, x, 31);
     }
     if (tid == 0) {
         const uint32_t Rn = sh_carry;
