@@ -1389,8 +1389,25 @@ __global__ void __launch_bounds__(1024) wang_kernel(Pool P, const uint32_t *runs
 // level if x rounds up to C[2N]); E = 2u - 2N, M = 0, family from the parent,
 // spin planes cleared (configurations are not represented).
 // --------------------------------------------------------------------------
+constexpr uint32_t DOS_SMEM_LEVELS = 4096;  // tables of L <= 44 are staged in shared memory
+
+// First level u with x < C[u], x = u53 2^-53 C[U] (binary search); the last
+// positive level, stored in C[U + 1], if x rounds up to C[U].
+__device__ __forceinline__ uint32_t dos_level(const double *C, uint32_t U, unsigned long long u53)
+{
+    const double x = __dmul_rn(__dmul_rn((double)u53, 1.0 / 9007199254740992.0), C[U]);
+    uint32_t lo = 0, hi = U + 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (x < C[mid]) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo <= U ? lo : (uint32_t)C[U + 1];
+}
+
 __global__ void __launch_bounds__(256) dos_sample_kernel(Pool P, const uint32_t *runs, int init)
 {
+    __shared__ double sC[DOS_SMEM_LEVELS];
     const uint32_t run = runs[blockIdx.y];
     const RunDev rd = P.runs[run];
     const RunState *st = &P.st[run];
@@ -1398,20 +1415,19 @@ __global__ void __launch_bounds__(256) dos_sample_kernel(Pool P, const uint32_t 
     const uint32_t i = init ? 0u : st->step + 1;
     if (i >= rd.n_beta) return;
     const uint32_t R = init ? rd.R : st->R_new;
+    if (blockIdx.x * blockDim.x >= R) return;  // uniform over the CTA
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= R) return;
     const uint32_t U = 2 * rd.N, b = i & 1u;
     const double *C = P.wt + rd.dos_off + (uint64_t)i * (U + 2);
+    const bool staged = U + 2 <= DOS_SMEM_LEVELS;
+    if (staged) {
+        for (uint32_t u = threadIdx.x; u < U + 2; u += blockDim.x) sC[u] = C[u];
+        __syncthreads();
+    }
+    if (k >= R) return;
     const uint4 o = philox4x32_10(k, 0u, i, TAG_DOS << 24, rd.seed, rd.run_id);
     const unsigned long long u53 = ((unsigned long long)(o.x >> 5) << 26) | (unsigned long long)(o.y >> 6);
-    const double x = __dmul_rn(__dmul_rn((double)u53, 1.0 / 9007199254740992.0), C[U]);
-    uint32_t lo = 0, hi = U + 1;  // first u with x < C[u]
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (x < C[mid]) hi = mid;
-        else lo = mid + 1;
-    }
-    const uint32_t lev = lo <= U ? lo : (uint32_t)C[U + 1];
+    const uint32_t lev = staged ? dos_level(sC, U, u53) : dos_level(C, U, u53);
     const uint64_t slot = rd.rep_off + k;
     P.E[b][slot] = (int32_t)(2 * (int64_t)lev - 2 * (int64_t)rd.N);
     P.M[b][slot] = 0;
@@ -1470,9 +1486,13 @@ __device__ __forceinline__ I128 warp_sum128(I128 v)
 // max-scan of run starts gives every replica its run start (the chunk's first
 // replica is treated as a start), and thread 0 then joins the runs that cross
 // chunk boundaries: pieces a and b of one family counted as a^2 + b^2 gain 2ab.
-__global__ void __launch_bounds__(512) measure_kernel(Pool P, const uint32_t *runs, int init)
+#ifndef PA_MEASURE_THREADS
+#define PA_MEASURE_THREADS 512
+#endif
+
+__global__ void __launch_bounds__(PA_MEASURE_THREADS) measure_kernel(Pool P, const uint32_t *runs, int init)
 {
-    __shared__ MeasurePart part[16];  // launched with 512 threads: 16 warps
+    __shared__ MeasurePart part[PA_MEASURE_THREADS / 32];
     const uint32_t run = runs ? runs[blockIdx.x] : blockIdx.x;
     const RunDev rd = P.runs[run];
     RunState *st = &P.st[run];
@@ -1918,7 +1938,7 @@ void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, ui
 
 void launch_measure(const Pool &P, const uint32_t *runs, uint32_t n_runs, int init, cudaStream_t s)
 {
-    measure_kernel<<<n_runs, 512, 0, s>>>(P, runs, init);
+    measure_kernel<<<n_runs, PA_MEASURE_THREADS, 0, s>>>(P, runs, init);
 }
 
 void launch_wavg_wang(const pa_step_record *recs, const unsigned long long *rec_off, const uint32_t *qh,
