@@ -970,6 +970,10 @@ __global__ void __launch_bounds__(MAXT) sweep_pow2_kernel(Pool P, const uint32_t
 // the range are shared with the neighbouring words and drawn by both), and
 // each comparison bit is placed at its padded position.
 // --------------------------------------------------------------------------
+// Compact sites of one padded plane word: RW rows of Lh sites with RW * pitch = 32 and
+// Lh <= pitch, i.e. at most 32 sites, starting anywhere in a Philox group: <= 9 groups.
+constexpr uint32_t PAD_MAX_GROUPS = 9;
+
 template <bool SG>
 __global__ void __launch_bounds__(256) sweep_pad_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off,
                                                         uint32_t n_group_runs, SweepCfg cfg)
@@ -1022,6 +1026,8 @@ __global__ void __launch_bounds__(256) sweep_pad_kernel(Pool P, const uint32_t *
     const uint32_t EVEN = Pt == 4 ? 0x0F0F0F0Fu : Pt == 8 ? 0x00FF00FFu : 0x0000FFFFu;  // rows 0, 2, ... (sub)
     const uint32_t VMASK = LOW * ((1u << Lh) - 1u);                                      // Lh < 32 here
     const uint32_t kb = y0 * Lh, kend = kb + RW * Lh;                                     // compact sites of the word
+    const uint32_t g0 = kb >> 2, off = kb & 3u, ng = (kend - 4 * g0 + 3) / 4;          // Philox groups (<= 9)
+    const uint32_t ROWMASK = (1u << Lh) - 1u;
 
     const unsigned long long T1 = P.thr[rd.thr_off + 2 * i], T2 = P.thr[rd.thr_off + 2 * i + 1];
     const uint32_t t1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T1;
@@ -1062,20 +1068,29 @@ __global__ void __launch_bounds__(256) sweep_pad_kernel(Pool P, const uint32_t *
                 const uint32_t a = x1 ^ x2, b = x1 & x2, e = x3 ^ x4, f = x3 & x4;
                 const uint32_t c0 = a ^ e, ge2 = b | f | (a & e);
                 const uint32_t ctr3 = (TAG_SWEEP << 24) | (t << 1) | c;
-                uint32_t B1 = 0, B2 = 0, r = 0, xp = 0;  // (r, xp): row and column of the next site
-                for (uint32_t g = kb >> 2; 4 * g < kend; ++g) {
-                    const uint4 u = philox_rk(g, child, ctr3, hi1_0, lo1_0, K);
+                // comparison bits of the word's compact sites kb..kend-1, in compact order from
+                // bit `off` of C1 / C2 (the Philox groups of 4 start at kb & ~3) ...
+                unsigned long long C1 = 0, C2 = 0;
 #pragma unroll
-                    for (uint32_t q = 0; q < 4; ++q) {
-                        const uint32_t k = 4 * g + q;
-                        if (k < kb || k >= kend) continue;
-                        const uint32_t pos = r * Pt + xp, v = pick(u, q);
-                        B1 |= (uint32_t)(v < t1) << pos;
-                        B2 |= (uint32_t)(v < t2) << pos;
-                        if (++xp == Lh) {
-                            xp = 0;
-                            ++r;
-                        }
+                for (uint32_t q = 0; q < PAD_MAX_GROUPS; ++q) {
+                    if (q < ng) {
+                        const uint4 u = philox_rk(g0 + q, child, ctr3, hi1_0, lo1_0, K);
+                        C1 |= (unsigned long long)((uint32_t)(u.x < t1) | ((uint32_t)(u.y < t1) << 1) |
+                                                   ((uint32_t)(u.z < t1) << 2) | ((uint32_t)(u.w < t1) << 3))
+                              << (4 * q);
+                        C2 |= (unsigned long long)((uint32_t)(u.x < t2) | ((uint32_t)(u.y < t2) << 1) |
+                                                   ((uint32_t)(u.z < t2) << 2) | ((uint32_t)(u.w < t2) << 3))
+                              << (4 * q);
+                    }
+                }
+                // ... then each row's Lh bits moved to its padded position r * Pt
+                uint32_t B1 = 0, B2 = 0;
+#pragma unroll
+                for (uint32_t r = 0; r < 8; ++r) {
+                    if (r < RW) {
+                        const uint32_t sh = off + r * Lh;
+                        B1 |= ((uint32_t)(C1 >> sh) & ROWMASK) << (r * Pt);
+                        B2 |= ((uint32_t)(C2 >> sh) & ROWMASK) << (r * Pt);
                     }
                 }
                 const uint32_t flip = (ge2 | (c0 & (B1 | all1)) | B2 | all2) & VMASK;
