@@ -974,8 +974,12 @@ __global__ void __launch_bounds__(MAXT) sweep_pow2_kernel(Pool P, const uint32_t
 // Lh <= pitch, i.e. at most 32 sites, starting anywhere in a Philox group: <= 9 groups.
 constexpr uint32_t PAD_MAX_GROUPS = 9;
 
+#ifndef PA_PAD_MIN_BLOCKS
+#define PA_PAD_MIN_BLOCKS 3  // caps registers at 85: 3 CTAs of 256 threads per SM (measured best of 1, 2, 3)
+#endif
+
 template <bool SG>
-__global__ void __launch_bounds__(256) sweep_pad_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off,
+__global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off,
                                                         uint32_t n_group_runs, SweepCfg cfg)
 {
     extern __shared__ __align__(16) uint32_t smw[];
