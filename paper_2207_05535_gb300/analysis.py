@@ -185,6 +185,9 @@ def main(argv=None):
     ap.add_argument("--temps", type=int, default=51)
     ap.add_argument("--Ms", default="1,2,4,8,16,32,64,128")
     ap.add_argument("--window", default="0.42,0.46", help="beta range the bias is averaged over")
+    ap.add_argument("--fit-min-snr", type=float, default=2.0,
+                    help="fit a M^-b only to the M whose bias exceeds this many standard errors (the rest is the "
+                         "statistical floor of all runs together)")
     a = ap.parse_args(argv)
     build.build()
     descs = W.ferro_runs(L=a.L, R=a.R, theta=a.theta, beta_f=a.beta_f, n=a.temps, M=a.runs, seed=1)
@@ -204,9 +207,9 @@ def main(argv=None):
     for obs, key, rel in (("W_e", "e", False), ("Wvar_c", "c", True), ("W_minus_betaF", "lnZ", False)):
         rows = bias_vs_M(eng, runs, Ms, lambda b, k=key: exact_ferro(a.L, b)[k], obs=obs, steps=steps,
                          relative=rel)
-        fit = fit_power_law([r[0] for r in rows], [r[2] for r in rows], [r[3] for r in rows]) \
-            if all(r[2] > 0 for r in rows) else None
-        out[obs] = {"rows": rows, "fit_a_b_sigma": fit}
+        use = [r for r in rows if r[2] > a.fit_min_snr * r[3]]
+        fit = fit_power_law([r[0] for r in use], [r[2] for r in use], [r[3] for r in use]) if len(use) >= 3 else None
+        out[obs] = {"rows": rows, "fit_a_b_sigma": fit, "fit_M": [r[0] for r in use]}
     t_an = time.perf_counter() - t1
     recs = np.stack([eng.records(k) for k in range(min(a.runs, 4096))])
     i_last = len(beta) - 1
