@@ -1263,28 +1263,57 @@ __global__ void __launch_bounds__(256) overlap_kernel(Pool P, const uint32_t *q_
 //   3. every thread takes pairs (k, pi*_k): Hamming distance of the colour
 //      planes, histogram, sum |N - 2d|.
 // --------------------------------------------------------------------------
-__device__ void bitonic_sort_u64(unsigned long long *a, uint32_t n)  // n a power of two, ascending
+constexpr uint32_t WANG_BUCKET_BITS = 12, WANG_BUCKETS = 1u << WANG_BUCKET_BITS;
+
+// Replica indices 0..R-1 in ascending order of their (distinct) 64-bit keys,
+// written to dst: a counting sort on the top 12 key bits (the keys are uniform,
+// so a bucket holds R / 4096 < 2 keys on average), then an insertion sort of
+// each bucket by the whole key.  cnt: WANG_BUCKETS counters in shared memory.
+__device__ void sort_by_key(const unsigned long long *key, uint32_t R, uint32_t *dst, uint32_t *cnt,
+                            uint32_t *sh_scan)
 {
-    for (uint32_t size = 2; size <= n; size <<= 1)
-        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t t = threadIdx.x; t < n / 2; t += blockDim.x) {
-                const uint32_t lo = 2 * stride * (t / stride) + (t % stride), hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const unsigned long long x = a[lo], y = a[hi];
-                if ((x > y) == up) {
-                    a[lo] = y;
-                    a[hi] = x;
-                }
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;  // nt * 4 == WANG_BUCKETS
+    for (uint32_t q = tid; q < WANG_BUCKETS; q += nt) cnt[q] = 0;
+    __syncthreads();
+    for (uint32_t j = tid; j < R; j += nt) atomicAdd(&cnt[key[j] >> (64 - WANG_BUCKET_BITS)], 1u);
+    __syncthreads();
+    uint32_t c[4], sum = 0;  // exclusive scan: each thread owns 4 consecutive buckets
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        c[q] = cnt[4 * tid + q];
+        sum += c[q];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(sum, sh_scan, total);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        cnt[4 * tid + q] = run;
+        run += c[q];
+    }
+    __syncthreads();
+    for (uint32_t j = tid; j < R; j += nt) dst[atomicAdd(&cnt[key[j] >> (64 - WANG_BUCKET_BITS)], 1u)] = j;
+    __syncthreads();  // cnt[q] is now the end of bucket q
+    for (uint32_t q = tid; q < WANG_BUCKETS; q += nt) {
+        const uint32_t lo = q ? cnt[q - 1] : 0u, hi = cnt[q];
+        for (uint32_t x = lo + 1; x < hi; ++x) {  // insertion sort of a few entries
+            const uint32_t v = dst[x];
+            const unsigned long long kv = key[v];
+            uint32_t y = x;
+            while (y > lo && key[dst[y - 1]] > kv) {
+                dst[y] = dst[y - 1];
+                --y;
             }
-            __syncthreads();
+            dst[y] = v;
         }
+    }
+    __syncthreads();
 }
 
-__global__ void __launch_bounds__(1024) wang_kernel(Pool P, const uint32_t *runs, int init, uint32_t n2,
-                                                    uint32_t cap)
+__global__ void __launch_bounds__(1024) wang_kernel(Pool P, const uint32_t *runs, int init, uint32_t cap)
 {
     extern __shared__ __align__(16) unsigned long long wsm[];
     __shared__ long long sh_l[32];
+    __shared__ uint32_t sh_scan[33];
     __shared__ uint32_t s_ok, s_swaps;
     const uint32_t run = runs[blockIdx.x];
     const RunDev rd = P.runs[run];
@@ -1294,27 +1323,21 @@ __global__ void __launch_bounds__(1024) wang_kernel(Pool P, const uint32_t *runs
     if (i >= rd.n_beta) return;
     const uint32_t R = init ? rd.R : st.R_new;
     const uint32_t b = i & 1u, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31u;
-    unsigned long long *key = wsm;                                // [n2] sort keys, then the families
+    unsigned long long *key = wsm;                                // [cap] sort keys, then the families
     uint32_t *fam = reinterpret_cast<uint32_t *>(wsm);            // [cap], over the keys once sorted
-    uint32_t *pi = reinterpret_cast<uint32_t *>(wsm + n2);        // [cap]
+    uint32_t *pi = reinterpret_cast<uint32_t *>(wsm + cap);       // [cap]
     uint32_t *sg = pi + cap;                                      // [cap]
+    uint32_t *cnt = sg + cap;                                     // [WANG_BUCKETS]
     const unsigned long long mask = (1ull << WANG_IDX_BITS) - 1;
-    uint32_t nr = 2;
-    while (nr < R) nr <<= 1;
     for (int which = 0; which < 2; ++which) {
-        for (uint32_t j = tid; j < nr; j += nt) {
-            unsigned long long k = ~0ull;  // padding sorts last, ties broken by index
-            if (j < R) {
-                const uint4 o = philox4x32_10(j, 0u, i, TAG_WANG << 24, rd.seed, rd.run_id);
-                k = which ? ((unsigned long long)o.z << 32 | o.w) : ((unsigned long long)o.x << 32 | o.y);
-            }
+        for (uint32_t j = tid; j < R; j += nt) {  // low 13 bits replaced by the index: no ties
+            const uint4 o = philox4x32_10(j, 0u, i, TAG_WANG << 24, rd.seed, rd.run_id);
+            const unsigned long long k = which ? ((unsigned long long)o.z << 32 | o.w)
+                                               : ((unsigned long long)o.x << 32 | o.y);
             key[j] = (k & ~mask) | j;
         }
         __syncthreads();
-        bitonic_sort_u64(key, nr);
-        uint32_t *dst = which ? sg : pi;
-        for (uint32_t k = tid; k < R; k += nt) dst[k] = (uint32_t)(key[k] & mask);
-        __syncthreads();
+        sort_by_key(key, R, which ? sg : pi, cnt, sh_scan);
     }
     for (uint32_t j = tid; j < R; j += nt) fam[j] = P.fam[b][rd.rep_off + j];
     __syncthreads();
@@ -1819,7 +1842,7 @@ cudaError_t prepare_kernels()
                                          200 * 1024);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sweep_kernel<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e == cudaSuccess)  // Wang pairing with R_cap up to 8192: 160 KB
+    if (e == cudaSuccess)  // Wang pairing with R_cap up to 8192: 144 KB
         e = cudaFuncSetAttribute(wang_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     return e;
 }
@@ -1981,26 +2004,19 @@ void launch_wavg(const pa_step_record *recs, const unsigned long long *rec_off, 
                      s);
 }
 
-static uint32_t wang_n2(uint32_t max_Rcap)
-{
-    uint32_t n2 = 32;
-    while (n2 < max_Rcap) n2 <<= 1;
-    return n2;
-}
-
-// keys (8 n2 bytes, reused for the families) + pi and sigma (4 R_cap bytes each):
-// about 110 KB at R_cap = 5630, so two CTAs fit on an SM
+// keys (8 R_cap bytes, reused for the families) + pi and sigma (4 R_cap bytes each)
+// + the bucket counters: about 104 KB at R_cap = 5630, so two CTAs fit on an SM
 size_t wang_smem_bytes(uint32_t max_Rcap)
 {
     const uint32_t cap = (max_Rcap + 3) / 4 * 4;
-    return (size_t)wang_n2(max_Rcap) * 8 + (size_t)cap * 8;
+    return (size_t)cap * 16 + (size_t)WANG_BUCKETS * 4;
 }
 
 void launch_wang(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap, int init, cudaStream_t s)
 {
     if (n_runs == 0) return;
-    const uint32_t n2 = wang_n2(max_Rcap), cap = (max_Rcap + 3) / 4 * 4;
-    wang_kernel<<<n_runs, 1024, wang_smem_bytes(max_Rcap), s>>>(P, runs, init, n2, cap);
+    const uint32_t cap = (max_Rcap + 3) / 4 * 4;
+    wang_kernel<<<n_runs, 1024, wang_smem_bytes(max_Rcap), s>>>(P, runs, init, cap);  // 1024 * 4 = WANG_BUCKETS
 }
 
 }  // namespace pa
