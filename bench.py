@@ -87,7 +87,7 @@ def work_units(d, R):
     return R if d.theta == 0xFFFFFFFF else d.theta * d.N * R
 # DRAM bytes per sweep launch from one ncu capture (profiles/sweep_pow2_glass_L16_R5000.md),
 # valid only for the kernel source it was taken on.
-SWEEP_TRAFFIC = {"sweep_source_sha256_16": "ac5a5ab9fb42dc5a", "workload": "glass_L16_R5000", "bytes_per_launch": 44.230144e6}
+SWEEP_TRAFFIC = {"sweep_source_sha256_16": "b4a70c0f58a0f125", "workload": "glass_L16_R5000", "bytes_per_launch": 44.163072e6}
 MULADD_LANES_PER_SM = 64
 
 
@@ -391,6 +391,18 @@ def main():
             rec = eng.records(k)
             per_replica = 2 * plane_words(d.L) * 4
             ov_bytes += int(np.sum(2 * rec["n_q"].astype(np.int64) + rec["n_q_pair"] + 2 * rec["n_q_wang"])) * per_replica
+    # resampling copy (a7), fused into the sweep's prologue: every child reads its parent's colour
+    # planes and E, M, family and writes its own, plus its parent index
+    gather_bytes = 0
+    for k, d in enumerate(descs):
+        if d.theta == 0xFFFFFFFF:
+            continue
+        rec = eng.records(k)
+        gather_bytes += int(np.sum(rec["R"][1:].astype(np.int64))) * (2 * 2 * plane_words(d.L) * 4 + 2 * 12 + 4)
+    gather = {"bytes_per_step": gather_bytes,
+              "GBps_within_sweep": gather_bytes / (sweep_ms / args.steps * 1e-3) / 1e9 if sweep_ms else None,
+              "basis": "children x (parent planes read + child planes written + 12 B E/M/family each way + "
+                       "4 B parent index); the copy is fused into the sweep kernel, so its rate is per sweep time"}
     roof_ov = None
     if ov_ms > 0 and ov_bytes:
         ach = ov_bytes / (ov_ms * 1e-3) / 1e9
@@ -482,6 +494,7 @@ def main():
                          "sweep_ms_per_step": sweep_ms / args.steps,
                          "sweep_share_of_kernel_time": sweep_ms / total_kernel_ms if total_kernel_ms else None},
             "roofline_overlap": roof_ov,
+            "resample_gather": gather,
             "kernel_ms_per_step": {k: t / args.steps for k, (t, n) in kt_tot.items()},
             "sweep_shapes": [{"L": L_, "words_per_thread": w_, "block": b_, "autotuned": bool(t_)}
                              for (L_, w_, b_, t_) in _lib.pa_sweep_shapes(eng.h)],
