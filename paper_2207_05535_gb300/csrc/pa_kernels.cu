@@ -1553,12 +1553,31 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS) measure_kernel(Pool P, con
     long long sE = 0, sE2 = 0, sAM = 0, sM2 = 0, c2 = 0;
     I128 sE3 = {0ull, 0ll}, sE4 = {0ull, 0ll}, sAM3 = {0ull, 0ll}, sM4 = {0ull, 0ll};
     uint32_t nfam = 0, cmax = 0, first = hi, open = lo;
+    // loads run one chunk of 32 ahead; fam[j - 1] comes from the neighbouring lane
+    int32_t e_nx = 0, m_nx = 0;
+    uint32_t f_nx = 0;
+    if (lo + lane < hi) {
+        e_nx = E[lo + lane];
+        m_nx = M[lo + lane];
+        f_nx = fam[lo + lane];
+    }
+    uint32_t f_prev = lo > 0 && lo < hi ? fam[lo - 1] : 0u;  // family before the chunk (lane 0's left)
     for (uint32_t base = lo; base < hi; base += 32) {
         const uint32_t j = base + lane;
         const bool ok = j < hi;
+        const int32_t e_cur = e_nx, m_cur = m_nx;
+        const uint32_t f_cur = f_nx;
+        if (base + 32 + lane < hi) {
+            e_nx = E[base + 32 + lane];
+            m_nx = M[base + 32 + lane];
+            f_nx = fam[base + 32 + lane];
+        }
+        uint32_t f_left = __shfl_up_sync(FULL, f_cur, 1);
+        if (lane == 0) f_left = f_prev;
+        f_prev = __shfl_sync(FULL, f_cur, 31);
         bool start = false, forced = false;
         if (ok) {
-            const long long e = E[j], m = M[j];
+            const long long e = e_cur, m = m_cur;
             const long long am = m < 0 ? -m : m;
             const long long e2 = e * e, m2 = m * m;  // |E| <= 2N = 2^17, |M| <= 2^16
             sE += e;
@@ -1569,7 +1588,7 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS) measure_kernel(Pool P, con
             add128_square(sE4, (unsigned long long)e2);
             add128_signed(sAM3, m2 * am);
             add128_square(sM4, (unsigned long long)m2);
-            start = j == 0 || fam[j] != fam[j - 1];
+            start = j == 0 || f_cur != f_left;
             forced = start || j == lo;
         }
         uint32_t sj = forced ? j : 0u;
