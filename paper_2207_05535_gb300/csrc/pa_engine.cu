@@ -1323,7 +1323,7 @@ pa_status pa_weighted_average_runs(pa_engine *e, const uint32_t *run_idx, uint32
         launch_wavg_wang(e->P.rec, d_roff, e->P.qh, e->P.qhp, e->P.qhw, d_qoff, n_groups, M, n_steps, N, weight_kind,
                          d_out, d_w, d_pq, d_pqp, d_pqw, e->stream);
     });
-    e->launches += 1 + ((d_pq || d_pqp || d_pqw) ? 1 : 0);
+    e->launches += 2 + ((d_pq || d_pqp || d_pqw) ? 1 : 0);  // with the one counted above: 3 passes + histograms
     e->h2d += 2 * sizeof(unsigned long long) * nGM;
     e->d2h += sizeof(pa_wavg) * n_groups * n_steps +
               sizeof(double) * nP * ((host_Pq ? 1 : 0) + (host_Pq_pair ? 1 : 0) + (host_Pq_wang ? 1 : 0));

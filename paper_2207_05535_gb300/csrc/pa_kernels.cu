@@ -1714,117 +1714,152 @@ __device__ __forceinline__ double central_from_raw(int k, const double *raw)
 // W_F, Wvar_C, Wvar_Chi) in FP64: one warp per group, lanes over the runs m,
 // temperatures in order.  w receives the weights [group][step][m].
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(64) wavg_kernel(const pa_step_record *recs, const unsigned long long *rec_off,
-                                                  uint32_t n_groups, uint32_t M, uint32_t n_steps, uint32_t N,
-                                                  uint32_t kind, pa_wavg *out, double *w)
+// pass 1, one thread per (group, run m): log weights over the temperatures,
+// lambda(i, m) = ln R_i + (-beta_i F_i) [+ sum_{k<=i} ln(R_{k-1} / R)], into w[g][i][m]
+__global__ void __launch_bounds__(128) wavg_lambda_kernel(const pa_step_record *recs,
+                                                          const unsigned long long *rec_off, uint32_t n_groups,
+                                                          uint32_t M, uint32_t n_steps, uint32_t kind, double *w)
 {
-    const uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (g >= n_groups) return;  // warp-uniform
-    const unsigned long long *off = rec_off + (uint64_t)g * M;
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (uint64_t)n_groups * M) return;
+    const uint32_t g = (uint32_t)(t / M), m = (uint32_t)(t % M);
+    const pa_step_record *r = recs + rec_off[t];
     double *wg = w + (uint64_t)g * n_steps * M;
-    const double Nd = (double)N;
-    // pass 1: log weights lambda(i, m) = ln R_i + (-beta_i F_i) [+ sum_{k<=i} ln(R_{k-1} / R)]
-    for (uint32_t m = lane; m < M; m += 32) {
-        const pa_step_record *r = recs + off[m];
-        double lsum = 0.0;
-        for (uint32_t i = 0; i < n_steps; ++i) {
-            if (kind == PA_WEIGHT_FULL && i > 0) lsum += log((double)r[i - 1].R / (double)r[i].R_target);
-            wg[(uint64_t)i * M + m] = log((double)r[i].R) + r[i].minus_betaF + lsum;
-        }
-    }
-    // pass 2: normalise per temperature and average (each lane touches only its own m)
-    double WF = Nd * log(2.0);
+    double lsum = 0.0;
     for (uint32_t i = 0; i < n_steps; ++i) {
-        double *wi = wg + (uint64_t)i * M;
-        double lmax = -INFINITY;
-        for (uint32_t m = lane; m < M; m += 32) lmax = wi[m] > lmax ? wi[m] : lmax;
-        lmax = warp_max(lmax);
-        double z = 0.0;
+        if (kind == PA_WEIGHT_FULL && i > 0) lsum += log((double)r[i - 1].R / (double)r[i].R_target);
+        wg[(uint64_t)i * M + m] = log((double)r[i].R) + r[i].minus_betaF + lsum;
+    }
+}
+
+// max and sum of exp(lambda - max) over the M runs of one temperature (warp-wide)
+__device__ __forceinline__ void weight_norm(const double *li, uint32_t M, uint32_t lane, double &lmax, double &z)
+{
+    lmax = -INFINITY;
+    for (uint32_t m = lane; m < M; m += 32) lmax = li[m] > lmax ? li[m] : lmax;
+    lmax = warp_max(lmax);
+    z = 0.0;
+    for (uint32_t m = lane; m < M; m += 32) z += exp(li[m] - lmax);
+    z = warp_sum(z);
+}
+
+// pass 2, one warp per (group, temperature): the weights w = exp(lambda - max) / z
+// and every weighted average; W_minus_betaF temporarily holds ln W[Q_i] (Eq. W_F).
+__global__ void __launch_bounds__(128) wavg_step_kernel(const pa_step_record *recs, const unsigned long long *rec_off,
+                                                        uint32_t n_groups, uint32_t M, uint32_t n_steps, uint32_t N,
+                                                        pa_wavg *out, const double *w)
+{
+    const uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), g = blockIdx.y, lane = threadIdx.x & 31;
+    if (i >= n_steps) return;  // warp-uniform
+    const unsigned long long *off = rec_off + (uint64_t)g * M;
+    const double *li = w + ((uint64_t)g * n_steps + i) * M;
+    const double Nd = (double)N;
+    double lmax, z;
+    weight_norm(li, M, lane, lmax, z);
+    const double beta = recs[off[0] + i].beta;
+    double se = 0.0, se2 = 0.0, sm = 0.0, sm2 = 0.0, sc = 0.0, schi = 0.0, sq = 0.0, sqp = 0.0, sw = 0.0,
+           wmax = 0.0, se3 = 0.0, se4 = 0.0, sm3 = 0.0, sm4 = 0.0, su4 = 0.0, sqw = 0.0;
+    const double N3 = Nd * Nd * Nd, N4 = N3 * Nd;
+    for (uint32_t m = lane; m < M; m += 32) {
+        const double wm = exp(li[m] - lmax) / z;
+        const pa_step_record *r = recs + off[m] + i;
+        const double Ri = (double)r->R;
+        const double e = (double)r->sumE / (Nd * Ri);
+        const double e2 = (double)r->sumE2 / (Nd * Nd * Ri);
+        const double mm = (double)r->sumAbsM / (Nd * Ri);
+        const double m2 = (double)r->sumM2 / (Nd * Nd * Ri);
+        const double c = beta * beta * Nd * (e2 - e * e);  // Eq. c
+        const double chi = beta * Nd * (m2 - mm * mm);     // Eq. chi
+        se += wm * e;
+        se2 += wm * e2;
+        sm += wm * mm;
+        sm2 += wm * m2;
+        sc += wm * c;
+        schi += wm * chi;
+        if (r->n_q) sq += wm * ((double)r->sum_absq / (Nd * (double)r->n_q));
+        if (r->n_q_pair) sqp += wm * ((double)r->sum_absq_pair / (Nd * (double)r->n_q_pair));
+        if (r->n_q_wang) sqw += wm * ((double)r->sum_absq_wang / (Nd * (double)r->n_q_wang));
+        const double e3 = i128_to_double(r->sumE3) / (N3 * Ri);
+        const double e4 = i128_to_double(r->sumE4) / (N4 * Ri);
+        const double m3 = i128_to_double(r->sumAbsM3) / (N3 * Ri);
+        const double m4 = i128_to_double(r->sumM4) / (N4 * Ri);
+        se3 += wm * e3;
+        se4 += wm * e4;
+        sm3 += wm * m3;
+        sm4 += wm * m4;
+        su4 += wm * (1.0 - m4 / (3.0 * m2 * m2));  // per-run Binder cumulant
+        sw += wm;
+        wmax = wm > wmax ? wm : wmax;
+    }
+    pa_wavg o;
+    o.beta = beta;
+    o.W_e = warp_sum(se);
+    o.W_e2 = warp_sum(se2);
+    o.W_m = warp_sum(sm);
+    o.W_m2 = warp_sum(sm2);
+    o.W_c = warp_sum(sc);
+    o.W_chi = warp_sum(schi);
+    o.W_absq = warp_sum(sq);
+    o.W_absq_pair = warp_sum(sqp);
+    o.sum_w = warp_sum(sw);
+    o.w_max = warp_max(wmax);
+    o.Wvar_c = beta * beta * Nd * (o.W_e2 - o.W_e * o.W_e);
+    o.Wvar_chi = beta * Nd * (o.W_m2 - o.W_m * o.W_m);
+    o.W_e3 = warp_sum(se3);
+    o.W_e4 = warp_sum(se4);
+    o.W_m3 = warp_sum(sm3);
+    o.W_m4 = warp_sum(sm4);
+    o.W_U4_conf = warp_sum(su4);
+    o.W_absq_wang = warp_sum(sqw);
+    {
+        const double re[5] = {1.0, o.W_e, o.W_e2, o.W_e3, o.W_e4};
+        const double rm[5] = {1.0, o.W_m, o.W_m2, o.W_m3, o.W_m4};
+        o.Wk3_e = central_from_raw(3, re);
+        o.Wk4_e = central_from_raw(4, re);
+        o.Wk3_m = central_from_raw(3, rm);
+        o.Wk4_m = central_from_raw(4, rm);
+        o.W_U4 = 1.0 - o.W_m4 / (3.0 * o.W_m2 * o.W_m2);
+    }
+    double dF = 0.0;
+    if (i > 0) {  // Eq. W_F: ln W[Q_i] = ln sum_m w_{i-1} Q_i as a log-sum-exp, ln w_{i-1} = lambda - max - ln z
+        const double *lp = li - M;
+        double pmax, pz;
+        weight_norm(lp, M, lane, pmax, pz);
+        const double lpz = pmax + log(pz);
+        double lm = -INFINITY;
         for (uint32_t m = lane; m < M; m += 32) {
-            wi[m] = exp(wi[m] - lmax);
-            z += wi[m];
+            const double l = lp[m] - lpz + recs[off[m] + i].lnQ;
+            lm = l > lm ? l : lm;
         }
-        z = warp_sum(z);
-        const double beta = recs[off[0] + i].beta;
-        double se = 0.0, se2 = 0.0, sm = 0.0, sm2 = 0.0, sc = 0.0, schi = 0.0, sq = 0.0, sqp = 0.0, sw = 0.0,
-               wmax = 0.0, se3 = 0.0, se4 = 0.0, sm3 = 0.0, sm4 = 0.0, su4 = 0.0, sqw = 0.0;
-        const double N3 = Nd * Nd * Nd, N4 = N3 * Nd;
-        for (uint32_t m = lane; m < M; m += 32) {
-            wi[m] = wi[m] / z;
-            const pa_step_record *r = recs + off[m] + i;
-            const double Ri = (double)r->R;
-            const double e = (double)r->sumE / (Nd * Ri);
-            const double e2 = (double)r->sumE2 / (Nd * Nd * Ri);
-            const double mm = (double)r->sumAbsM / (Nd * Ri);
-            const double m2 = (double)r->sumM2 / (Nd * Nd * Ri);
-            const double c = beta * beta * Nd * (e2 - e * e);  // Eq. c
-            const double chi = beta * Nd * (m2 - mm * mm);     // Eq. chi
-            const double wm = wi[m];
-            se += wm * e;
-            se2 += wm * e2;
-            sm += wm * mm;
-            sm2 += wm * m2;
-            sc += wm * c;
-            schi += wm * chi;
-            if (r->n_q) sq += wm * ((double)r->sum_absq / (Nd * (double)r->n_q));
-            if (r->n_q_pair) sqp += wm * ((double)r->sum_absq_pair / (Nd * (double)r->n_q_pair));
-            if (r->n_q_wang) sqw += wm * ((double)r->sum_absq_wang / (Nd * (double)r->n_q_wang));
-            const double e3 = i128_to_double(r->sumE3) / (N3 * Ri);
-            const double e4 = i128_to_double(r->sumE4) / (N4 * Ri);
-            const double m3 = i128_to_double(r->sumAbsM3) / (N3 * Ri);
-            const double m4 = i128_to_double(r->sumM4) / (N4 * Ri);
-            se3 += wm * e3;
-            se4 += wm * e4;
-            sm3 += wm * m3;
-            sm4 += wm * m4;
-            su4 += wm * (1.0 - m4 / (3.0 * m2 * m2));  // per-run Binder cumulant
-            sw += wm;
-            wmax = wm > wmax ? wm : wmax;
+        lm = warp_max(lm);
+        double zz = 0.0;
+        for (uint32_t m = lane; m < M; m += 32) zz += exp(lp[m] - lpz + recs[off[m] + i].lnQ - lm);
+        zz = warp_sum(zz);
+        dF = lm + log(zz);
+    }
+    o.W_minus_betaF = dF;
+    if (lane == 0) out[(uint64_t)g * n_steps + i] = o;
+}
+
+// pass 3: the weights normalised in place (for the overlap distributions) and,
+// per group in temperature order, -beta_i W[F_i] = N ln 2 + sum_{k<=i} ln W[Q_k].
+__global__ void __launch_bounds__(128) wavg_finish_kernel(uint32_t n_groups, uint32_t M, uint32_t n_steps,
+                                                          uint32_t N, pa_wavg *out, double *w)
+{
+    const uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), g = blockIdx.y, lane = threadIdx.x & 31;
+    if (i < n_steps) {
+        double *li = w + ((uint64_t)g * n_steps + i) * M;
+        double lmax, z;
+        weight_norm(li, M, lane, lmax, z);
+        for (uint32_t m = lane; m < M; m += 32) li[m] = exp(li[m] - lmax) / z;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        pa_wavg *og = out + (uint64_t)g * n_steps;
+        double WF = (double)N * log(2.0);
+        for (uint32_t k = 0; k < n_steps; ++k) {
+            if (k > 0) WF = WF + og[k].W_minus_betaF;
+            og[k].W_minus_betaF = WF;
         }
-        pa_wavg o;
-        o.beta = beta;
-        o.W_e = warp_sum(se);
-        o.W_e2 = warp_sum(se2);
-        o.W_m = warp_sum(sm);
-        o.W_m2 = warp_sum(sm2);
-        o.W_c = warp_sum(sc);
-        o.W_chi = warp_sum(schi);
-        o.W_absq = warp_sum(sq);
-        o.W_absq_pair = warp_sum(sqp);
-        o.sum_w = warp_sum(sw);
-        o.w_max = warp_max(wmax);
-        o.Wvar_c = beta * beta * Nd * (o.W_e2 - o.W_e * o.W_e);
-        o.Wvar_chi = beta * Nd * (o.W_m2 - o.W_m * o.W_m);
-        o.W_e3 = warp_sum(se3);
-        o.W_e4 = warp_sum(se4);
-        o.W_m3 = warp_sum(sm3);
-        o.W_m4 = warp_sum(sm4);
-        o.W_U4_conf = warp_sum(su4);
-        o.W_absq_wang = warp_sum(sqw);
-        {
-            const double re[5] = {1.0, o.W_e, o.W_e2, o.W_e3, o.W_e4};
-            const double rm[5] = {1.0, o.W_m, o.W_m2, o.W_m3, o.W_m4};
-            o.Wk3_e = central_from_raw(3, re);
-            o.Wk4_e = central_from_raw(4, re);
-            o.Wk3_m = central_from_raw(3, rm);
-            o.Wk4_m = central_from_raw(4, rm);
-            o.W_U4 = 1.0 - o.W_m4 / (3.0 * o.W_m2 * o.W_m2);
-        }
-        if (i > 0) {  // Eq. W_F: W[Q_i] = sum_m w_{i-1} Q_i, as a log-sum-exp
-            const double *wp = wi - M;
-            double lm = -INFINITY;
-            for (uint32_t m = lane; m < M; m += 32) {
-                const double l = log(wp[m]) + recs[off[m] + i].lnQ;
-                lm = l > lm ? l : lm;
-            }
-            lm = warp_max(lm);
-            double zz = 0.0;
-            for (uint32_t m = lane; m < M; m += 32) zz += exp(log(wp[m]) + recs[off[m] + i].lnQ - lm);
-            zz = warp_sum(zz);
-            WF = WF + (lm + log(zz));
-        }
-        o.W_minus_betaF = WF;
-        if (lane == 0) out[(uint64_t)g * n_steps + i] = o;
     }
 }
 
@@ -2007,7 +2042,11 @@ void launch_wavg_wang(const pa_step_record *recs, const unsigned long long *rec_
                       uint32_t M, uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w, double *Pq,
                       double *Pqp, double *Pqw, cudaStream_t s)
 {
-    wavg_kernel<<<(n_groups + 1) / 2, 64, 0, s>>>(recs, rec_off, n_groups, M, n_steps, N, kind, out, w);
+    const uint64_t nGM = (uint64_t)n_groups * M;
+    wavg_lambda_kernel<<<(unsigned)((nGM + 127) / 128), 128, 0, s>>>(recs, rec_off, n_groups, M, n_steps, kind, w);
+    const dim3 grid((n_steps + 3) / 4, n_groups);  // one warp per (temperature, group)
+    wavg_step_kernel<<<grid, 128, 0, s>>>(recs, rec_off, n_groups, M, n_steps, N, out, w);
+    wavg_finish_kernel<<<grid, 128, 0, s>>>(n_groups, M, n_steps, N, out, w);
     if (Pq || Pqp || Pqw) {
         dim3 grid(n_steps, n_groups);
         wavg_q_kernel<<<grid, 256, 0, s>>>(recs, rec_off, qh, qhp, qhw, qh_off, M, n_steps, N, w, Pq, Pqp, Pqw);
