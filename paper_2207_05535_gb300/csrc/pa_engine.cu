@@ -762,7 +762,7 @@ void enqueue_tick(pa_engine *e)
 {
     const uint32_t *act = meta(e, e->active_off);
     const uint32_t na = (uint32_t)e->active.size();
-    timed_launch(e, PA_K_RESAMPLE, [&] { launch_resample(e->P, act, na, e->stream); });
+    timed_launch(e, PA_K_RESAMPLE, [&] { launch_resample(e->P, act, na, e->max_Rcap_active, e->stream); });
     for (auto &g : e->groups) timed_launch(e, PA_K_SWEEP, [&] { launch_group_sweep(e, g, e->tuning[g.L].pick); });
     enqueue_dos_sample(e);
     if (!e->q_runs.empty())
@@ -781,7 +781,7 @@ pa_status enqueue_tuning_tick(pa_engine *e)
 {
     const uint32_t *act = meta(e, e->active_off);
     const uint32_t na = (uint32_t)e->active.size();
-    timed_launch(e, PA_K_RESAMPLE, [&] { launch_resample(e->P, act, na, e->stream); });
+    timed_launch(e, PA_K_RESAMPLE, [&] { launch_resample(e->P, act, na, e->max_Rcap_active, e->stream); });
     for (auto &g : e->groups) {
         Tuning &t = e->tuning[g.L];
         if (t.tuned) {

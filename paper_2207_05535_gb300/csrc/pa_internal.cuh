@@ -129,7 +129,8 @@ void launch_init_couplings(const Pool &P, const uint32_t *runs, uint32_t n_runs,
 // Work lists: tile_off = prefix of per-run tile counts (n + 1 entries).
 void launch_init_population(const Pool &P, const uint32_t *tile_off, const uint32_t *runs, uint32_t n_runs,
                             uint32_t n_tiles, uint32_t max_pw, cudaStream_t s);
-void launch_resample(const Pool &P, const uint32_t *runs, uint32_t n_runs, cudaStream_t s);
+// max_Rcap: the largest R_cap among the runs (sets the energies staged in shared memory)
+void launch_resample(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap, cudaStream_t s);
 // Launch shapes to try for lattice size L (first = default); one entry unless
 // the bit-sliced kernel applies.
 std::vector<SweepCfg> sweep_candidates(uint32_t L, int allow_fast);

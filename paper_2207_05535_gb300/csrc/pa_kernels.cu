@@ -381,8 +381,12 @@ __global__ void __launch_bounds__(128)
 // --------------------------------------------------------------------------
 // Resampling (Sec. II.B steps (ii)-(iii), Eqs. tauBoltz and QBoltz).
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *runs)
+// Populations of up to this many replicas have their energies staged in shared memory.
+constexpr uint32_t RESAMPLE_STAGE_MAX = 24576;  // 96 KB
+
+__global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *runs, uint32_t stage)
 {
+    extern __shared__ int32_t sE[];  // [stage]
     __shared__ uint32_t sh_hist[SMEM_BINS];
     __shared__ int32_t sh_i[32];
     __shared__ uint32_t sh_u[33];
@@ -399,13 +403,17 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *r
     const int32_t *E = P.E[(i - 1) & 1] + rd.rep_off;
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
 
-    // energy range of the population at beta_{i-1}
+    // energy range of the population at beta_{i-1}; the energies are read once from
+    // global memory and, when they fit, kept in shared memory for the later passes
+    const bool staged = Rprev <= stage;
     int32_t lo = INT32_MAX, hi = INT32_MIN;
     for (uint32_t j = tid; j < Rprev; j += nt) {
         const int32_t e = E[j];
+        if (staged) sE[j] = e;
         lo = e < lo ? e : lo;
         hi = e > hi ? e : hi;
     }
+    const int32_t *Ev = staged ? sE : E;
     const int32_t Emin = block_min(lo, sh_i, INT32_MAX);
     const int32_t Emax = block_max(hi, sh_i, INT32_MIN);
     const uint32_t nb = (uint32_t)(Emax - Emin) / 4u + 1u;  // energies differ by multiples of 4
@@ -419,7 +427,7 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *r
     uint32_t *h = nb <= SMEM_BINS ? sh_hist : g_hist;
     for (uint32_t n = tid; n < nb; n += nt) h[n] = 0;
     __syncthreads();
-    for (uint32_t j = tid; j < Rprev; j += nt) atomicAdd(&h[(uint32_t)(E[j] - Emin) >> 2], 1u);
+    for (uint32_t j = tid; j < Rprev; j += nt) atomicAdd(&h[(uint32_t)(Ev[j] - Emin) >> 2], 1u);
     __syncthreads();
 
     const double dbeta = P.beta[rd.beta_off + i] - P.beta[rd.beta_off + i - 1];
@@ -458,7 +466,7 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *r
             for (uint32_t base = 0; base < Rprev; base += 32) {
                 const uint32_t j = base + tid;
                 const bool ok = j < Rprev;
-                const uint32_t n = ok ? (uint32_t)(E[j] - Emin) >> 2 : 0xffffffffu;
+                const uint32_t n = ok ? (uint32_t)(Ev[j] - Emin) >> 2 : 0xffffffffu;
                 const unsigned peers = __match_any_sync(FULL, n);
                 const uint32_t rank = __popc(peers & ((1u << tid) - 1u));
                 uint32_t pos = 0;
@@ -523,7 +531,7 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *r
             if (multi) {
                 r = cnt[j];
             } else {
-                const uint32_t n = (uint32_t)(E[j] - Emin) >> 2;
+                const uint32_t n = (uint32_t)(Ev[j] - Emin) >> 2;
                 const uint32_t u = philox4x32_10(j, 0, i, TAG_RESAMPLE << 24, rd.seed, rd.run_id).x;
                 r = h[n] + ((unsigned long long)u < thr[n] ? 1u : 0u);
                 cnt[j] = r;
@@ -1896,6 +1904,9 @@ cudaError_t prepare_kernels()
                                          200 * 1024);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sweep_kernel<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(resample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 RESAMPLE_STAGE_MAX * sizeof(int32_t));
     if (e == cudaSuccess)  // Wang pairing with R_cap up to 8192: 144 KB
         e = cudaFuncSetAttribute(wang_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     return e;
@@ -1919,9 +1930,10 @@ void launch_dos_sample(const Pool &P, const uint32_t *runs, uint32_t n_runs, uin
     dos_sample_kernel<<<dim3((max_R + 255) / 256, n_runs), 256, 0, s>>>(P, runs, init);
 }
 
-void launch_resample(const Pool &P, const uint32_t *runs, uint32_t n_runs, cudaStream_t s)
+void launch_resample(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap, cudaStream_t s)
 {
-    resample_kernel<<<n_runs, 512, 0, s>>>(P, runs);
+    const uint32_t stage = max_Rcap < RESAMPLE_STAGE_MAX ? max_Rcap : RESAMPLE_STAGE_MAX;
+    resample_kernel<<<n_runs, 512, stage * sizeof(int32_t), s>>>(P, runs, stage);
 }
 
 // Launch shapes of the bit-sliced kernel: WPT plane words per thread and
