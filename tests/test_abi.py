@@ -121,3 +121,26 @@ def test_binding_argument_counts_match_the_header(lib):
         assert name in decls, name
         params = [p for p in decls[name].split(",") if p.strip() and p.strip() != "void"]
         assert len(getattr(lib, name).argtypes) == len(params), name
+
+
+def test_benchmark_plane_words_follow_the_engine_layout(tmp_path):
+    """bench.py's byte counts use the engine's colour-plane size (row pitch)."""
+    import bench
+    prog = tmp_path / "pw.cpp"
+    prog.write_text(r'''
+#include <cstdio>
+#include <cuda_runtime.h>
+#include "pa_internal.cuh"
+int main() {
+  for (unsigned L = 4; L <= 256; L += 2) std::printf("%u %u\n", L, pa::plane_words_of(L));
+  return 0;
+}
+''')
+    exe = tmp_path / "pw"
+    subprocess.run(["g++", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I",
+                    os.path.join(ROOT, "paper_2207_05535_gb300", "csrc"), "-I", "/usr/local/cuda/include", str(prog),
+                    "-o", str(exe)], check=True)
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n"):
+        if line:
+            L, pw = (int(x) for x in line.split())
+            assert bench.plane_words(L) == pw, L
