@@ -87,7 +87,7 @@ def work_units(d, R):
     return R if d.theta == 0xFFFFFFFF else d.theta * d.N * R
 # DRAM bytes per sweep launch from one ncu capture (profiles/sweep_pow2_glass_L16_R5000.md),
 # valid only for the kernel source it was taken on.
-SWEEP_TRAFFIC = {"sweep_source_sha256_16": "2a8b8dc4573a6d46", "workload": "glass_L16_R5000", "bytes_per_launch": 44.189696e6}
+SWEEP_TRAFFIC = {"sweep_source_sha256_16": "9767cc20b7a2f7fc", "workload": "glass_L16_R5000", "bytes_per_launch": 44.930816e6}
 MULADD_LANES_PER_SM = 64
 
 
@@ -378,6 +378,9 @@ def main():
     pk, pk_kind = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak_tops = 152 * MULADD_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # integer multiply-add slots, T/s
+    # the multiplier roof, checked live: Philox4x32-10 alone (40 multiply-add slots per call)
+    cal = {"calls_per_s_split": _lib.pa_calibrate_philox(False), "calls_per_s_wide": _lib.pa_calibrate_philox(True)}
+    cal["frac_of_peak_split"] = cal["calls_per_s_split"] * 40 / (peak_tops * 1e12)
     inf = wl in INF_WORKLOADS
     slots = ALGO_MULADD_PER_DRAW if inf else ALGO_MULADD_PER_UPDATE
     achieved_tops = updates * slots / (sweep_ms / args.steps * 1e-3) / 1e12
@@ -492,7 +495,8 @@ def main():
                                   f"({pk_kind})",
                          "updates_per_ns_sweep_only": updates / (sweep_ms / args.steps * 1e-3) / 1e9,
                          "sweep_ms_per_step": sweep_ms / args.steps,
-                         "sweep_share_of_kernel_time": sweep_ms / total_kernel_ms if total_kernel_ms else None},
+                         "sweep_share_of_kernel_time": sweep_ms / total_kernel_ms if total_kernel_ms else None,
+                         "philox_calibration": cal},
             "roofline_overlap": roof_ov,
             "resample_gather": gather,
             "kernel_ms_per_step": {k: t / args.steps for k, (t, n) in kt_tot.items()},

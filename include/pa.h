@@ -311,6 +311,16 @@ pa_status pa_kernel_times(pa_engine *e, double *ms_out, uint64_t *launches_out);
 /* Bytes this engine has copied host->device and device->host so far. */
 pa_status pa_transfer_bytes(const pa_engine *e, uint64_t *h2d, uint64_t *d2h);
 
+/* Throughput of Philox4x32-10 alone on the current device, in calls per second:
+ * a loop of independent calls (8 per thread, 2432 CTAs of 128 threads, 64
+ * iterations), timed with CUDA events after one warm-up launch, best of `reps`.
+ * wide = 0 writes each 32x32->64 multiply as separate high and low halves, 1 as
+ * one 64-bit product.  It measures the integer-multiplier roof that the sweep
+ * kernels are compared against (40 multiply-add slots per call).  Allocates and
+ * frees a small device buffer; runs on `cuda_stream` (cudaStream_t or NULL);
+ * blocking. */
+pa_status pa_calibrate_philox(uint32_t wide, uint32_t reps, void *cuda_stream, double *calls_per_s);
+
 /* Free all device memory of the engine.  Synchronises first. */
 pa_status pa_destroy(pa_engine *e);
 

@@ -62,7 +62,7 @@ WAVG_DTYPE = np.dtype([
 EXPORTS = ["pa_create", "pa_create_ex", "pa_server_create", "pa_admit", "pa_retire", "pa_finished", "pa_run_state",
            "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population", "pa_population_slice",
            "pa_weighted_average_runs", "pa_weighted_average", "pa_weighted_average_noalloc", "pa_launch_count", "pa_set_profiling",
-           "pa_kernel_times", "pa_transfer_bytes", "pa_sweep_shape", "pa_destroy", "pa_status_string"]
+           "pa_kernel_times", "pa_transfer_bytes", "pa_calibrate_philox", "pa_sweep_shape", "pa_destroy", "pa_status_string"]
 KERNEL_KINDS = ["resample", "sweep", "overlap", "measure", "init", "wavg"]
 
 _lock = threading.Lock()
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
         lib.pa_set_profiling.argtypes = [vp, C.c_int]
         lib.pa_kernel_times.argtypes = [vp, P(C.c_double), P(C.c_uint64)]
         lib.pa_transfer_bytes.argtypes = [vp, P(C.c_uint64), P(C.c_uint64)]
+        lib.pa_calibrate_philox.argtypes = [u32, u32, vp, P(C.c_double)]
         lib.pa_destroy.argtypes = [vp]
         lib.pa_status_string.argtypes = [C.c_int]
         lib.pa_status_string.restype = C.c_char_p
@@ -254,6 +255,14 @@ def pa_population_slice(h, run, first, count, N, spins=True):
                                       _p(fam, C.c_uint32), C.byref(R), C.byref(step)), "pa_population_slice")
     n = max(0, min(count, R.value - min(first, R.value)))
     return (s[:n] if spins else None), E[:n], M[:n], fam[:n], R.value, step.value
+
+
+def pa_calibrate_philox(wide=False, reps=5, stream=None):
+    """Philox4x32-10 calls per second on the current device (see pa.h)."""
+    v = C.c_double(0.0)
+    _check(load().pa_calibrate_philox(int(bool(wide)), reps, C.c_void_p(stream) if stream else None, C.byref(v)),
+           "pa_calibrate_philox")
+    return v.value
 
 
 def pa_weighted_average_runs(h, run_idx, M, n_steps, N, kind=0, q=False, wang=False):

@@ -1173,6 +1173,38 @@ pa_status pa_transfer_bytes(const pa_engine *e, uint64_t *h2d, uint64_t *d2h)
     return PA_OK;
 }
 
+pa_status pa_calibrate_philox(uint32_t wide, uint32_t reps, void *cuda_stream, double *calls_per_s)
+{
+    if (!calls_per_s || reps == 0 || reps > 1000) return PA_ERR_INVALID_ARG;
+    const uint32_t blocks = 2432, threads = 128, iters = 64;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    uint32_t *out = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    double best = 0.0;
+    cudaError_t err = cudaMalloc(&out, sizeof(uint32_t) * blocks * threads);
+    if (!err) err = cudaEventCreate(&a);
+    if (!err) err = cudaEventCreate(&b);
+    for (uint32_t r = 0; r <= reps && !err; ++r) {  // launch 0 warms up
+        err = cudaEventRecord(a, s);
+        if (!err) launch_philox_calibration(out, blocks, threads, iters, wide != 0, s);
+        if (!err) err = cudaGetLastError();
+        if (!err) err = cudaEventRecord(b, s);
+        if (!err) err = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (!err) err = cudaEventElapsedTime(&ms, a, b);
+        if (!err && r > 0 && ms > 0.f) {
+            const double v = (double)blocks * threads * iters * 8 / (ms * 1e-3);
+            best = v > best ? v : best;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (out) cudaFree(out);
+    if (err) return cuda_fail(err, "pa_calibrate_philox");
+    *calls_per_s = best;
+    return PA_OK;
+}
+
 pa_status pa_records(pa_engine *e, uint32_t run, pa_step_record *host_out, uint32_t *host_qhist,
                      uint32_t *host_qhist_pair, uint32_t *host_qhist_wang)
 {

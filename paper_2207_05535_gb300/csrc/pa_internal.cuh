@@ -156,5 +156,8 @@ void launch_wavg(const pa_step_record *recs, const unsigned long long *rec_off, 
                  uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w, double *Pq, double *Pqp,
                  cudaStream_t s);
 cudaError_t prepare_kernels();
+// Philox-only calibration loop: blocks x threads threads, iters x 8 calls each.
+void launch_philox_calibration(uint32_t *out, uint32_t blocks, uint32_t threads, uint32_t iters, bool wide,
+                               cudaStream_t s);
 
 }  // namespace pa

@@ -226,3 +226,9 @@ def test_uneven_batch_work_list():
     for k, (L, R) in enumerate([(16, 5), (16, 2000), (16, 37), (32, 3), (32, 500), (8, 1), (8, 1000), (64, 17)]):
         descs.append(W.RunDesc(L, W.FERRO if k % 2 else W.EA_PMJ, R, 2, b, seed=8, run_id=k, disorder_id=k))
     run_case(descs)
+
+
+def test_philox_calibration_reports_a_plausible_rate():
+    split = _lib.pa_calibrate_philox(False, reps=2)
+    wide = _lib.pa_calibrate_philox(True, reps=2)
+    assert 1e10 < split < 1e13 and 1e10 < wide < 1e13
