@@ -38,7 +38,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 #ifndef PA_PACK_MODE
-#define PA_PACK_MODE 2  // packing of the comparison bits: 0 add/add, 1 or/or, 2 or/add (fastest), 3 add/or
+#define PA_PACK_MODE 0  // packing of the comparison bits: 0 add/add (fastest with single 64-bit Philox products), 1 or/or, 2 or/add, 3 add/or
 #endif
 constexpr uint32_t SMEM_BINS = 4096;
 
