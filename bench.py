@@ -87,7 +87,7 @@ def work_units(d, R):
     return R if d.theta == 0xFFFFFFFF else d.theta * d.N * R
 # DRAM bytes per sweep launch from one ncu capture (profiles/sweep_pow2_glass_L16_R5000.md),
 # valid only for the kernel source it was taken on.
-SWEEP_TRAFFIC = {"sweep_source_sha256_16": "9767cc20b7a2f7fc", "workload": "glass_L16_R5000", "bytes_per_launch": 44.930816e6}
+SWEEP_TRAFFIC = {"sweep_source_sha256_16": "905354196dfd27df", "workload": "glass_L16_R5000", "bytes_per_launch": 45.18144e6}
 MULADD_LANES_PER_SM = 64
 
 
