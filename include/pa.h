@@ -153,6 +153,9 @@ pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream,
  *     (both give identical results; the option exists to check that);
  *   PA_CREATE_NO_AUTOTUNE skips timing the bit-sliced kernel's launch shapes on
  *     the first anneal step and uses the default shape.
+ * Without it, the first anneal step of a lattice size times every candidate shape
+ * and keeps the fastest; the choice is shared with every later engine of the
+ * process on the same device, which then skips the timing for that size.
  * Results never depend on the launch shape. */
 enum { PA_CREATE_GENERIC_SWEEP = 1, PA_CREATE_NO_AUTOTUNE = 2 };
 pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, uint32_t flags,

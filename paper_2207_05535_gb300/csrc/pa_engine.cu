@@ -26,8 +26,10 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -88,6 +90,19 @@ struct Tuning {
     bool tuned = false;
     float ms = 0.f;
 };
+
+// Launch shapes chosen by timing are shared by every engine of the process on the
+// same device: a new engine reuses the choice for a lattice size instead of timing
+// the candidates again.  Key: (device, L, bit-sliced kernels allowed).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, uint32_t, int>, uint32_t> g_tuned;
+
+std::tuple<int, uint32_t, int> tune_key(uint32_t L, uint32_t flags)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return std::make_tuple(dev, L, (flags & PA_CREATE_GENERIC_SWEEP) ? 0 : 1);
+}
 
 struct SweepGroup {  // runs of one lattice size among the resident runs
     uint32_t L = 0;
@@ -595,6 +610,14 @@ pa_status rebuild(pa_engine *e)
                 Tuning t;
                 t.candidates = sweep_candidates(L, (e->flags & PA_CREATE_GENERIC_SWEEP) ? 0 : 1);
                 t.tuned = t.candidates.size() < 2 || (e->flags & PA_CREATE_NO_AUTOTUNE);
+                if (!t.tuned) {
+                    std::lock_guard<std::mutex> lock(g_tune_mu);
+                    auto c = g_tuned.find(tune_key(L, e->flags));
+                    if (c != g_tuned.end() && c->second < t.candidates.size()) {
+                        t.pick = c->second;
+                        t.tuned = true;
+                    }
+                }
                 e->tuning[L] = t;
             }
         }
@@ -810,6 +833,8 @@ pa_status enqueue_tuning_tick(pa_engine *e)
         for (auto &x : ev) cudaEventDestroy(x);
         t.tuned = true;
         t.ms = best;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tuned[tune_key(g.L, e->flags)] = t.pick;
     }
     enqueue_dos_sample(e);
     if (!e->q_runs.empty())

@@ -232,3 +232,22 @@ def test_philox_calibration_reports_a_plausible_rate():
     split = _lib.pa_calibrate_philox(False, reps=2)
     wide = _lib.pa_calibrate_philox(True, reps=2)
     assert 1e10 < split < 1e13 and 1e10 < wide < 1e13
+
+
+def test_tuned_shapes_are_reused_by_later_engines():
+    b = W.schedule(1.0, 4)
+    descs = [W.RunDesc(32, W.FERRO, 300, 2, b, seed=9, run_id=r) for r in range(3)]
+    with _lib.Engine(descs) as a:
+        a.step(3, False)
+        shape_a = _lib.pa_sweep_shapes(a.h)
+        rec_a = a.records(0)
+    assert shape_a[0][3] == 1
+    with _lib.Engine(descs) as e:
+        assert _lib.pa_sweep_shapes(e.h) == shape_a  # chosen, without timing, before any step
+        counts = []
+        for _ in range(3):
+            l0 = e.launches
+            e.step(1, False)
+            counts.append(e.launches - l0)
+        assert counts[0] == counts[1] == counts[2]   # no candidate launches on the first step
+        assert np.array_equal(e.records(0), rec_a)
