@@ -157,6 +157,9 @@ struct pa_engine {
     std::vector<uint32_t> q_runs;
     uint32_t init_n = 0, init_tiles = 0;
     std::vector<uint32_t> inf_runs;  // resident theta = PA_THETA_INF runs
+    std::vector<uint32_t> near_runs, multi_runs;  // resident runs by resampling scheme
+    uint64_t near_off = 0, multi_off = 0;
+    uint32_t near_maxcap = 0, multi_maxcap = 0;
     std::vector<uint32_t> wang_runs;  // resident runs with PA_Q_WANG
     uint64_t wang_off = 0, init_wang_off = 0;
     uint32_t wang_maxcap = 0, init_wang_n = 0, init_wang_maxcap = 0;
@@ -318,7 +321,7 @@ pa_status alloc_pools(pa_engine *e, const pa_server_config &c)
     PA_TRY(dalloc(e, &e->d_thr, 2 * c.record_capacity));
     PA_TRY(dalloc(e, &e->d_wtoff, c.record_capacity));
     PA_TRY(dalloc(e, &e->d_wt, c.table_doubles));
-    e->meta_cap = 13ull * e->S + 3ull * 128 + 1024;
+    e->meta_cap = 14ull * e->S + 3ull * 128 + 1024;
     PA_TRY(dalloc(e, &e->d_meta, e->meta_cap));
     PA_CUDA(cudaMemsetAsync(e->P.status, 0, sizeof(uint32_t), e->stream));
     e->P.runs = e->d_runs;
@@ -527,6 +530,8 @@ pa_status admit(pa_engine *e, const pa_run_desc *runs, uint32_t n, uint32_t *slo
         rs.R_new = d.R;
         rs.status = 0;
         rs.lnQ = 0.0;
+        rs.ticket = 0;
+        rs.Emin = 0;
         const uint64_t nq = sizes_of(d).qh;
         cudaError_t err = cudaMemcpyAsync(e->d_runs + s, &e->rd[s], sizeof(RunDev), cudaMemcpyHostToDevice, e->stream);
         if (!err) err = cudaMemcpyAsync(e->P.st + s, &rs, sizeof rs, cudaMemcpyHostToDevice, e->stream);
@@ -543,6 +548,8 @@ pa_status admit(pa_engine *e, const pa_run_desc *runs, uint32_t n, uint32_t *slo
         if (!err && nq) err = cudaMemsetAsync(e->P.qh + g.qh, 0, sizeof(uint32_t) * nq, e->stream);
         if (!err && nq) err = cudaMemsetAsync(e->P.qhp + g.qh, 0, sizeof(uint32_t) * nq, e->stream);
         if (!err && nq) err = cudaMemsetAsync(e->P.qhw + g.qh, 0, sizeof(uint32_t) * nq, e->stream);
+        // the resampling's level histogram starts (and is left by every step) cleared
+        if (!err) err = cudaMemsetAsync(e->P.scratch + g.scr, 0, 8 * scr_table_off(N), e->stream);
         if (!err) err = cudaStreamSynchronize(e->stream);  // host buffers must outlive the copies
         if (err) return cuda_fail(err, "admit upload");
         e->h2d += sizeof(RunDev) + sizeof rs + sizeof(double) * d.n_beta +
@@ -580,6 +587,19 @@ pa_status rebuild(pa_engine *e)
     }
     e->q_off = m.size();
     m.insert(m.end(), e->q_runs.begin(), e->q_runs.end());
+    e->near_runs.clear();
+    e->multi_runs.clear();
+    e->near_maxcap = e->multi_maxcap = 0;
+    for (uint32_t s : e->active) {
+        const bool multi = e->rd[s].resample == PA_MULTINOMIAL;
+        (multi ? e->multi_runs : e->near_runs).push_back(s);
+        uint32_t &cap = multi ? e->multi_maxcap : e->near_maxcap;
+        cap = std::max(cap, e->rd[s].R_cap);
+    }
+    e->near_off = m.size();
+    m.insert(m.end(), e->near_runs.begin(), e->near_runs.end());
+    e->multi_off = m.size();
+    m.insert(m.end(), e->multi_runs.begin(), e->multi_runs.end());
     e->wang_runs.clear();
     e->wang_maxcap = 0;
     for (uint32_t s : e->active)
@@ -662,7 +682,8 @@ pa_status rebuild(pa_engine *e)
         if (e->rd[s].theta == PA_THETA_INF) {
             m.push_back(s);
             ++e->init_inf_n;
-            e->init_inf_maxR = std::max(e->init_inf_maxR, e->rd[s].R);
+            // the beta_0 draw also clears the planes of all R_cap slots
+            e->init_inf_maxR = std::max(e->init_inf_maxR, e->rd[s].R_cap);
         }
     e->init_wang_off = m.size();
     e->init_wang_n = 0;
@@ -756,7 +777,8 @@ pa_status enqueue_pending(pa_engine *e)
         timed_launch(e, PA_K_OVERLAP, [&] {
             launch_wang(e->P, meta(e, e->init_wang_off), e->init_wang_n, e->init_wang_maxcap, 1, e->stream);
         });
-    timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, runs, e->init_n, 1, e->stream); });
+    timed_launch(e, PA_K_MEASURE,
+                 [&] { launch_measure(e->P, runs, e->init_n, e->max_Rcap_active, 1, e->stream); });
     e->pending.clear();
     e->dirty = true;  // the pending list is consumed
     PA_CUDA(cudaGetLastError());
@@ -772,6 +794,24 @@ void enqueue_wang(pa_engine *e)
     });
 }
 
+// Resampling of every resident run: the nearest-integer runs split over
+// several CTAs each (three launches), the multinomial runs one CTA each.
+void enqueue_resample(pa_engine *e)
+{
+    if (!e->near_runs.empty()) {
+        timed_launch(e, PA_K_RESAMPLE, [&] {
+            launch_resample_nearest(e->P, meta(e, e->near_off), (uint32_t)e->near_runs.size(), e->near_maxcap,
+                                    e->stream);
+        });
+        e->launches += RESAMPLE_NEAREST_LAUNCHES - 1;
+    }
+    if (!e->multi_runs.empty())
+        timed_launch(e, PA_K_RESAMPLE, [&] {
+            launch_resample_multinomial(e->P, meta(e, e->multi_off), (uint32_t)e->multi_runs.size(),
+                                        e->multi_maxcap, e->stream);
+        });
+}
+
 // Fresh energies for the theta = PA_THETA_INF runs (in place of their sweeps).
 void enqueue_dos_sample(pa_engine *e)
 {
@@ -785,7 +825,7 @@ void enqueue_tick(pa_engine *e)
 {
     const uint32_t *act = meta(e, e->active_off);
     const uint32_t na = (uint32_t)e->active.size();
-    timed_launch(e, PA_K_RESAMPLE, [&] { launch_resample(e->P, act, na, e->max_Rcap_active, e->stream); });
+    enqueue_resample(e);
     for (auto &g : e->groups) timed_launch(e, PA_K_SWEEP, [&] { launch_group_sweep(e, g, e->tuning[g.L].pick); });
     enqueue_dos_sample(e);
     if (!e->q_runs.empty())
@@ -793,7 +833,7 @@ void enqueue_tick(pa_engine *e)
             launch_overlap(e->P, meta(e, e->q_off), (uint32_t)e->q_runs.size(), e->max_Rcap_active, 0, e->stream);
         });
     enqueue_wang(e);
-    timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, act, na, 0, e->stream); });
+    timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, act, na, e->max_Rcap_active, 0, e->stream); });
 }
 
 // One eager step that first times every candidate sweep shape of the lattice
@@ -804,7 +844,7 @@ pa_status enqueue_tuning_tick(pa_engine *e)
 {
     const uint32_t *act = meta(e, e->active_off);
     const uint32_t na = (uint32_t)e->active.size();
-    timed_launch(e, PA_K_RESAMPLE, [&] { launch_resample(e->P, act, na, e->max_Rcap_active, e->stream); });
+    enqueue_resample(e);
     for (auto &g : e->groups) {
         Tuning &t = e->tuning[g.L];
         if (t.tuned) {
@@ -842,7 +882,7 @@ pa_status enqueue_tuning_tick(pa_engine *e)
             launch_overlap(e->P, meta(e, e->q_off), (uint32_t)e->q_runs.size(), e->max_Rcap_active, 0, e->stream);
         });
     enqueue_wang(e);
-    timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, act, na, 0, e->stream); });
+    timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, act, na, e->max_Rcap_active, 0, e->stream); });
     PA_CUDA(cudaGetLastError());
     return PA_OK;
 }
@@ -1086,8 +1126,11 @@ pa_status pa_reset(pa_engine *e)
         st[k].R_new = x.R;
         st[k].status = 0;
         st[k].lnQ = 0.0;
+        st[k].ticket = 0;
+        st[k].Emin = 0;
         PA_CUDA(cudaMemcpyAsync(e->P.st + s, &st[k], sizeof(RunState), cudaMemcpyHostToDevice, e->stream));
         PA_CUDA(cudaMemsetAsync(e->P.rec + x.rec_off, 0, sizeof(pa_step_record) * x.n_beta, e->stream));
+        PA_CUDA(cudaMemsetAsync(e->P.scratch + x.scr_off, 0, 8 * scr_table_off(x.N), e->stream));
         if (x.overlap) {
             const uint64_t nq = (uint64_t)x.n_beta * (x.N + 1);
             PA_CUDA(cudaMemsetAsync(e->P.qh + x.qh_off, 0, sizeof(uint32_t) * nq, e->stream));

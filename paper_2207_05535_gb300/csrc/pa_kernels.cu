@@ -380,11 +380,20 @@ __global__ void __launch_bounds__(128)
 
 // --------------------------------------------------------------------------
 // Resampling (Sec. II.B steps (ii)-(iii), Eqs. tauBoltz and QBoltz).
+//
+// Both schemes share the normalisation: the population's energies are counted
+// per level n = (E - E_min) / 4 (energies of one population differ by
+// multiples of 4: a spin flip changes E by 0, +-4 or +-8), and
+// S = sum_j exp(-dbeta (E_j - E_min)) is summed level by level in ascending
+// order with the shared table w[n] = exp(-4 n dbeta); Q = exp(-dbeta E_min) S / R.
 // --------------------------------------------------------------------------
 // Populations of up to this many replicas have their energies staged in shared memory.
 constexpr uint32_t RESAMPLE_STAGE_MAX = 24576;  // 96 KB
 
-__global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *runs, uint32_t stage)
+// Multinomial resampling (PA_MULTINOMIAL), one CTA per run: R draws, each
+// picking a level from the cumulative weights and a member of that level
+// uniformly; then the copy numbers' scan and the parent map as below.
+__global__ void __launch_bounds__(512) resample_multinomial_kernel(Pool P, const uint32_t *runs, uint32_t stage)
 {
     extern __shared__ int32_t sE[];  // [stage]
     __shared__ uint32_t sh_hist[SMEM_BINS];
@@ -393,7 +402,7 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *r
     __shared__ double sh_S;
     __shared__ uint32_t sh_carry;
 
-    const uint32_t run = runs ? runs[blockIdx.x] : blockIdx.x;
+    const uint32_t run = runs[blockIdx.x];
     const RunDev rd = P.runs[run];
     RunState *st = &P.st[run];
     if (st->status) return;
@@ -416,14 +425,13 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *r
     const int32_t *Ev = staged ? sE : E;
     const int32_t Emin = block_min(lo, sh_i, INT32_MAX);
     const int32_t Emax = block_max(hi, sh_i, INT32_MIN);
-    const uint32_t nb = (uint32_t)(Emax - Emin) / 4u + 1u;  // energies differ by multiples of 4
+    const uint32_t nb = (uint32_t)(Emax - Emin) / 4u + 1u;
 
     unsigned long long *scr = P.scratch + rd.scr_off;
-    const uint32_t n1 = rd.N + 1;
     uint32_t *g_hist = reinterpret_cast<uint32_t *>(scr);
-    double *cdf = reinterpret_cast<double *>(scr + (n1 + 1) / 2);
-    uint32_t *fill = reinterpret_cast<uint32_t *>(scr + (n1 + 1) / 2 + n1);
-    uint32_t *members = reinterpret_cast<uint32_t *>(scr + (n1 + 1) / 2 + n1 + (n1 + 1) / 2);
+    double *cdf = reinterpret_cast<double *>(scr + scr_table_off(rd.N));
+    uint32_t *fill = reinterpret_cast<uint32_t *>(scr + scr_level_off(rd.N));
+    uint32_t *members = reinterpret_cast<uint32_t *>(scr + scr_tail_off(rd.N));
     uint32_t *h = nb <= SMEM_BINS ? sh_hist : g_hist;
     for (uint32_t n = tid; n < nb; n += nt) h[n] = 0;
     __syncthreads();
@@ -432,13 +440,11 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *r
 
     const double dbeta = P.beta[rd.beta_off + i] - P.beta[rd.beta_off + i - 1];
     const double *w = P.wt + P.wtoff[rd.wt_off + i];  // w[n] = exp(-4 n dbeta_i), shared table
-    const bool multi = rd.resample == PA_MULTINOMIAL;
     if (tid == 0) {
-        // S = sum_j exp(-dbeta (E_j - E_min)), level by level in ascending order
         double S = 0.0;
         for (uint32_t n = 0; n < nb; ++n) {
             S = __dadd_rn(S, __dmul_rn((double)h[n], w[n]));
-            if (multi) cdf[n] = S;
+            cdf[n] = S;
         }
         sh_S = S;
         st->lnQ = (-dbeta) * (double)Emin + log(S) - log((double)Rprev);
@@ -447,98 +453,67 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *r
     const double S = sh_S;
     uint32_t *cnt = P.cnt + rd.rep_off;
 
-    if (multi) {
-        // stable list of replicas by level: members[first(n) + rank]
-        if (tid < 32) {
-            uint32_t acc = 0;
-            for (uint32_t base = 0; base < nb; base += 32) {  // fill[n] = first(n)
-                const uint32_t n = base + tid;
-                const uint32_t v = n < nb ? h[n] : 0u;
-                uint32_t x = v;
-                for (int o = 1; o < 32; o <<= 1) {
-                    uint32_t y = __shfl_up_sync(FULL, x, o);
-                    if ((int)tid >= o) x += y;
-                }
-                if (n < nb) fill[n] = acc + x - v;
-                acc += __shfl_sync(FULL, x, 31);
+    // stable list of replicas by level: members[first(n) + rank]
+    if (tid < 32) {
+        uint32_t acc = 0;
+        for (uint32_t base = 0; base < nb; base += 32) {  // fill[n] = first(n)
+            const uint32_t n = base + tid;
+            const uint32_t v = n < nb ? h[n] : 0u;
+            uint32_t x = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(FULL, x, o);
+                if ((int)tid >= o) x += y;
+            }
+            if (n < nb) fill[n] = acc + x - v;
+            acc += __shfl_sync(FULL, x, 31);
+        }
+        __syncwarp();
+        for (uint32_t base = 0; base < Rprev; base += 32) {
+            const uint32_t j = base + tid;
+            const bool ok = j < Rprev;
+            const uint32_t n = ok ? (uint32_t)(Ev[j] - Emin) >> 2 : 0xffffffffu;
+            const unsigned peers = __match_any_sync(FULL, n);
+            const uint32_t rank = __popc(peers & ((1u << tid) - 1u));
+            uint32_t pos = 0;
+            if (ok) pos = fill[n] + rank;
+            __syncwarp();
+            if (ok) {
+                members[pos] = j;
+                if (rank == 0) fill[n] += __popc(peers);
             }
             __syncwarp();
-            for (uint32_t base = 0; base < Rprev; base += 32) {
-                const uint32_t j = base + tid;
-                const bool ok = j < Rprev;
-                const uint32_t n = ok ? (uint32_t)(Ev[j] - Emin) >> 2 : 0xffffffffu;
-                const unsigned peers = __match_any_sync(FULL, n);
-                const uint32_t rank = __popc(peers & ((1u << tid) - 1u));
-                uint32_t pos = 0;
-                if (ok) pos = fill[n] + rank;
-                __syncwarp();
-                if (ok) {
-                    members[pos] = j;
-                    if (rank == 0) fill[n] += __popc(peers);
-                }
-                __syncwarp();
-            }
         }
-        for (uint32_t j = tid; j < Rprev; j += nt) cnt[j] = 0;
-        __syncthreads();
-        const uint32_t last = nb - 1;
-        for (uint32_t d = tid; d < rd.R; d += nt) {
-            const uint4 o = philox4x32_10(d, 0, i, TAG_MULTINOMIAL << 24, rd.seed, rd.run_id);
-            const unsigned long long u53 = ((unsigned long long)(o.x >> 5) << 26) | (unsigned long long)(o.y >> 6);
-            const double x = __dmul_rn(__dmul_rn((double)u53, 1.0 / 9007199254740992.0), S);
-            uint32_t a = 0, b = nb;  // first n with cdf[n] > x
-            while (a < b) {
-                const uint32_t m = (a + b) >> 1;
-                if (cdf[m] > x)
-                    b = m;
-                else
-                    a = m + 1;
-            }
-            const uint32_t lev = a < nb ? a : last;
-            const uint32_t idx = (uint32_t)(((unsigned long long)o.z * (unsigned long long)h[lev]) >> 32);
-            const uint32_t first = fill[lev] - h[lev];
-            atomicAdd(&cnt[members[first + idx]], 1u);
-        }
-        __syncthreads();
-    } else {
-        // nearest-integer resampling: r_j = floor(tau) + [u 2^-32 < tau - floor(tau)], tau = R w[n_j] / S.
-        // tau depends on the level only: per level the floor (over the histogram, no longer
-        // needed) and the integer threshold ceil(frac 2^32), since u 2^-32 < frac <=> u < frac 2^32
-        // exactly (scaling by 2^32 is exact and u is an integer).
-        unsigned long long *thr = reinterpret_cast<unsigned long long *>(cdf);
-        for (uint32_t n = tid; n < nb; n += nt) {
-            const double tau = __ddiv_rn(__dmul_rn((double)rd.R, w[n]), S);
-            const double fl = floor(tau);
-            h[n] = (uint32_t)fl;
-            thr[n] = (unsigned long long)ceil(__dmul_rn(__dsub_rn(tau, fl), 4294967296.0));
-        }
-        __syncthreads();
     }
+    for (uint32_t j = tid; j < Rprev; j += nt) cnt[j] = 0;
+    __syncthreads();
+    const uint32_t last = nb - 1;
+    for (uint32_t d = tid; d < rd.R; d += nt) {
+        const uint4 o = philox4x32_10(d, 0, i, TAG_MULTINOMIAL << 24, rd.seed, rd.run_id);
+        const unsigned long long u53 = ((unsigned long long)(o.x >> 5) << 26) | (unsigned long long)(o.y >> 6);
+        const double x = __dmul_rn(__dmul_rn((double)u53, 1.0 / 9007199254740992.0), S);
+        uint32_t a = 0, b = nb;  // first n with cdf[n] > x
+        while (a < b) {
+            const uint32_t m = (a + b) >> 1;
+            if (cdf[m] > x)
+                b = m;
+            else
+                a = m + 1;
+        }
+        const uint32_t lev = a < nb ? a : last;
+        const uint32_t idx = (uint32_t)(((unsigned long long)o.z * (unsigned long long)h[lev]) >> 32);
+        const uint32_t first = fill[lev] - h[lev];
+        atomicAdd(&cnt[members[first + idx]], 1u);
+    }
+    __syncthreads();
 
-    // copy numbers (nearest-integer: drawn here), their exclusive scan and the parent map
-    // (contiguous families).  Each warp takes a contiguous chunk of the replicas; one
-    // barrier joins the chunks.
+    // the copy numbers' exclusive scan and the parent map (contiguous families).
+    // Each warp takes a contiguous chunk of the replicas; one barrier joins the chunks.
     uint32_t *parent = P.parent + rd.rep_off;
     const uint32_t lane = tid & 31u, wid = tid >> 5, nwarp = nt >> 5;
     const uint32_t chunk = (Rprev + nwarp - 1) / nwarp;
     const uint32_t c_lo = min(Rprev, wid * chunk), c_hi = min(Rprev, c_lo + chunk);
-    const unsigned long long *thr = reinterpret_cast<const unsigned long long *>(cdf);
     uint32_t wsum = 0;
-    for (uint32_t base = c_lo; base < c_hi; base += 32) {
-        const uint32_t j = base + lane;
-        uint32_t r = 0;
-        if (j < c_hi) {
-            if (multi) {
-                r = cnt[j];
-            } else {
-                const uint32_t n = (uint32_t)(Ev[j] - Emin) >> 2;
-                const uint32_t u = philox4x32_10(j, 0, i, TAG_RESAMPLE << 24, rd.seed, rd.run_id).x;
-                r = h[n] + ((unsigned long long)u < thr[n] ? 1u : 0u);
-                cnt[j] = r;
-            }
-        }
-        wsum += r;
-    }
+    for (uint32_t j = c_lo + lane; j < c_hi; j += 32) wsum += cnt[j];
     wsum = warp_sum(wsum);
     if (lane == 0) sh_u[wid] = wsum;
     __syncthreads();
@@ -569,6 +544,218 @@ __global__ void __launch_bounds__(512) resample_kernel(Pool P, const uint32_t *r
     }
     if (tid == 0) {
         const uint32_t Rn = sh_carry;
+        st->R_new = Rn;
+        if (Rn == 0)
+            set_status(P, run, PA_ERR_EXTINCT);
+        else if (Rn > rd.R_cap)
+            set_status(P, run, PA_ERR_CAPACITY);
+        if (Rn == 0 || Rn > rd.R_cap) P.rec[rd.rec_off + i].status = st->status;
+    }
+}
+
+// Nearest-integer resampling (PA_NEAREST): r_j = floor(tau) + [u 2^-32 < tau - floor(tau)],
+// tau = R w[n_j] / S.  tau depends on the level only, so per level the floor and
+// the integer threshold ceil(frac 2^32) are tabulated once (u 2^-32 < frac <=>
+// u < frac 2^32 exactly: scaling by 2^32 is exact and u is an integer).
+//
+// A run's population is split over nc = run_ctas(R_cap) CTAs (CTA c of the
+// run: blockIdx.y = c, replicas [c ceil(R/nc), (c+1) ceil(R/nc))), in three
+// launches:
+//   resample_levels_kernel   each CTA adds its chunk's level counts to the run's
+//                            histogram; the last CTA to finish (a ticket in the
+//                            run state) finds E_min, sums S and Q, tabulates the
+//                            floors and thresholds and clears the histogram
+//   resample_counts_kernel   r_j of every replica and each CTA's total
+//   resample_parents_kernel  offsets (earlier CTAs' totals plus a scan inside
+//                            the CTA) and the parent map
+// The histogram is counted from the base b = -2N + ((E_0 + 2N) mod 4): every
+// energy of the population is congruent to E_0 mod 4 and |E| <= 2N, so
+// (E - b) / 4 lies in 0..N.
+constexpr uint32_t RESAMPLE_THREADS = 512;
+
+struct RunChunk {
+    uint32_t lo, hi;  // this CTA's replicas
+};
+
+__device__ __forceinline__ RunChunk cta_chunk(uint32_t R, uint32_t nc, uint32_t c)
+{
+    const uint32_t chunk = (R + nc - 1) / nc;
+    const uint32_t lo = min(R, c * chunk);
+    return {lo, min(R, lo + chunk)};
+}
+
+__global__ void __launch_bounds__(RESAMPLE_THREADS) resample_levels_kernel(Pool P, const uint32_t *runs)
+{
+    __shared__ uint32_t sh_hist[SMEM_BINS];
+    __shared__ uint32_t sh_r[32];
+    __shared__ double sh_S;
+    __shared__ uint32_t sh_last;
+    const uint32_t run = runs[blockIdx.x];
+    const RunDev rd = P.runs[run];
+    RunState *st = &P.st[run];
+    if (st->status) return;
+    const uint32_t i = st->step + 1;
+    if (i >= rd.n_beta) return;
+    const uint32_t nc = min(gridDim.y, run_ctas(rd.R_cap));
+    if (blockIdx.y >= nc) return;
+    const uint32_t Rprev = st->R_cur;
+    const int32_t *E = P.E[(i - 1) & 1] + rd.rep_off;
+    const RunChunk ch = cta_chunk(Rprev, nc, blockIdx.y);
+    const uint32_t tid = threadIdx.x, nt = blockDim.x, n1 = rd.N + 1;
+    const int32_t twoN = 2 * (int32_t)rd.N;
+    const int32_t base = -twoN + ((E[0] + twoN) & 3);
+
+    unsigned long long *scr = P.scratch + rd.scr_off;
+    uint32_t *g_hist = reinterpret_cast<uint32_t *>(scr);
+    if (n1 <= SMEM_BINS) {  // this CTA's counts in shared memory, then the non-zero bins added to the run's
+        for (uint32_t n = tid; n < n1; n += nt) sh_hist[n] = 0;
+        __syncthreads();
+        for (uint32_t j = ch.lo + tid; j < ch.hi; j += nt) atomicAdd(&sh_hist[(uint32_t)(E[j] - base) >> 2], 1u);
+        __syncthreads();
+        for (uint32_t n = tid; n < n1; n += nt)
+            if (sh_hist[n]) atomicAdd(&g_hist[n], sh_hist[n]);
+    } else {
+        for (uint32_t j = ch.lo + tid; j < ch.hi; j += nt) atomicAdd(&g_hist[(uint32_t)(E[j] - base) >> 2], 1u);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sh_last = atomicAdd(&st->ticket, 1u) == nc - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+
+    // the last CTA: the occupied level range, S and Q, the per-level tables
+    uint32_t lo = 0xffffffffu, hi = 0;
+    for (uint32_t n = tid; n < n1; n += nt)
+        if (__ldcg(&g_hist[n])) {
+            lo = n < lo ? n : lo;
+            hi = n > hi ? n : hi;
+        }
+    lo = block_min(lo, sh_r, 0xffffffffu);
+    hi = block_max(hi, sh_r, 0u);
+    const uint32_t nb = hi - lo + 1;
+    const int32_t Emin = base + 4 * (int32_t)lo;
+    const double dbeta = P.beta[rd.beta_off + i] - P.beta[rd.beta_off + i - 1];
+    const double *w = P.wt + P.wtoff[rd.wt_off + i];  // w[n] = exp(-4 n dbeta_i), shared table
+    if (tid == 0) {
+        double S = 0.0;
+        for (uint32_t n = 0; n < nb; ++n) S = __dadd_rn(S, __dmul_rn((double)__ldcg(&g_hist[lo + n]), w[n]));
+        sh_S = S;
+        st->lnQ = (-dbeta) * (double)Emin + log(S) - log((double)Rprev);
+        st->Emin = Emin;
+    }
+    __syncthreads();
+    const double S = sh_S;
+    unsigned long long *thr = scr + scr_table_off(rd.N);
+    uint32_t *flo = reinterpret_cast<uint32_t *>(scr + scr_level_off(rd.N));
+    for (uint32_t n = tid; n < nb; n += nt) {
+        const double tau = __ddiv_rn(__dmul_rn((double)rd.R, w[n]), S);
+        const double fl = floor(tau);
+        flo[n] = (uint32_t)fl;
+        thr[n] = (unsigned long long)ceil(__dmul_rn(__dsub_rn(tau, fl), 4294967296.0));
+    }
+    for (uint32_t n = tid; n < n1; n += nt) g_hist[n] = 0u;  // ready for the next step
+    if (tid == 0) st->ticket = 0u;
+}
+
+__global__ void __launch_bounds__(RESAMPLE_THREADS) resample_counts_kernel(Pool P, const uint32_t *runs)
+{
+    __shared__ uint32_t sh_r[32];
+    const uint32_t run = runs[blockIdx.x];
+    const RunDev rd = P.runs[run];
+    const RunState *st = &P.st[run];
+    if (st->status) return;
+    const uint32_t i = st->step + 1;
+    if (i >= rd.n_beta) return;
+    const uint32_t nc = min(gridDim.y, run_ctas(rd.R_cap));
+    if (blockIdx.y >= nc) return;
+    const RunChunk ch = cta_chunk(st->R_cur, nc, blockIdx.y);
+    const int32_t *E = P.E[(i - 1) & 1] + rd.rep_off;
+    const int32_t Emin = st->Emin;
+    const unsigned long long *scr = P.scratch + rd.scr_off;
+    const unsigned long long *thr = scr + scr_table_off(rd.N);
+    const uint32_t *flo = reinterpret_cast<const uint32_t *>(scr + scr_level_off(rd.N));
+    uint32_t *cnt = P.cnt + rd.rep_off;
+    uint32_t sum = 0;
+    for (uint32_t j = ch.lo + threadIdx.x; j < ch.hi; j += blockDim.x) {
+        const uint32_t n = (uint32_t)(E[j] - Emin) >> 2;
+        const uint32_t u = philox4x32_10(j, 0, i, TAG_RESAMPLE << 24, rd.seed, rd.run_id).x;
+        const uint32_t r = flo[n] + ((unsigned long long)u < thr[n] ? 1u : 0u);
+        cnt[j] = r;
+        sum += r;
+    }
+    sum = block_sum(sum, sh_r);
+    if (threadIdx.x == 0) reinterpret_cast<uint32_t *>(P.scratch + rd.scr_off + scr_tail_off(rd.N))[blockIdx.y] = sum;
+}
+
+__global__ void __launch_bounds__(RESAMPLE_THREADS) resample_parents_kernel(Pool P, const uint32_t *runs)
+{
+    __shared__ uint32_t sh_u[RESAMPLE_THREADS / 32];
+    __shared__ uint32_t sh_off, sh_total;
+    const uint32_t run = runs[blockIdx.x];
+    const RunDev rd = P.runs[run];
+    RunState *st = &P.st[run];
+    if (st->status) return;
+    const uint32_t i = st->step + 1;
+    if (i >= rd.n_beta) return;
+    const uint32_t nc = min(gridDim.y, run_ctas(rd.R_cap));
+    if (blockIdx.y >= nc) return;
+    const uint32_t Rprev = st->R_cur;
+    const RunChunk ch = cta_chunk(Rprev, nc, blockIdx.y);
+    const uint32_t *cta_tot = reinterpret_cast<const uint32_t *>(P.scratch + rd.scr_off + scr_tail_off(rd.N));
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5, nwarp = blockDim.x >> 5;
+    const uint32_t *cnt = P.cnt + rd.rep_off;
+    uint32_t *parent = P.parent + rd.rep_off;
+
+    // warp 0: the earlier CTAs' totals (this CTA's offset) and, in CTA 0, the new size
+    if (wid == 0) {
+        uint32_t before = 0, all = 0;
+        for (uint32_t k = lane; k < nc; k += 32) {
+            const uint32_t v = cta_tot[k];
+            before += k < blockIdx.y ? v : 0u;
+            all += v;
+        }
+        before = warp_sum(before);
+        all = warp_sum(all);
+        if (lane == 0) {
+            sh_off = before;
+            sh_total = all;
+        }
+    }
+    // each warp takes a contiguous piece of the CTA's chunk
+    const uint32_t wchunk = (ch.hi - ch.lo + nwarp - 1) / nwarp;
+    const uint32_t w_lo = min(ch.hi, ch.lo + wid * wchunk), w_hi = min(ch.hi, w_lo + wchunk);
+    uint32_t wsum = 0;
+    for (uint32_t j = w_lo + lane; j < w_hi; j += 32) wsum += cnt[j];
+    wsum = warp_sum(wsum);
+    if (lane == 0) sh_u[wid] = wsum;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t acc = sh_off;
+        for (uint32_t k = 0; k < nwarp; ++k) {
+            const uint32_t v = sh_u[k];
+            sh_u[k] = acc;
+            acc += v;
+        }
+    }
+    __syncthreads();
+    uint32_t carry = sh_u[wid];
+    for (uint32_t b0 = w_lo; b0 < w_hi; b0 += 32) {
+        const uint32_t j = b0 + lane;
+        const uint32_t r = j < w_hi ? cnt[j] : 0u;
+        uint32_t x = r;  // inclusive scan over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        const uint32_t o = carry + x - r;
+        for (uint32_t c = 0; c < r; ++c)
+            if (o + c < rd.R_cap) parent[o + c] = j;
+        carry += __shfl_sync(FULL, x, 31);
+    }
+    if (blockIdx.y == 0 && tid == 0) {
+        const uint32_t Rn = sh_total;
         st->R_new = Rn;
         if (Rn == 0)
             set_status(P, run, PA_ERR_EXTINCT);
@@ -1458,28 +1645,64 @@ __global__ void __launch_bounds__(1024) wang_kernel(Pool P, const uint32_t *runs
 // exact energy distribution.  One thread per child: a 53-bit uniform from
 // Philox (words 0, 1), x = u * C[2N], the first level u with x < C[u] by
 // binary search over the host-built cumulative weights (the last positive
-// level if x rounds up to C[2N]); E = 2u - 2N, M = 0, family from the parent,
-// spin planes cleared (configurations are not represented).
+// level if x rounds up to C[2N]); E = 2u - 2N, M = 0, family from the parent.
+// Configurations are not represented: the spin planes of both buffers are
+// cleared once, when the population is drawn at beta_0, and nothing writes
+// them afterwards.
+//
+// GB300 issues double-precision instructions at a small fraction of the
+// integer rate, so the draw uses one: u 2^-53 is assembled exactly from its
+// IEEE-754 fields, and since C and x are non-negative and never NaN, x < C[u]
+// is decided on the bit patterns as unsigned integers (the order of
+// non-negative doubles is the order of their encodings).
 // --------------------------------------------------------------------------
 constexpr uint32_t DOS_SMEM_LEVELS = 4096;  // tables of L <= 44 are staged in shared memory
+constexpr uint32_t DOS_THREADS = 256, DOS_PER_THREAD = 4;  // replicas k0 + r DOS_THREADS + threadIdx.x
 
-// First level u with x < C[u], x = u53 2^-53 C[U] (binary search); the last
-// positive level, stored in C[U + 1], if x rounds up to C[U].
-__device__ __forceinline__ uint32_t dos_level(const double *C, uint32_t U, unsigned long long u53)
+// u 2^-53 as a double, exactly, for 0 <= u < 2^53: the leading bit p of u sets
+// the exponent p - 53, the 52 bits below it the fraction.
+__device__ __forceinline__ double unit_from_u53(unsigned long long u)
 {
-    const double x = __dmul_rn(__dmul_rn((double)u53, 1.0 / 9007199254740992.0), C[U]);
-    uint32_t lo = 0, hi = U + 1;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (x < C[mid]) hi = mid;
-        else lo = mid + 1;
-    }
-    return lo <= U ? lo : (uint32_t)C[U + 1];
+    if (u == 0) return 0.0;
+    const uint32_t p = 63u - (uint32_t)__clzll((long long)u);
+    const unsigned long long frac = (u << (52u - p)) & ((1ull << 52) - 1ull);
+    return __longlong_as_double((long long)(((unsigned long long)(p + 1023u - 53u) << 52) | frac));
 }
 
-__global__ void __launch_bounds__(256) dos_sample_kernel(Pool P, const uint32_t *runs, int init)
+// The DOS_PER_THREAD draws of one thread: the first level u with x < C[u],
+// x = u53 2^-53 C[U], found by a branch-free binary search on the encodings Cb
+// of C whose ceil(log2(U + 1)) steps are the same for every replica, so the
+// searches interleave; the last positive level (stored in C[U + 1]) if x
+// rounds up to C[U].  The level is unique because C is non-decreasing.
+__device__ __forceinline__ void dos_levels(const unsigned long long *Cb, uint32_t U, const unsigned long long *u53,
+                                           uint32_t *lev)
 {
-    __shared__ double sC[DOS_SMEM_LEVELS];
+    const double top = __longlong_as_double((long long)Cb[U]);
+    unsigned long long xb[DOS_PER_THREAD];
+    uint32_t base[DOS_PER_THREAD];
+#pragma unroll
+    for (uint32_t r = 0; r < DOS_PER_THREAD; ++r) {
+        xb[r] = (unsigned long long)__double_as_longlong(__dmul_rn(unit_from_u53(u53[r]), top));
+        base[r] = 0;
+    }
+    // invariant: the answer lies in [base, base + len], indices read stay <= U
+    for (uint32_t len = U + 1; len > 1;) {
+        const uint32_t half = len >> 1;
+#pragma unroll
+        for (uint32_t r = 0; r < DOS_PER_THREAD; ++r) base[r] += Cb[base[r] + half] <= xb[r] ? half : 0u;
+        len -= half;
+    }
+    const uint32_t last = (uint32_t)__longlong_as_double((long long)Cb[U + 1]);
+#pragma unroll
+    for (uint32_t r = 0; r < DOS_PER_THREAD; ++r) {
+        const uint32_t u = base[r] + (Cb[base[r]] <= xb[r] ? 1u : 0u);
+        lev[r] = u <= U ? u : last;
+    }
+}
+
+__global__ void __launch_bounds__(DOS_THREADS) dos_sample_kernel(Pool P, const uint32_t *runs, int init)
+{
+    __shared__ unsigned long long sC[DOS_SMEM_LEVELS];
     const uint32_t run = runs[blockIdx.y];
     const RunDev rd = P.runs[run];
     const RunState *st = &P.st[run];
@@ -1487,25 +1710,56 @@ __global__ void __launch_bounds__(256) dos_sample_kernel(Pool P, const uint32_t 
     const uint32_t i = init ? 0u : st->step + 1;
     if (i >= rd.n_beta) return;
     const uint32_t R = init ? rd.R : st->R_new;
-    if (blockIdx.x * blockDim.x >= R) return;  // uniform over the CTA
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t span = DOS_THREADS * DOS_PER_THREAD;
+    const uint32_t k0 = blockIdx.x * span;
+    if (k0 >= (init ? rd.R_cap : R)) return;  // uniform over the CTA
+    if (init) {  // clear both buffers' planes of replicas k0 .. k0 + span - 1 (coalesced)
+        const uint32_t k1 = min(rd.R_cap, k0 + span);
+        const uint64_t w0 = rd.spin_off + (uint64_t)k0 * rd.wstride, nw = (uint64_t)(k1 - k0) * rd.wstride;
+        for (uint64_t w = threadIdx.x; w < nw; w += blockDim.x) {
+            P.spins[0][w0 + w] = 0u;
+            P.spins[1][w0 + w] = 0u;
+        }
+        if (k0 >= R) return;
+    }
     const uint32_t U = 2 * rd.N, b = i & 1u;
-    const double *C = P.wt + rd.dos_off + (uint64_t)i * (U + 2);
+    const unsigned long long *C =
+        reinterpret_cast<const unsigned long long *>(P.wt + rd.dos_off + (uint64_t)i * (U + 2));
     const bool staged = U + 2 <= DOS_SMEM_LEVELS;
     if (staged) {
         for (uint32_t u = threadIdx.x; u < U + 2; u += blockDim.x) sC[u] = C[u];
         __syncthreads();
     }
-    if (k >= R) return;
-    const uint4 o = philox4x32_10(k, 0u, i, TAG_DOS << 24, rd.seed, rd.run_id);
-    const unsigned long long u53 = ((unsigned long long)(o.x >> 5) << 26) | (unsigned long long)(o.y >> 6);
-    const uint32_t lev = staged ? dos_level(sC, U, u53) : dos_level(C, U, u53);
-    const uint64_t slot = rd.rep_off + k;
-    P.E[b][slot] = (int32_t)(2 * (int64_t)lev - 2 * (int64_t)rd.N);
-    P.M[b][slot] = 0;
-    P.fam[b][slot] = init ? k : P.fam[b ^ 1u][rd.rep_off + P.parent[slot]];
-    uint32_t *dst = P.spins[b] + rd.spin_off + (uint64_t)k * rd.wstride;
-    for (uint32_t w = 0; w < rd.wstride; ++w) dst[w] = 0u;
+    // parents first (their families are gathered after the draws), then the draws
+    uint32_t par[DOS_PER_THREAD];
+    unsigned long long u53[DOS_PER_THREAD];
+#pragma unroll
+    for (uint32_t r = 0; r < DOS_PER_THREAD; ++r) {
+        const uint32_t k = k0 + r * DOS_THREADS + threadIdx.x;
+        par[r] = !init && k < R ? P.parent[rd.rep_off + k] : 0u;
+    }
+#pragma unroll
+    for (uint32_t r = 0; r < DOS_PER_THREAD; ++r) {
+        const uint4 o = philox4x32_10(k0 + r * DOS_THREADS + threadIdx.x, 0u, i, TAG_DOS << 24, rd.seed, rd.run_id);
+        u53[r] = ((unsigned long long)(o.x >> 5) << 26) | (unsigned long long)(o.y >> 6);
+    }
+    uint32_t f[DOS_PER_THREAD];
+#pragma unroll
+    for (uint32_t r = 0; r < DOS_PER_THREAD; ++r) {
+        const uint32_t k = k0 + r * DOS_THREADS + threadIdx.x;
+        f[r] = init ? k : (k < R ? P.fam[b ^ 1u][rd.rep_off + par[r]] : 0u);
+    }
+    uint32_t lev[DOS_PER_THREAD];
+    dos_levels(staged ? sC : C, U, u53, lev);
+#pragma unroll
+    for (uint32_t r = 0; r < DOS_PER_THREAD; ++r) {
+        const uint32_t k = k0 + r * DOS_THREADS + threadIdx.x;
+        if (k >= R) continue;
+        const uint64_t slot = rd.rep_off + k;
+        P.E[b][slot] = (int32_t)(2 * (int64_t)lev[r] - 2 * (int64_t)rd.N);
+        P.M[b][slot] = 0;
+        P.fam[b][slot] = f[r];
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -1534,13 +1788,17 @@ __device__ __forceinline__ void add128_square(I128 &a, unsigned long long v)
     add128(a, v * v, (long long)__umul64hi(v, v));
 }
 
-// Per-warp partial results of the measurement: moment sums and the family
-// run statistics of one contiguous chunk of replicas.
+// Partial results of the measurement over one contiguous chunk of replicas
+// (a warp's, a CTA's): moment sums and the family run statistics.  lead: the
+// replicas at the chunk's start that continue the family open before it;
+// trail: the length of the chunk's last run (counted from the chunk's start
+// when the chunk has no family start).
 struct MeasurePart {
     long long sE, sE2, sAM, sM2, c2;
     I128 sE3, sE4, sAM3, sM4;
-    uint32_t nfam, cmax, lead, trail, len;
+    uint32_t nfam, cmax, lead, trail, len, pad;
 };
+static_assert(sizeof(MeasurePart) == MEASURE_PART_WORDS * 8, "MeasurePart fills its scratch words");
 
 __device__ __forceinline__ I128 warp_sum128(I128 v)
 {
@@ -1553,32 +1811,93 @@ __device__ __forceinline__ I128 warp_sum128(I128 v)
     return v;
 }
 
-// Each warp takes a contiguous chunk of the R_i replicas.  Families are
-// contiguous runs of equal ancestor id; inside a chunk a warp-wide inclusive
-// max-scan of run starts gives every replica its run start (the chunk's first
-// replica is treated as a start), and thread 0 then joins the runs that cross
-// chunk boundaries: pieces a and b of one family counted as a^2 + b^2 gain 2ab.
+// Appends chunk q (the next one in replica order) to t.  A family open at the
+// end of t that continues into q was counted as pieces a and b, a^2 + b^2: the
+// join adds 2ab.
+__device__ __forceinline__ void join_part(MeasurePart &t, const MeasurePart &q)
+{
+    if (q.len == 0) return;
+    if (t.len == 0) {
+        t = q;
+        return;
+    }
+    t.sE += q.sE;
+    t.sE2 += q.sE2;
+    t.sAM += q.sAM;
+    t.sM2 += q.sM2;
+    t.c2 += q.c2;
+    add128(t.sE3, q.sE3.lo, q.sE3.hi);
+    add128(t.sE4, q.sE4.lo, q.sE4.hi);
+    add128(t.sAM3, q.sAM3.lo, q.sAM3.hi);
+    add128(t.sM4, q.sM4.lo, q.sM4.hi);
+    t.nfam += q.nfam;
+    t.cmax = q.cmax > t.cmax ? q.cmax : t.cmax;
+    if (q.lead > 0) {
+        t.c2 += 2 * (long long)t.trail * q.lead;
+        const uint32_t merged = t.trail + q.lead;
+        t.cmax = merged > t.cmax ? merged : t.cmax;
+        if (t.lead == t.len) t.lead += q.lead;
+        t.trail = q.lead == q.len ? merged : q.trail;
+    } else {
+        t.trail = q.trail;
+    }
+    t.len += q.len;
+}
+
+__device__ __forceinline__ void store_part_cg(MeasurePart *dst, const MeasurePart &v)
+{
+    const unsigned long long *a = reinterpret_cast<const unsigned long long *>(&v);
+    unsigned long long *b = reinterpret_cast<unsigned long long *>(dst);
+#pragma unroll
+    for (int k = 0; k < (int)MEASURE_PART_WORDS; ++k) __stcg(b + k, a[k]);
+}
+
+__device__ __forceinline__ MeasurePart load_part_cg(const MeasurePart *src)
+{
+    MeasurePart v;
+    unsigned long long *a = reinterpret_cast<unsigned long long *>(&v);
+    const unsigned long long *b = reinterpret_cast<const unsigned long long *>(src);
+#pragma unroll
+    for (int k = 0; k < (int)MEASURE_PART_WORDS; ++k) a[k] = __ldcg(b + k);
+    return v;
+}
+
+// A run's R_i replicas are split over nc = run_ctas(R_cap) CTAs (blockIdx.y)
+// and each CTA's chunk over its warps.  Families are contiguous runs of equal
+// ancestor id; inside a warp's chunk a warp-wide inclusive max-scan of run
+// starts gives every replica its run start (the chunk's first replica is
+// treated as a start), and the chunks are then joined in order (join_part):
+// a CTA's warps by its thread 0, the CTAs by the last CTA of the run to
+// finish (a ticket in the run state), which writes the step record.
 #ifndef PA_MEASURE_THREADS
 #define PA_MEASURE_THREADS 512
 #endif
+#ifndef PA_MEASURE_MIN_BLOCKS
+#define PA_MEASURE_MIN_BLOCKS 2  // two CTAs per SM: at most 64 registers
+#endif
 
-__global__ void __launch_bounds__(PA_MEASURE_THREADS) measure_kernel(Pool P, const uint32_t *runs, int init)
+__global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) measure_kernel(Pool P, const uint32_t *runs, int init)
 {
-    __shared__ MeasurePart part[PA_MEASURE_THREADS / 32];
-    const uint32_t run = runs ? runs[blockIdx.x] : blockIdx.x;
+    __shared__ MeasurePart part[32];
+    __shared__ uint32_t sh_last;
+    const uint32_t run = runs[blockIdx.x];
     const RunDev rd = P.runs[run];
     RunState *st = &P.st[run];
     if (st->status) return;
     const uint32_t i = init ? 0u : st->step + 1;
     if (i >= rd.n_beta) return;
+    const uint32_t nc = min(gridDim.y, run_ctas(rd.R_cap));
+    if (blockIdx.y >= nc) return;
     const uint32_t R = init ? rd.R : st->R_new;
     const uint32_t b = i & 1u;
     const int32_t *E = P.E[b] + rd.rep_off;
     const int32_t *M = P.M[b] + rd.rep_off;
     const uint32_t *fam = P.fam[b] + rd.rep_off;
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t chunk = (R + nw - 1) / nw;
-    const uint32_t lo = min(R, wid * chunk), hi = min(R, lo + chunk);
+    const uint32_t cchunk = (R + nc - 1) / nc;
+    const uint32_t c_lo = min(R, blockIdx.y * cchunk), c_hi = min(R, c_lo + cchunk);
+    const uint32_t chunk = (c_hi - c_lo + nw - 1) / nw;
+    const uint32_t lo = min(c_hi, c_lo + wid * chunk), hi = min(c_hi, lo + chunk);
 
     long long sE = 0, sE2 = 0, sAM = 0, sM2 = 0, c2 = 0;
     I128 sE3 = {0ull, 0ll}, sE4 = {0ull, 0ll}, sAM3 = {0ull, 0ll}, sM4 = {0ull, 0ll};
@@ -1651,35 +1970,37 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS) measure_kernel(Pool P, con
     w.lead = warp_min(first) - lo;  // replicas continuing the previous chunk's family
     w.trail = hi - open;            // length of the chunk's last run
     w.len = hi - lo;
+    w.pad = 0;
     if (lane == 0) part[wid] = w;
     __syncthreads();
-    if (threadIdx.x != 0) return;
+    if (wid != 0) return;
 
-    MeasurePart t = part[0];
-    uint32_t run_open = t.trail;
-    for (uint32_t k = 1; k < nw; ++k) {
-        const MeasurePart &q = part[k];
-        if (q.len == 0) continue;
-        t.sE += q.sE;
-        t.sE2 += q.sE2;
-        t.sAM += q.sAM;
-        t.sM2 += q.sM2;
-        t.c2 += q.c2;
-        add128(t.sE3, q.sE3.lo, q.sE3.hi);
-        add128(t.sE4, q.sE4.lo, q.sE4.hi);
-        add128(t.sAM3, q.sAM3.lo, q.sAM3.hi);
-        add128(t.sM4, q.sM4.lo, q.sM4.hi);
-        t.nfam += q.nfam;
-        t.cmax = q.cmax > t.cmax ? q.cmax : t.cmax;
-        if (q.lead > 0) {  // the family open at the end of the previous chunks continues
-            t.c2 += 2 * (long long)run_open * q.lead;
-            const uint32_t merged = run_open + q.lead;
-            t.cmax = merged > t.cmax ? merged : t.cmax;
-            run_open = q.lead == q.len ? merged : q.trail;
-        } else {
-            run_open = q.trail;
-        }
+    MeasurePart t;
+    if (lane == 0) {
+        t = part[0];
+        for (uint32_t k = 1; k < nw; ++k) join_part(t, part[k]);
     }
+    if (nc > 1) {  // the CTAs' parts are joined, in order, by the last CTA of the run to finish
+        MeasurePart *gp = reinterpret_cast<MeasurePart *>(P.scratch + rd.scr_off + scr_tail_off(rd.N));
+        if (lane == 0) {
+            store_part_cg(gp + blockIdx.y, t);
+            __threadfence();
+            sh_last = atomicAdd(&st->ticket, 1u) == nc - 1 ? 1u : 0u;
+        }
+        __syncwarp();
+        if (!sh_last) return;
+        __threadfence();
+        t.len = 0;
+        for (uint32_t k0 = 0; k0 < nc; k0 += 32) {  // 32 parts at a time, loaded by the warp's lanes
+            if (k0 + lane < nc) part[lane] = load_part_cg(gp + k0 + lane);
+            __syncwarp();
+            if (lane == 0)
+                for (uint32_t k = 0; k < 32 && k0 + k < nc; ++k) join_part(t, part[k]);
+            __syncwarp();
+        }
+        if (lane == 0) st->ticket = 0u;
+    }
+    if (lane != 0) return;
 
     pa_step_record *rec = P.rec + rd.rec_off + i;
     const double lnQ = init ? 0.0 : st->lnQ;
@@ -1949,7 +2270,7 @@ cudaError_t prepare_kernels()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sweep_kernel<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(resample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(resample_multinomial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  RESAMPLE_STAGE_MAX * sizeof(int32_t));
     if (e == cudaSuccess)  // Wang pairing with R_cap up to 8192: 144 KB
         e = cudaFuncSetAttribute(wang_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1971,13 +2292,25 @@ void launch_dos_sample(const Pool &P, const uint32_t *runs, uint32_t n_runs, uin
                        cudaStream_t s)
 {
     if (n_runs == 0 || max_R == 0) return;
-    dos_sample_kernel<<<dim3((max_R + 255) / 256, n_runs), 256, 0, s>>>(P, runs, init);
+    const uint32_t span = DOS_THREADS * DOS_PER_THREAD;
+    dos_sample_kernel<<<dim3((max_R + span - 1) / span, n_runs), DOS_THREADS, 0, s>>>(P, runs, init);
 }
 
-void launch_resample(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap, cudaStream_t s)
+void launch_resample_multinomial(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap,
+                                 cudaStream_t s)
 {
+    if (n_runs == 0) return;
     const uint32_t stage = max_Rcap < RESAMPLE_STAGE_MAX ? max_Rcap : RESAMPLE_STAGE_MAX;
-    resample_kernel<<<n_runs, 512, stage * sizeof(int32_t), s>>>(P, runs, stage);
+    resample_multinomial_kernel<<<n_runs, 512, stage * sizeof(int32_t), s>>>(P, runs, stage);
+}
+
+void launch_resample_nearest(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap, cudaStream_t s)
+{
+    if (n_runs == 0) return;
+    const dim3 grid(n_runs, run_ctas(max_Rcap));
+    resample_levels_kernel<<<grid, RESAMPLE_THREADS, 0, s>>>(P, runs);
+    resample_counts_kernel<<<grid, RESAMPLE_THREADS, 0, s>>>(P, runs);
+    resample_parents_kernel<<<grid, RESAMPLE_THREADS, 0, s>>>(P, runs);
 }
 
 // Launch shapes of the bit-sliced kernel: WPT plane words per thread and
@@ -2088,9 +2421,11 @@ void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, ui
     overlap_kernel<<<grid, 256, 0, s>>>(P, q_runs, init);
 }
 
-void launch_measure(const Pool &P, const uint32_t *runs, uint32_t n_runs, int init, cudaStream_t s)
+void launch_measure(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap, int init,
+                    cudaStream_t s)
 {
-    measure_kernel<<<n_runs, PA_MEASURE_THREADS, 0, s>>>(P, runs, init);
+    if (n_runs == 0) return;
+    measure_kernel<<<dim3(n_runs, run_ctas(max_Rcap)), PA_MEASURE_THREADS, 0, s>>>(P, runs, init);
 }
 
 void launch_philox_calibration(uint32_t *out, uint32_t blocks, uint32_t threads, uint32_t iters, bool wide,

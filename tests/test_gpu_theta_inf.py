@@ -65,6 +65,19 @@ def test_theta_inf_runs_bit_exact(L, model, R, resample):
             check(eng, descs, ora, k)
 
 
+@pytest.mark.parametrize("R,resample", [(9000, 0), (20000, 0), (6000, 1)])
+def test_theta_inf_populations_over_several_ctas(R, resample):
+    """Populations spanning several CTAs of the draw, resampling and
+    measurement kernels (4096 replicas per CTA), L = 8 ferromagnet."""
+    betas = W.schedule(0.6, 13)
+    descs = [_inf(8, 0, R, betas, r, resample=resample) for r in range(2)]
+    ora = oracle_runs(descs)
+    with _lib.Engine(descs) as eng:
+        eng.run_to_end()
+        for k in range(len(descs)):
+            check(eng, descs, ora, k)
+
+
 def test_theta_inf_mixed_with_sweeping_runs():
     b8 = W.schedule(0.5, 7)
     descs = [_inf(8, 0, 400, b8, 0), W.RunDesc(8, W.FERRO, 300, 2, b8, seed=3, run_id=1),
