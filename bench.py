@@ -87,7 +87,8 @@ def work_units(d, R):
     return R if d.theta == 0xFFFFFFFF else d.theta * d.N * R
 # DRAM bytes per sweep launch from one ncu capture (profiles/sweep_pow2_glass_L16_R5000.md),
 # valid only for the kernel source it was taken on.
-SWEEP_TRAFFIC = {"sweep_source_sha256_16": "905354196dfd27df", "workload": "glass_L16_R5000", "bytes_per_launch": 45.18144e6}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu (the commands are in profiles/)
+TRAFFIC = []
 MULADD_LANES_PER_SM = 64
 
 
@@ -211,23 +212,32 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def sweep_source_sha():
-    """Hash of the source the sweep kernels compile from: the shared header and
-    the part of the kernel file before the overlap and measurement kernels."""
+# Sections of the kernel file each roofline kernel compiles from (beside the
+# shared header and the helpers before the resampling section).
+KERNEL_SECTIONS = {"sweep": (b"// Fused gather + theta checkerboard", b"// Overlaps (Sec. III.D)"),
+                   "measure": (b"// Measurement (Sec. III.B", b"// A record's 128-bit sum as a double")}
+
+
+def source_sha(kernel):
+    """Hash of the source a kernel compiles from: the shared header, the shared
+    helpers at the top of the kernel file and the kernel's own section."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2207_05535_gb300", "csrc")
     with open(os.path.join(csrc, "pa_internal.cuh"), "rb") as f:
         head = f.read()
     with open(os.path.join(csrc, "pa_kernels.cu"), "rb") as f:
         body = f.read()
-    cut = body.find(b"// Overlaps (Sec. III.D)")
-    return hashlib.sha256(head + body[:cut]).hexdigest()[:16]
+    a, b = KERNEL_SECTIONS[kernel]
+    common = body[:body.find(b"// Resampling (Sec. II.B")]
+    return hashlib.sha256(head + common + body[body.find(a):body.find(b)]).hexdigest()[:16]
 
 
-def sweep_traffic(wl):
-    """Measured DRAM bytes per sweep launch, or None when the sweep source changed since."""
-    if sweep_source_sha() == SWEEP_TRAFFIC["sweep_source_sha256_16"] and wl == SWEEP_TRAFFIC["workload"]:
-        return SWEEP_TRAFFIC["bytes_per_launch"]
+def measured_traffic(kernel, wl):
+    """DRAM bytes per launch from an ncu capture, or None when the kernel's
+    source changed since the capture (or it was taken on another workload)."""
+    for t in TRAFFIC:
+        if t["kernel"] == kernel and t["workload"] == wl and source_sha(kernel) == t["source_sha256_16"]:
+            return t["bytes_per_launch"]
     return None
 
 
@@ -386,6 +396,44 @@ def main():
     achieved_tops = updates * slots / (sweep_ms / args.steps * 1e-3) / 1e12
     metric, unit = metric_unit(wl)
     total_kernel_ms = sum(t for t, _ in kt_tot.values())
+    sweep_roof = {"bound": "alu", "kernel": "dos_sample_kernel" if inf else "sweep_pow2_kernel",
+                  "achieved": achieved_tops, "peak": peak_tops, "unit": "Tmuladd/s", "frac": achieved_tops / peak_tops,
+                  "traffic": None if inf else measured_traffic("sweep", wl),
+                  "basis": (f"{ALGO_MULADD_PER_DRAW:g} integer multiply-add slots per energy draw "
+                            f"(one Philox4x32-10 call)" if inf else
+                            f"{ALGO_MULADD_PER_UPDATE:g} integer multiply-add slots per attempted update "
+                            f"(Philox4x32-10: 40 per call, 4 updates per call)") + "; peak = 152 SMs x "
+                           f"{MULADD_LANES_PER_SM} lanes x {sm_mhz:g} MHz, clock from MEASURED_PEAKS.json "
+                           f"({pk_kind})",
+                  "updates_per_ns_sweep_only": updates / (sweep_ms / args.steps * 1e-3) / 1e9,
+                  "sweep_ms_per_step": sweep_ms / args.steps,
+                  "sweep_share_of_kernel_time": sweep_ms / total_kernel_ms if total_kernel_ms else None,
+                  "philox_calibration": cal}
+    # HBM rooflines of the measurement and the nearest-integer resampling (algorithmic bytes per anneal)
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    meas_bytes = res_bytes = 0
+    for k, d in enumerate(descs):
+        Rs = eng.records(k)["R"].astype(np.int64)
+        meas_bytes += 12 * int(Rs.sum())
+        if d.resample != W.MULTINOMIAL:
+            res_bytes += int(12 * Rs[:-1].sum() + 4 * Rs[1:].sum())
+
+    def hbm_roof(name, key, nbytes, traffic, basis):
+        ms_ = kt_tot.get(key, (0.0, 0))[0] / args.steps
+        if not ms_ or not nbytes:
+            return None
+        ach = nbytes / (ms_ * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": traffic, "bytes_per_step": nbytes, "ms_per_step": ms_,
+                "basis": basis + f"; peak = HBM copy bandwidth from MEASURED_PEAKS.json ({pk_kind})"}
+
+    roof_meas = hbm_roof("measure_kernel", "measure", meas_bytes, measured_traffic("measure", wl),
+                         "12 B read per measured replica (E, M, family)")
+    roof_res = hbm_roof("resample_counts_kernel + resample_parents_kernel", "resample", res_bytes, None,
+                        "per parent: E read, copy number written and read back (12 B); per child: its parent "
+                        "index written (4 B)")
+    dominant = max(("sweep", "measure", "resample"), key=lambda k_: kt_tot.get(k_, (0.0, 0))[0])
+    roofline = {"sweep": sweep_roof, "measure": roof_meas, "resample": roof_res}[dominant] or sweep_roof
     # overlap kernels (a10): HBM-bound; algorithmic bytes = both replicas' colour planes per pair
     ov_ms = kt_tot.get("overlap", (0.0, 0))[0] / args.steps
     ov_bytes = 0
@@ -483,20 +531,11 @@ def main():
                        "form": "batched: all runs in one launch per kernel, anneal captured as a CUDA graph",
                        "parallelism": f"replicas x{world} (independent runs per GPU)"},
             "runs_per_s": runs_per_s,
-            "roofline": {"bound": "alu", "kernel": "dos_sample_kernel" if inf else "sweep_pow2_kernel",
-                         "achieved": achieved_tops,
-                         "peak": peak_tops, "unit": "Tmuladd/s", "frac": achieved_tops / peak_tops,
-                         "traffic": sweep_traffic(wl),
-                         "basis": (f"{ALGO_MULADD_PER_DRAW:g} integer multiply-add slots per energy draw "
-                                   f"(one Philox4x32-10 call)" if inf else
-                                   f"{ALGO_MULADD_PER_UPDATE:g} integer multiply-add slots per attempted update "
-                                   f"(Philox4x32-10: 40 per call, 4 updates per call)") + "; peak = 152 SMs x "
-                                  f"{MULADD_LANES_PER_SM} lanes x {sm_mhz:g} MHz, clock from MEASURED_PEAKS.json "
-                                  f"({pk_kind})",
-                         "updates_per_ns_sweep_only": updates / (sweep_ms / args.steps * 1e-3) / 1e9,
-                         "sweep_ms_per_step": sweep_ms / args.steps,
-                         "sweep_share_of_kernel_time": sweep_ms / total_kernel_ms if total_kernel_ms else None,
-                         "philox_calibration": cal},
+            "roofline": roofline,
+            "roofline_sweep": sweep_roof if roofline is not sweep_roof else None,
+            "roofline_measure": roof_meas,
+            "roofline_resample": roof_res,
+
             "roofline_overlap": roof_ov,
             "resample_gather": gather,
             "kernel_ms_per_step": {k: t / args.steps for k, (t, n) in kt_tot.items()},

@@ -83,7 +83,9 @@ typedef struct pa_run_desc {
     uint32_t reserved;    /* must be 0 */
     const double *log_g;  /* theta = PA_THETA_INF: host, 2N+1 entries, ln g(E) of the exact density of
                              states at E = 2u - 2N, u = 0..2N (-INFINITY where g(E) = 0; no NaN or
-                             +INFINITY); read at admission.  Ignored (may be NULL) otherwise. */
+                             +INFINITY; the finite entries all at even u or all at odd u, as the
+                             energies of one lattice's states differ by multiples of 4); read at
+                             admission.  Ignored (may be NULL) otherwise. */
 } pa_run_desc;
 
 /* Per-temperature record of one run (Sec. III.B-D, Eq. rho_t).  Integer sums

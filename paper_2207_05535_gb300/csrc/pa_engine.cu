@@ -262,13 +262,16 @@ pa_status validate(const pa_run_desc *runs, uint32_t n)
         if (d.R < 1 || d.n_beta < 1 || !d.beta) return PA_ERR_INVALID_ARG;
         if (d.theta == PA_THETA_INF) {  // needs a density of states; no configurations, so no overlaps
             if (!d.log_g || d.overlap) return PA_ERR_INVALID_ARG;
-            bool any = false;
+            int parity = -1;  // energies of a lattice's states differ by multiples of 4: u of one parity
             for (uint32_t u = 0; u <= 2 * d.L * d.L; ++u) {
                 const double v = d.log_g[u];
                 if (std::isnan(v) || v == INFINITY) return PA_ERR_INVALID_ARG;
-                any = any || v > -INFINITY;
+                if (v > -INFINITY) {
+                    if (parity >= 0 && (int)(u & 1u) != parity) return PA_ERR_INVALID_ARG;
+                    parity = (int)(u & 1u);
+                }
             }
-            if (!any) return PA_ERR_INVALID_ARG;
+            if (parity < 0) return PA_ERR_INVALID_ARG;
         } else if (d.theta > (1u << 22)) {
             return PA_ERR_INVALID_ARG;
         }
@@ -532,6 +535,8 @@ pa_status admit(pa_engine *e, const pa_run_desc *runs, uint32_t n, uint32_t *slo
         rs.lnQ = 0.0;
         rs.ticket = 0;
         rs.Emin = 0;
+        rs.n_levels = 0;
+        rs.pad = 0;
         const uint64_t nq = sizes_of(d).qh;
         cudaError_t err = cudaMemcpyAsync(e->d_runs + s, &e->rd[s], sizeof(RunDev), cudaMemcpyHostToDevice, e->stream);
         if (!err) err = cudaMemcpyAsync(e->P.st + s, &rs, sizeof rs, cudaMemcpyHostToDevice, e->stream);
@@ -548,7 +553,7 @@ pa_status admit(pa_engine *e, const pa_run_desc *runs, uint32_t n, uint32_t *slo
         if (!err && nq) err = cudaMemsetAsync(e->P.qh + g.qh, 0, sizeof(uint32_t) * nq, e->stream);
         if (!err && nq) err = cudaMemsetAsync(e->P.qhp + g.qh, 0, sizeof(uint32_t) * nq, e->stream);
         if (!err && nq) err = cudaMemsetAsync(e->P.qhw + g.qh, 0, sizeof(uint32_t) * nq, e->stream);
-        // the resampling's level histogram starts (and is left by every step) cleared
+        // the measurement's histograms start (and every step leaves them) cleared
         if (!err) err = cudaMemsetAsync(e->P.scratch + g.scr, 0, 8 * scr_table_off(N), e->stream);
         if (!err) err = cudaStreamSynchronize(e->stream);  // host buffers must outlive the copies
         if (err) return cuda_fail(err, "admit upload");
@@ -1128,6 +1133,8 @@ pa_status pa_reset(pa_engine *e)
         st[k].lnQ = 0.0;
         st[k].ticket = 0;
         st[k].Emin = 0;
+        st[k].n_levels = 0;
+        st[k].pad = 0;
         PA_CUDA(cudaMemcpyAsync(e->P.st + s, &st[k], sizeof(RunState), cudaMemcpyHostToDevice, e->stream));
         PA_CUDA(cudaMemsetAsync(e->P.rec + x.rec_off, 0, sizeof(pa_step_record) * x.n_beta, e->stream));
         PA_CUDA(cudaMemsetAsync(e->P.scratch + x.scr_off, 0, 8 * scr_table_off(x.N), e->stream));

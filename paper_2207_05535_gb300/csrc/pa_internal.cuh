@@ -22,9 +22,10 @@
 //   J                    per run: site-order "J = -1" bits of right / down bonds
 //                        (2 wstride words), then per colour plane word the four bond
 //                        masks (same, rotated, up, down neighbour) [2][4][PW]
-//   scratch              per run: level histogram (N+1 u32), level CDF or thresholds
-//                        (N+1 f64 / u64), level fill counters or floors (N+1 u32), then
-//                        members (R_cap u32) / per-CTA totals / per-CTA partial sums
+//   scratch              per run: energy and magnetisation histograms (N+1 u32 each),
+//                        level CDF or thresholds (N+1 f64 / u64), level fill counters or
+//                        floors (N+1 u32), then members (R_cap u32) / per-CTA totals /
+//                        per-CTA family statistics
 #pragma once
 
 #include <cstdint>
@@ -65,13 +66,15 @@ struct RunState {
     uint32_t R_new;  // population size produced by the resampling in flight
     uint32_t status; // 0 or a pa_status that stopped the run
     double lnQ;      // ln Q of the resampling in flight
-    uint32_t ticket; // CTAs of the run done in the launch in flight (0 between launches)
-    int32_t Emin;    // lowest energy of the population being resampled
+    uint32_t ticket;   // CTAs of the run done in the launch in flight (0 between launches)
+    int32_t Emin;      // nearest-integer resampling in flight: lowest energy of the population
+    uint32_t n_levels; // and its number of energy levels (Emax - Emin) / 4 + 1
+    uint32_t pad;
 };
 
 // Kernels that split one population over several CTAs give each CTA about
 // CTA_REPLICAS replicas, at most MAX_RUN_CTAS CTAs per run.
-constexpr uint32_t CTA_REPLICAS = 4096, MAX_RUN_CTAS = 256;
+constexpr uint32_t CTA_REPLICAS = 16384, MAX_RUN_CTAS = 256;
 __host__ __device__ inline uint32_t run_ctas(uint32_t R_cap)
 {
     const uint32_t c = (R_cap + CTA_REPLICAS - 1) / CTA_REPLICAS;
@@ -128,15 +131,19 @@ inline uint32_t row_pitch(uint32_t L)
 
 inline uint32_t plane_words_of(uint32_t L) { return (L * row_pitch(L) + 31) / 32; }
 
-// Scratch of one run, in 64-bit words from scr_off: level histogram (N + 1
-// u32), a per-level f64 / u64 table (N + 1), a per-level u32 table (N + 1),
-// then a tail used by one kernel at a time: the multinomial member list
-// (R_cap u32), or the per-CTA replica totals of the resampling (MAX_RUN_CTAS
-// u32), or the measurement's per-CTA partial sums (MEASURE_PART_WORDS each).
-constexpr uint64_t MEASURE_PART_WORDS = 16;
-__host__ __device__ inline uint64_t scr_table_off(uint32_t N) { return (uint64_t(N) + 2) / 2; }
+// Scratch of one run, in 64-bit words from scr_off: the energy and the
+// magnetisation histograms of the measurement (N + 1 u32 each, left cleared
+// between steps), a per-level f64 / u64 table (N + 1), a per-level u32 table
+// (N + 1), then a tail used by one kernel at a time: the multinomial member
+// list (R_cap u32), or the per-CTA replica totals of the resampling
+// (MAX_RUN_CTAS u32), or the measurement's per-CTA family statistics
+// (MEASURE_PART_WORDS each).
+constexpr uint64_t MEASURE_PART_WORDS = 4;
+__host__ __device__ inline uint64_t scr_hist_words(uint32_t N) { return (uint64_t(N) + 2) / 2; }
+__host__ __device__ inline uint64_t scr_mhist_off(uint32_t N) { return scr_hist_words(N); }
+__host__ __device__ inline uint64_t scr_table_off(uint32_t N) { return 2 * scr_hist_words(N); }
 __host__ __device__ inline uint64_t scr_level_off(uint32_t N) { return scr_table_off(N) + N + 1; }
-__host__ __device__ inline uint64_t scr_tail_off(uint32_t N) { return scr_level_off(N) + (uint64_t(N) + 2) / 2; }
+__host__ __device__ inline uint64_t scr_tail_off(uint32_t N) { return scr_level_off(N) + scr_hist_words(N); }
 inline uint64_t scratch_words(uint32_t N, uint32_t R_cap)
 {
     const uint64_t members = (uint64_t(R_cap) + 1) / 2;
@@ -156,9 +163,10 @@ void launch_init_population(const Pool &P, const uint32_t *tile_off, const uint3
 // largest R_cap among the runs (sets the energies staged in shared memory).
 void launch_resample_multinomial(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap,
                                  cudaStream_t s);
-// Nearest-integer resampling (PA_NEAREST), run_ctas(R_cap) CTAs per run, in
+// Nearest-integer resampling (PA_NEAREST) from the tables the measurement of
+// the previous step prepared, run_ctas(R_cap) CTAs per run, in
 // RESAMPLE_NEAREST_LAUNCHES kernel launches.
-constexpr uint32_t RESAMPLE_NEAREST_LAUNCHES = 3;
+constexpr uint32_t RESAMPLE_NEAREST_LAUNCHES = 2;
 void launch_resample_nearest(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap, cudaStream_t s);
 // Launch shapes to try for lattice size L (first = default); one entry unless
 // the bit-sliced kernel applies.
@@ -167,7 +175,8 @@ void launch_sweep(const Pool &P, const uint32_t *group_runs, const uint32_t *til
                   uint32_t n_tiles, const SweepCfg &cfg, int any_glass, cudaStream_t s);
 void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, uint32_t max_Rcap, int init,
                     cudaStream_t s);
-// run_ctas(R_cap) CTAs per run (at most run_ctas(max_Rcap)).
+// run_ctas(R_cap) CTAs per run (at most run_ctas(max_Rcap)); also prepares the
+// next nearest-integer resampling of each run.
 void launch_measure(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap, int init,
                     cudaStream_t s);
 // theta = PA_THETA_INF runs: fresh energies from the exact distribution for

@@ -505,6 +505,8 @@ __global__ void __launch_bounds__(512) resample_multinomial_kernel(Pool P, const
         atomicAdd(&cnt[members[first + idx]], 1u);
     }
     __syncthreads();
+    if (h == g_hist)  // leave the measurement's histogram cleared
+        for (uint32_t n = tid; n < nb; n += nt) g_hist[n] = 0u;
 
     // the copy numbers' exclusive scan and the parent map (contiguous families).
     // Each warp takes a contiguous chunk of the replicas; one barrier joins the chunks.
@@ -556,22 +558,20 @@ __global__ void __launch_bounds__(512) resample_multinomial_kernel(Pool P, const
 // Nearest-integer resampling (PA_NEAREST): r_j = floor(tau) + [u 2^-32 < tau - floor(tau)],
 // tau = R w[n_j] / S.  tau depends on the level only, so per level the floor and
 // the integer threshold ceil(frac 2^32) are tabulated once (u 2^-32 < frac <=>
-// u < frac 2^32 exactly: scaling by 2^32 is exact and u is an integer).
+// u < frac 2^32 exactly: scaling by 2^32 is exact and u is an integer).  The
+// measurement of the previous step, which counts the population per energy
+// level anyway, finds E_min, sums S and Q and writes these tables.
 //
 // A run's population is split over nc = run_ctas(R_cap) CTAs (CTA c of the
-// run: blockIdx.y = c, replicas [c ceil(R/nc), (c+1) ceil(R/nc))), in three
+// run: blockIdx.y = c, replicas [c ceil(R/nc), (c+1) ceil(R/nc))), in two
 // launches:
-//   resample_levels_kernel   each CTA adds its chunk's level counts to the run's
-//                            histogram; the last CTA to finish (a ticket in the
-//                            run state) finds E_min, sums S and Q, tabulates the
-//                            floors and thresholds and clears the histogram
 //   resample_counts_kernel   r_j of every replica and each CTA's total
 //   resample_parents_kernel  offsets (earlier CTAs' totals plus a scan inside
 //                            the CTA) and the parent map
-// The histogram is counted from the base b = -2N + ((E_0 + 2N) mod 4): every
-// energy of the population is congruent to E_0 mod 4 and |E| <= 2N, so
-// (E - b) / 4 lies in 0..N.
 constexpr uint32_t RESAMPLE_THREADS = 512;
+constexpr uint32_t COUNTS_SMEM_LEVELS = 2048;  // level tables staged in shared memory (L <= 45)
+constexpr uint32_t COUNTS_BATCH = 4;           // replicas per thread in flight
+constexpr uint32_t PARENT_BATCH = 8;           // rows of 32 copy numbers a warp loads at once
 
 struct RunChunk {
     uint32_t lo, hi;  // this CTA's replicas
@@ -584,82 +584,10 @@ __device__ __forceinline__ RunChunk cta_chunk(uint32_t R, uint32_t nc, uint32_t 
     return {lo, min(R, lo + chunk)};
 }
 
-__global__ void __launch_bounds__(RESAMPLE_THREADS) resample_levels_kernel(Pool P, const uint32_t *runs)
+__global__ void __launch_bounds__(RESAMPLE_THREADS, 2) resample_counts_kernel(Pool P, const uint32_t *runs)
 {
-    __shared__ uint32_t sh_hist[SMEM_BINS];
-    __shared__ uint32_t sh_r[32];
-    __shared__ double sh_S;
-    __shared__ uint32_t sh_last;
-    const uint32_t run = runs[blockIdx.x];
-    const RunDev rd = P.runs[run];
-    RunState *st = &P.st[run];
-    if (st->status) return;
-    const uint32_t i = st->step + 1;
-    if (i >= rd.n_beta) return;
-    const uint32_t nc = min(gridDim.y, run_ctas(rd.R_cap));
-    if (blockIdx.y >= nc) return;
-    const uint32_t Rprev = st->R_cur;
-    const int32_t *E = P.E[(i - 1) & 1] + rd.rep_off;
-    const RunChunk ch = cta_chunk(Rprev, nc, blockIdx.y);
-    const uint32_t tid = threadIdx.x, nt = blockDim.x, n1 = rd.N + 1;
-    const int32_t twoN = 2 * (int32_t)rd.N;
-    const int32_t base = -twoN + ((E[0] + twoN) & 3);
-
-    unsigned long long *scr = P.scratch + rd.scr_off;
-    uint32_t *g_hist = reinterpret_cast<uint32_t *>(scr);
-    if (n1 <= SMEM_BINS) {  // this CTA's counts in shared memory, then the non-zero bins added to the run's
-        for (uint32_t n = tid; n < n1; n += nt) sh_hist[n] = 0;
-        __syncthreads();
-        for (uint32_t j = ch.lo + tid; j < ch.hi; j += nt) atomicAdd(&sh_hist[(uint32_t)(E[j] - base) >> 2], 1u);
-        __syncthreads();
-        for (uint32_t n = tid; n < n1; n += nt)
-            if (sh_hist[n]) atomicAdd(&g_hist[n], sh_hist[n]);
-    } else {
-        for (uint32_t j = ch.lo + tid; j < ch.hi; j += nt) atomicAdd(&g_hist[(uint32_t)(E[j] - base) >> 2], 1u);
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) sh_last = atomicAdd(&st->ticket, 1u) == nc - 1 ? 1u : 0u;
-    __syncthreads();
-    if (!sh_last) return;
-    __threadfence();
-
-    // the last CTA: the occupied level range, S and Q, the per-level tables
-    uint32_t lo = 0xffffffffu, hi = 0;
-    for (uint32_t n = tid; n < n1; n += nt)
-        if (__ldcg(&g_hist[n])) {
-            lo = n < lo ? n : lo;
-            hi = n > hi ? n : hi;
-        }
-    lo = block_min(lo, sh_r, 0xffffffffu);
-    hi = block_max(hi, sh_r, 0u);
-    const uint32_t nb = hi - lo + 1;
-    const int32_t Emin = base + 4 * (int32_t)lo;
-    const double dbeta = P.beta[rd.beta_off + i] - P.beta[rd.beta_off + i - 1];
-    const double *w = P.wt + P.wtoff[rd.wt_off + i];  // w[n] = exp(-4 n dbeta_i), shared table
-    if (tid == 0) {
-        double S = 0.0;
-        for (uint32_t n = 0; n < nb; ++n) S = __dadd_rn(S, __dmul_rn((double)__ldcg(&g_hist[lo + n]), w[n]));
-        sh_S = S;
-        st->lnQ = (-dbeta) * (double)Emin + log(S) - log((double)Rprev);
-        st->Emin = Emin;
-    }
-    __syncthreads();
-    const double S = sh_S;
-    unsigned long long *thr = scr + scr_table_off(rd.N);
-    uint32_t *flo = reinterpret_cast<uint32_t *>(scr + scr_level_off(rd.N));
-    for (uint32_t n = tid; n < nb; n += nt) {
-        const double tau = __ddiv_rn(__dmul_rn((double)rd.R, w[n]), S);
-        const double fl = floor(tau);
-        flo[n] = (uint32_t)fl;
-        thr[n] = (unsigned long long)ceil(__dmul_rn(__dsub_rn(tau, fl), 4294967296.0));
-    }
-    for (uint32_t n = tid; n < n1; n += nt) g_hist[n] = 0u;  // ready for the next step
-    if (tid == 0) st->ticket = 0u;
-}
-
-__global__ void __launch_bounds__(RESAMPLE_THREADS) resample_counts_kernel(Pool P, const uint32_t *runs)
-{
+    __shared__ unsigned long long s_thr[COUNTS_SMEM_LEVELS];
+    __shared__ uint32_t s_flo[COUNTS_SMEM_LEVELS];
     __shared__ uint32_t sh_r[32];
     const uint32_t run = runs[blockIdx.x];
     const RunDev rd = P.runs[run];
@@ -672,20 +600,51 @@ __global__ void __launch_bounds__(RESAMPLE_THREADS) resample_counts_kernel(Pool 
     const RunChunk ch = cta_chunk(st->R_cur, nc, blockIdx.y);
     const int32_t *E = P.E[(i - 1) & 1] + rd.rep_off;
     const int32_t Emin = st->Emin;
+    const uint32_t nb = st->n_levels, tid = threadIdx.x, nt = blockDim.x;
     const unsigned long long *scr = P.scratch + rd.scr_off;
     const unsigned long long *thr = scr + scr_table_off(rd.N);
     const uint32_t *flo = reinterpret_cast<const uint32_t *>(scr + scr_level_off(rd.N));
+    // the first batch's energies and uniforms are requested before the tables are staged
+    int32_t e[COUNTS_BATCH];
+    uint32_t u[COUNTS_BATCH];
+    const uint32_t j_first = ch.lo + tid;
+#pragma unroll
+    for (uint32_t r = 0; r < COUNTS_BATCH; ++r) {
+        const uint32_t j = j_first + r * nt;
+        e[r] = j < ch.hi ? E[j] : Emin;
+        u[r] = philox4x32_10(j, 0, i, TAG_RESAMPLE << 24, rd.seed, rd.run_id).x;
+    }
+    if (nb <= COUNTS_SMEM_LEVELS) {
+        for (uint32_t n = tid; n < nb; n += nt) {
+            s_thr[n] = thr[n];
+            s_flo[n] = flo[n];
+        }
+        __syncthreads();
+        thr = s_thr;
+        flo = s_flo;
+    }
     uint32_t *cnt = P.cnt + rd.rep_off;
     uint32_t sum = 0;
-    for (uint32_t j = ch.lo + threadIdx.x; j < ch.hi; j += blockDim.x) {
-        const uint32_t n = (uint32_t)(E[j] - Emin) >> 2;
-        const uint32_t u = philox4x32_10(j, 0, i, TAG_RESAMPLE << 24, rd.seed, rd.run_id).x;
-        const uint32_t r = flo[n] + ((unsigned long long)u < thr[n] ? 1u : 0u);
-        cnt[j] = r;
-        sum += r;
+    for (uint32_t j0 = j_first; j0 < ch.hi; j0 += COUNTS_BATCH * nt) {
+        if (j0 != j_first) {
+#pragma unroll
+            for (uint32_t r = 0; r < COUNTS_BATCH; ++r) e[r] = j0 + r * nt < ch.hi ? E[j0 + r * nt] : Emin;
+#pragma unroll
+            for (uint32_t r = 0; r < COUNTS_BATCH; ++r)
+                u[r] = philox4x32_10(j0 + r * nt, 0, i, TAG_RESAMPLE << 24, rd.seed, rd.run_id).x;
+        }
+#pragma unroll
+        for (uint32_t r = 0; r < COUNTS_BATCH; ++r) {
+            const uint32_t j = j0 + r * nt;
+            if (j >= ch.hi) break;
+            const uint32_t n = (uint32_t)(e[r] - Emin) >> 2;
+            const uint32_t c = flo[n] + ((unsigned long long)u[r] < thr[n] ? 1u : 0u);
+            cnt[j] = c;
+            sum += c;
+        }
     }
     sum = block_sum(sum, sh_r);
-    if (threadIdx.x == 0) reinterpret_cast<uint32_t *>(P.scratch + rd.scr_off + scr_tail_off(rd.N))[blockIdx.y] = sum;
+    if (tid == 0) reinterpret_cast<uint32_t *>(P.scratch + rd.scr_off + scr_tail_off(rd.N))[blockIdx.y] = sum;
 }
 
 __global__ void __launch_bounds__(RESAMPLE_THREADS) resample_parents_kernel(Pool P, const uint32_t *runs)
@@ -722,11 +681,23 @@ __global__ void __launch_bounds__(RESAMPLE_THREADS) resample_parents_kernel(Pool
             sh_total = all;
         }
     }
-    // each warp takes a contiguous piece of the CTA's chunk
+    // each warp takes a contiguous piece of the CTA's chunk, PARENT_BATCH rows of
+    // 32 at a time; the first batch stays in registers between the two passes
     const uint32_t wchunk = (ch.hi - ch.lo + nwarp - 1) / nwarp;
     const uint32_t w_lo = min(ch.hi, ch.lo + wid * wchunk), w_hi = min(ch.hi, w_lo + wchunk);
-    uint32_t wsum = 0;
-    for (uint32_t j = w_lo + lane; j < w_hi; j += 32) wsum += cnt[j];
+    uint32_t wsum = 0, cq[PARENT_BATCH];
+    for (uint32_t b0 = w_lo; b0 < w_hi; b0 += 32 * PARENT_BATCH) {
+        uint32_t t[PARENT_BATCH];
+#pragma unroll
+        for (uint32_t r = 0; r < PARENT_BATCH; ++r) {
+            const uint32_t j = b0 + 32 * r + lane;
+            t[r] = j < w_hi ? cnt[j] : 0u;
+            wsum += t[r];
+        }
+        if (b0 == w_lo)
+#pragma unroll
+            for (uint32_t r = 0; r < PARENT_BATCH; ++r) cq[r] = t[r];
+    }
     wsum = warp_sum(wsum);
     if (lane == 0) sh_u[wid] = wsum;
     __syncthreads();
@@ -740,19 +711,28 @@ __global__ void __launch_bounds__(RESAMPLE_THREADS) resample_parents_kernel(Pool
     }
     __syncthreads();
     uint32_t carry = sh_u[wid];
-    for (uint32_t b0 = w_lo; b0 < w_hi; b0 += 32) {
-        const uint32_t j = b0 + lane;
-        const uint32_t r = j < w_hi ? cnt[j] : 0u;
-        uint32_t x = r;  // inclusive scan over the lanes
+    for (uint32_t b0 = w_lo; b0 < w_hi; b0 += 32 * PARENT_BATCH) {
+        uint32_t t[PARENT_BATCH];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, x, o);
-            if ((int)lane >= o) x += y;
+        for (uint32_t r = 0; r < PARENT_BATCH; ++r) {
+            const uint32_t j = b0 + 32 * r + lane;
+            t[r] = b0 == w_lo ? cq[r] : (j < w_hi ? cnt[j] : 0u);
         }
-        const uint32_t o = carry + x - r;
-        for (uint32_t c = 0; c < r; ++c)
-            if (o + c < rd.R_cap) parent[o + c] = j;
-        carry += __shfl_sync(FULL, x, 31);
+#pragma unroll
+        for (uint32_t q = 0; q < PARENT_BATCH; ++q) {
+            if (b0 + 32 * q >= w_hi) break;  // uniform over the warp
+            const uint32_t j = b0 + 32 * q + lane, r = t[q];
+            uint32_t x = r;  // inclusive scan over the lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, x, o);
+                if ((int)lane >= o) x += y;
+            }
+            const uint32_t o = carry + x - r;
+            for (uint32_t c = 0; c < r; ++c)
+                if (o + c < rd.R_cap) parent[o + c] = j;
+            carry += __shfl_sync(FULL, x, 31);
+        }
     }
     if (blockIdx.y == 0 && tid == 0) {
         const uint32_t Rn = sh_total;
@@ -1738,9 +1718,12 @@ __global__ void __launch_bounds__(DOS_THREADS) dos_sample_kernel(Pool P, const u
         const uint32_t k = k0 + r * DOS_THREADS + threadIdx.x;
         par[r] = !init && k < R ? P.parent[rd.rep_off + k] : 0u;
     }
+    PhiloxKeys K;  // counters (k, 0, i, TAG_DOS << 24): key schedule and first product of i shared
+    philox_keys(K, rd.seed, rd.run_id);
+    const uint32_t hi1_0 = __umulhi(0xCD9E8D57u, i), lo1_0 = 0xCD9E8D57u * i;
 #pragma unroll
     for (uint32_t r = 0; r < DOS_PER_THREAD; ++r) {
-        const uint4 o = philox4x32_10(k0 + r * DOS_THREADS + threadIdx.x, 0u, i, TAG_DOS << 24, rd.seed, rd.run_id);
+        const uint4 o = philox_rk<true>(k0 + r * DOS_THREADS + threadIdx.x, 0u, TAG_DOS << 24, hi1_0, lo1_0, K);
         u53[r] = ((unsigned long long)(o.x >> 5) << 26) | (unsigned long long)(o.y >> 6);
     }
     uint32_t f[DOS_PER_THREAD];
@@ -1780,25 +1763,27 @@ __device__ __forceinline__ void add128(I128 &a, unsigned long long lo, long long
     a.lo = s;
 }
 
-__device__ __forceinline__ void add128_signed(I128 &a, long long v) { add128(a, (unsigned long long)v, v >> 63); }
+__device__ __forceinline__ void add128(I128 &a, const I128 &b) { add128(a, b.lo, b.hi); }
 
-// a += v * v for 0 <= v < 2^63 (full 128-bit product)
-__device__ __forceinline__ void add128_square(I128 &a, unsigned long long v)
+// The full product of two unsigned 64-bit integers.
+__device__ __forceinline__ I128 mul_u64(unsigned long long a, unsigned long long b)
 {
-    add128(a, v * v, (long long)__umul64hi(v, v));
+    return {a * b, (long long)__umul64hi(a, b)};
 }
 
-// Partial results of the measurement over one contiguous chunk of replicas
-// (a warp's, a CTA's): moment sums and the family run statistics.  lead: the
-// replicas at the chunk's start that continue the family open before it;
-// trail: the length of the chunk's last run (counted from the chunk's start
-// when the chunk has no family start).
-struct MeasurePart {
-    long long sE, sE2, sAM, sM2, c2;
-    I128 sE3, sE4, sAM3, sM4;
-    uint32_t nfam, cmax, lead, trail, len, pad;
-};
-static_assert(sizeof(MeasurePart) == MEASURE_PART_WORDS * 8, "MeasurePart fills its scratch words");
+// a b for a >= 0 and a b < 2^127.
+__device__ __forceinline__ I128 mul_128_u64(const I128 &a, unsigned long long b)
+{
+    I128 r = mul_u64(a.lo, b);
+    r.hi += (long long)((unsigned long long)a.hi * b);
+    return r;
+}
+
+__device__ __forceinline__ I128 neg128(const I128 &a)
+{
+    const unsigned long long lo = ~a.lo + 1ull;
+    return {lo, ~a.hi + (lo == 0ull ? 1ll : 0ll)};
+}
 
 __device__ __forceinline__ I128 warp_sum128(I128 v)
 {
@@ -1811,25 +1796,27 @@ __device__ __forceinline__ I128 warp_sum128(I128 v)
     return v;
 }
 
+// Family run statistics of one contiguous chunk of replicas (a warp's, a
+// CTA's).  lead: the replicas at the chunk's start that continue the family
+// open before it; trail: the length of the chunk's last run (counted from the
+// chunk's start when the chunk has no family start).
+struct FamPart {
+    long long c2;  // sum over the chunk's runs of length^2
+    uint32_t nfam, cmax, lead, trail, len, pad;
+};
+static_assert(sizeof(FamPart) == MEASURE_PART_WORDS * 8, "FamPart fills its scratch words");
+
 // Appends chunk q (the next one in replica order) to t.  A family open at the
 // end of t that continues into q was counted as pieces a and b, a^2 + b^2: the
 // join adds 2ab.
-__device__ __forceinline__ void join_part(MeasurePart &t, const MeasurePart &q)
+__device__ __forceinline__ void join_part(FamPart &t, const FamPart &q)
 {
     if (q.len == 0) return;
     if (t.len == 0) {
         t = q;
         return;
     }
-    t.sE += q.sE;
-    t.sE2 += q.sE2;
-    t.sAM += q.sAM;
-    t.sM2 += q.sM2;
     t.c2 += q.c2;
-    add128(t.sE3, q.sE3.lo, q.sE3.hi);
-    add128(t.sE4, q.sE4.lo, q.sE4.hi);
-    add128(t.sAM3, q.sAM3.lo, q.sAM3.hi);
-    add128(t.sM4, q.sM4.lo, q.sM4.hi);
     t.nfam += q.nfam;
     t.cmax = q.cmax > t.cmax ? q.cmax : t.cmax;
     if (q.lead > 0) {
@@ -1844,7 +1831,7 @@ __device__ __forceinline__ void join_part(MeasurePart &t, const MeasurePart &q)
     t.len += q.len;
 }
 
-__device__ __forceinline__ void store_part_cg(MeasurePart *dst, const MeasurePart &v)
+__device__ __forceinline__ void store_part_cg(FamPart *dst, const FamPart &v)
 {
     const unsigned long long *a = reinterpret_cast<const unsigned long long *>(&v);
     unsigned long long *b = reinterpret_cast<unsigned long long *>(dst);
@@ -1852,9 +1839,9 @@ __device__ __forceinline__ void store_part_cg(MeasurePart *dst, const MeasurePar
     for (int k = 0; k < (int)MEASURE_PART_WORDS; ++k) __stcg(b + k, a[k]);
 }
 
-__device__ __forceinline__ MeasurePart load_part_cg(const MeasurePart *src)
+__device__ __forceinline__ FamPart load_part_cg(const FamPart *src)
 {
-    MeasurePart v;
+    FamPart v;
     unsigned long long *a = reinterpret_cast<unsigned long long *>(&v);
     const unsigned long long *b = reinterpret_cast<const unsigned long long *>(src);
 #pragma unroll
@@ -1862,23 +1849,51 @@ __device__ __forceinline__ MeasurePart load_part_cg(const MeasurePart *src)
     return v;
 }
 
-// A run's R_i replicas are split over nc = run_ctas(R_cap) CTAs (blockIdx.y)
-// and each CTA's chunk over its warps.  Families are contiguous runs of equal
-// ancestor id; inside a warp's chunk a warp-wide inclusive max-scan of run
-// starts gives every replica its run start (the chunk's first replica is
-// treated as a start), and the chunks are then joined in order (join_part):
-// a CTA's warps by its thread 0, the CTAs by the last CTA of the run to
-// finish (a ticket in the run state), which writes the step record.
+// Sums of E^k and |M|^k, k = 1..4.
+struct Moments {
+    long long sE, sE2, sAM, sM2;
+    I128 sE3, sE4, sAM3, sM4;
+};
+
+// Measurement of a run's population at beta_i, split over nc = run_ctas(R_cap)
+// CTAs (blockIdx.y) and each CTA's chunk over its warps.
+//  - Moments: energies and magnetisations take N + 1 values each, E = b + 4n
+//    with b = -2N + ((E_0 + 2N) mod 4) (every energy of a population is
+//    congruent to E_0 mod 4: a spin flip changes E by 0, +-4 or +-8; |E| <= 2N)
+//    and M = 2n - N.  Every CTA counts its replicas per value (a per-lane
+//    run-length cache in front of the shared-memory counters) and adds its
+//    counts into the run's histograms; the sums of E^k and |M|^k (k <= 4,
+//    128-bit for k >= 3) are exact integer sums over the histograms.
+//  - Families are contiguous runs of equal ancestor id.  Within a warp the run
+//    starts are a ballot and a replica's run start is the highest start at or
+//    below it (the chunk's first replica counts as a start); chunks are then
+//    joined in order (join_part): a CTA's warps by its thread 0, the CTAs by
+//    the last CTA of the run to finish (a ticket in the run state).
+// The last CTA writes the step record and, for a nearest-integer run with a
+// next temperature, prepares that resampling (Sec. II.B, Eqs. tauBoltz and
+// QBoltz): E_min from the histogram, S = sum_j exp(-dbeta (E_j - E_min))
+// summed level by level in ascending order with the table w[n] =
+// exp(-4 n dbeta_{i+1}), ln Q_{i+1} = -dbeta E_min + ln S - ln R_i, and per
+// level floor(tau) and the draw threshold ceil(frac 2^32).  It leaves the
+// histograms cleared.
 #ifndef PA_MEASURE_THREADS
 #define PA_MEASURE_THREADS 512
 #endif
 #ifndef PA_MEASURE_MIN_BLOCKS
 #define PA_MEASURE_MIN_BLOCKS 2  // two CTAs per SM: at most 64 registers
 #endif
+constexpr uint32_t MEASURE_SMEM_BINS = 4097;  // L <= 64: counts in shared memory
+constexpr uint32_t MEASURE_BATCH = 4;         // rows of 32 replicas a warp loads at once
+constexpr uint32_t MEASURE_SMEM_TERMS = MEASURE_SMEM_BINS;  // doubles that fit in the counters' space
 
-__global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) measure_kernel(Pool P, const uint32_t *runs, int init)
+__global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) measure_kernel(Pool P, const uint32_t *runs,
+                                                                                           int init)
 {
-    __shared__ MeasurePart part[32];
+    __shared__ __align__(16) uint32_t sh_h[2][MEASURE_SMEM_BINS];
+    __shared__ FamPart part[32];
+    __shared__ Moments mom[PA_MEASURE_THREADS / 32];
+    __shared__ uint32_t sh_lohi[2];
+    __shared__ double sh_S;
     __shared__ uint32_t sh_last;
     const uint32_t run = runs[blockIdx.x];
     const RunDev rd = P.runs[run];
@@ -1893,142 +1908,278 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) mea
     const int32_t *E = P.E[b] + rd.rep_off;
     const int32_t *M = P.M[b] + rd.rep_off;
     const uint32_t *fam = P.fam[b] + rd.rep_off;
-    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31u, wid = tid >> 5, nw = nt >> 5;
+    const uint32_t N = rd.N, n1 = N + 1;
+    const int32_t twoN = 2 * (int32_t)N;
+    const int32_t eb = -twoN + ((E[0] + twoN) & 3);
+    unsigned long long *scr = P.scratch + rd.scr_off;
+    uint32_t *gE = reinterpret_cast<uint32_t *>(scr);
+    uint32_t *gM = reinterpret_cast<uint32_t *>(scr + scr_mhist_off(N));
+    const bool smem = n1 <= MEASURE_SMEM_BINS;
+    uint32_t *hE = smem ? sh_h[0] : gE, *hM = smem ? sh_h[1] : gM;
+    if (smem) {
+        for (uint32_t n = tid; n < n1; n += nt) {
+            sh_h[0][n] = 0u;
+            sh_h[1][n] = 0u;
+        }
+        __syncthreads();
+    }
+
     const uint32_t cchunk = (R + nc - 1) / nc;
     const uint32_t c_lo = min(R, blockIdx.y * cchunk), c_hi = min(R, c_lo + cchunk);
     const uint32_t chunk = (c_hi - c_lo + nw - 1) / nw;
     const uint32_t lo = min(c_hi, c_lo + wid * chunk), hi = min(c_hi, lo + chunk);
 
-    long long sE = 0, sE2 = 0, sAM = 0, sM2 = 0, c2 = 0;
-    I128 sE3 = {0ull, 0ll}, sE4 = {0ull, 0ll}, sAM3 = {0ull, 0ll}, sM4 = {0ull, 0ll};
-    uint32_t nfam = 0, cmax = 0, first = hi, open = lo;
-    // loads run one chunk of 32 ahead; fam[j - 1] comes from the neighbouring lane
-    int32_t e_nx = 0, m_nx = 0;
-    uint32_t f_nx = 0;
-    if (lo + lane < hi) {
-        e_nx = E[lo + lane];
-        m_nx = M[lo + lane];
-        f_nx = fam[lo + lane];
-    }
+    uint32_t e_bin = 0, e_cnt = 0, m_bin = 0, m_cnt = 0;  // per-lane run-length caches of the counts
+    long long c2 = 0;
+    uint32_t nfam = 0, cmax = 0, first = hi, open = lo;  // nfam, first, open: warp-uniform
     uint32_t f_prev = lo > 0 && lo < hi ? fam[lo - 1] : 0u;  // family before the chunk (lane 0's left)
-    for (uint32_t base = lo; base < hi; base += 32) {
-        const uint32_t j = base + lane;
-        const bool ok = j < hi;
-        const int32_t e_cur = e_nx, m_cur = m_nx;
-        const uint32_t f_cur = f_nx;
-        if (base + 32 + lane < hi) {
-            e_nx = E[base + 32 + lane];
-            m_nx = M[base + 32 + lane];
-            f_nx = fam[base + 32 + lane];
-        }
-        uint32_t f_left = __shfl_up_sync(FULL, f_cur, 1);
-        if (lane == 0) f_left = f_prev;
-        f_prev = __shfl_sync(FULL, f_cur, 31);
-        bool start = false, forced = false;
-        if (ok) {
-            const long long e = e_cur, m = m_cur;
-            const long long am = m < 0 ? -m : m;
-            const long long e2 = e * e, m2 = m * m;  // |E| <= 2N = 2^17, |M| <= 2^16
-            sE += e;
-            sE2 += e2;
-            sAM += am;
-            sM2 += m2;
-            add128_signed(sE3, e2 * e);
-            add128_square(sE4, (unsigned long long)e2);
-            add128_signed(sAM3, m2 * am);
-            add128_square(sM4, (unsigned long long)m2);
-            start = j == 0 || f_cur != f_left;
-            forced = start || j == lo;
-        }
-        uint32_t sj = forced ? j : 0u;
+    // rows of 32 replicas in batches of MEASURE_BATCH: the next batch's loads are
+    // issued before the current batch is walked row by row; fam[j - 1] comes from
+    // the neighbouring lane
+    int32_t eq[MEASURE_BATCH], mq[MEASURE_BATCH];
+    uint32_t fq[MEASURE_BATCH];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, sj, o);
-            if ((int)lane >= o) sj = y > sj ? y : sj;
-        }
-        sj = sj > open ? sj : open;
-        if (ok) {
-            c2 += 2 * (long long)(j - sj) + 1;  // sum over a run of (2r + 1) = length^2
-            nfam += start ? 1u : 0u;
-            cmax = j - sj + 1 > cmax ? j - sj + 1 : cmax;
-            first = start && j < first ? j : first;
-        }
-        open = __shfl_sync(FULL, sj, 31);
+    for (uint32_t r = 0; r < MEASURE_BATCH; ++r) {
+        const uint32_t j = lo + 32 * r + lane;
+        eq[r] = j < hi ? E[j] : 0;
+        mq[r] = j < hi ? M[j] : 0;
+        fq[r] = j < hi ? fam[j] : 0u;
     }
-    MeasurePart w;
-    w.sE = warp_sum(sE);
-    w.sE2 = warp_sum(sE2);
-    w.sAM = warp_sum(sAM);
-    w.sM2 = warp_sum(sM2);
+    for (uint32_t b0 = lo; b0 < hi; b0 += 32 * MEASURE_BATCH) {
+        int32_t en[MEASURE_BATCH], mn[MEASURE_BATCH];
+        uint32_t fn[MEASURE_BATCH];
+#pragma unroll
+        for (uint32_t r = 0; r < MEASURE_BATCH; ++r) {
+            const uint32_t j = b0 + 32 * (MEASURE_BATCH + r) + lane;
+            en[r] = j < hi ? E[j] : 0;
+            mn[r] = j < hi ? M[j] : 0;
+            fn[r] = j < hi ? fam[j] : 0u;
+        }
+#pragma unroll
+        for (uint32_t r = 0; r < MEASURE_BATCH; ++r) {
+            const uint32_t base = b0 + 32 * r;
+            if (base >= hi) break;  // uniform over the warp
+            const uint32_t j = base + lane;
+            const bool ok = j < hi;
+            const uint32_t f_cur = fq[r];
+            uint32_t f_left = __shfl_up_sync(FULL, f_cur, 1);
+            if (lane == 0) f_left = f_prev;
+            f_prev = __shfl_sync(FULL, f_cur, 31);
+            if (ok) {
+                const uint32_t ne = (uint32_t)(eq[r] - eb) >> 2, nm = (uint32_t)(mq[r] + (int32_t)N) >> 1;
+                if (ne != e_bin) {
+                    if (e_cnt) atomicAdd(&hE[e_bin], e_cnt);
+                    e_bin = ne;
+                    e_cnt = 0;
+                }
+                ++e_cnt;
+                if (nm != m_bin) {
+                    if (m_cnt) atomicAdd(&hM[m_bin], m_cnt);
+                    m_bin = nm;
+                    m_cnt = 0;
+                }
+                ++m_cnt;
+            }
+            const bool start = ok && (j == 0 || f_cur != f_left);
+            const uint32_t smask = __ballot_sync(FULL, start);
+            const uint32_t fmask = __ballot_sync(FULL, start || (ok && j == lo));
+            const uint32_t below = fmask & (0xffffffffu >> (31u - lane));
+            const uint32_t sj = below ? base + 31u - (uint32_t)__clz(below) : open;
+            if (ok) {
+                c2 += 2 * (long long)(j - sj) + 1;  // sum over a run of (2r + 1) = length^2
+                cmax = j - sj + 1 > cmax ? j - sj + 1 : cmax;
+            }
+            nfam += (uint32_t)__popc(smask);
+            if (smask && first == hi) first = base + (uint32_t)__ffs(smask) - 1u;
+            if (fmask) open = base + 31u - (uint32_t)__clz(fmask);
+        }
+#pragma unroll
+        for (uint32_t r = 0; r < MEASURE_BATCH; ++r) {
+            eq[r] = en[r];
+            mq[r] = mn[r];
+            fq[r] = fn[r];
+        }
+    }
+    if (e_cnt) atomicAdd(&hE[e_bin], e_cnt);
+    if (m_cnt) atomicAdd(&hM[m_bin], m_cnt);
+    FamPart w;
     w.c2 = warp_sum(c2);
-    w.sE3 = warp_sum128(sE3);
-    w.sE4 = warp_sum128(sE4);
-    w.sAM3 = warp_sum128(sAM3);
-    w.sM4 = warp_sum128(sM4);
-    w.nfam = warp_sum(nfam);
     w.cmax = warp_max(cmax);
-    w.lead = warp_min(first) - lo;  // replicas continuing the previous chunk's family
-    w.trail = hi - open;            // length of the chunk's last run
+    w.nfam = nfam;
+    w.lead = first - lo;  // replicas continuing the previous chunk's family
+    w.trail = hi - open;  // length of the chunk's last run
     w.len = hi - lo;
     w.pad = 0;
     if (lane == 0) part[wid] = w;
     __syncthreads();
-    if (wid != 0) return;
-
-    MeasurePart t;
-    if (lane == 0) {
-        t = part[0];
-        for (uint32_t k = 1; k < nw; ++k) join_part(t, part[k]);
-    }
-    if (nc > 1) {  // the CTAs' parts are joined, in order, by the last CTA of the run to finish
-        MeasurePart *gp = reinterpret_cast<MeasurePart *>(P.scratch + rd.scr_off + scr_tail_off(rd.N));
-        if (lane == 0) {
-            store_part_cg(gp + blockIdx.y, t);
-            __threadfence();
-            sh_last = atomicAdd(&st->ticket, 1u) == nc - 1 ? 1u : 0u;
+    if (smem)  // this CTA's counts into the run's histograms
+        for (uint32_t n = tid; n < n1; n += nt) {
+            if (sh_h[0][n]) atomicAdd(&gE[n], sh_h[0][n]);
+            if (sh_h[1][n]) atomicAdd(&gM[n], sh_h[1][n]);
         }
-        __syncwarp();
+    FamPart *gp = reinterpret_cast<FamPart *>(scr + scr_tail_off(N));
+    if (tid == 0) {
+        FamPart t = part[0];
+        for (uint32_t k = 1; k < nw; ++k) join_part(t, part[k]);
+        if (nc > 1) store_part_cg(gp + blockIdx.y, t);
+        else part[0] = t;
+    }
+    if (nc > 1) {  // the last CTA of the run to finish goes on
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) sh_last = atomicAdd(&st->ticket, 1u) == nc - 1 ? 1u : 0u;
+        __syncthreads();
         if (!sh_last) return;
         __threadfence();
-        t.len = 0;
-        for (uint32_t k0 = 0; k0 < nc; k0 += 32) {  // 32 parts at a time, loaded by the warp's lanes
-            if (k0 + lane < nc) part[lane] = load_part_cg(gp + k0 + lane);
-            __syncwarp();
-            if (lane == 0)
-                for (uint32_t k = 0; k < 32 && k0 + k < nc; ++k) join_part(t, part[k]);
-            __syncwarp();
+        if (wid == 0) {  // the CTAs' family statistics, joined in order, 32 loaded at a time
+            FamPart t;
+            t.len = 0;
+            for (uint32_t k0 = 0; k0 < nc; k0 += 32) {
+                if (k0 + lane < nc) part[lane] = load_part_cg(gp + k0 + lane);
+                __syncwarp();
+                if (lane == 0)
+                    for (uint32_t k = 0; k < 32 && k0 + k < nc; ++k) join_part(t, part[k]);
+                __syncwarp();
+            }
+            if (lane == 0) {
+                part[0] = t;
+                st->ticket = 0u;
+            }
         }
-        if (lane == 0) st->ticket = 0u;
     }
-    if (lane != 0) return;
+    __syncthreads();
 
-    pa_step_record *rec = P.rec + rd.rec_off + i;
-    const double lnQ = init ? 0.0 : st->lnQ;
-    rec->beta = P.beta[rd.beta_off + i];
-    rec->lnQ = lnQ;
-    rec->minus_betaF = init ? rd.ln2N : P.rec[rd.rec_off + i - 1].minus_betaF + lnQ;
-    rec->sumE = t.sE;
-    rec->sumE2 = t.sE2;
-    rec->sumAbsM = t.sAM;
-    rec->sumM2 = t.sM2;
-    rec->sum_c2 = t.c2;
-    rec->sumE3[0] = t.sE3.lo;
-    rec->sumE3[1] = (unsigned long long)t.sE3.hi;
-    rec->sumE4[0] = t.sE4.lo;
-    rec->sumE4[1] = (unsigned long long)t.sE4.hi;
-    rec->sumAbsM3[0] = t.sAM3.lo;
-    rec->sumAbsM3[1] = (unsigned long long)t.sAM3.hi;
-    rec->sumM4[0] = t.sM4.lo;
-    rec->sumM4[1] = (unsigned long long)t.sM4.hi;
-    rec->R = R;
-    rec->R_target = rd.R;
-    rec->n_fam = t.nfam;
-    rec->max_fam = t.cmax;
-    rec->N = rd.N;
-    rec->status = 0;
-    st->step = i;
-    st->R_cur = R;
-    st->R_new = R;
+    // the moments from the run's histograms, and the occupied energy levels
+    Moments mo = {0, 0, 0, 0, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}};
+    uint32_t elo = 0xffffffffu, ehi = 0u;
+    for (uint32_t n = tid; n < n1; n += nt) {
+        const uint32_t he = __ldcg(&gE[n]), hm = __ldcg(&gM[n]);
+        if (he) {
+            elo = n < elo ? n : elo;
+            ehi = n > ehi ? n : ehi;
+            const long long e = (long long)eb + 4ll * n;
+            const unsigned long long ae = (unsigned long long)(e < 0 ? -e : e), e2 = ae * ae;  // |E| <= 2^17
+            mo.sE += (long long)he * e;
+            mo.sE2 += (long long)((unsigned long long)he * e2);
+            const I128 t3 = mul_u64(he, ae * e2);
+            add128(mo.sE3, e < 0 ? neg128(t3) : t3);
+            add128(mo.sE4, mul_128_u64(mul_u64(he, e2), e2));
+        }
+        if (hm) {
+            const long long m = 2ll * n - (long long)N;
+            const unsigned long long am = (unsigned long long)(m < 0 ? -m : m), m2 = am * am;  // |M| <= 2^16
+            mo.sAM += (long long)((unsigned long long)hm * am);
+            mo.sM2 += (long long)((unsigned long long)hm * m2);
+            add128(mo.sAM3, mul_u64(hm, am * m2));
+            add128(mo.sM4, mul_128_u64(mul_u64(hm, m2), m2));
+        }
+    }
+    mo.sE = warp_sum(mo.sE);
+    mo.sE2 = warp_sum(mo.sE2);
+    mo.sAM = warp_sum(mo.sAM);
+    mo.sM2 = warp_sum(mo.sM2);
+    mo.sE3 = warp_sum128(mo.sE3);
+    mo.sE4 = warp_sum128(mo.sE4);
+    mo.sAM3 = warp_sum128(mo.sAM3);
+    mo.sM4 = warp_sum128(mo.sM4);
+    elo = warp_min(elo);
+    ehi = warp_max(ehi);
+    if (lane == 0) {
+        mom[wid] = mo;
+        reinterpret_cast<uint32_t *>(sh_h[0])[wid] = elo;  // the counters are no longer needed
+        reinterpret_cast<uint32_t *>(sh_h[1])[wid] = ehi;
+    }
+    __syncthreads();
+    const bool prep = rd.resample != PA_MULTINOMIAL && i + 1 < rd.n_beta;
+    if (tid == 0) {
+        Moments t = mom[0];
+        uint32_t l = sh_h[0][0], h = sh_h[1][0];
+        for (uint32_t k = 1; k < nw; ++k) {
+            const Moments &q = mom[k];
+            t.sE += q.sE;
+            t.sE2 += q.sE2;
+            t.sAM += q.sAM;
+            t.sM2 += q.sM2;
+            add128(t.sE3, q.sE3);
+            add128(t.sE4, q.sE4);
+            add128(t.sAM3, q.sAM3);
+            add128(t.sM4, q.sM4);
+            l = sh_h[0][k] < l ? sh_h[0][k] : l;
+            h = sh_h[1][k] > h ? sh_h[1][k] : h;
+        }
+        const FamPart f = part[0];
+        pa_step_record *rec = P.rec + rd.rec_off + i;
+        const double lnQ = init ? 0.0 : st->lnQ;
+        rec->beta = P.beta[rd.beta_off + i];
+        rec->lnQ = lnQ;
+        rec->minus_betaF = init ? rd.ln2N : P.rec[rd.rec_off + i - 1].minus_betaF + lnQ;
+        rec->sumE = t.sE;
+        rec->sumE2 = t.sE2;
+        rec->sumAbsM = t.sAM;
+        rec->sumM2 = t.sM2;
+        rec->sum_c2 = f.c2;
+        rec->sumE3[0] = t.sE3.lo;
+        rec->sumE3[1] = (unsigned long long)t.sE3.hi;
+        rec->sumE4[0] = t.sE4.lo;
+        rec->sumE4[1] = (unsigned long long)t.sE4.hi;
+        rec->sumAbsM3[0] = t.sAM3.lo;
+        rec->sumAbsM3[1] = (unsigned long long)t.sAM3.hi;
+        rec->sumM4[0] = t.sM4.lo;
+        rec->sumM4[1] = (unsigned long long)t.sM4.hi;
+        rec->R = R;
+        rec->R_target = rd.R;
+        rec->n_fam = f.nfam;
+        rec->max_fam = f.cmax;
+        rec->N = rd.N;
+        rec->status = 0;
+        st->step = i;
+        st->R_cur = R;
+        st->R_new = R;
+        sh_lohi[0] = l;
+        sh_lohi[1] = h;
+    }
+    __syncthreads();
+    if (prep) {  // S, ln Q and E_min of the next resampling
+        const uint32_t l = sh_lohi[0], nb = sh_lohi[1] - l + 1;
+        const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];  // exp(-4 n dbeta_{i+1})
+        // the terms h_n w[n] in parallel (the counters' shared memory is free now),
+        // then their sum by one thread in ascending order
+        double *terms = reinterpret_cast<double *>(&sh_h[0][0]);
+        const bool staged = nb <= MEASURE_SMEM_TERMS;
+        if (staged) {
+            for (uint32_t n = tid; n < nb; n += nt) terms[n] = __dmul_rn((double)__ldcg(&gE[l + n]), wt[n]);
+            __syncthreads();
+        }
+        if (tid == 0) {
+            double S = 0.0;
+            if (staged)
+                for (uint32_t n = 0; n < nb; ++n) S = __dadd_rn(S, terms[n]);
+            else
+                for (uint32_t n = 0; n < nb; ++n) S = __dadd_rn(S, __dmul_rn((double)__ldcg(&gE[l + n]), wt[n]));
+            const int32_t Emin = eb + 4 * (int32_t)l;
+            const double dbeta = P.beta[rd.beta_off + i + 1] - P.beta[rd.beta_off + i];
+            sh_S = S;
+            st->lnQ = (-dbeta) * (double)Emin + log(S) - log((double)R);
+            st->Emin = Emin;
+            st->n_levels = nb;
+        }
+        __syncthreads();
+        // per level: floor(tau) and the draw threshold, tau = R_target w[n] / S
+        const double S = sh_S;
+        unsigned long long *thr = scr + scr_table_off(N);
+        uint32_t *flo = reinterpret_cast<uint32_t *>(scr + scr_level_off(N));
+        for (uint32_t n = tid; n < nb; n += nt) {
+            const double tau = __ddiv_rn(__dmul_rn((double)rd.R, wt[n]), S);
+            const double fl = floor(tau);
+            flo[n] = (uint32_t)fl;
+            thr[n] = (unsigned long long)ceil(__dmul_rn(__dsub_rn(tau, fl), 4294967296.0));
+        }
+    }
+    for (uint32_t n = tid; n < n1; n += nt) {  // cleared for the next step
+        gE[n] = 0u;
+        gM[n] = 0u;
+    }
 }
 
 // A record's 128-bit sum as a double: sign and magnitude, then hi 2^64 + lo
@@ -2308,7 +2459,6 @@ void launch_resample_nearest(const Pool &P, const uint32_t *runs, uint32_t n_run
 {
     if (n_runs == 0) return;
     const dim3 grid(n_runs, run_ctas(max_Rcap));
-    resample_levels_kernel<<<grid, RESAMPLE_THREADS, 0, s>>>(P, runs);
     resample_counts_kernel<<<grid, RESAMPLE_THREADS, 0, s>>>(P, runs);
     resample_parents_kernel<<<grid, RESAMPLE_THREADS, 0, s>>>(P, runs);
 }

@@ -79,6 +79,7 @@ def test_status_strings(lib):
     dict(betas=np.array([0.0, 0.5, 0.4])), dict(betas=np.array([])), dict(overlap=8),
     dict(theta=W.THETA_INF), dict(theta=W.THETA_INF, log_g=np.zeros(129), overlap=1),
     dict(theta=W.THETA_INF, log_g=np.full(129, -np.inf)), dict(theta=W.THETA_INF, log_g=np.full(129, np.nan)),
+    dict(theta=W.THETA_INF, log_g=np.where(np.arange(129) < 2, 0.0, -np.inf)),
     dict(theta=(1 << 22) + 1), dict(overlap=W.Q_WANG, R=9000), dict(overlap=W.Q_WANG, R=8000, R_cap=8193),
 ])
 def test_invalid_descriptors_rejected_before_any_device_work(lib, bad):

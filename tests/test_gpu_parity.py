@@ -115,11 +115,11 @@ def test_multinomial_resampling():
 
 
 def test_populations_split_over_several_ctas():
-    """Populations of more than 4096 replicas are measured and (nearest-integer)
+    """Populations of more than 16384 replicas are measured and (nearest-integer)
     resampled by several CTAs each, with families crossing the CTAs'
     boundaries; a small run and a multinomial run share the same launches."""
-    descs = [W.RunDesc(8, W.FERRO, 9000, 1, W.schedule(0.6, 10), seed=6, run_id=0),
-             W.RunDesc(6, W.EA_PMJ, 13000, 1, W.schedule(2.5, 9), seed=6, run_id=1, disorder_id=2),
+    descs = [W.RunDesc(8, W.FERRO, 40000, 1, W.schedule(0.6, 7), seed=6, run_id=0),
+             W.RunDesc(6, W.EA_PMJ, 20000, 1, W.schedule(2.5, 8), seed=6, run_id=1, disorder_id=2),
              W.RunDesc(8, W.FERRO, 300, 2, W.schedule(0.5, 7), seed=6, run_id=2),
              W.RunDesc(8, W.EA_PMJ, 8300, 1, W.schedule(2.0, 6), seed=6, run_id=3, disorder_id=1,
                        resample=W.MULTINOMIAL)]

@@ -65,10 +65,10 @@ def test_theta_inf_runs_bit_exact(L, model, R, resample):
             check(eng, descs, ora, k)
 
 
-@pytest.mark.parametrize("R,resample", [(9000, 0), (20000, 0), (6000, 1)])
+@pytest.mark.parametrize("R,resample", [(20000, 0), (36000, 0), (6000, 1)])
 def test_theta_inf_populations_over_several_ctas(R, resample):
     """Populations spanning several CTAs of the draw, resampling and
-    measurement kernels (4096 replicas per CTA), L = 8 ferromagnet."""
+    measurement kernels (16384 replicas per CTA), L = 8 ferromagnet."""
     betas = W.schedule(0.6, 13)
     descs = [_inf(8, 0, R, betas, r, resample=resample) for r in range(2)]
     ora = oracle_runs(descs)
