@@ -800,7 +800,8 @@ void enqueue_wang(pa_engine *e)
 }
 
 // Resampling of every resident run: the nearest-integer runs split over
-// several CTAs each (three launches), the multinomial runs one CTA each.
+// several CTAs each (two launches; one when every population fits one CTA),
+// the multinomial runs one CTA each.
 void enqueue_resample(pa_engine *e)
 {
     if (!e->near_runs.empty()) {
@@ -808,7 +809,7 @@ void enqueue_resample(pa_engine *e)
             launch_resample_nearest(e->P, meta(e, e->near_off), (uint32_t)e->near_runs.size(), e->near_maxcap,
                                     e->stream);
         });
-        e->launches += RESAMPLE_NEAREST_LAUNCHES - 1;
+        e->launches += resample_nearest_launches(e->near_maxcap) - 1;
     }
     if (!e->multi_runs.empty())
         timed_launch(e, PA_K_RESAMPLE, [&] {

@@ -165,8 +165,9 @@ void launch_resample_multinomial(const Pool &P, const uint32_t *runs, uint32_t n
                                  cudaStream_t s);
 // Nearest-integer resampling (PA_NEAREST) from the tables the measurement of
 // the previous step prepared, run_ctas(R_cap) CTAs per run, in
-// RESAMPLE_NEAREST_LAUNCHES kernel launches.
-constexpr uint32_t RESAMPLE_NEAREST_LAUNCHES = 2;
+// resample_nearest_launches(max_Rcap) kernel launches (one when every
+// population fits one CTA).
+inline uint32_t resample_nearest_launches(uint32_t max_Rcap) { return run_ctas(max_Rcap) == 1 ? 1u : 2u; }
 void launch_resample_nearest(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t max_Rcap, cudaStream_t s);
 // Launch shapes to try for lattice size L (first = default); one entry unless
 // the bit-sliced kernel applies.

@@ -584,14 +584,92 @@ __device__ __forceinline__ RunChunk cta_chunk(uint32_t R, uint32_t nc, uint32_t 
     return {lo, min(R, lo + chunk)};
 }
 
+// The parent map of one CTA's chunk (copy numbers in cnt, written before a
+// barrier): exclusive offsets from `off` (the earlier CTAs' copies) plus a scan
+// per warp chunk; the CTA holding the run's first chunk records the new size
+// R_new = total and the capacity or extinction status.
+__device__ __forceinline__ void parents_pass(const Pool &P, uint32_t run, const RunDev &rd, RunState *st, uint32_t i,
+                                             RunChunk ch, uint32_t off, uint32_t total, bool first_cta,
+                                             uint32_t *sh_u)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5, nwarp = blockDim.x >> 5;
+    const uint32_t *cnt = P.cnt + rd.rep_off;
+    uint32_t *parent = P.parent + rd.rep_off;
+    // each warp takes a contiguous piece of the CTA's chunk, PARENT_BATCH rows of
+    // 32 at a time; the first batch stays in registers between the two passes
+    const uint32_t wchunk = (ch.hi - ch.lo + nwarp - 1) / nwarp;
+    const uint32_t w_lo = min(ch.hi, ch.lo + wid * wchunk), w_hi = min(ch.hi, w_lo + wchunk);
+    uint32_t wsum = 0, cq[PARENT_BATCH];
+    for (uint32_t b0 = w_lo; b0 < w_hi; b0 += 32 * PARENT_BATCH) {
+        uint32_t t[PARENT_BATCH];
+#pragma unroll
+        for (uint32_t r = 0; r < PARENT_BATCH; ++r) {
+            const uint32_t j = b0 + 32 * r + lane;
+            t[r] = j < w_hi ? cnt[j] : 0u;
+            wsum += t[r];
+        }
+        if (b0 == w_lo)
+#pragma unroll
+            for (uint32_t r = 0; r < PARENT_BATCH; ++r) cq[r] = t[r];
+    }
+    wsum = warp_sum(wsum);
+    if (lane == 0) sh_u[wid] = wsum;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t acc = off;
+        for (uint32_t k = 0; k < nwarp; ++k) {
+            const uint32_t v = sh_u[k];
+            sh_u[k] = acc;
+            acc += v;
+        }
+    }
+    __syncthreads();
+    uint32_t carry = sh_u[wid];
+    for (uint32_t b0 = w_lo; b0 < w_hi; b0 += 32 * PARENT_BATCH) {
+        uint32_t t[PARENT_BATCH];
+#pragma unroll
+        for (uint32_t r = 0; r < PARENT_BATCH; ++r) {
+            const uint32_t j = b0 + 32 * r + lane;
+            t[r] = b0 == w_lo ? cq[r] : (j < w_hi ? cnt[j] : 0u);
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < PARENT_BATCH; ++q) {
+            if (b0 + 32 * q >= w_hi) break;  // uniform over the warp
+            const uint32_t j = b0 + 32 * q + lane, r = t[q];
+            uint32_t x = r;  // inclusive scan over the lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, x, o);
+                if ((int)lane >= o) x += y;
+            }
+            const uint32_t o = carry + x - r;
+            for (uint32_t c = 0; c < r; ++c)
+                if (o + c < rd.R_cap) parent[o + c] = j;
+            carry += __shfl_sync(FULL, x, 31);
+        }
+    }
+    if (first_cta && tid == 0) {
+        const uint32_t Rn = total;
+        st->R_new = Rn;
+        if (Rn == 0)
+            set_status(P, run, PA_ERR_EXTINCT);
+        else if (Rn > rd.R_cap)
+            set_status(P, run, PA_ERR_CAPACITY);
+        if (Rn == 0 || Rn > rd.R_cap) P.rec[rd.rec_off + i].status = st->status;
+    }
+}
+
+// FUSED (every run in one CTA): the parent map follows in the same CTA.
+template <bool FUSED>
 __global__ void __launch_bounds__(RESAMPLE_THREADS, 2) resample_counts_kernel(Pool P, const uint32_t *runs)
 {
     __shared__ unsigned long long s_thr[COUNTS_SMEM_LEVELS];
     __shared__ uint32_t s_flo[COUNTS_SMEM_LEVELS];
     __shared__ uint32_t sh_r[32];
+    __shared__ uint32_t sh_u[RESAMPLE_THREADS / 32];
     const uint32_t run = runs[blockIdx.x];
     const RunDev rd = P.runs[run];
-    const RunState *st = &P.st[run];
+    RunState *st = &P.st[run];
     if (st->status) return;
     const uint32_t i = st->step + 1;
     if (i >= rd.n_beta) return;
@@ -643,8 +721,11 @@ __global__ void __launch_bounds__(RESAMPLE_THREADS, 2) resample_counts_kernel(Po
             sum += c;
         }
     }
-    sum = block_sum(sum, sh_r);
-    if (tid == 0) reinterpret_cast<uint32_t *>(P.scratch + rd.scr_off + scr_tail_off(rd.N))[blockIdx.y] = sum;
+    sum = block_sum(sum, sh_r);  // ends with a barrier: this CTA's copy numbers are visible
+    if (FUSED)
+        parents_pass(P, run, rd, st, i, ch, 0u, sum, true, sh_u);
+    else if (tid == 0)
+        reinterpret_cast<uint32_t *>(P.scratch + rd.scr_off + scr_tail_off(rd.N))[blockIdx.y] = sum;
 }
 
 __global__ void __launch_bounds__(RESAMPLE_THREADS) resample_parents_kernel(Pool P, const uint32_t *runs)
@@ -659,15 +740,10 @@ __global__ void __launch_bounds__(RESAMPLE_THREADS) resample_parents_kernel(Pool
     if (i >= rd.n_beta) return;
     const uint32_t nc = min(gridDim.y, run_ctas(rd.R_cap));
     if (blockIdx.y >= nc) return;
-    const uint32_t Rprev = st->R_cur;
-    const RunChunk ch = cta_chunk(Rprev, nc, blockIdx.y);
+    const RunChunk ch = cta_chunk(st->R_cur, nc, blockIdx.y);
     const uint32_t *cta_tot = reinterpret_cast<const uint32_t *>(P.scratch + rd.scr_off + scr_tail_off(rd.N));
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5, nwarp = blockDim.x >> 5;
-    const uint32_t *cnt = P.cnt + rd.rep_off;
-    uint32_t *parent = P.parent + rd.rep_off;
-
-    // warp 0: the earlier CTAs' totals (this CTA's offset) and, in CTA 0, the new size
-    if (wid == 0) {
+    if (threadIdx.x < 32) {  // the earlier CTAs' totals (this CTA's offset) and the new size
+        const uint32_t lane = threadIdx.x;
         uint32_t before = 0, all = 0;
         for (uint32_t k = lane; k < nc; k += 32) {
             const uint32_t v = cta_tot[k];
@@ -681,68 +757,8 @@ __global__ void __launch_bounds__(RESAMPLE_THREADS) resample_parents_kernel(Pool
             sh_total = all;
         }
     }
-    // each warp takes a contiguous piece of the CTA's chunk, PARENT_BATCH rows of
-    // 32 at a time; the first batch stays in registers between the two passes
-    const uint32_t wchunk = (ch.hi - ch.lo + nwarp - 1) / nwarp;
-    const uint32_t w_lo = min(ch.hi, ch.lo + wid * wchunk), w_hi = min(ch.hi, w_lo + wchunk);
-    uint32_t wsum = 0, cq[PARENT_BATCH];
-    for (uint32_t b0 = w_lo; b0 < w_hi; b0 += 32 * PARENT_BATCH) {
-        uint32_t t[PARENT_BATCH];
-#pragma unroll
-        for (uint32_t r = 0; r < PARENT_BATCH; ++r) {
-            const uint32_t j = b0 + 32 * r + lane;
-            t[r] = j < w_hi ? cnt[j] : 0u;
-            wsum += t[r];
-        }
-        if (b0 == w_lo)
-#pragma unroll
-            for (uint32_t r = 0; r < PARENT_BATCH; ++r) cq[r] = t[r];
-    }
-    wsum = warp_sum(wsum);
-    if (lane == 0) sh_u[wid] = wsum;
     __syncthreads();
-    if (tid == 0) {
-        uint32_t acc = sh_off;
-        for (uint32_t k = 0; k < nwarp; ++k) {
-            const uint32_t v = sh_u[k];
-            sh_u[k] = acc;
-            acc += v;
-        }
-    }
-    __syncthreads();
-    uint32_t carry = sh_u[wid];
-    for (uint32_t b0 = w_lo; b0 < w_hi; b0 += 32 * PARENT_BATCH) {
-        uint32_t t[PARENT_BATCH];
-#pragma unroll
-        for (uint32_t r = 0; r < PARENT_BATCH; ++r) {
-            const uint32_t j = b0 + 32 * r + lane;
-            t[r] = b0 == w_lo ? cq[r] : (j < w_hi ? cnt[j] : 0u);
-        }
-#pragma unroll
-        for (uint32_t q = 0; q < PARENT_BATCH; ++q) {
-            if (b0 + 32 * q >= w_hi) break;  // uniform over the warp
-            const uint32_t j = b0 + 32 * q + lane, r = t[q];
-            uint32_t x = r;  // inclusive scan over the lanes
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(FULL, x, o);
-                if ((int)lane >= o) x += y;
-            }
-            const uint32_t o = carry + x - r;
-            for (uint32_t c = 0; c < r; ++c)
-                if (o + c < rd.R_cap) parent[o + c] = j;
-            carry += __shfl_sync(FULL, x, 31);
-        }
-    }
-    if (blockIdx.y == 0 && tid == 0) {
-        const uint32_t Rn = sh_total;
-        st->R_new = Rn;
-        if (Rn == 0)
-            set_status(P, run, PA_ERR_EXTINCT);
-        else if (Rn > rd.R_cap)
-            set_status(P, run, PA_ERR_CAPACITY);
-        if (Rn == 0 || Rn > rd.R_cap) P.rec[rd.rec_off + i].status = st->status;
-    }
+    parents_pass(P, run, rd, st, i, ch, sh_off, sh_total, blockIdx.y == 0, sh_u);
 }
 
 // --------------------------------------------------------------------------
@@ -2459,7 +2475,11 @@ void launch_resample_nearest(const Pool &P, const uint32_t *runs, uint32_t n_run
 {
     if (n_runs == 0) return;
     const dim3 grid(n_runs, run_ctas(max_Rcap));
-    resample_counts_kernel<<<grid, RESAMPLE_THREADS, 0, s>>>(P, runs);
+    if (grid.y == 1) {  // every population in one CTA: one launch
+        resample_counts_kernel<true><<<grid, RESAMPLE_THREADS, 0, s>>>(P, runs);
+        return;
+    }
+    resample_counts_kernel<false><<<grid, RESAMPLE_THREADS, 0, s>>>(P, runs);
     resample_parents_kernel<<<grid, RESAMPLE_THREADS, 0, s>>>(P, runs);
 }
 
