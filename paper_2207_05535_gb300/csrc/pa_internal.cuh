@@ -154,7 +154,8 @@ inline uint64_t scratch_words(uint32_t N, uint32_t R_cap)
 }
 
 // Launch wrappers implemented in pa_kernels.cu (all asynchronous on `s`).
-// `runs`: indices of the runs to process (NULL: runs 0..n_runs-1).
+// `runs`: device list of the indices of the runs to process (the two
+// initialisation launches also take NULL for runs 0..n_runs-1).
 void launch_init_couplings(const Pool &P, const uint32_t *runs, uint32_t n_runs, cudaStream_t s);
 // Work lists: tile_off = prefix of per-run tile counts (n + 1 entries).
 void launch_init_population(const Pool &P, const uint32_t *tile_off, const uint32_t *runs, uint32_t n_runs,

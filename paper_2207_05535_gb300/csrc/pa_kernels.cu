@@ -1,19 +1,31 @@
 // Kernels of the population-annealing hot path for sm_103a (GB300).
 //
-// One anneal step (arXiv:2207.05535, Sec. II.B steps (ii)-(v)) is four launches
-// over every run of the engine:
-//   resample_kernel  one CTA per run: energy-level histogram, FP64 normalisation
-//                    Q_i (Eq. QBoltz), copy numbers r_j (nearest-integer, or
-//                    multinomial), exclusive scan and the parent map that places
-//                    copies of one ancestor next to each other (Sec. V.A.1)
-//   sweep_kernel     per lattice size: each replica is gathered from its parent
-//                    (the resampling copy), unpacked into shared memory as two
-//                    checkerboard colour planes, swept theta times with Philox
-//                    thresholds (Sec. V.A.1), packed and written back
-//   overlap_kernel   XOR + popcount overlaps of index-shift pairs j <-> j+floor(R/2)
-//                    and of pairs with a partner population (Sec. III.D)
-//   measure_kernel   integer reductions of E^k, |M|^k (k <= 4; 128-bit for k >= 3), family statistics
-//                    (Eq. rho_t) and the free-energy running sum (Eq. F)
+// One anneal step (arXiv:2207.05535, Sec. II.B steps (ii)-(v)) runs over every
+// run of the engine in a handful of launches:
+//   resample_counts_kernel / resample_parents_kernel
+//                    nearest-integer resampling, a population split over several
+//                    CTAs: copy numbers r_j from the per-level tables the previous
+//                    measurement prepared, then the exclusive scan and the parent
+//                    map that places copies of one ancestor next to each other
+//                    (Sec. V.A.1); one launch when every population fits one CTA
+//   resample_multinomial_kernel
+//                    multinomial resampling, one CTA per run (level histogram,
+//                    Q_i of Eq. QBoltz, R draws, scan, parent map)
+//   sweep_pow2_kernel / sweep_pad_kernel / sweep_kernel
+//                    per lattice size: each replica is gathered from its parent
+//                    (the resampling copy) and swept theta times with Philox
+//                    thresholds (Sec. V.A.1), bit-sliced where L/2 allows
+//   dos_sample_kernel
+//                    theta = infinity runs (Sec. V.B): fresh energies from the exact
+//                    distribution instead of sweeps
+//   overlap_kernel / wang_kernel
+//                    overlaps of index-shift pairs, partner populations and Wang
+//                    et al.'s pairings (Sec. III.D)
+//   measure_kernel   moments of E and |M| (k <= 4, exact integers) from per-level
+//                    histograms, family statistics (Eq. rho_t), the free-energy
+//                    running sum (Eq. F), and the next nearest-integer resampling's
+//                    E_min, Q_{i+1} and per-level tables
+// The weighted averages of Sec. IV run after the anneal (wavg_*_kernel).
 // Nothing here allocates memory; no spin-wait exists in any kernel.
 //
 // Randomness: Philox4x32-10 (Salmon et al., SC'11), key (seed, run_id):
@@ -23,6 +35,8 @@
 //   nearest-integer draw of j  ctr (j, 0, i, RESAMPLE<<24)               word 0
 //   multinomial draw d         ctr (d, 0, i, MULTINOMIAL<<24)            words 0,1 level; word 2 member
 //   Metropolis, sublattice k   ctr (k>>2, child, i, SWEEP<<24|t<<1|c)     word k&3
+//   theta = infinity draw of j ctr (j, 0, i, DOS<<24)                    words 0,1 (53-bit uniform)
+//   Wang keys of replica j     ctr (j, 0, i, WANG<<24)                   words 0,1 pi, words 2,3 sigma
 // FP64 arithmetic that decides an integer uses explicit round-to-nearest
 // intrinsics (no contraction), in the same order as the plain definition.
 #include <cuda_runtime.h>
