@@ -88,10 +88,8 @@ def work_units(d, R):
 # DRAM bytes per sweep launch from one ncu capture (profiles/sweep_pow2_glass_L16_R5000.md),
 # valid only for the kernel source it was taken on.
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu (the commands are in profiles/)
-TRAFFIC = [{"kernel": "sweep", "workload": "glass_L16_R5000", "source_sha256_16": "58ec477f7e7a53a0",
-            "bytes_per_launch": 44.164096e6},
-           {"kernel": "measure", "workload": "ferro_L8_theta_inf", "source_sha256_16": "aa5cfcf5a394c4e6",
-            "bytes_per_launch": 48.396928e6}]
+TRAFFIC = [{"kernel": "sweep", "workload": "glass_L16_R5000", "source_sha256_16": "a605edff3d3727c8",
+            "bytes_per_launch": 44.134144e6}]
 MULADD_LANES_PER_SM = 64
 
 
