@@ -145,3 +145,86 @@ int main() {
         if line:
             L, pw = (int(x) for x in line.split())
             assert bench.plane_words(L) == pw, L
+
+
+def test_run_scratch_regions_fit_and_do_not_overlap(tmp_path):
+    """A run's scratch (histograms, level tables, and the tail shared by the
+    multinomial member list, the per-CTA totals and the per-CTA family
+    statistics) holds every region the kernels index, for any lattice size and
+    capacity; the CTA count of a run covers its replicas."""
+    prog = tmp_path / "scr.cpp"
+    prog.write_text(r'''
+#include <cstdio>
+#include <cuda_runtime.h>
+#include "pa_internal.cuh"
+int main() {
+  const unsigned caps[] = {1u, 2u, 31u, 4096u, 16383u, 16384u, 16385u, 100000u, 1000000u, 5000000u, 4200000000u};
+  for (unsigned L = 4; L <= 256; L += 2)
+    for (unsigned cap : caps) {
+      const unsigned N = L * L;
+      std::printf("%u %u %llu %llu %llu %llu %llu %u %u %u %u %llu\n", N, cap,
+                  (unsigned long long)pa::scr_mhist_off(N), (unsigned long long)pa::scr_table_off(N),
+                  (unsigned long long)pa::scr_level_off(N), (unsigned long long)pa::scr_tail_off(N),
+                  (unsigned long long)pa::scratch_words(N, cap), pa::run_ctas(cap), pa::CTA_REPLICAS,
+                  pa::MAX_RUN_CTAS, pa::resample_nearest_launches(cap),
+                  (unsigned long long)pa::MEASURE_PART_WORDS);
+    }
+  return 0;
+}
+''')
+    exe = tmp_path / "scr"
+    subprocess.run(["g++", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I",
+                    os.path.join(ROOT, "paper_2207_05535_gb300", "csrc"), "-I", "/usr/local/cuda/include", str(prog),
+                    "-o", str(exe)], check=True)
+    rows = [list(map(int, line.split())) for line in
+            subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n") if line]
+    assert rows
+    for N, cap, mh, tab, lev, tail, words, nc, per_cta, max_ctas, launches, part_words in rows:
+        n1 = N + 1
+        assert 4 * n1 <= 8 * mh  # energy histogram, u32
+        assert 4 * n1 <= 8 * (tab - mh)  # magnetisation histogram, u32
+        assert 8 * n1 <= 8 * (lev - tab)  # CDF / thresholds, f64 / u64
+        assert 4 * n1 <= 8 * (tail - lev)  # fill counters / floors, u32
+        room = 8 * (words - tail)
+        assert room >= 4 * cap  # multinomial member list
+        assert room >= 4 * max_ctas  # per-CTA replica totals
+        assert room >= 8 * part_words * nc  # per-CTA family statistics
+        assert 1 <= nc <= max_ctas
+        assert nc == max_ctas or nc * per_cta >= cap
+        assert (nc - 1) * per_cta < cap or nc == 1
+        assert launches == (1 if nc == 1 else 2)
+
+
+def test_measured_traffic_is_keyed_by_each_kernels_own_source(tmp_path, monkeypatch):
+    """bench.py reports an ncu traffic figure only for the source it was taken
+    on: an edit in one kernel's section changes that kernel's hash and no other,
+    an edit in the shared header changes both."""
+    import shutil
+
+    import bench
+    src = os.path.join(ROOT, "paper_2207_05535_gb300", "csrc")
+    dst = tmp_path / "paper_2207_05535_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in ("pa_internal.cuh", "pa_kernels.cu"):
+        shutil.copy(os.path.join(src, f), dst / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    base = {k: bench.source_sha(k) for k in bench.KERNEL_SECTIONS}
+
+    def edit(name, marker, text):
+        p = dst / name
+        body = p.read_text()
+        i = body.index(marker) + len(marker)
+        p.write_text(body[:i] + text + body[i:])
+
+    edit("pa_kernels.cu", "// Measurement (Sec. III.B", " ")
+    assert bench.source_sha("sweep") == base["sweep"] and bench.source_sha("measure") != base["measure"]
+    edit("pa_kernels.cu", "// Overlaps (Sec. III.D)", " ")  # the end marker of the sweep section: outside it
+    assert bench.source_sha("sweep") == base["sweep"]
+    edit("pa_kernels.cu", "// Fused gather + theta checkerboard", " ")
+    assert bench.source_sha("sweep") != base["sweep"]
+    mid = {k: bench.source_sha(k) for k in bench.KERNEL_SECTIONS}
+    edit("pa_internal.cuh", "#pragma once", "\n")
+    assert all(bench.source_sha(k) != mid[k] for k in bench.KERNEL_SECTIONS)
+    monkeypatch.undo()
+    for t in bench.TRAFFIC:
+        assert bench.measured_traffic(t["kernel"], "no such workload") is None
