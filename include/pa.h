@@ -248,6 +248,28 @@ pa_status pa_population_slice(pa_engine *e, uint32_t run, uint32_t first, uint32
                               int32_t *host_E, int32_t *host_M, uint32_t *host_fam, uint32_t *R_out,
                               uint32_t *step_out);
 
+/* Checkpoint and resume of one run between anneal steps.  The state after
+ * temperature i of Sec. II.B is everything the rest of the anneal reads: the
+ * population at beta_i (spins, E, M, family ids), the records of steps 0..i
+ * (with ln Q and -beta F), the overlap histograms, the couplings, and the
+ * next resampling's level tables.  Counter-based randomness needs no
+ * generator state, so a resumed run continues exactly as if never stopped.
+ *
+ * pa_checkpoint copies run `run`'s state into host_buf.  *bytes: capacity of
+ * host_buf on entry, bytes written (or needed) on return; host_buf NULL asks
+ * for the size only.  PA_ERR_INVALID_ARG if the buffer is too small (*bytes
+ * then holds the size), PA_ERR_STATE if the run stopped with an error status.
+ * Synchronous (waits for the work queued before it).
+ *
+ * pa_restore overwrites run `run` of any engine with a checkpoint.  The run
+ * must have been admitted with the same descriptor (L, model, R, R_cap, theta,
+ * schedule, seed, run_id, disorder_id, resample, overlap); otherwise, or if
+ * the buffer is not a whole checkpoint, PA_ERR_INVALID_ARG and nothing is
+ * changed.  Paired runs (PA_Q_PAIR) are restored together, from checkpoints
+ * of the same step.  Synchronous; host_buf may be reused on return. */
+pa_status pa_checkpoint(pa_engine *e, uint32_t run, void *host_buf, size_t *bytes);
+pa_status pa_restore(pa_engine *e, uint32_t run, const void *host_buf, size_t bytes);
+
 /* Weighted averages (Sec. IV) over groups of runs resident in the engine:
  * group g holds runs run_idx[g*M .. g*M+M-1] (same N and n_beta).  Writes
  * host_out[g][n_beta] and, when non-NULL, the weighted overlap distributions

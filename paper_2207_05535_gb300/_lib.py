@@ -61,6 +61,7 @@ WAVG_DTYPE = np.dtype([
 
 EXPORTS = ["pa_create", "pa_create_ex", "pa_server_create", "pa_admit", "pa_retire", "pa_finished", "pa_run_state",
            "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population", "pa_population_slice",
+           "pa_checkpoint", "pa_restore",
            "pa_weighted_average_runs", "pa_weighted_average", "pa_weighted_average_noalloc", "pa_launch_count", "pa_set_profiling",
            "pa_kernel_times", "pa_transfer_bytes", "pa_calibrate_philox", "pa_sweep_shape", "pa_destroy", "pa_status_string"]
 KERNEL_KINDS = ["resample", "sweep", "overlap", "measure", "init", "wavg"]
@@ -95,6 +96,8 @@ def load(path: str = LIB_PATH):
         lib.pa_population.argtypes = [vp, u32, P(C.c_int8), P(C.c_int32), P(C.c_int32), P(u32), P(u32), P(u32)]
         lib.pa_population_slice.argtypes = [vp, u32, u32, u32, P(C.c_int8), P(C.c_int32), P(C.c_int32), P(u32),
                                             P(u32), P(u32)]
+        lib.pa_checkpoint.argtypes = [vp, u32, vp, P(C.c_size_t)]
+        lib.pa_restore.argtypes = [vp, u32, vp, C.c_size_t]
         lib.pa_weighted_average_runs.argtypes = [vp, P(u32), u32, u32, u32, vp, P(C.c_double), P(C.c_double),
                                                  P(C.c_double)]
         lib.pa_weighted_average.argtypes = [vp, P(u32), P(u32), P(u32), u32, u32, u32, u32, vp, P(C.c_double),
@@ -257,6 +260,21 @@ def pa_population_slice(h, run, first, count, N, spins=True):
     return (s[:n] if spins else None), E[:n], M[:n], fam[:n], R.value, step.value
 
 
+def pa_checkpoint(h, run):
+    """Run `run`'s state between anneal steps, as bytes (see pa.h)."""
+    n = C.c_size_t(0)
+    _check(load().pa_checkpoint(h, run, None, C.byref(n)), "pa_checkpoint")
+    buf = (C.c_char * n.value)()
+    _check(load().pa_checkpoint(h, run, buf, C.byref(n)), "pa_checkpoint")
+    return bytes(buf[:n.value])
+
+
+def pa_restore(h, run, data):
+    """Overwrite run `run` with a checkpoint taken by pa_checkpoint (see pa.h)."""
+    buf = C.create_string_buffer(bytes(data), len(data))
+    _check(load().pa_restore(h, run, buf, len(data)), "pa_restore")
+
+
 def pa_calibrate_philox(wide=False, reps=5, stream=None):
     """Philox4x32-10 calls per second on the current device (see pa.h)."""
     v = C.c_double(0.0)
@@ -383,6 +401,12 @@ class Engine:
     def records(self, run, qhist=False, wang=False):
         r = self.runs[run]
         return pa_records(self.h, run, r.n_beta, r.N, qhist, wang)
+
+    def checkpoint(self, run):
+        return pa_checkpoint(self.h, run)
+
+    def restore(self, run, data):
+        pa_restore(self.h, run, data)
 
     def population(self, run):
         r = self.runs[run]

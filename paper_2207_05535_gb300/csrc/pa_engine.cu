@@ -172,6 +172,7 @@ struct pa_engine {
     uint64_t launches = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_tick_launches = 0;  // kernel launches in one replay of the graph
     pa_status latched = PA_OK;
     bool profiling = false;
     std::vector<cudaEvent_t> ev_free;
@@ -959,6 +960,51 @@ pa_status engine_new(void *cuda_stream, uint32_t flags, pa_engine **out)
 
 bool slot_ok(const pa_engine *e, uint32_t s) { return e && s < e->S && e->rh[s].used; }
 
+// Checkpoint of one run: a fixed header, the run state, the schedule, then the
+// device sections below in this order.
+constexpr char CKPT_MAGIC[8] = {'P', 'A', 'C', 'K', 'P', 'T', '0', '1'};
+struct CkptHeader {
+    char magic[8];
+    uint32_t L, model, R, R_cap, theta, n_beta, seed, run_id, disorder_id, resample, overlap;
+    uint32_t steps_done, R_cur, buffer, wstride, pad;
+    uint64_t scratch_words, J_words, total_bytes;
+};
+
+struct CkptSection {
+    void *dev;      // device address
+    size_t bytes;
+};
+
+// The run's device sections, given its state (population of buffer st.step & 1).
+std::vector<CkptSection> ckpt_sections(pa_engine *e, uint32_t run, const RunState &st)
+{
+    const RunDev &x = e->rd[run];
+    const uint32_t b = st.step & 1u;
+    const uint64_t nq = (uint64_t)x.n_beta * (x.N + 1);
+    std::vector<CkptSection> v = {
+        {e->P.spins[b] + x.spin_off, sizeof(uint32_t) * (size_t)st.R_cur * x.wstride},
+        {e->P.E[b] + x.rep_off, sizeof(int32_t) * (size_t)st.R_cur},
+        {e->P.M[b] + x.rep_off, sizeof(int32_t) * (size_t)st.R_cur},
+        {e->P.fam[b] + x.rep_off, sizeof(uint32_t) * (size_t)st.R_cur},
+        {e->P.rec + x.rec_off, sizeof(pa_step_record) * (size_t)x.n_beta},
+        {e->P.scratch + x.scr_off, sizeof(unsigned long long) * (size_t)scratch_words(x.N, x.R_cap)},
+        {e->P.J + x.J_off, sizeof(uint32_t) * (size_t)(2ull * stride_words(x.L) + 8ull * plane_words(x.L))},
+    };
+    if (x.overlap) {
+        v.push_back({e->P.qh + x.qh_off, sizeof(uint32_t) * (size_t)nq});
+        v.push_back({e->P.qhp + x.qh_off, sizeof(uint32_t) * (size_t)nq});
+        v.push_back({e->P.qhw + x.qh_off, sizeof(uint32_t) * (size_t)nq});
+    }
+    return v;
+}
+
+size_t ckpt_bytes(const RunDev &x, const std::vector<CkptSection> &v)
+{
+    size_t n = sizeof(CkptHeader) + sizeof(RunState) + sizeof(double) * x.n_beta;
+    for (const auto &c : v) n += c.bytes;
+    return n;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1176,11 +1222,11 @@ pa_status pa_anneal_step(pa_engine *e, uint32_t n_steps, int use_graph)
             enqueue_tick(e);
             PA_CUDA(cudaStreamEndCapture(e->stream, &e->graph));
             PA_CUDA(cudaGraphInstantiate(&e->graph_exec, e->graph, 0));
-            e->launches = l0;  // capturing launched nothing
+            e->graph_tick_launches = e->launches - l0;  // the kernels one replay launches
+            e->launches = l0;                            // capturing launched nothing
         }
-        const uint64_t per_tick = 2 + e->groups.size() + (e->q_runs.empty() ? 0 : 1);
         for (uint32_t k = 0; k < n_steps; ++k) PA_CUDA(cudaGraphLaunch(e->graph_exec, e->stream));
-        e->launches += per_tick * n_steps;
+        e->launches += e->graph_tick_launches * n_steps;
     } else {
         for (uint32_t k = 0; k < n_steps; ++k) enqueue_tick(e);
         PA_CUDA(cudaGetLastError());
@@ -1511,4 +1557,106 @@ pa_status pa_weighted_average(const pa_step_record *recs, const uint32_t *qhist,
     return s;
 }
 
+pa_status pa_checkpoint(pa_engine *e, uint32_t run, void *host_buf, size_t *bytes)
+{
+    if (!slot_ok(e, run) || !bytes) return PA_ERR_INVALID_ARG;
+    PA_TRY(prepare(e));
+    const RunDev &x = e->rd[run];
+    RunState st;
+    PA_CUDA(cudaMemcpyAsync(&st, e->P.st + run, sizeof st, cudaMemcpyDeviceToHost, e->stream));
+    PA_CUDA(cudaStreamSynchronize(e->stream));
+    if (st.status) return PA_ERR_STATE;  // a stopped run is inspected, not resumed
+    const std::vector<CkptSection> sec = ckpt_sections(e, run, st);
+    const size_t need = ckpt_bytes(x, sec);
+    if (!host_buf) {
+        *bytes = need;
+        return PA_OK;
+    }
+    if (*bytes < need) {
+        *bytes = need;
+        return PA_ERR_INVALID_ARG;
+    }
+    const pa_run_desc &d = e->rh[run].d;
+    CkptHeader h{};
+    std::memcpy(h.magic, CKPT_MAGIC, sizeof h.magic);
+    h.L = d.L;
+    h.model = d.model;
+    h.R = d.R;
+    h.R_cap = x.R_cap;
+    h.theta = d.theta;
+    h.n_beta = d.n_beta;
+    h.seed = d.seed;
+    h.run_id = d.run_id;
+    h.disorder_id = d.disorder_id;
+    h.resample = d.resample;
+    h.overlap = d.overlap;
+    h.steps_done = e->rh[run].steps_done;
+    h.R_cur = st.R_cur;
+    h.buffer = st.step & 1u;
+    h.wstride = x.wstride;
+    h.scratch_words = scratch_words(x.N, x.R_cap);
+    h.J_words = 2ull * stride_words(x.L) + 8ull * plane_words(x.L);
+    h.total_bytes = need;
+    char *out = static_cast<char *>(host_buf);
+    std::memcpy(out, &h, sizeof h);
+    size_t o = sizeof h;
+    std::memcpy(out + o, &st, sizeof st);
+    o += sizeof st;
+    PA_CUDA(cudaMemcpyAsync(out + o, e->d_beta + x.beta_off, sizeof(double) * x.n_beta, cudaMemcpyDeviceToHost,
+                            e->stream));
+    o += sizeof(double) * x.n_beta;
+    for (const auto &c : sec) {
+        if (c.bytes) PA_CUDA(cudaMemcpyAsync(out + o, c.dev, c.bytes, cudaMemcpyDeviceToHost, e->stream));
+        o += c.bytes;
+    }
+    e->d2h += need;
+    *bytes = need;
+    return sync_read(e);
+}
+
+pa_status pa_restore(pa_engine *e, uint32_t run, const void *host_buf, size_t bytes)
+{
+    if (!slot_ok(e, run) || !host_buf || bytes < sizeof(CkptHeader) + sizeof(RunState)) return PA_ERR_INVALID_ARG;
+    PA_TRY(prepare(e));  // the slot's beta_0 draw, if pending, must not run after the restore
+    PA_CUDA(cudaStreamSynchronize(e->stream));
+    const RunDev &x = e->rd[run];
+    const pa_run_desc &d = e->rh[run].d;
+    CkptHeader h;
+    std::memcpy(&h, host_buf, sizeof h);
+    if (std::memcmp(h.magic, CKPT_MAGIC, sizeof h.magic) != 0 || h.total_bytes != bytes) return PA_ERR_INVALID_ARG;
+    if (h.L != d.L || h.model != d.model || h.R != d.R || h.R_cap != x.R_cap || h.theta != d.theta ||
+        h.n_beta != d.n_beta || h.seed != d.seed || h.run_id != d.run_id || h.disorder_id != d.disorder_id ||
+        h.resample != d.resample || h.overlap != d.overlap || h.wstride != x.wstride ||
+        h.scratch_words != scratch_words(x.N, x.R_cap) ||
+        h.J_words != 2ull * stride_words(x.L) + 8ull * plane_words(x.L))
+        return PA_ERR_INVALID_ARG;
+    const char *in = static_cast<const char *>(host_buf);
+    RunState st;
+    std::memcpy(&st, in + sizeof h, sizeof st);
+    if (st.R_cur != h.R_cur || (st.step & 1u) != h.buffer || st.R_cur > x.R_cap || st.step >= d.n_beta ||
+        h.steps_done != st.step)
+        return PA_ERR_INVALID_ARG;
+    std::vector<double> beta(x.n_beta);
+    PA_CUDA(cudaMemcpyAsync(beta.data(), e->d_beta + x.beta_off, sizeof(double) * x.n_beta, cudaMemcpyDeviceToHost,
+                            e->stream));
+    PA_CUDA(cudaStreamSynchronize(e->stream));
+    if (std::memcmp(beta.data(), in + sizeof h + sizeof st, sizeof(double) * x.n_beta) != 0)
+        return PA_ERR_INVALID_ARG;  // another schedule
+    const std::vector<CkptSection> sec = ckpt_sections(e, run, st);
+    if (ckpt_bytes(x, sec) != bytes) return PA_ERR_INVALID_ARG;
+    st.ticket = 0;
+    size_t o = sizeof h + sizeof st + sizeof(double) * x.n_beta;
+    for (const auto &c : sec) {
+        if (c.bytes) PA_CUDA(cudaMemcpyAsync(c.dev, in + o, c.bytes, cudaMemcpyHostToDevice, e->stream));
+        o += c.bytes;
+    }
+    PA_CUDA(cudaMemcpyAsync(e->P.st + run, &st, sizeof st, cudaMemcpyHostToDevice, e->stream));
+    PA_CUDA(cudaStreamSynchronize(e->stream));  // the caller's buffer and st must outlive the copies
+    e->h2d += bytes;
+    e->rh[run].steps_done = h.steps_done;
+    e->dirty = true;
+    return PA_OK;
+}
+
 }  // extern "C"
+
