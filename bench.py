@@ -85,9 +85,8 @@ def work_units(d, R):
     """Work of one temperature at population R: attempted spin updates (theta N R),
     or R energy draws for theta = infinity runs."""
     return R if d.theta == 0xFFFFFFFF else d.theta * d.N * R
-# DRAM bytes per sweep launch from one ncu capture (profiles/sweep_pow2_glass_L16_R5000.md),
-# valid only for the kernel source it was taken on.
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu (the commands are in profiles/)
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+# capture of the kernel, valid only for the kernel source it was taken on.
 TRAFFIC = [{"kernel": "sweep", "workload": "glass_L16_R5000", "source_sha256_16": "a605edff3d3727c8",
             "bytes_per_launch": 44.134144e6}]
 MULADD_LANES_PER_SM = 64

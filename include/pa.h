@@ -263,10 +263,13 @@ pa_status pa_population_slice(pa_engine *e, uint32_t run, uint32_t first, uint32
  *
  * pa_restore overwrites run `run` of any engine with a checkpoint.  The run
  * must have been admitted with the same descriptor (L, model, R, R_cap, theta,
- * schedule, seed, run_id, disorder_id, resample, overlap); otherwise, or if
- * the buffer is not a whole checkpoint, PA_ERR_INVALID_ARG and nothing is
- * changed.  Paired runs (PA_Q_PAIR) are restored together, from checkpoints
- * of the same step.  Synchronous; host_buf may be reused on return. */
+ * schedule, seed, run_id, disorder_id, resample, overlap, and for theta =
+ * PA_THETA_INF the same ln g); otherwise, or if the buffer is not a whole
+ * checkpoint, PA_ERR_INVALID_ARG and nothing is changed.  Paired runs
+ * (PA_Q_PAIR) are restored together, from checkpoints of the same step.  When
+ * no resident run is left stopped afterwards, the engine's latched error
+ * (capacity, extinction) is cleared, so a run that failed can be resumed from
+ * an earlier checkpoint.  Synchronous; host_buf may be reused on return. */
 pa_status pa_checkpoint(pa_engine *e, uint32_t run, void *host_buf, size_t *bytes);
 pa_status pa_restore(pa_engine *e, uint32_t run, const void *host_buf, size_t bytes);
 
@@ -294,11 +297,12 @@ pa_status pa_weighted_average(const pa_step_record *recs, const uint32_t *qhist,
 #define PA_NOALLOC_MAX_WEIGHTS 65536u  /* M * n_steps */
 
 /* Weighted averages (same arithmetic as pa_weighted_average, no overlap
- * distributions) for callers that cannot allocate device memory: work
- * recorded inside a CUDA graph capture, serving loops that reserve all device
- * memory up front and must not call into the allocator, or processes whose
- * device memory belongs to another allocator.  The paper has no counterpart;
- * this is a deployment variant.
+ * distributions) for callers that cannot allocate device memory: serving
+ * loops that reserve all device memory up front and must not call into the
+ * allocator in the steady state (cudaMalloc can synchronise the device and
+ * stall the other streams), or processes whose device memory belongs to
+ * another allocator (a framework's caching allocator or a pre-sized arena).
+ * The paper has no counterpart; this is a deployment variant.
  *   d_recs: device pointer, M * n_steps records laid out [m][i] (run m, step i);
  *   d_out:  device pointer, n_steps results; N: spins per run.
  * Nothing is allocated or freed.  The scratch (record offsets and weights) is
@@ -306,8 +310,10 @@ pa_status pa_weighted_average(const pa_step_record *recs, const uint32_t *qhist,
  * libpa.so holds until the process exits; M > PA_NOALLOC_MAX_RUNS or
  * M * n_steps > PA_NOALLOC_MAX_WEIGHTS is rejected with PA_ERR_INVALID_ARG
  * (and a message on stderr).  The first call on each device looks up the
- * array's device address (with that device current); make that first call
- * before any stream capture.  The work is enqueued on cuda_stream (a
+ * array's device address (with that device current) and keeps it for the
+ * life of the process; make that first call before any stream capture.  A
+ * cudaDeviceReset of that device makes the kept address stale: do not call
+ * this entry point on a device after resetting it.  The work is enqueued on cuda_stream (a
  * cudaStream_t or NULL) and the call returns without waiting.  Every call
  * shares the one array: calls whose work overlaps on the GPU (other streams,
  * or other host threads) race and must be serialised by the caller. */

@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s, *headers]):
-            jobs.append([nv, *_flags(extra), "-dc" if False else "-c", s, "-o", o])
+            jobs.append([nv, *_flags(extra), "-c", s, "-o", o])
     with cf.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         for cmd, res in zip(jobs, ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs)):
             if verbose or res.returncode:

@@ -123,7 +123,18 @@ struct RunHost {  // host view of a resident run
     pa_run_desc d{};
     Ranges g;
     uint32_t steps_done = 0;  // temperature index reached (mirrors the device while no error)
+    uint64_t dos_hash = 0;    // theta = PA_THETA_INF: hash of ln g (a checkpoint must come from the same one)
 };
+
+// FNV-1a over the bytes of ln g(E), 2N + 1 doubles (0 when the run has none).
+uint64_t dos_hash_of(const pa_run_desc &d)
+{
+    if (d.theta != PA_THETA_INF || !d.log_g) return 0;
+    uint64_t h = 1469598103934665603ull;
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(d.log_g);
+    for (size_t k = 0; k < sizeof(double) * (2ull * d.L * d.L + 1); ++k) h = (h ^ b[k]) * 1099511628211ull;
+    return h;
+}
 
 }  // namespace
 
@@ -563,6 +574,7 @@ pa_status admit(pa_engine *e, const pa_run_desc *runs, uint32_t n, uint32_t *slo
         RunHost &h = e->rh[s];
         h.used = true;
         h.d = d;
+        h.dos_hash = dos_hash_of(d);
         h.d.beta = nullptr;  // not kept: the caller owns it
         h.d.log_g = nullptr;
         h.g = g;
@@ -968,6 +980,7 @@ struct CkptHeader {
     uint32_t L, model, R, R_cap, theta, n_beta, seed, run_id, disorder_id, resample, overlap;
     uint32_t steps_done, R_cur, buffer, wstride, pad;
     uint64_t scratch_words, J_words, total_bytes;
+    uint64_t dos_hash;  // theta = PA_THETA_INF: hash of the run's ln g (0 otherwise)
 };
 
 struct CkptSection {
@@ -988,7 +1001,7 @@ std::vector<CkptSection> ckpt_sections(pa_engine *e, uint32_t run, const RunStat
         {e->P.fam[b] + x.rep_off, sizeof(uint32_t) * (size_t)st.R_cur},
         {e->P.rec + x.rec_off, sizeof(pa_step_record) * (size_t)x.n_beta},
         {e->P.scratch + x.scr_off, sizeof(unsigned long long) * (size_t)scratch_words(x.N, x.R_cap)},
-        {e->P.J + x.J_off, sizeof(uint32_t) * (size_t)(2ull * stride_words(x.L) + 8ull * plane_words(x.L))},
+        {e->P.J + x.J_off, sizeof(uint32_t) * (size_t)sizes_of(e->rh[run].d).J},
     };
     if (x.overlap) {
         v.push_back({e->P.qh + x.qh_off, sizeof(uint32_t) * (size_t)nq});
@@ -1595,8 +1608,9 @@ pa_status pa_checkpoint(pa_engine *e, uint32_t run, void *host_buf, size_t *byte
     h.buffer = st.step & 1u;
     h.wstride = x.wstride;
     h.scratch_words = scratch_words(x.N, x.R_cap);
-    h.J_words = 2ull * stride_words(x.L) + 8ull * plane_words(x.L);
+    h.J_words = sizes_of(d).J;
     h.total_bytes = need;
+    h.dos_hash = e->rh[run].dos_hash;
     char *out = static_cast<char *>(host_buf);
     std::memcpy(out, &h, sizeof h);
     size_t o = sizeof h;
@@ -1627,8 +1641,8 @@ pa_status pa_restore(pa_engine *e, uint32_t run, const void *host_buf, size_t by
     if (h.L != d.L || h.model != d.model || h.R != d.R || h.R_cap != x.R_cap || h.theta != d.theta ||
         h.n_beta != d.n_beta || h.seed != d.seed || h.run_id != d.run_id || h.disorder_id != d.disorder_id ||
         h.resample != d.resample || h.overlap != d.overlap || h.wstride != x.wstride ||
-        h.scratch_words != scratch_words(x.N, x.R_cap) ||
-        h.J_words != 2ull * stride_words(x.L) + 8ull * plane_words(x.L))
+        h.scratch_words != scratch_words(x.N, x.R_cap) || h.J_words != sizes_of(d).J ||
+        h.dos_hash != e->rh[run].dos_hash)
         return PA_ERR_INVALID_ARG;
     const char *in = static_cast<const char *>(host_buf);
     RunState st;
@@ -1655,6 +1669,18 @@ pa_status pa_restore(pa_engine *e, uint32_t run, const void *host_buf, size_t by
     e->h2d += bytes;
     e->rh[run].steps_done = h.steps_done;
     e->dirty = true;
+    // An engine-level error (capacity, extinction) is cleared once no resident run is stopped any
+    // more, so that restoring the run that failed from an earlier checkpoint lets the anneal go on.
+    std::vector<RunState> all(e->S);
+    PA_CUDA(cudaMemcpyAsync(all.data(), e->P.st, sizeof(RunState) * e->S, cudaMemcpyDeviceToHost, e->stream));
+    PA_CUDA(cudaStreamSynchronize(e->stream));
+    bool stopped = false;
+    for (uint32_t s : e->active) stopped |= all[s].status != 0;
+    if (!stopped) {
+        PA_CUDA(cudaMemsetAsync(e->P.status, 0, sizeof(uint32_t), e->stream));
+        PA_CUDA(cudaStreamSynchronize(e->stream));
+        e->latched = PA_OK;
+    }
     return PA_OK;
 }
 

@@ -2,8 +2,6 @@
 //
 // pa_weighted_average copies host records to the device and allocates its
 // scratch with cudaMalloc on every call.  Some callers cannot do that:
-//  - code that enqueues work while a stream is being captured into a CUDA
-//    graph (allocation calls are refused during a global-mode capture),
 //  - serving loops that reserve all device memory up front and must not enter
 //    the driver's allocator in the steady state (cudaMalloc may synchronise
 //    the whole device and stall the other streams),
@@ -36,7 +34,8 @@ void *g_addr[MAX_DEVICES] = {};
 
 // Device address of the scratch array for the current device.  In host code
 // the array's name is only a host-side stand-in, so the address comes from
-// cudaGetSymbolAddress, looked up once per device with that device current.
+// cudaGetSymbolAddress, looked up once per device with that device current
+// and kept for the life of the process (a cudaDeviceReset makes it stale).
 pa_status scratch_address(void **out)
 {
     int dev = -1;

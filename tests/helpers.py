@@ -47,14 +47,14 @@ def compare_records(gpu, ora, rtol=1e-12):
         assert err.max() <= rtol, (f, err.max(), np.argmax(err))
 
 
-def wavg_scale(o, f):
+def wavg_scale(o, f, N):
     """Magnitude against which the rounding of weighted average f is judged.
     Differences of O(1) terms (variances, central moments by binomial
     expansion, 1 - ratio) are judged relative to the terms combined."""
     import math
     scale = np.maximum(np.abs(o[f]), 1e-300)
     if f in ("Wvar_c", "Wvar_chi", "W_c", "W_chi"):
-        scale = np.maximum(scale, np.abs(o["beta"]) ** 2 * 64 * (np.abs(o["W_e2"]) + np.abs(o["W_m2"])) + 1e-300)
+        scale = np.maximum(scale, np.abs(o["beta"]) ** 2 * N * (np.abs(o["W_e2"]) + np.abs(o["W_m2"])) + 1e-300)
     if f.startswith("Wk"):
         k, obs = int(f[2]), f[-1]
         raw = [np.ones_like(o["W_e"])] + [o[n] for n in ((f"W_{obs}", f"W_{obs}2", f"W_{obs}3", f"W_{obs}4"))]
@@ -65,12 +65,12 @@ def wavg_scale(o, f):
     return scale
 
 
-def wavg_close(g, o, names, rtol=1e-12):
+def wavg_close(g, o, names, N, rtol=1e-12):
     for f in names:
         if f in ("W_U4_conf",) and np.any(np.isnan(o[f])):
             assert np.array_equal(np.isnan(g[f]), np.isnan(o[f])), f
             ok = ~np.isnan(o[f])
-            err = np.abs(g[f][ok] - o[f][ok]) / wavg_scale(o, f)[ok]
+            err = np.abs(g[f][ok] - o[f][ok]) / wavg_scale(o, f, N)[ok]
         else:
-            err = np.abs(g[f] - o[f]) / wavg_scale(o, f)
+            err = np.abs(g[f] - o[f]) / wavg_scale(o, f, N)
         assert np.all(err <= rtol), (f, err.max())

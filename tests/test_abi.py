@@ -13,6 +13,8 @@ from paper_2207_05535_gb300 import _lib, build
 from paper_2207_05535_gb300 import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+# CUDA headers of the toolkit whose nvcc builds the engine (<toolkit>/bin/nvcc -> <toolkit>/include)
+CUDA_INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(build.nvcc()))), "include")
 HEADER = os.path.join(ROOT, "include", "pa.h")
 
 
@@ -139,7 +141,7 @@ int main() {
 ''')
     exe = tmp_path / "pw"
     subprocess.run(["g++", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I",
-                    os.path.join(ROOT, "paper_2207_05535_gb300", "csrc"), "-I", "/usr/local/cuda/include", str(prog),
+                    os.path.join(ROOT, "paper_2207_05535_gb300", "csrc"), "-I", CUDA_INCLUDE, str(prog),
                     "-o", str(exe)], check=True)
     for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n"):
         if line:
@@ -174,7 +176,7 @@ int main() {
 ''')
     exe = tmp_path / "scr"
     subprocess.run(["g++", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I",
-                    os.path.join(ROOT, "paper_2207_05535_gb300", "csrc"), "-I", "/usr/local/cuda/include", str(prog),
+                    os.path.join(ROOT, "paper_2207_05535_gb300", "csrc"), "-I", CUDA_INCLUDE, str(prog),
                     "-o", str(exe)], check=True)
     rows = [list(map(int, line.split())) for line in
             subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n") if line]

@@ -39,10 +39,10 @@ def test_moment_sums_beyond_64_bits_and_their_weighted_averages():
             compare_records(eng.records(k), orecs[k])
         g = eng.weighted_average(np.arange(2, dtype=np.uint32), 2, 0)
     o, _, _ = O.weighted_average(orecs, 256 * 256, 0)
-    wavg_close(g[0], o, _lib.WAVG_DTYPE.names)
+    wavg_close(g[0], o, _lib.WAVG_DTYPE.names, 256 * 256)
     h, _, _ = _lib.pa_weighted_average(orecs, 256 * 256, 1)
     o1, _, _ = O.weighted_average(orecs, 256 * 256, 1)
-    wavg_close(h, o1, MOMENT_FIELDS)
+    wavg_close(h, o1, MOMENT_FIELDS, 256 * 256)
 
 
 @pytest.mark.parametrize("kind", [0, 1])
@@ -55,4 +55,4 @@ def test_central_moments_and_binder_over_many_ferromagnet_runs(kind):
         g = eng.weighted_average(np.arange(len(descs), dtype=np.uint32), 4, kind)
     for grp in range(3):
         o, _, _ = O.weighted_average(orecs[4 * grp:4 * grp + 4], 64, kind)
-        wavg_close(g[grp], o, MOMENT_FIELDS)
+        wavg_close(g[grp], o, MOMENT_FIELDS, 64)

@@ -154,8 +154,8 @@ def test_capacity_overflow_is_reported_not_written():
 
 
 # ------------------------------------------------------------------ weighted averages
-def _wavg_close(g, o):
-    wavg_close(g, o, _lib.WAVG_DTYPE.names)
+def _wavg_close(g, o, N=64):
+    wavg_close(g, o, _lib.WAVG_DTYPE.names, N)
 
 
 def test_weighted_averages_from_host_records():

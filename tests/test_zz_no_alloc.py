@@ -1,8 +1,8 @@
 """pa_weighted_average_noalloc: weighted averages with no device allocation.
 
-For callers that cannot call cudaMalloc (work recorded inside a CUDA graph
-capture, serving loops that reserve all device memory up front, processes
-whose device memory belongs to another allocator) the library offers an entry
+For callers that cannot call cudaMalloc (serving loops that reserve all
+device memory up front and must not enter the allocator, processes whose
+device memory belongs to another allocator) the library offers an entry
 point that takes records and output already in device memory and keeps its
 scratch in a fixed device array.  This test calls it through the C ABI twice
 in a row, with different sizes, and checks each result against the allocating
