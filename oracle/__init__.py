@@ -16,6 +16,7 @@ from .oracle import (  # noqa: F401
     wang_pairing,
     kaufman_lnZ,
     load,
+    log_weights,
     metropolis_threshold,
     philox4x32_10,
     sweep_lattice,

@@ -121,6 +121,8 @@ def load():
         lib.or_weighted_average.argtypes = [C.c_void_p, P(u32), P(u32), P(u32), u32, u32, u32, u32, C.c_void_p,
                                             P(f64), P(f64), P(f64), P(f64)]
         lib.or_weighted_average.restype = C.c_int
+        lib.or_log_weight.argtypes = [C.c_void_p, u32, u32, u32, u32]
+        lib.or_log_weight.restype = f64
         lib.or_bruteforce.argtypes = [u32, P(C.c_int8), P(C.c_int8), f64, P(f64), P(f64), P(f64), P(f64),
                                       P(f64), P(f64)]
         lib.or_bruteforce.restype = C.c_int
@@ -351,3 +353,12 @@ def weighted_average(recs, N, kind=0, qh=None, qh_pair=None, return_weights=Fals
         raise ValueError(f"or_weighted_average failed ({rc})")
     res = (out, Pq, Pp) + ((Pw,) if qh_wang is not None else ()) + ((w,) if return_weights else ())
     return res
+
+
+def log_weights(recs, kind=0):
+    """The exponents lambda[i, m] that weighted_average normalises into its weights
+    (Eq. appropriateWeight for kind 0, Eq. simpleWeight for kind 1)."""
+    lib = load()
+    recs = np.ascontiguousarray(recs, dtype=RECORD_DTYPE)
+    M, n = recs.shape
+    return np.array([[lib.or_log_weight(recs.ctypes.data, n, m, i, kind) for m in range(M)] for i in range(n)])

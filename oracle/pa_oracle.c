@@ -854,6 +854,12 @@ static double log_weight(const or_record *recs, uint32_t n_steps, uint32_t m, ui
     return lam;
 }
 
+/* The exponent that or_weighted_average normalises (run m, step i), for the tests. */
+double or_log_weight(const or_record *recs, uint32_t n_steps, uint32_t m, uint32_t i, uint32_t kind)
+{
+    return log_weight(recs, n_steps, m, i, kind);
+}
+
 int or_weighted_average(const or_record *recs, const uint32_t *qh, const uint32_t *qh_pair, const uint32_t *qh_wang,
                         uint32_t M, uint32_t n_steps, uint32_t N, uint32_t kind, or_wavg *out, double *Pq,
                         double *Pq_pair, double *Pq_wang, double *w_out /* [n_steps][M] or NULL */)
