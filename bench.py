@@ -1,21 +1,26 @@
 #!/usr/bin/env python
 """Benchmark: attempted spin updates per ns of population annealing on GB300.
 
-Workload (one "step" = one whole anneal of the batch, every hot-path stage):
-2D +-J Edwards-Anderson glass, L=16 periodic, R=5000, beta 0 -> 3 in 101
-temperatures, theta = 10 checkerboard Metropolis sweeps per temperature,
-nearest-integer resampling, 100 disorder samples x 2 independent populations,
-overlaps by index shift and between the two populations, free-energy-weighted
-averages over the two populations of each sample.  Inputs are seeded and
-synthetic (the paper's instances are not available).
+Default workload (the largest single-GPU configuration): 4096 independent 2D
+Ising ferromagnet runs in one batch, L drawn from {16, 32, 64, 128} and R from
+{1e3, 1e4, 5e4} by seed, beta 0 -> 1 in 101 temperatures, theta = 10
+checkerboard Metropolis sweeps per temperature, nearest-integer resampling;
+about 120 GB of bit-packed populations resident in HBM.  One "step" is one
+anneal temperature of the whole batch (resampling, sweeps and measurement of
+every run); the warm-up and the timed steps walk the schedule from beta_0 on
+(the timed temperature range is in `config`).  `--workload` selects the other
+workloads, where one step is one whole anneal (small batches) or the serving
+stream.  Inputs are seeded and synthetic (the paper's instances are not
+available).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 
 Prints one JSON line on rank 0.  `value` is device-timed with the populations
 resident in HBM; `e2e` times the same work through the C ABI from host
-descriptors to host results (engine creation, uploads and result copies
-inside the timed region).  `--impl reference` times the CPU oracle on the
-host cores over a bounded sample of the same workload.
+descriptors to host results (engine creation and uploads, the K steps, each
+followed by a copy of every run's new record to pinned host memory).
+`--impl reference` times the CPU oracle on the host cores over a bounded
+sample of the same workload.
 """
 from __future__ import annotations
 
@@ -52,7 +57,9 @@ WORKLOADS = {
                 "R log-uniform in 1e3..5e4, 50..300 temperatures, beta_f 1 (FM) / 3 (glass), theta=10), "
                 "continuous batching in one server engine with a 64 GB pool budget"),
 }
-WORKLOAD = WORKLOADS["glass_L16_R5000"]
+# Workloads whose bench step is one temperature of the whole batch (a whole
+# anneal takes minutes); the others time whole anneals.
+TEMPERATURE_STEP = {"uneven_4096", "ising_L256_R1e5"}
 # Algorithmic work of one attempted update on the binding unit, the 32-bit
 # integer multiplier: a quarter of a Philox4x32-10 call, whose 10 rounds hold
 # two 32x32->64 multiplies each, i.e. 20 wide multiplies = 40 multiply-add
@@ -98,7 +105,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="glass_L16_R5000", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="uneven_4096", choices=sorted(WORKLOADS))
     ap.add_argument("--samples", type=int, default=100, help="glass: disorder samples (2 populations each)")
     ap.add_argument("--runs", type=int, default=0, help="ising/uneven: number of runs (0 = the workload's)")
     ap.add_argument("--window", type=float, default=2.0, help="serving: seconds of arrivals")
@@ -108,6 +115,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the small whole-anneal workloads in `extra`")
     return ap.parse_args()
 
 
@@ -309,6 +317,8 @@ def main():
     wl = args.workload
     if wl == "serving":
         return serving_main(args, rank, world, cpu)
+    if wl in TEMPERATURE_STEP:
+        return temperature_main(args, rank, world, local, cpu, dist, barrier)
     # weak scaling: every rank anneals its own batch (disorder samples / runs offset by rank)
     if wl == "glass_L16_R5000":
         descs, M_avg = W.glass_L16_R5000(n_samples=args.samples), 2
@@ -385,6 +395,10 @@ def main():
             kt_tot[kk] = (a + t, b + n)
     _lib.pa_set_profiling(eng.h, False)
     sweep_ms, sweep_n = kt_tot["sweep"]
+    small_ms = kt_tot.get("small", (0.0, 0))[0]
+    small = small_ms > sweep_ms  # runs on the one-launch-per-step path: its kernel holds the sweeps
+    if small:
+        sweep_ms = small_ms
     pk, pk_kind = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak_tops = 152 * MULADD_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # integer multiply-add slots, T/s
@@ -396,9 +410,10 @@ def main():
     achieved_tops = updates * slots / (sweep_ms / args.steps * 1e-3) / 1e12
     metric, unit = metric_unit(wl)
     total_kernel_ms = sum(t for t, _ in kt_tot.values())
-    sweep_roof = {"bound": "alu", "kernel": "dos_sample_kernel" if inf else "sweep_pow2_kernel",
+    sweep_roof = {"bound": "alu", "kernel": "dos_sample_kernel" if inf else
+                  ("anneal_small_kernel (resampling, sweeps and measurement of a step)" if small else "sweep_pow2_kernel"),
                   "achieved": achieved_tops, "peak": peak_tops, "unit": "Tmuladd/s", "frac": achieved_tops / peak_tops,
-                  "traffic": None if inf else measured_traffic("sweep", wl),
+                  "traffic": None if inf or small else measured_traffic("sweep", wl),
                   "basis": (f"{ALGO_MULADD_PER_DRAW:g} integer multiply-add slots per energy draw "
                             f"(one Philox4x32-10 call)" if inf else
                             f"{ALGO_MULADD_PER_UPDATE:g} integer multiply-add slots per attempted update "
@@ -432,7 +447,8 @@ def main():
     roof_res = hbm_roof("resample_counts_kernel + resample_parents_kernel", "resample", res_bytes, None,
                         "per parent: E read, copy number written and read back (12 B); per child: its parent "
                         "index written (4 B)")
-    dominant = max(("sweep", "measure", "resample"), key=lambda k_: kt_tot.get(k_, (0.0, 0))[0])
+    dominant = max(("sweep", "measure", "resample", "small"), key=lambda k_: kt_tot.get(k_, (0.0, 0))[0])
+    dominant = "sweep" if dominant == "small" else dominant
     roofline = {"sweep": sweep_roof, "measure": roof_meas, "resample": roof_res}[dominant] or sweep_roof
     # overlap kernels (a10): HBM-bound; algorithmic bytes = both replicas' colour planes per pair
     ov_ms = kt_tot.get("overlap", (0.0, 0))[0] / args.steps
@@ -528,7 +544,8 @@ def main():
             "config": {"workload": WORKLOADS[wl] + ("; plus Wang pairing overlaps" if args.wang else ""), "name": wl, "runs_per_gpu": len(descs), "temperatures": n_ticks + 1,
                        ("energy_draws_per_step" if inf else "attempted_updates_per_step"): updates,
                        "l2": "flushed between steps (256 MB write)",
-                       "form": "batched: all runs in one launch per kernel, anneal captured as a CUDA graph",
+                       "form": "batched: all runs share each launch; small runs (L <= 32, no overlaps) anneal in one "
+                               "launch per lattice size, the others in one CUDA graph replay per temperature",
                        "parallelism": f"replicas x{world} (independent runs per GPU)"},
             "runs_per_s": runs_per_s,
             "roofline": roofline,
@@ -552,6 +569,269 @@ def main():
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def sweep_roofline(kernel, updates, sweep_ms, total_kernel_ms, traffic):
+    """The sweep against the integer-multiplier roof: 10 multiply-add slots per
+    attempted update over the sweep's CUDA-event time, plus the live Philox-only
+    calibration of that roof."""
+    from paper_2207_05535_gb300 import _lib
+    pk, pk_kind = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tops = 152 * MULADD_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    cal = {"calls_per_s_split": _lib.pa_calibrate_philox(False), "calls_per_s_wide": _lib.pa_calibrate_philox(True)}
+    cal["frac_of_peak_split"] = cal["calls_per_s_split"] * 40 / (peak_tops * 1e12)
+    achieved = updates * ALGO_MULADD_PER_UPDATE / (sweep_ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_tops, "unit": "Tmuladd/s",
+            "frac": achieved / peak_tops, "traffic": traffic,
+            "basis": f"{ALGO_MULADD_PER_UPDATE:g} integer multiply-add slots per attempted update (Philox4x32-10: "
+                     f"40 per call, 4 updates per call); peak = 152 SMs x {MULADD_LANES_PER_SM} lanes x {sm_mhz:g} MHz, "
+                     f"clock from MEASURED_PEAKS.json ({pk_kind})",
+            "updates_per_ns_sweep_only": updates / (sweep_ms * 1e-3) / 1e9, "sweep_ms_per_step": sweep_ms,
+            "sweep_share_of_kernel_time": sweep_ms / total_kernel_ms if total_kernel_ms else None,
+            "philox_calibration": cal}
+
+
+def hbm_roofline(name, nbytes, ms, traffic, basis):
+    pk, pk_kind = peaks()
+    if not ms or not nbytes:
+        return None
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    ach = nbytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": traffic, "bytes_per_step": nbytes, "ms_per_step": ms,
+            "basis": basis + f"; peak = HBM copy bandwidth from MEASURED_PEAKS.json ({pk_kind})"}
+
+
+def step_units(descs, recs_R, temps):
+    """Attempted updates of temperatures `temps` (indices into each run's records)."""
+    tot = 0
+    for d, R in zip(descs, recs_R):
+        for t in temps:
+            tot += work_units(d, int(R[t]))
+    return tot
+
+
+def temperature_main(args, rank, world, local, cpu, dist, barrier):
+    """One step = one temperature of the whole batch; the warm-up and the timed
+    steps walk the schedule (a reset between steps, untimed, when it ends)."""
+    import dataclasses
+    import numpy as np
+    import torch
+    from paper_2207_05535_gb300 import _lib, replicas
+    from paper_2207_05535_gb300 import workloads as W
+    wl = args.workload
+    descs = W.batched_uneven(n_runs=args.runs or 4096) if wl == "uneven_4096" else \
+        W.ising_L256_R1e5(M=args.runs or 16)
+    descs = replicas.shard(descs, rank)
+    n_ticks = max(d.n_beta for d in descs) - 1
+    K, Wm = args.steps, args.warmup
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    eng = _lib.Engine(descs, stream.cuda_stream)
+    every = np.arange(len(descs), dtype=np.uint32)
+    cur = [0]  # temperature index every run has reached
+
+    def fit(n):  # make room for n more temperatures in this pass (untimed reset otherwise)
+        if cur[0] + n > n_ticks:
+            eng.reset()
+            eng.sync()
+            cur[0] = 0
+
+    def R_of_steps():
+        return [eng.records(k)["R"] for k in range(len(descs))]
+
+    for _ in range(Wm):  # warm-up: the first step also times the candidate sweep shapes
+        fit(1)
+        eng.step(1, True)
+        cur[0] += 1
+    eng.sync()
+    fit(K)
+    first = cur[0] + 1
+
+    # ---- timed region: K temperatures, device-timed, L2 flushed before each
+    clocks = Clocks(local) if rank == 0 else None
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    l0 = eng.launches
+    for k in range(K):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[k][0].record(stream)
+        eng.step(1, True)
+        ev[k][1].record(stream)
+    barrier()
+    launches = eng.launches - l0
+    cur[0] += K
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    clk = clocks.stop() if clocks else None
+    temps = list(range(first, first + K))
+    Rs = R_of_steps()
+    updates = step_units(descs, Rs, temps)
+    t_max, upd_all = replicas.reduce_timing(ms, updates, dist, device="cuda")
+    value = upd_all / (t_max * 1e6)
+
+    # ---- per-kernel device time: eager launches bracketed by events, the next temperatures
+    Kp = min(K, 5)
+    fit(Kp)
+    p_first = cur[0] + 1
+    _lib.pa_set_profiling(eng.h, True)
+    _lib.pa_kernel_times(eng.h)
+    for k in range(Kp):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        eng.step(1, False)
+    kt = _lib.pa_kernel_times(eng.h)
+    _lib.pa_set_profiling(eng.h, False)
+    cur[0] += Kp
+    Rp = R_of_steps()
+    p_temps = list(range(p_first, p_first + Kp))
+    p_updates = step_units(descs, Rp, p_temps)
+    kt_step = {k_: t / Kp for k_, (t, n) in kt.items()}
+    total_kernel_ms = sum(kt_step.values())
+    sweep_roof = sweep_roofline("sweep_pow2_kernel", p_updates / Kp, kt_step["sweep"], total_kernel_ms,
+                                measured_traffic("sweep", wl))
+    meas_bytes = 12 * sum(int(R[t]) for R in Rp for t in p_temps) // Kp
+    res_bytes = sum(12 * int(R[t - 1]) + 4 * int(R[t]) for R in Rp for t in p_temps) // Kp
+    roof_meas = hbm_roofline("measure_kernel", meas_bytes, kt_step.get("measure"), measured_traffic("measure", wl),
+                             "12 B read per measured replica (E, M, family)")
+    roof_res = hbm_roofline("resample_counts_kernel + resample_parents_kernel", res_bytes, kt_step.get("resample"),
+                            None, "per parent: E read, copy number written and read back (12 B); per child: its "
+                                  "parent index written (4 B)")
+    gather_bytes = sum(int(R[t]) * (2 * 2 * plane_words(d.L) * 4 + 2 * 12 + 4)
+                       for d, R in zip(descs, Rp) for t in p_temps) // Kp
+    gather = {"bytes_per_step": gather_bytes, "GBps_within_sweep": gather_bytes / (kt_step["sweep"] * 1e-3) / 1e9,
+              "basis": "children x (parent planes read + child planes written + 12 B E/M/family each way + 4 B "
+                       "parent index); the copy is fused into the sweep kernel, so its rate is per sweep time"}
+    shapes = [{"L": L_, "words_per_thread": w_, "block": b_, "autotuned": bool(t_)}
+              for (L_, w_, b_, t_) in _lib.pa_sweep_shapes(eng.h)]
+    eng.close()
+    del flush
+
+    # ---- plain form: 20 of the runs, one engine (one run) each, eager launches, one after another
+    plain = None
+    if not args.no_plain and rank == 0:
+        units = descs[:min(len(descs), 20)]
+        engines = [_lib.Engine([dataclasses.replace(d)], stream.cuda_stream) for d in units]
+        for e in engines:
+            for _ in range(min(Wm, n_ticks - K)):
+                e.step(1, False)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k in range(K):
+            for e in engines:
+                e.step(1, False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b)
+        p0 = min(Wm, n_ticks - K) + 1
+        pupd = step_units(units, [e.records(0)["R"] for e in engines], range(p0, p0 + K))
+        for e in engines:
+            e.close()
+        plain = {"value": pupd / (pms * 1e6), "unit": UNIT, "runs": len(units),
+                 "form": "20 of the batch's runs, one engine and eager launch sequence per run, one after another, "
+                         "the same number of temperatures"}
+
+    # ---- end to end through the C ABI: host descriptors in, every run's record of each step out
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.empty(len(descs) * _lib.RECORD_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+        host = pinned.numpy().view(_lib.RECORD_DTYPE)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e = _lib.Engine(descs, stream.cuda_stream)
+        for k in range(K):
+            e.step(1, True)
+            e.step_records(every, host)
+        wall = time.perf_counter() - t0
+        h2d, d2h = _lib.pa_transfer_bytes(e.h)
+        eupd = step_units(descs, [e.records(k)["R"] for k in range(len(descs))], range(1, K + 1))
+        e.close()
+        e2e = {"value": eupd * world / (wall * 1e9), "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+               "d2h_bytes_per_step": d2h / K,
+               "includes": "pa_create from host descriptors (pool allocation, descriptor/schedule/table uploads, "
+                           "beta_0 draw) + K anneal steps, each followed by pa_step_records of every run into pinned "
+                           "host memory; wall clock"}
+
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra = {w_: small_workload(w_, stream) for w_ in ("ising_L8_R500", "glass_L16_R5000")}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+            "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32/f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[wl], "name": wl, "runs_per_gpu": len(descs),
+                       "temperatures": n_ticks + 1, "step": "one temperature of the whole batch",
+                       "timed_temperatures": [temps[0], temps[-1]], "attempted_updates_timed": updates,
+                       "l2": "inputs larger than L2 (about 120 GB of populations) and a 256 MB write before each step",
+                       "form": "batched: all runs in one launch per kernel, each temperature one CUDA graph replay",
+                       "parallelism": f"replicas x{world} (independent runs per GPU)"},
+            "roofline": sweep_roof, "roofline_measure": roof_meas, "roofline_resample": roof_res,
+            "resample_gather": gather, "kernel_ms_per_step": kt_step, "sweep_shapes": shapes,
+            "gpu_launches": launches, "clocks": clk, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
+            "extra": extra,
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def small_workload(wl, stream, K=3, Wm=2):
+    """Device-timed value of a small workload (one step = one whole anneal of its
+    batch, graph replays) beside its plain form (one run, or one disorder sample
+    of two populations, per engine; eager launches)."""
+    import dataclasses
+    import numpy as np
+    import torch
+    from paper_2207_05535_gb300 import _lib
+    from paper_2207_05535_gb300 import workloads as W
+    descs = W.ising_L8_R500(M=20) if wl == "ising_L8_R500" else W.glass_L16_R5000()
+    n_ticks = max(d.n_beta for d in descs) - 1
+    eng = _lib.Engine(descs, stream.cuda_stream)
+    for _ in range(Wm):
+        eng.reset()
+        eng.step(n_ticks, True)
+    eng.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(K):
+        eng.reset()
+        eng.sync()
+        a.record(stream)
+        eng.step(n_ticks, True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+    upd = sum(work_units(d, int(r)) for k, d in enumerate(descs) for r in eng.records(k)["R"][1:]) * K
+    eng.close()
+    if wl == "glass_L16_R5000":
+        units = [[dataclasses.replace(descs[2 * s_ + p_], paired=1 - p_) for p_ in range(2)] for s_ in range(10)]
+    else:
+        units = [[dataclasses.replace(d)] for d in descs]
+    engines = [_lib.Engine(u, stream.cuda_stream) for u in units]
+    for e in engines:
+        e.step(n_ticks, False)
+        e.reset()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for e in engines:
+        e.step(n_ticks, False)
+    b.record(stream)
+    torch.cuda.synchronize()
+    pms = a.elapsed_time(b)
+    pupd = sum(work_units(d, int(r)) for u, e in zip(units, engines) for k, d in enumerate(u)
+               for r in e.records(k)["R"][1:])
+    for e in engines:
+        e.close()
+    return {"workload": WORKLOADS[wl], "value": upd / (ms * 1e6), "unit": UNIT, "anneals_timed": K,
+            "ms_per_anneal": ms / K, "plain": pupd / (pms * 1e6),
+            "form": "batched: all runs share each launch (small runs: one launch for the whole anneal; the others: "
+                    "one CUDA graph replay per temperature); plain: one run "
+                    "(glass: one disorder sample of two populations) per engine, eager launches"}
 
 
 def serving_main(args, rank, world, cpu):

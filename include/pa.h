@@ -13,7 +13,8 @@
  *  - Every call returns a pa_status; nothing else crosses the ABI on error.
  *  - Pointers named host_* or documented as "host" are host memory owned by
  *    the caller; the engine copies what it needs and keeps no reference.
- *  - The engine owns all device memory it allocates and frees it in
+ *  - The engine owns all device memory it allocates (from cudaMalloc, or from
+ *    the allocator installed by pa_set_allocator) and frees it in
  *    pa_destroy.  Work is enqueued asynchronously on the engine's CUDA stream;
  *    device-side errors (capacity overflow, extinction, timeouts) are latched in
  *    a device status word and returned by pa_sync and pa_weighted_average_runs;
@@ -141,6 +142,25 @@ typedef struct pa_wavg {
 
 typedef struct pa_engine pa_engine;
 
+/* Device memory allocator.  By default an engine takes its device memory from
+ * cudaMalloc; pa_set_allocator installs callbacks that every engine created
+ * afterwards (and every pa_weighted_average call) uses instead, for example a
+ * framework's caching allocator, so that the engine's pools come from the same
+ * memory as the caller's tensors.  alloc returns a device pointer to at least
+ * `bytes` bytes (256-byte aligned) usable on `stream` of `device`, or NULL when
+ * it cannot, which the engine reports as PA_ERR_OOM after releasing what it
+ * already holds.  free_ receives every block back with the size it was asked
+ * for, when the engine no longer uses it (pa_destroy, or a growing scratch
+ * buffer after its work finished).  An engine keeps the allocator it was created
+ * with until it is destroyed.  pa_set_allocator(NULL, NULL, NULL) restores
+ * cudaMalloc.  The engine allocates only in pa_create, pa_server_create and
+ * the first calls of pa_weighted_average_runs / pa_step_records with a larger
+ * batch than before; never during an anneal step.  PA_ERR_INVALID_ARG if only
+ * one of the two callbacks is given. */
+typedef void *(*pa_alloc_fn)(size_t bytes, int device, void *stream, void *ctx);
+typedef void (*pa_free_fn)(void *ptr, size_t bytes, int device, void *stream, void *ctx);
+pa_status pa_set_allocator(pa_alloc_fn alloc, pa_free_fn free_, void *ctx);
+
 /* Create an engine holding n_runs runs, allocate their device memory, draw the
  * beta_0 = 0 populations (Sec. II.B step (i): uniform states), the couplings
  * (Eq. H_SG) and measure step 0.  cuda_stream: a cudaStream_t to enqueue on,
@@ -154,12 +174,19 @@ pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream,
  *     sweep kernel instead of the bit-sliced kernel used for L = 8, 16, ..., 256
  *     (both give identical results; the option exists to check that);
  *   PA_CREATE_NO_AUTOTUNE skips timing the bit-sliced kernel's launch shapes on
- *     the first anneal step and uses the default shape.
+ *     the first anneal step and uses the default shape;
+ *   PA_CREATE_SEPARATE_KERNELS keeps small runs on the per-stage kernels.
+ * Without it, a small run (L = 8, 16 or 32, nearest-integer resampling, no
+ * overlaps, R_cap <= 8192) is annealed by one launch per step: a cluster of
+ * CTAs that resamples, sweeps and measures it (when every resident run is
+ * small, pa_anneal_step(n) is one launch per lattice size for all n steps).
+ * Both paths give identical results; PA_CREATE_GENERIC_SWEEP implies the
+ * per-stage kernels.
  * Without it, the first anneal step of a lattice size times every candidate shape
  * and keeps the fastest; the choice is shared with every later engine of the
  * process on the same device, which then skips the timing for that size.
  * Results never depend on the launch shape. */
-enum { PA_CREATE_GENERIC_SWEEP = 1, PA_CREATE_NO_AUTOTUNE = 2 };
+enum { PA_CREATE_GENERIC_SWEEP = 1, PA_CREATE_NO_AUTOTUNE = 2, PA_CREATE_SEPARATE_KERNELS = 4 };
 pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, uint32_t flags,
                        pa_engine **out);
 
@@ -229,6 +256,13 @@ pa_status pa_sync(pa_engine *e);
  * (index shift, paired population, Wang pairs) when non-NULL.  Synchronises. */
 pa_status pa_records(pa_engine *e, uint32_t run, pa_step_record *host_out, uint32_t *host_qhist,
                      uint32_t *host_qhist_pair, uint32_t *host_qhist_wang);
+
+/* The record of each run in runs[0..n_runs) at the temperature it has reached
+ * (its current temperature index) into host_out[n_runs]: one gather on the
+ * device and one copy back, for streaming a batch's or a server's results
+ * after every anneal step.  Synchronises.  PA_ERR_INVALID_ARG for a run that
+ * is not resident. */
+pa_status pa_step_records(pa_engine *e, const uint32_t *runs, uint32_t n_runs, pa_step_record *host_out);
 
 /* Copy one record (and optional histograms, N+1 entries each). Synchronises. */
 pa_status pa_measure(pa_engine *e, uint32_t run, uint32_t step, pa_step_record *host_out, uint32_t *host_qhist,
@@ -331,7 +365,7 @@ pa_status pa_sweep_shape(const pa_engine *e, uint32_t group, uint32_t *L, uint32
 
 /* Kernel classes timed by the profiling mode. */
 enum { PA_K_RESAMPLE = 0, PA_K_SWEEP = 1, PA_K_OVERLAP = 2, PA_K_MEASURE = 3, PA_K_INIT = 4, PA_K_WAVG = 5,
-       PA_K_COUNT = 6 };
+       PA_K_SMALL = 6, PA_K_COUNT = 7 };  /* PA_K_SMALL: the one-launch-per-step path of small runs */
 
 /* Profiling mode: with on != 0 every kernel launch is bracketed by CUDA events
  * on the engine's stream and pa_anneal_step launches eagerly (no graph). */

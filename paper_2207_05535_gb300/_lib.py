@@ -63,8 +63,13 @@ EXPORTS = ["pa_create", "pa_create_ex", "pa_server_create", "pa_admit", "pa_reti
            "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population", "pa_population_slice",
            "pa_checkpoint", "pa_restore",
            "pa_weighted_average_runs", "pa_weighted_average", "pa_weighted_average_noalloc", "pa_launch_count", "pa_set_profiling",
+           "pa_step_records", "pa_set_allocator",
            "pa_kernel_times", "pa_transfer_bytes", "pa_calibrate_philox", "pa_sweep_shape", "pa_destroy", "pa_status_string"]
-KERNEL_KINDS = ["resample", "sweep", "overlap", "measure", "init", "wavg"]
+KERNEL_KINDS = ["resample", "sweep", "overlap", "measure", "init", "wavg", "small"]
+
+# pa_alloc_fn / pa_free_fn (include/pa.h)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_int, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p, C.c_void_p)
 
 _lock = threading.Lock()
 _lib = None
@@ -93,6 +98,8 @@ def load(path: str = LIB_PATH):
         lib.pa_sync.argtypes = [vp]
         lib.pa_records.argtypes = [vp, u32, vp, P(u32), P(u32), P(u32)]
         lib.pa_measure.argtypes = [vp, u32, u32, vp, P(u32), P(u32), P(u32)]
+        lib.pa_step_records.argtypes = [vp, P(u32), u32, vp]
+        lib.pa_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
         lib.pa_population.argtypes = [vp, u32, P(C.c_int8), P(C.c_int32), P(C.c_int32), P(u32), P(u32), P(u32)]
         lib.pa_population_slice.argtypes = [vp, u32, u32, u32, P(C.c_int8), P(C.c_int32), P(C.c_int32), P(u32),
                                             P(u32), P(u32)]
@@ -317,6 +324,31 @@ def pa_weighted_average(recs, N, kind=0, qh=None, qh_pair=None, stream=None, qh_
     return (out, Pq, Pp) + ((Pw,) if qh_wang is not None else ())
 
 
+def pa_step_records(h, runs, out=None):
+    """Records of runs[k] at the temperature each has reached (RECORD_DTYPE[n]);
+    `out`: optional preallocated host array (for example in pinned memory)."""
+    runs = np.ascontiguousarray(runs, dtype=np.uint32)
+    if out is None:
+        out = np.zeros(len(runs), dtype=RECORD_DTYPE)
+    _check(load().pa_step_records(h, _p(runs, C.c_uint32), len(runs), out.ctypes.data), "pa_step_records")
+    return out
+
+
+_allocator_keep = []  # every installed pair: engines created with it call it until destroyed
+
+
+def pa_set_allocator(alloc=None, free=None, ctx=None):
+    """Install device allocator callbacks (Python callables with the pa_alloc_fn /
+    pa_free_fn signatures) for engines created afterwards; no arguments restores
+    cudaMalloc.  The callbacks are kept alive here while installed."""
+    if alloc is None:
+        _check(load().pa_set_allocator(ALLOC_FN(), FREE_FN(), None), "pa_set_allocator")
+        return
+    a, f = ALLOC_FN(alloc), FREE_FN(free)
+    _check(load().pa_set_allocator(a, f, ctx), "pa_set_allocator")
+    _allocator_keep.append((a, f))
+
+
 def pa_launch_count(h):
     return int(load().pa_launch_count(h))
 
@@ -397,6 +429,9 @@ class Engine:
 
     def sync(self):
         pa_sync(self.h)
+
+    def step_records(self, runs, out=None):
+        return pa_step_records(self.h, runs, out)
 
     def records(self, run, qhist=False, wang=False):
         r = self.runs[run]

@@ -104,6 +104,60 @@ std::tuple<int, uint32_t, int> tune_key(uint32_t L, uint32_t flags)
     return std::make_tuple(dev, L, (flags & PA_CREATE_GENERIC_SWEEP) ? 0 : 1);
 }
 
+// Device allocator: cudaMalloc / cudaFree unless the caller installed callbacks
+// with pa_set_allocator.  An engine keeps the allocator it was created with, so
+// every block is freed by the allocator that made it.
+struct Allocator {
+    pa_alloc_fn alloc = nullptr;
+    pa_free_fn free_ = nullptr;
+    void *ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+
+Allocator current_allocator()
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    return g_alloc;
+}
+
+// One block from allocator `a` on `stream`; nullptr when it is refused.
+void *device_alloc(const Allocator &a, size_t bytes, cudaStream_t stream)
+{
+    if (bytes == 0) bytes = 16;
+    if (a.alloc) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        return a.alloc(bytes, dev, stream, a.ctx);
+    }
+    void *q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return q;
+}
+
+void device_free(const Allocator &a, void *p, size_t bytes, cudaStream_t stream)
+{
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    if (a.free_) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        a.free_(p, bytes, dev, stream, a.ctx);
+    } else {
+        cudaFree(p);
+    }
+}
+
+struct SmallGroup {  // small runs of one lattice size, annealed by anneal_small_kernel
+    uint32_t L = 0;
+    int any_glass = 0;
+    std::vector<uint32_t> runs;
+    uint64_t runs_off = 0;  // in d_meta
+};
+
 struct SweepGroup {  // runs of one lattice size among the resident runs
     uint32_t L = 0;
     int any_glass = 0;
@@ -177,6 +231,10 @@ struct pa_engine {
     uint64_t inf_off = 0, init_inf_off = 0;
     uint32_t inf_maxR = 0, init_inf_n = 0, init_inf_maxR = 0;
     std::vector<SweepGroup> groups;
+    std::vector<SmallGroup> small;     // runs on the one-launch-per-step path
+    uint32_t small_cs = 1;             // CTAs (one cluster) per small run
+    std::vector<uint32_t> big;         // the other resident runs (per-stage kernels)
+    uint64_t big_off = 0;
     std::map<uint32_t, Tuning> tuning;  // per lattice size
     uint32_t max_Rcap_active = 0, max_pw = 1;
     // execution
@@ -193,9 +251,12 @@ struct pa_engine {
     };
     std::vector<Timed> timed;
     uint64_t h2d = 0, d2h = 0;
-    void *wa_buf = nullptr;
+    Allocator alloc;                                   // the allocator of every block below
+    void *wa_buf = nullptr;                            // weighted averages of resident runs
     size_t wa_bytes = 0;
-    std::vector<void *> allocs;
+    void *sr_buf = nullptr;                            // pa_step_records staging
+    size_t sr_bytes = 0;
+    std::vector<std::pair<void *, size_t>> allocs;     // pools
 };
 
 namespace {
@@ -222,16 +283,29 @@ pa_status cuda_fail(cudaError_t e, const char *what)
 template <typename T>
 pa_status dalloc(pa_engine *e, T **p, size_t count)
 {
-    void *q = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
-    cudaError_t err = cudaMalloc(&q, bytes);
-    if (err != cudaSuccess) {
-        cudaGetLastError();
-        return err == cudaErrorMemoryAllocation ? PA_ERR_OOM : cuda_fail(err, "cudaMalloc");
-    }
-    e->allocs.push_back(q);
+    void *q = device_alloc(e->alloc, bytes, e->stream);
+    if (!q) return PA_ERR_OOM;
+    e->allocs.emplace_back(q, bytes);
     *p = static_cast<T *>(q);
+    return PA_OK;
+}
+
+// A growable engine-owned buffer (the old contents are not kept).
+pa_status ensure_buffer(pa_engine *e, void **buf, size_t *have, size_t bytes)
+{
+    if (*have >= bytes) return PA_OK;
+    if (*buf) {
+        cudaStreamSynchronize(e->stream);  // no queued work may still use it
+        device_free(e->alloc, *buf, *have, e->stream);
+    }
+    *buf = nullptr;
+    *have = 0;
+    void *q = device_alloc(e->alloc, bytes, e->stream);
+    if (!q) return PA_ERR_OOM;
+    *buf = q;
+    *have = bytes;
     return PA_OK;
 }
 
@@ -336,7 +410,7 @@ pa_status alloc_pools(pa_engine *e, const pa_server_config &c)
     PA_TRY(dalloc(e, &e->d_thr, 2 * c.record_capacity));
     PA_TRY(dalloc(e, &e->d_wtoff, c.record_capacity));
     PA_TRY(dalloc(e, &e->d_wt, c.table_doubles));
-    e->meta_cap = 14ull * e->S + 3ull * 128 + 1024;
+    e->meta_cap = 16ull * e->S + 3ull * 128 + 1024;
     PA_TRY(dalloc(e, &e->d_meta, e->meta_cap));
     PA_CUDA(cudaMemsetAsync(e->P.status, 0, sizeof(uint32_t), e->stream));
     e->P.runs = e->d_runs;
@@ -597,10 +671,42 @@ pa_status rebuild(pa_engine *e)
     m.clear();
     e->active_off = m.size();
     m.insert(m.end(), e->active.begin(), e->active.end());
+    // small runs (one launch per step) and the others
+    e->small.clear();
+    e->big.clear();
+    const bool fuse = !(e->flags & (PA_CREATE_SEPARATE_KERNELS | PA_CREATE_GENERIC_SWEEP));
+    uint32_t n_small = 0, max_tiles = 1;
+    for (uint32_t s : e->active) {
+        const RunDev &x = e->rd[s];
+        if (!fuse || !small_eligible(x)) {
+            e->big.push_back(s);
+            continue;
+        }
+        size_t k = 0;
+        while (k < e->small.size() && e->small[k].L != x.L) ++k;
+        if (k == e->small.size()) {
+            e->small.emplace_back();
+            e->small[k].L = x.L;
+        }
+        e->small[k].runs.push_back(s);
+        if (x.model == PA_EA_PMJ) e->small[k].any_glass = 1;
+        ++n_small;
+        const uint32_t tr = small_tile_replicas(x.L);
+        max_tiles = std::max(max_tiles, (x.R_cap + tr - 1) / tr);
+    }
+    for (auto &g : e->small) {
+        g.runs_off = m.size();
+        m.insert(m.end(), g.runs.begin(), g.runs.end());
+    }
+    // cluster size: about two CTAs per SM over all small runs, at most 8 (portable), at most the tiles
+    e->small_cs = 1;
+    while (e->small_cs < 8 && 2 * e->small_cs * n_small <= 2u * 152u && 2 * e->small_cs <= max_tiles) e->small_cs *= 2;
+    e->big_off = m.size();
+    m.insert(m.end(), e->big.begin(), e->big.end());
     e->q_runs.clear();
     e->max_Rcap_active = 0;
     for (uint32_t s : e->active) {
-        if (e->rd[s].overlap) e->q_runs.push_back(s);
+        if (e->rd[s].overlap) e->q_runs.push_back(s);  // small runs have none
         e->max_Rcap_active = std::max(e->max_Rcap_active, e->rd[s].R_cap);
     }
     e->q_off = m.size();
@@ -608,7 +714,7 @@ pa_status rebuild(pa_engine *e)
     e->near_runs.clear();
     e->multi_runs.clear();
     e->near_maxcap = e->multi_maxcap = 0;
-    for (uint32_t s : e->active) {
+    for (uint32_t s : e->big) {
         const bool multi = e->rd[s].resample == PA_MULTINOMIAL;
         (multi ? e->multi_runs : e->near_runs).push_back(s);
         uint32_t &cap = multi ? e->multi_maxcap : e->near_maxcap;
@@ -631,7 +737,7 @@ pa_status rebuild(pa_engine *e)
     std::map<uint32_t, size_t> gi;  // lattice size -> group, in order of first appearance
     e->inf_runs.clear();
     e->inf_maxR = 0;
-    for (uint32_t s : e->active) {
+    for (uint32_t s : e->big) {
         if (e->rd[s].theta == PA_THETA_INF) {  // sampled from the density of states, no sweep
             e->inf_runs.push_back(s);
             e->inf_maxR = std::max(e->inf_maxR, e->rd[s].R_cap);
@@ -840,10 +946,22 @@ void enqueue_dos_sample(pa_engine *e)
     });
 }
 
+// n_steps temperatures of every small run, one launch per lattice size.
+void enqueue_small(pa_engine *e, uint32_t n_steps)
+{
+    for (auto &g : e->small)
+        timed_launch(e, PA_K_SMALL, [&] {
+            launch_anneal_small(e->P, meta(e, g.runs_off), (uint32_t)g.runs.size(), g.L, e->small_cs, g.any_glass,
+                                n_steps, e->stream);
+        });
+}
+
 void enqueue_tick(pa_engine *e)
 {
-    const uint32_t *act = meta(e, e->active_off);
-    const uint32_t na = (uint32_t)e->active.size();
+    enqueue_small(e, 1);
+    if (e->big.empty()) return;
+    const uint32_t *act = meta(e, e->big_off);
+    const uint32_t na = (uint32_t)e->big.size();
     enqueue_resample(e);
     for (auto &g : e->groups) timed_launch(e, PA_K_SWEEP, [&] { launch_group_sweep(e, g, e->tuning[g.L].pick); });
     enqueue_dos_sample(e);
@@ -861,8 +979,9 @@ void enqueue_tick(pa_engine *e)
 // harmless; the last launch leaves the children in place.
 pa_status enqueue_tuning_tick(pa_engine *e)
 {
-    const uint32_t *act = meta(e, e->active_off);
-    const uint32_t na = (uint32_t)e->active.size();
+    enqueue_small(e, 1);
+    const uint32_t *act = meta(e, e->big_off);
+    const uint32_t na = (uint32_t)e->big.size();
     enqueue_resample(e);
     for (auto &g : e->groups) {
         Tuning &t = e->tuning[g.L];
@@ -901,7 +1020,7 @@ pa_status enqueue_tuning_tick(pa_engine *e)
             launch_overlap(e->P, meta(e, e->q_off), (uint32_t)e->q_runs.size(), e->max_Rcap_active, 0, e->stream);
         });
     enqueue_wang(e);
-    timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, act, na, e->max_Rcap_active, 0, e->stream); });
+    if (na) timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, act, na, e->max_Rcap_active, 0, e->stream); });
     PA_CUDA(cudaGetLastError());
     return PA_OK;
 }
@@ -951,11 +1070,13 @@ pa_status latch_device_status(pa_engine *e)
 
 pa_status engine_new(void *cuda_stream, uint32_t flags, pa_engine **out)
 {
-    if (flags & ~(uint32_t)(PA_CREATE_GENERIC_SWEEP | PA_CREATE_NO_AUTOTUNE)) return PA_ERR_INVALID_ARG;
+    if (flags & ~(uint32_t)(PA_CREATE_GENERIC_SWEEP | PA_CREATE_NO_AUTOTUNE | PA_CREATE_SEPARATE_KERNELS))
+        return PA_ERR_INVALID_ARG;
     PA_CUDA(prepare_kernels());
     pa_engine *e = new (std::nothrow) pa_engine();
     if (!e) return PA_ERR_OOM;
     e->flags = flags;
+    e->alloc = current_allocator();
     if (cuda_stream) {
         e->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -1044,8 +1165,9 @@ pa_status pa_destroy(pa_engine *e)
     if (e->stream) cudaStreamSynchronize(e->stream);
     if (e->graph_exec) cudaGraphExecDestroy(e->graph_exec);
     if (e->graph) cudaGraphDestroy(e->graph);
-    for (void *p : e->allocs) cudaFree(p);
-    if (e->wa_buf) cudaFree(e->wa_buf);
+    for (auto &b : e->allocs) device_free(e->alloc, b.first, b.second, e->stream);
+    device_free(e->alloc, e->wa_buf, e->wa_bytes, e->stream);
+    device_free(e->alloc, e->sr_buf, e->sr_bytes, e->stream);
     for (auto &t : e->timed) {
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
@@ -1227,6 +1349,12 @@ pa_status pa_anneal_step(pa_engine *e, uint32_t n_steps, int use_graph)
         PA_TRY(enqueue_tuning_tick(e));
         advance_host_steps(e, 1);
         if (--n_steps == 0) return PA_OK;
+    }
+    if (e->big.empty()) {  // every run on the small path: n temperatures in one launch per lattice size
+        enqueue_small(e, n_steps);
+        PA_CUDA(cudaGetLastError());
+        advance_host_steps(e, n_steps);
+        return PA_OK;
     }
     if (use_graph && !e->profiling) {
         if (!e->graph_exec) {
@@ -1431,22 +1559,39 @@ pa_status pa_population(pa_engine *e, uint32_t run, int8_t *host_spins, int32_t 
     return pa_population_slice(e, run, 0u, 0xFFFFFFFFu, host_spins, host_E, host_M, host_fam, R_out, step_out);
 }
 
-static pa_status ensure_wa(pa_engine *e, size_t bytes)
+static pa_status ensure_wa(pa_engine *e, size_t bytes) { return ensure_buffer(e, &e->wa_buf, &e->wa_bytes, bytes); }
+
+static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+pa_status pa_set_allocator(pa_alloc_fn alloc, pa_free_fn free_, void *ctx)
 {
-    if (e->wa_bytes >= bytes) return PA_OK;
-    if (e->wa_buf) cudaFree(e->wa_buf);
-    e->wa_buf = nullptr;
-    e->wa_bytes = 0;
-    cudaError_t err = cudaMalloc(&e->wa_buf, bytes);
-    if (err != cudaSuccess) {
-        cudaGetLastError();
-        return PA_ERR_OOM;
-    }
-    e->wa_bytes = bytes;
+    if ((alloc == nullptr) != (free_ == nullptr)) return PA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.free_ = free_;
+    g_alloc.ctx = alloc ? ctx : nullptr;
     return PA_OK;
 }
 
-static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+pa_status pa_step_records(pa_engine *e, const uint32_t *runs, uint32_t n_runs, pa_step_record *host_out)
+{
+    if (!e || !runs || !n_runs || !host_out) return PA_ERR_INVALID_ARG;
+    for (uint32_t k = 0; k < n_runs; ++k)
+        if (!slot_ok(e, runs[k])) return PA_ERR_INVALID_ARG;
+    PA_TRY(prepare(e));
+    const size_t b_rec = align256(sizeof(uint32_t) * n_runs);
+    PA_TRY(ensure_buffer(e, &e->sr_buf, &e->sr_bytes, b_rec + sizeof(pa_step_record) * n_runs));
+    auto *d_runs = static_cast<uint32_t *>(e->sr_buf);
+    auto *d_out = reinterpret_cast<pa_step_record *>(static_cast<char *>(e->sr_buf) + b_rec);
+    PA_CUDA(cudaMemcpyAsync(d_runs, runs, sizeof(uint32_t) * n_runs, cudaMemcpyHostToDevice, e->stream));
+    e->launches += 1;
+    launch_gather_records(e->P, d_runs, n_runs, d_out, e->stream);
+    PA_CUDA(cudaGetLastError());
+    PA_CUDA(cudaMemcpyAsync(host_out, d_out, sizeof(pa_step_record) * n_runs, cudaMemcpyDeviceToHost, e->stream));
+    e->h2d += sizeof(uint32_t) * n_runs;
+    e->d2h += sizeof(pa_step_record) * n_runs;
+    return sync_read(e);
+}
 
 pa_status pa_weighted_average_runs(pa_engine *e, const uint32_t *run_idx, uint32_t n_groups, uint32_t M,
                                    uint32_t weight_kind, pa_wavg *host_out, double *host_Pq, double *host_Pq_pair,
@@ -1524,12 +1669,10 @@ pa_status pa_weighted_average(const pa_step_record *recs, const uint32_t *qhist,
     const size_t b_pq = b_w + align256(Pq ? sizeof(double) * nP : 0);
     const size_t b_pqp = b_pq + align256(Pq_pair ? sizeof(double) * nP : 0);
     const size_t total = b_pqp + align256(Pq_wang ? sizeof(double) * nP : 0);
-    char *base = nullptr;
-    cudaError_t err = cudaMalloc(&base, total);
-    if (err != cudaSuccess) {
-        cudaGetLastError();
-        return PA_ERR_OOM;
-    }
+    const Allocator alloc = current_allocator();
+    char *base = static_cast<char *>(device_alloc(alloc, total, st));
+    if (!base) return PA_ERR_OOM;
+    cudaError_t err = cudaSuccess;
     pa_status s = PA_OK;
     std::vector<unsigned long long> roff(M), qoff(M);
     for (uint32_t m = 0; m < M; ++m) {
@@ -1566,7 +1709,7 @@ pa_status pa_weighted_average(const pa_step_record *recs, const uint32_t *qhist,
         err = cudaStreamSynchronize(st);
     } while (0);
     if (err != cudaSuccess) s = cuda_fail(err, "pa_weighted_average");
-    cudaFree(base);
+    device_free(alloc, base, total, st);
     return s;
 }
 

@@ -153,6 +153,17 @@ inline uint64_t scratch_words(uint32_t N, uint32_t R_cap)
     return scr_tail_off(N) + tail + 4;
 }
 
+// Small populations annealed by one launch per step (anneal_small_kernel): one
+// thread-block cluster per run, cluster size small_cluster().
+constexpr uint32_t SMALL_MAX_RCAP = 8192;
+inline bool small_eligible(const RunDev &x)
+{
+    return (x.L == 8 || x.L == 16 || x.L == 32) && x.theta != PA_THETA_INF && x.resample == PA_NEAREST &&
+           x.overlap == 0 && x.R_cap <= SMALL_MAX_RCAP;
+}
+// Replicas one CTA of the small-population kernel sweeps at a time.
+inline uint32_t small_tile_replicas(uint32_t L) { return L == 8 ? 64u : 16u; }
+
 // Launch wrappers implemented in pa_kernels.cu (all asynchronous on `s`).
 // `runs`: device list of the indices of the runs to process (the two
 // initialisation launches also take NULL for runs 0..n_runs-1).
@@ -197,6 +208,13 @@ void launch_wavg(const pa_step_record *recs, const unsigned long long *rec_off, 
                  const uint32_t *qhp, const unsigned long long *qh_off, uint32_t n_groups, uint32_t M,
                  uint32_t n_steps, uint32_t N, uint32_t kind, pa_wavg *out, double *w, double *Pq, double *Pqp,
                  cudaStream_t s);
+// Copies the record of each listed run at the temperature it has reached to out[k].
+void launch_gather_records(const Pool &P, const uint32_t *runs, uint32_t n_runs, pa_step_record *out,
+                           cudaStream_t s);
+// n_steps temperatures of the small runs `runs` (all of lattice size L), cs
+// CTAs (a cluster) per run.
+void launch_anneal_small(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t L, uint32_t cs, int any_glass,
+                         uint32_t n_steps, cudaStream_t s);
 cudaError_t prepare_kernels();
 // Philox-only calibration loop: blocks x threads threads, iters x 8 calls each.
 void launch_philox_calibration(uint32_t *out, uint32_t blocks, uint32_t threads, uint32_t iters, bool wide,

@@ -39,6 +39,7 @@
 //   Wang keys of replica j     ctr (j, 0, i, WANG<<24)                   words 0,1 pi, words 2,3 sigma
 // FP64 arithmetic that decides an integer uses explicit round-to-nearest
 // intrinsics (no contraction), in the same order as the plain definition.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -48,11 +49,13 @@
 
 namespace pa {
 
+namespace cg = cooperative_groups;
+
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 #ifndef PA_PACK_MODE
-#define PA_PACK_MODE 0  // packing of the comparison bits: 0 add/add (fastest with single 64-bit Philox products), 1 or/or, 2 or/add, 3 add/or
+#define PA_PACK_MODE 0  // packing of the comparison bits: 0 add/add (fastest with single 64-bit Philox products), 1 or/or, 2 or/add, 3 add/or, 4 predicated or, 5 select + or
 #endif
 constexpr uint32_t SMEM_BINS = 4096;
 
@@ -75,6 +78,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
     }
     return make_uint4(c0, c1, c2, c3);
 }
+
+#if PA_PACK_MODE >= 4
+// acc |= bit where u < t: a compare and a predicated or, both integer-ALU instructions.
+__device__ __forceinline__ void or_if_below(uint32_t &acc, uint32_t u, uint32_t t, uint32_t bit)
+{
+#if PA_PACK_MODE == 5
+    uint32_t m;
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\tselp.b32 %0, %3, 0, p;\n\t}" : "=r"(m) : "r"(u), "r"(t), "r"(bit));
+    acc |= m;
+#else
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}" : "+r"(acc) : "r"(u), "r"(t), "r"(bit));
+#endif
+}
+#endif
 
 __device__ __forceinline__ uint32_t pick(const uint4 &u, uint32_t q)
 {
@@ -1121,14 +1138,24 @@ __global__ void __launch_bounds__(MAXT) sweep_pow2_kernel(Pool P, const uint32_t
 #pragma unroll
                     for (uint32_t g = 0; g < 8; ++g) {
                         const uint4 u = philox_rk<true>(8 * w + g, child, ctr3, hi1_0, lo1_0, K);
-#if PA_PACK_MODE == 1 || PA_PACK_MODE == 2
+#if PA_PACK_MODE >= 4
+                        or_if_below(B1, u.x, t1, 1u << (4 * g));
+                        or_if_below(B1, u.y, t1, 2u << (4 * g));
+                        or_if_below(B1, u.z, t1, 4u << (4 * g));
+                        or_if_below(B1, u.w, t1, 8u << (4 * g));
+                        or_if_below(B2, u.x, t2, 1u << (4 * g));
+                        or_if_below(B2, u.y, t2, 2u << (4 * g));
+                        or_if_below(B2, u.z, t2, 4u << (4 * g));
+                        or_if_below(B2, u.w, t2, 8u << (4 * g));
+#elif PA_PACK_MODE == 1 || PA_PACK_MODE == 2
                         B1 |= ((uint32_t)(u.x < t1) << (4 * g)) | ((uint32_t)(u.y < t1) << (4 * g + 1)) |
                               ((uint32_t)(u.z < t1) << (4 * g + 2)) | ((uint32_t)(u.w < t1) << (4 * g + 3));
 #else
                         B1 += ((uint32_t)(u.x < t1) << (4 * g)) + ((uint32_t)(u.y < t1) << (4 * g + 1)) +
                               ((uint32_t)(u.z < t1) << (4 * g + 2)) + ((uint32_t)(u.w < t1) << (4 * g + 3));
 #endif
-#if PA_PACK_MODE == 1 || PA_PACK_MODE == 3
+#if PA_PACK_MODE >= 4
+#elif PA_PACK_MODE == 1 || PA_PACK_MODE == 3
                         B2 |= ((uint32_t)(u.x < t2) << (4 * g)) | ((uint32_t)(u.y < t2) << (4 * g + 1)) |
                               ((uint32_t)(u.z < t2) << (4 * g + 2)) | ((uint32_t)(u.w < t2) << (4 * g + 3));
 #else
@@ -1204,6 +1231,9 @@ constexpr uint32_t PAD_MAX_GROUPS = 9;
 #ifndef PA_PAD_MIN_BLOCKS
 #define PA_PAD_MIN_BLOCKS 3  // caps registers at 85: 3 CTAs of 256 threads per SM (measured best of 1, 2, 3)
 #endif
+#ifndef PA_PAD_MODE
+#define PA_PAD_MODE 0  // 0: each word's groups drawn by its thread; 1: aligned 32-site chunks, bits through shared memory
+#endif
 
 template <bool SG>
 __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off,
@@ -1229,6 +1259,11 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
     uint32_t *pl = smw + rloc * 2 * HW;
     int32_t *acc = reinterpret_cast<int32_t *>(smw + cfg.RPC * 2 * HW);
     if (threadIdx.x < 2 * cfg.RPC) acc[threadIdx.x] = 0;
+#if PA_PAD_MODE == 1
+    // comparison bits in compact site order, one 32-site chunk per thread: [2][HW] per replica
+    uint32_t *cmp = smw + cfg.RPC * 2 * HW + 2 * cfg.RPC + rloc * 2 * HW;
+    const uint32_t Nh = N / 2, n_chunks = (Nh + 31) / 32;
+#endif
 
     const uint32_t ob = (i - 1) & 1u, nbuf = i & 1u;
     uint32_t own[2] = {0u, 0u}, parent = 0;
@@ -1290,6 +1325,25 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
     for (uint32_t t = 0; t < rd.theta; ++t) {
 #pragma unroll
         for (uint32_t c = 0; c < 2; ++c) {
+#if PA_PAD_MODE == 1
+            if (active && w < n_chunks) {  // the 8 groups of compact sites [32 w, 32 w + 32), each drawn once
+                const uint32_t ctr3 = (TAG_SWEEP << 24) | (t << 1) | c;
+                uint32_t m1 = 0, m2 = 0;
+#pragma unroll
+                for (uint32_t g = 0; g < 8; ++g) {
+                    if (32 * w + 4 * g < Nh) {
+                        const uint4 u = philox_rk<false>(8 * w + g, child, ctr3, hi1_0, lo1_0, K);
+                        m1 += ((uint32_t)(u.x < t1) << (4 * g)) + ((uint32_t)(u.y < t1) << (4 * g + 1)) +
+                              ((uint32_t)(u.z < t1) << (4 * g + 2)) + ((uint32_t)(u.w < t1) << (4 * g + 3));
+                        m2 += ((uint32_t)(u.x < t2) << (4 * g)) + ((uint32_t)(u.y < t2) << (4 * g + 1)) +
+                              ((uint32_t)(u.z < t2) << (4 * g + 2)) + ((uint32_t)(u.w < t2) << (4 * g + 3));
+                    }
+                }
+                cmp[w] = m1;
+                cmp[HW + w] = m2;
+            }
+            __syncthreads();
+#endif
             if (active) {
                 uint32_t same, rot, up, dn;
                 neighbours(c, same, rot, up, dn);
@@ -1298,6 +1352,20 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
                 const uint32_t x3 = S ^ up ^ J[c][2], x4 = S ^ dn ^ J[c][3];
                 const uint32_t a = x1 ^ x2, b = x1 & x2, e = x3 ^ x4, f = x3 & x4;
                 const uint32_t c0 = a ^ e, ge2 = b | f | (a & e);
+#if PA_PAD_MODE == 1
+                // the word's compact sites kb .. kb + RW Lh - 1 (<= 32): a window of the chunk bits
+                const uint32_t q0 = kb >> 5, sh0 = kb & 31u;
+                const uint32_t C1 = __funnelshift_r(cmp[q0], q0 + 1 < n_chunks ? cmp[q0 + 1] : 0u, sh0);
+                const uint32_t C2 = __funnelshift_r(cmp[HW + q0], q0 + 1 < n_chunks ? cmp[HW + q0 + 1] : 0u, sh0);
+                uint32_t B1 = 0, B2 = 0;
+#pragma unroll
+                for (uint32_t r = 0; r < 8; ++r) {
+                    if (r < RW) {
+                        B1 |= ((C1 >> (r * Lh)) & ROWMASK) << (r * Pt);
+                        B2 |= ((C2 >> (r * Lh)) & ROWMASK) << (r * Pt);
+                    }
+                }
+#else
                 const uint32_t ctr3 = (TAG_SWEEP << 24) | (t << 1) | c;
                 // comparison bits of the word's compact sites kb..kend-1, in compact order from
                 // bit `off` of C1 / C2 (the Philox groups of 4 start at kb & ~3) ...
@@ -1324,6 +1392,7 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
                         B2 |= ((uint32_t)(C2 >> sh) & ROWMASK) << (r * Pt);
                     }
                 }
+#endif
                 const uint32_t flip = (ge2 | (c0 & (B1 | all1)) | B2 | all2) & VMASK;
                 own[c] = S ^ flip;
                 pl[c * HW + w] = own[c];
@@ -2420,6 +2489,360 @@ __global__ void wavg_q_kernel(const pa_step_record *recs, const unsigned long lo
 }
 
 // --------------------------------------------------------------------------
+// Small populations: one launch per anneal step, or per whole anneal (Sec. II.B
+// steps (ii)-(v)).  A run with nearest-integer resampling, no overlap pairs,
+// L/2 a power of two with 8 <= L <= 32 and R_cap <= SMALL_MAX_RCAP is annealed
+// by one thread-block cluster of CS CTAs (CS = gridDim.x / number of runs, set
+// by the launch).  Per temperature:
+//   CTA 0       copy numbers, their scan and the parent map (as
+//               resample_counts_kernel with one CTA per run);
+//   every CTA   its share of the children: the resampling copy and theta
+//               sweeps, each plane word's 8 Philox groups spread over LPW lanes
+//               whose comparison bits are joined by shuffles, so that even a
+//               few hundred replicas fill the SMs of the cluster;
+//   CTA 0       the measurement of the new population and the next
+//               resampling's tables (as measure_kernel with one CTA per run).
+// The phases are separated by cluster barriers (barrier.cluster arrive with
+// release and wait with acquire semantics at cluster scope, so each phase sees
+// the global memory the previous one wrote).  Every CTA of a cluster reads the
+// same run state after the same barrier, so all of them take the same number
+// of barriers.  The arithmetic, the Philox counters and the device state left
+// behind (records, scratch tables, run state) are those of the multi-kernel
+// path, so a run can move between the two paths at any step.
+// --------------------------------------------------------------------------
+constexpr uint32_t SMALL_THREADS = 512;
+constexpr uint32_t SMALL_MAX_N = 1024;  // L <= 32
+
+template <bool SG, uint32_t HW>  // HW: words of a colour plane (L = 8: 1, 16: 4, 32: 16)
+__global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, const uint32_t *runs, uint32_t n_steps)
+{
+    constexpr uint32_t LPW = HW >= 16 ? 2u : 8u;  // lanes per plane word
+    constexpr uint32_t GPL = 8u / LPW;             // Philox groups per lane and word
+    constexpr uint32_t LPR = HW * LPW;             // lanes per replica (divides 32)
+    constexpr uint32_t TR = SMALL_THREADS / LPR;   // replicas per tile
+    static_assert(LPR <= 32 && 32 % LPR == 0, "a replica's lanes lie in one warp");
+    __shared__ uint32_t s_pl[TR][2 * HW];
+    __shared__ uint32_t s_cnt[SMALL_MAX_RCAP];
+    __shared__ uint32_t s_hE[SMALL_MAX_N + 1], s_hM[SMALL_MAX_N + 1];
+    __shared__ uint32_t sh_u[32];
+    __shared__ long long sh_ll[32];
+    __shared__ Moments mom[SMALL_THREADS / 32];
+    __shared__ uint32_t sh_lo[SMALL_THREADS / 32], sh_hi[SMALL_THREADS / 32];
+    __shared__ double sh_S;
+    __shared__ uint32_t sh_carry;
+
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t CS = cl.num_blocks(), rank = cl.block_rank();
+    const uint32_t run = runs[blockIdx.x / CS];
+    const RunDev rd = P.runs[run];
+    RunState *st = &P.st[run];
+    const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31u, wid = tid >> 5, nw = nt >> 5;
+    const uint32_t N = rd.N, n1 = N + 1, Lh = rd.Lh;
+    const uint32_t rl = tid / LPR, ll = tid % LPR, w = ll / LPW, sub = ll % LPW;
+    unsigned long long *scr = P.scratch + rd.scr_off;
+    unsigned long long *thr_tab = scr + scr_table_off(N);
+    uint32_t *flo_tab = reinterpret_cast<uint32_t *>(scr + scr_level_off(N));
+    uint32_t *parent = P.parent + rd.rep_off;
+    PhiloxKeys K;
+    philox_keys(K, rd.seed, rd.run_id);
+    uint32_t J[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    if (SG) {  // the bond masks of this lane's plane word, both colours
+        const uint32_t *Jp = P.J + rd.J_off + 2 * rd.wstride;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int d = 0; d < 4; ++d) J[c][d] = Jp[(c * 4 + d) * HW + w];
+    }
+
+    // Every CTA decides from values that no CTA writes between the barriers
+    // around the read, so all of them leave the loop at the same point: the
+    // status before any barrier of this launch, the temperature index (written
+    // only by the measurement, between the second and third barrier of a step),
+    // and the status after the resampling (between its first and second barrier).
+    if (st->status) return;
+    for (uint32_t s = 0; s < n_steps; ++s) {
+        const uint32_t i = st->step + 1;
+        if (i >= rd.n_beta) break;
+        const uint32_t ob = (i - 1) & 1u, nb = i & 1u;
+
+        // ---- CTA 0: copy numbers r_j = floor(tau) + [u < threshold] per level, scan, parent map
+        if (rank == 0) {
+            const uint32_t Rc = st->R_cur;
+            const int32_t *E = P.E[ob] + rd.rep_off;
+            const int32_t Emin = st->Emin;
+            for (uint32_t j = tid; j < Rc; j += nt) {
+                const uint32_t n = (uint32_t)(E[j] - Emin) >> 2;
+                const uint32_t u = philox4x32_10(j, 0, i, TAG_RESAMPLE << 24, rd.seed, rd.run_id).x;
+                s_cnt[j] = flo_tab[n] + ((unsigned long long)u < thr_tab[n] ? 1u : 0u);
+            }
+            __syncthreads();
+            uint32_t carry = 0;
+            for (uint32_t base = 0; base < Rc; base += nt) {
+                const uint32_t j = base + tid, r = j < Rc ? s_cnt[j] : 0u;
+                uint32_t tot;
+                const uint32_t o = carry + block_exclusive_scan(r, sh_u, tot);
+                for (uint32_t c = 0; c < r; ++c)
+                    if (o + c < rd.R_cap) parent[o + c] = j;
+                carry += tot;
+            }
+            if (tid == 0) {
+                st->R_new = carry;
+                if (carry == 0)
+                    set_status(P, run, PA_ERR_EXTINCT);
+                else if (carry > rd.R_cap)
+                    set_status(P, run, PA_ERR_CAPACITY);
+                if (carry == 0 || carry > rd.R_cap) P.rec[rd.rec_off + i].status = st->status;
+            }
+        }
+        cl.sync();
+        if (st->status) break;
+
+        // ---- every CTA: its children, gathered from their parents and swept theta times
+        {
+            const uint32_t Rn = st->R_new;
+            const uint32_t chunk = (Rn + CS - 1) / CS;
+            const uint32_t c_lo = min(Rn, rank * chunk), c_hi = min(Rn, c_lo + chunk);
+            const unsigned long long T1 = P.thr[rd.thr_off + 2 * i], T2 = P.thr[rd.thr_off + 2 * i + 1];
+            const uint32_t t1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T1;
+            const uint32_t t2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T2;
+            const uint32_t all1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : 0u;
+            const uint32_t all2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : 0u;
+            const uint32_t hi1_0 = __umulhi(0xCD9E8D57u, i), lo1_0 = 0xCD9E8D57u * i;
+            uint32_t *pl = s_pl[rl];
+            for (uint32_t tile0 = c_lo; tile0 < c_hi; tile0 += TR) {
+                const uint32_t child = tile0 + rl;
+                const bool active = child < c_hi;
+                const uint32_t par = active ? parent[child] : 0u;
+                const uint32_t *src = P.spins[ob] + rd.spin_off + (uint64_t)par * rd.wstride;
+                uint32_t own[2];
+                own[0] = active ? src[w] : 0u;
+                own[1] = active ? src[HW + w] : 0u;
+                if (sub == 0) {
+                    pl[w] = own[0];
+                    pl[HW + w] = own[1];
+                }
+                __syncwarp();
+                for (uint32_t t = 0; t < rd.theta; ++t) {
+#pragma unroll
+                    for (uint32_t c = 0; c < 2; ++c) {
+                        uint32_t same, rot, up, dn;
+                        plane_neighbours(pl + (c ^ 1u) * HW, HW, Lh, c, w, same, rot, up, dn);
+                        const uint32_t S = own[c];
+                        const uint32_t x1 = S ^ same ^ J[c][0], x2 = S ^ rot ^ J[c][1];
+                        const uint32_t x3 = S ^ up ^ J[c][2], x4 = S ^ dn ^ J[c][3];
+                        const uint32_t a = x1 ^ x2, b = x1 & x2, e = x3 ^ x4, f = x3 & x4;
+                        const uint32_t c0 = a ^ e, ge2 = b | f | (a & e);
+                        const uint32_t ctr3 = (TAG_SWEEP << 24) | (t << 1) | c;
+                        uint32_t B1 = 0, B2 = 0;
+#pragma unroll
+                        for (uint32_t q = 0; q < GPL; ++q) {
+                            const uint32_t g = sub * GPL + q;
+                            const uint4 u = philox_rk<true>(8 * w + g, child, ctr3, hi1_0, lo1_0, K);
+                            B1 += ((uint32_t)(u.x < t1) << (4 * g)) + ((uint32_t)(u.y < t1) << (4 * g + 1)) +
+                                  ((uint32_t)(u.z < t1) << (4 * g + 2)) + ((uint32_t)(u.w < t1) << (4 * g + 3));
+                            B2 += ((uint32_t)(u.x < t2) << (4 * g)) + ((uint32_t)(u.y < t2) << (4 * g + 1)) +
+                                  ((uint32_t)(u.z < t2) << (4 * g + 2)) + ((uint32_t)(u.w < t2) << (4 * g + 3));
+                        }
+#pragma unroll
+                        for (uint32_t o = 1; o < LPW; o <<= 1) {  // the word's lanes are adjacent
+                            B1 |= __shfl_xor_sync(FULL, B1, o);
+                            B2 |= __shfl_xor_sync(FULL, B2, o);
+                        }
+                        own[c] = S ^ (ge2 | (c0 & (B1 | all1)) | B2 | all2);
+                        if (sub == 0) pl[c * HW + w] = own[c];
+                        __syncwarp();
+                    }
+                }
+                // the child: planes, E from the final lattice (every bond touches one colour-0 site), M
+                int32_t unsat = 0, up1 = 0;
+                if (sub == 0) {
+                    uint32_t same, rot, up, dn;
+                    plane_neighbours(pl + HW, HW, Lh, 0, w, same, rot, up, dn);
+                    const uint32_t S = own[0];
+                    unsat = __popc(S ^ same ^ J[0][0]) + __popc(S ^ rot ^ J[0][1]) + __popc(S ^ up ^ J[0][2]) +
+                            __popc(S ^ dn ^ J[0][3]);
+                    up1 = __popc(own[0]) + __popc(own[1]);
+                    if (active) {
+                        uint32_t *dst = P.spins[nb] + rd.spin_off + (uint64_t)child * rd.wstride;
+                        dst[w] = own[0];
+                        dst[HW + w] = own[1];
+                    }
+                }
+#pragma unroll
+                for (uint32_t o = LPW; o < LPR; o <<= 1) {
+                    unsat += __shfl_xor_sync(FULL, unsat, o);
+                    up1 += __shfl_xor_sync(FULL, up1, o);
+                }
+                if (active && ll == 0) {
+                    const uint64_t cc = rd.rep_off + child;
+                    P.E[nb][cc] = 2 * unsat - 2 * (int32_t)N;
+                    P.M[nb][cc] = 2 * up1 - (int32_t)N;
+                    P.fam[nb][cc] = P.fam[ob][rd.rep_off + par];
+                }
+                __syncwarp();
+            }
+        }
+        cl.sync();
+
+        // ---- CTA 0: measurement at beta_i and the next resampling's tables
+        if (rank == 0) {
+            const uint32_t R = st->R_new;
+            const int32_t *E = P.E[nb] + rd.rep_off;
+            const int32_t *M = P.M[nb] + rd.rep_off;
+            const uint32_t *fam = P.fam[nb] + rd.rep_off;
+            const int32_t twoN = 2 * (int32_t)N;
+            const int32_t eb = -twoN + ((E[0] + twoN) & 3);
+            for (uint32_t n = tid; n < n1; n += nt) {
+                s_hE[n] = 0u;
+                s_hM[n] = 0u;
+            }
+            if (tid == 0) sh_carry = 0u;
+            __syncthreads();
+            // per-value counts; family runs: a replica's run starts at the last start at or below it
+            long long c2 = 0;
+            uint32_t nfam = 0, cmax = 0;
+            for (uint32_t base = 0; base < R; base += nt) {
+                const uint32_t j = base + tid;
+                const bool ok = j < R;
+                bool start = false;
+                if (ok) {
+                    atomicAdd(&s_hE[(uint32_t)(E[j] - eb) >> 2], 1u);
+                    atomicAdd(&s_hM[(uint32_t)(M[j] + (int32_t)N) >> 1], 1u);
+                    start = j == 0 || fam[j] != fam[j - 1];
+                }
+                const uint32_t before = sh_carry;
+                uint32_t sj = block_inclusive_max(start ? j : 0u, sh_u);
+                sj = sj > before ? sj : before;
+                if (ok) {
+                    c2 += 2 * (long long)(j - sj) + 1;  // sum over a run of (2r + 1) = length^2
+                    cmax = j - sj + 1 > cmax ? j - sj + 1 : cmax;
+                    nfam += start ? 1u : 0u;
+                }
+                __syncthreads();
+                if (tid == nt - 1) sh_carry = sj;
+                __syncthreads();
+            }
+            c2 = block_sum(c2, sh_ll);
+            nfam = block_sum(nfam, sh_u);
+            cmax = block_max(cmax, sh_u, 0u);
+            // the moments from the histograms, and the occupied energy levels
+            Moments mo = {0, 0, 0, 0, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}};
+            uint32_t elo = 0xffffffffu, ehi = 0u;
+            for (uint32_t n = tid; n < n1; n += nt) {
+                const uint32_t he = s_hE[n], hm = s_hM[n];
+                if (he) {
+                    elo = n < elo ? n : elo;
+                    ehi = n > ehi ? n : ehi;
+                    const long long e = (long long)eb + 4ll * n;
+                    const unsigned long long ae = (unsigned long long)(e < 0 ? -e : e), e2 = ae * ae;
+                    mo.sE += (long long)he * e;
+                    mo.sE2 += (long long)((unsigned long long)he * e2);
+                    const I128 t3 = mul_u64(he, ae * e2);
+                    add128(mo.sE3, e < 0 ? neg128(t3) : t3);
+                    add128(mo.sE4, mul_128_u64(mul_u64(he, e2), e2));
+                }
+                if (hm) {
+                    const long long m = 2ll * n - (long long)N;
+                    const unsigned long long am = (unsigned long long)(m < 0 ? -m : m), m2 = am * am;
+                    mo.sAM += (long long)((unsigned long long)hm * am);
+                    mo.sM2 += (long long)((unsigned long long)hm * m2);
+                    add128(mo.sAM3, mul_u64(hm, am * m2));
+                    add128(mo.sM4, mul_128_u64(mul_u64(hm, m2), m2));
+                }
+            }
+            mo.sE = warp_sum(mo.sE);
+            mo.sE2 = warp_sum(mo.sE2);
+            mo.sAM = warp_sum(mo.sAM);
+            mo.sM2 = warp_sum(mo.sM2);
+            mo.sE3 = warp_sum128(mo.sE3);
+            mo.sE4 = warp_sum128(mo.sE4);
+            mo.sAM3 = warp_sum128(mo.sAM3);
+            mo.sM4 = warp_sum128(mo.sM4);
+            elo = warp_min(elo);
+            ehi = warp_max(ehi);
+            if (lane == 0) {
+                mom[wid] = mo;
+                sh_lo[wid] = elo;
+                sh_hi[wid] = ehi;
+            }
+            __syncthreads();
+            const bool prep = i + 1 < rd.n_beta;
+            if (tid == 0) {
+                Moments t = mom[0];
+                uint32_t l = sh_lo[0], h = sh_hi[0];
+                for (uint32_t k = 1; k < nw; ++k) {
+                    const Moments &q = mom[k];
+                    t.sE += q.sE;
+                    t.sE2 += q.sE2;
+                    t.sAM += q.sAM;
+                    t.sM2 += q.sM2;
+                    add128(t.sE3, q.sE3);
+                    add128(t.sE4, q.sE4);
+                    add128(t.sAM3, q.sAM3);
+                    add128(t.sM4, q.sM4);
+                    l = sh_lo[k] < l ? sh_lo[k] : l;
+                    h = sh_hi[k] > h ? sh_hi[k] : h;
+                }
+                pa_step_record *rec = P.rec + rd.rec_off + i;
+                const double lnQ = st->lnQ;
+                rec->beta = P.beta[rd.beta_off + i];
+                rec->lnQ = lnQ;
+                rec->minus_betaF = P.rec[rd.rec_off + i - 1].minus_betaF + lnQ;
+                rec->sumE = t.sE;
+                rec->sumE2 = t.sE2;
+                rec->sumAbsM = t.sAM;
+                rec->sumM2 = t.sM2;
+                rec->sum_c2 = c2;
+                rec->sumE3[0] = t.sE3.lo;
+                rec->sumE3[1] = (unsigned long long)t.sE3.hi;
+                rec->sumE4[0] = t.sE4.lo;
+                rec->sumE4[1] = (unsigned long long)t.sE4.hi;
+                rec->sumAbsM3[0] = t.sAM3.lo;
+                rec->sumAbsM3[1] = (unsigned long long)t.sAM3.hi;
+                rec->sumM4[0] = t.sM4.lo;
+                rec->sumM4[1] = (unsigned long long)t.sM4.hi;
+                rec->R = R;
+                rec->R_target = rd.R;
+                rec->n_fam = nfam;
+                rec->max_fam = cmax;
+                rec->N = N;
+                rec->status = 0;
+                st->step = i;
+                st->R_cur = R;
+                st->R_new = R;
+                sh_lo[0] = l;
+                sh_hi[0] = h;
+                if (prep) {  // S in ascending level order by one thread, then ln Q_{i+1} and E_min
+                    const uint32_t nb_l = h - l + 1;
+                    const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
+                    double S = 0.0;
+                    for (uint32_t n = 0; n < nb_l; ++n) S = __dadd_rn(S, __dmul_rn((double)s_hE[l + n], wt[n]));
+                    const int32_t Emin = eb + 4 * (int32_t)l;
+                    const double dbeta = P.beta[rd.beta_off + i + 1] - P.beta[rd.beta_off + i];
+                    sh_S = S;
+                    st->lnQ = (-dbeta) * (double)Emin + log(S) - log((double)R);
+                    st->Emin = Emin;
+                    st->n_levels = nb_l;
+                }
+            }
+            __syncthreads();
+            if (prep) {  // per level: floor(tau) and the draw threshold, tau = R_target w[n] / S
+                const uint32_t l = sh_lo[0], nb_l = sh_hi[0] - l + 1;
+                const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
+                const double S = sh_S;
+                for (uint32_t n = tid; n < nb_l; n += nt) {
+                    const double tau = __ddiv_rn(__dmul_rn((double)rd.R, wt[n]), S);
+                    const double fl = floor(tau);
+                    flo_tab[n] = (uint32_t)fl;
+                    thr_tab[n] = (unsigned long long)ceil(__dmul_rn(__dsub_rn(tau, fl), 4294967296.0));
+                }
+            }
+        }
+        cl.sync();
+    }
+}
+
+// --------------------------------------------------------------------------
 // Calibration of the integer-multiplier roof: independent Philox4x32-10 calls
 // (8 per thread and iteration), results folded into one word per thread.
 // --------------------------------------------------------------------------
@@ -2441,9 +2864,51 @@ __global__ void __launch_bounds__(128) philox_calibration_kernel(uint32_t *out, 
     out[t] = acc;
 }
 
+// The record of each listed run at the temperature it has reached (a gather
+// for pa_step_records: one copy back to the host for a whole batch).
+__global__ void gather_records_kernel(Pool P, const uint32_t *runs, uint32_t n, pa_step_record *out)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const uint32_t run = runs[t];
+    out[t] = P.rec[P.runs[run].rec_off + P.st[run].step];
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
+void launch_anneal_small(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t L, uint32_t cs, int any_glass,
+                         uint32_t n_steps, cudaStream_t s)
+{
+    if (n_runs == 0 || n_steps == 0) return;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_runs * cs);
+    cfg.blockDim = dim3(SMALL_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (L == 8)
+        any_glass ? cudaLaunchKernelEx(&cfg, anneal_small_kernel<true, 1>, P, runs, n_steps)
+                  : cudaLaunchKernelEx(&cfg, anneal_small_kernel<false, 1>, P, runs, n_steps);
+    else if (L == 16)
+        any_glass ? cudaLaunchKernelEx(&cfg, anneal_small_kernel<true, 4>, P, runs, n_steps)
+                  : cudaLaunchKernelEx(&cfg, anneal_small_kernel<false, 4>, P, runs, n_steps);
+    else
+        any_glass ? cudaLaunchKernelEx(&cfg, anneal_small_kernel<true, 16>, P, runs, n_steps)
+                  : cudaLaunchKernelEx(&cfg, anneal_small_kernel<false, 16>, P, runs, n_steps);
+}
+
+void launch_gather_records(const Pool &P, const uint32_t *runs, uint32_t n_runs, pa_step_record *out, cudaStream_t s)
+{
+    gather_records_kernel<<<(n_runs + 127) / 128, 128, 0, s>>>(P, runs, n_runs, out);
+}
+
 cudaError_t prepare_kernels()
 {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2546,7 +3011,7 @@ std::vector<SweepCfg> sweep_candidates(uint32_t L, int allow_fast)
             c.block = c.RPC * HW;
             c.G = (N + 7) / 8;
             c.PS = 0;
-            c.smem = c.RPC * 2 * HW * 4 + 8 * c.RPC;
+            c.smem = c.RPC * 2 * HW * 4 + 8 * c.RPC + (PA_PAD_MODE == 1 ? c.RPC * 2 * HW * 4 : 0);
             v.push_back(c);
         }
         return v;

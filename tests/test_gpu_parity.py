@@ -248,7 +248,7 @@ def test_philox_calibration_reports_a_plausible_rate():
 
 def test_tuned_shapes_are_reused_by_later_engines():
     b = W.schedule(1.0, 4)
-    descs = [W.RunDesc(32, W.FERRO, 300, 2, b, seed=9, run_id=r) for r in range(3)]
+    descs = [W.RunDesc(64, W.FERRO, 100, 2, b, seed=9, run_id=r) for r in range(3)]
     with _lib.Engine(descs) as a:
         a.step(3, False)
         shape_a = _lib.pa_sweep_shapes(a.h)

@@ -51,3 +51,86 @@ def test_two_gloo_ranks_shard_and_reduce():
 
 def test_single_process_reduce_is_identity():
     assert replicas.reduce_timing(3.5, 7.0, None) == (3.5, 7.0)
+
+
+def _split_worker(rank, world, port, q):
+    import numpy as np
+
+    import oracle as O
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        batch = _batch()
+    except Exception as exc:  # report instead of leaving the parent waiting
+        q.put(([], repr(exc)))
+        raise
+    try:
+        local, idx = replicas.split(batch, rank, world)
+        recs = [O.OracleRun.from_desc(d) for d in local]
+        for r in recs:
+            r.run_to_end()
+        out = replicas.gather_records([r.records() for r in recs], idx, len(batch), dist)
+        if rank == 0:
+            q.put((idx, [np.asarray(x).tobytes() for x in out]))
+        else:
+            q.put((idx, None))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def _batch():
+    import dataclasses
+    fm = W.ferro_runs(L=6, R=60, theta=1, beta_f=0.6, n=5, M=5, seed=2)
+    return fm + [dataclasses.replace(d, paired=d.paired + len(fm))
+                 for d in W.glass_pairs(L=6, R=50, theta=1, beta_f=1.5, n=5, n_samples=2, seed=3)]
+
+
+def test_fixed_batch_split_over_two_ranks_gives_one_rank_weighted_averages():
+    """A fixed batch (5 ferromagnet runs and 2 glass samples of two paired
+    populations) split over two gloo ranks: the records gathered to rank 0 are
+    those of one process annealing the whole batch, so the free-energy
+    weighted averages (Eqs. W_conf, W_F) over groups of runs are identical."""
+    import numpy as np
+
+    import oracle as O
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 31500 + os.getpid() % 2000
+    procs = [ctx.Process(target=_split_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=300) for _ in range(world)]
+    assert not any(isinstance(g, str) for _, g in res), res
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    idx = sorted(j for i, _ in res for j in i)
+    batch = _batch()
+    assert idx == list(range(len(batch)))                                  # every run exactly once
+    gathered = next(g for _, g in res if g is not None)
+    one = []
+    for d in batch:
+        r = O.OracleRun.from_desc(d)
+        r.run_to_end()
+        one.append(r.records())
+    assert gathered == [x.tobytes() for x in one]
+    recs = np.stack([np.frombuffer(x, dtype=O.RECORD_DTYPE) for x in gathered])
+    for grp, (lo, hi) in enumerate([(0, 5), (5, 7), (7, 9)]):
+        a = O.weighted_average(recs[lo:hi], 36, 0)[0]
+        b = O.weighted_average(np.stack(one[lo:hi]), 36, 0)[0]
+        assert a.tobytes() == b.tobytes(), grp
+
+
+def test_split_keeps_pairs_together_and_covers_the_batch():
+    batch = _batch()
+    for world in (1, 2, 3, 4):
+        seen = []
+        for rank in range(world):
+            local, idx = replicas.split(batch, rank, world)
+            seen += idx
+            for d, j in zip(local, idx):
+                if d.paired >= 0:
+                    assert idx[d.paired] == batch[j].paired
+        assert seen == list(range(len(batch)))
