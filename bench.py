@@ -108,7 +108,10 @@ def parse():
     ap.add_argument("--workload", default="uneven_4096", choices=sorted(WORKLOADS))
     ap.add_argument("--samples", type=int, default=100, help="glass: disorder samples (2 populations each)")
     ap.add_argument("--runs", type=int, default=0, help="ising/uneven: number of runs (0 = the workload's)")
-    ap.add_argument("--window", type=float, default=2.0, help="serving: seconds of arrivals")
+    ap.add_argument("--window", type=float, default=10.0, help="serving: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--rates", default="", help="serving: comma-separated arrival rates to sweep for the largest "
+                                                "sustainable rate (then 50 %% and 80 %% of it are measured too)")
     ap.add_argument("--wang", action="store_true", help="also measure Wang pairing overlaps (Sec. III.D)")
     ap.add_argument("--max-temps", type=int, default=0,
                     help="anneal only the first T temperatures of the schedule (0 = all); reported in config")
@@ -843,7 +846,7 @@ def serving_main(args, rank, world, cpu):
     from paper_2207_05535_gb300 import workloads as W
     stream = torch.cuda.Stream()
     cfg = serve.config_for_budget(64 << 30)
-    arrivals = W.serving_stream(duration=args.window, seed=11 + 1000 * rank)
+    arrivals = W.serving_stream(rate=args.rate, duration=args.window, seed=11 + 1000 * rank)
     # warm-up: a short stream (tunes the sweep shapes of the lattice sizes it meets)
     warm = W.serving_stream(duration=0.2, seed=99)
     for _ in range(max(1, args.warmup)):
@@ -874,11 +877,16 @@ def serving_main(args, rank, world, cpu):
         pt = time.perf_counter() - t0
         plain = {"value": upd / (pt * 1e9), "unit": UNIT, "runs": 20, "runs_per_s": 20 / pt,
                  "form": "the first 20 jobs one after another, one engine and launch sequence each"}
+    sweep = None
+    if args.rates:
+        sweep = rate_sweep([float(x) for x in args.rates.split(",")], args.window, cfg, stream, rank)
     out = {"metric": METRIC, "value": summ["updates_per_ns"], "unit": UNIT, "n_gpus": world, "steps": 1,
            "warmup": args.warmup, "ms_per_step": 1e3 * st["wall_s"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
-           "config": {"workload": WORKLOADS["serving"], "name": "serving", "window_s": args.window,
-                      "jobs": len(arrivals), "form": "continuous batching (admit/retire between steps)"},
+           "config": {"workload": WORKLOADS["serving"].replace("200/s", f"{args.rate:g}/s"), "name": "serving",
+                      "window_s": args.window, "jobs": len(arrivals),
+                      "form": "continuous batching (admit/retire between steps)"},
+           "rate_sweep": sweep,
            "serving": summ, "runs_per_s": summ["jobs_per_s"], "gpu_launches": launches, "clocks": clk,
            "plain": plain, "cpu_baseline": cpu,
            "e2e": {"value": summ["updates_per_ns"], "unit": UNIT, "h2d_bytes_per_step": None,
@@ -886,6 +894,43 @@ def serving_main(args, rank, world, cpu):
                    "(descriptor and table uploads), steps, record copies, retirements"}}
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def serve_rate(rate, window, cfg, stream, seed):
+    """One Poisson stream at `rate` jobs/s for `window` s through a fresh server."""
+    import numpy as np
+    from paper_2207_05535_gb300 import serve
+    from paper_2207_05535_gb300 import workloads as W
+    arrivals = W.serving_stream(rate=rate, duration=window, seed=seed)
+    srv = serve.Server(cfg, stream.cuda_stream)
+    done, st = serve.serve(arrivals, srv)
+    srv.close()
+    summ = serve.summarize(done, st["wall_s"])
+    by_arrival = sorted(done, key=lambda j: j.arrival)
+    third = max(1, len(by_arrival) // 3)
+    wait_first = float(np.mean([j.admitted - j.arrival for j in by_arrival[:third]]))
+    wait_last = float(np.mean([j.admitted - j.arrival for j in by_arrival[-third:]]))
+    summ.update(rate=rate, offered_jobs=len(arrivals), mean_wait_first_third_s=wait_first,
+                mean_wait_last_third_s=wait_last,
+                sustained=bool(wait_last <= max(2.0 * wait_first, 0.5)))
+    return summ
+
+
+def rate_sweep(rates, window, cfg, stream, rank):
+    """Largest sustainable arrival rate: the queue does not grow over the window
+    (the last third of the arrivals waits at most twice as long for admission as
+    the first third, or under 0.5 s); then latencies at 50 % and 80 % of it."""
+    points = [serve_rate(r, window, cfg, stream, 21 + 1000 * rank) for r in sorted(rates)]
+    ok = [p["rate"] for p in points if p["sustained"]]
+    lam = max(ok) if ok else None
+    at = {}
+    if lam:
+        for f in (0.5, 0.8):
+            at[f"{int(f * 100)}%"] = serve_rate(f * lam, window, cfg, stream, 21 + 1000 * rank)
+        at["100%"] = next(p for p in points if p["rate"] == lam)
+    return {"points": points, "max_sustainable_rate": lam, "at_fraction_of_max": at,
+            "criterion": "queue not growing: mean admission wait of the last third of the arrivals <= max(2 x that "
+                         "of the first third, 0.5 s)"}
 
 
 if __name__ == "__main__":

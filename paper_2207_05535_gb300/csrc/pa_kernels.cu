@@ -55,7 +55,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 #ifndef PA_PACK_MODE
-#define PA_PACK_MODE 0  // packing of the comparison bits: 0 add/add (fastest with single 64-bit Philox products), 1 or/or, 2 or/add, 3 add/or, 4 predicated or, 5 select + or
+#define PA_PACK_MODE 0  // packing of the comparison bits: 0 compare + predicated or (integer ALU), 1 shifted adds
 #endif
 constexpr uint32_t SMEM_BINS = 4096;
 
@@ -79,19 +79,34 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
     return make_uint4(c0, c1, c2, c3);
 }
 
-#if PA_PACK_MODE >= 4
-// acc |= bit where u < t: a compare and a predicated or, both integer-ALU instructions.
+// acc |= bit where u < t: a compare and a predicated or, both on the integer
+// ALU, which leaves the multiplier pipe to Philox (the sweeps' binding unit).
 __device__ __forceinline__ void or_if_below(uint32_t &acc, uint32_t u, uint32_t t, uint32_t bit)
 {
-#if PA_PACK_MODE == 5
-    uint32_t m;
-    asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\tselp.b32 %0, %3, 0, p;\n\t}" : "=r"(m) : "r"(u), "r"(t), "r"(bit));
-    acc |= m;
-#else
     asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}" : "+r"(acc) : "r"(u), "r"(t), "r"(bit));
+}
+
+// The comparison bits of one Philox group g (uniforms u) against t1 and t2 into
+// bits 4g..4g+3 of B1 and B2.
+__device__ __forceinline__ void pack_group(uint32_t &B1, uint32_t &B2, const uint4 &u, uint32_t g, uint32_t t1,
+                                           uint32_t t2)
+{
+#if PA_PACK_MODE == 1
+    B1 += ((uint32_t)(u.x < t1) << (4 * g)) + ((uint32_t)(u.y < t1) << (4 * g + 1)) +
+          ((uint32_t)(u.z < t1) << (4 * g + 2)) + ((uint32_t)(u.w < t1) << (4 * g + 3));
+    B2 += ((uint32_t)(u.x < t2) << (4 * g)) + ((uint32_t)(u.y < t2) << (4 * g + 1)) +
+          ((uint32_t)(u.z < t2) << (4 * g + 2)) + ((uint32_t)(u.w < t2) << (4 * g + 3));
+#else
+    or_if_below(B1, u.x, t1, 1u << (4 * g));
+    or_if_below(B1, u.y, t1, 2u << (4 * g));
+    or_if_below(B1, u.z, t1, 4u << (4 * g));
+    or_if_below(B1, u.w, t1, 8u << (4 * g));
+    or_if_below(B2, u.x, t2, 1u << (4 * g));
+    or_if_below(B2, u.y, t2, 2u << (4 * g));
+    or_if_below(B2, u.z, t2, 4u << (4 * g));
+    or_if_below(B2, u.w, t2, 8u << (4 * g));
 #endif
 }
-#endif
 
 __device__ __forceinline__ uint32_t pick(const uint4 &u, uint32_t q)
 {
@@ -1138,30 +1153,7 @@ __global__ void __launch_bounds__(MAXT) sweep_pow2_kernel(Pool P, const uint32_t
 #pragma unroll
                     for (uint32_t g = 0; g < 8; ++g) {
                         const uint4 u = philox_rk<true>(8 * w + g, child, ctr3, hi1_0, lo1_0, K);
-#if PA_PACK_MODE >= 4
-                        or_if_below(B1, u.x, t1, 1u << (4 * g));
-                        or_if_below(B1, u.y, t1, 2u << (4 * g));
-                        or_if_below(B1, u.z, t1, 4u << (4 * g));
-                        or_if_below(B1, u.w, t1, 8u << (4 * g));
-                        or_if_below(B2, u.x, t2, 1u << (4 * g));
-                        or_if_below(B2, u.y, t2, 2u << (4 * g));
-                        or_if_below(B2, u.z, t2, 4u << (4 * g));
-                        or_if_below(B2, u.w, t2, 8u << (4 * g));
-#elif PA_PACK_MODE == 1 || PA_PACK_MODE == 2
-                        B1 |= ((uint32_t)(u.x < t1) << (4 * g)) | ((uint32_t)(u.y < t1) << (4 * g + 1)) |
-                              ((uint32_t)(u.z < t1) << (4 * g + 2)) | ((uint32_t)(u.w < t1) << (4 * g + 3));
-#else
-                        B1 += ((uint32_t)(u.x < t1) << (4 * g)) + ((uint32_t)(u.y < t1) << (4 * g + 1)) +
-                              ((uint32_t)(u.z < t1) << (4 * g + 2)) + ((uint32_t)(u.w < t1) << (4 * g + 3));
-#endif
-#if PA_PACK_MODE >= 4
-#elif PA_PACK_MODE == 1 || PA_PACK_MODE == 3
-                        B2 |= ((uint32_t)(u.x < t2) << (4 * g)) | ((uint32_t)(u.y < t2) << (4 * g + 1)) |
-                              ((uint32_t)(u.z < t2) << (4 * g + 2)) | ((uint32_t)(u.w < t2) << (4 * g + 3));
-#else
-                        B2 += ((uint32_t)(u.x < t2) << (4 * g)) + ((uint32_t)(u.y < t2) << (4 * g + 1)) +
-                              ((uint32_t)(u.z < t2) << (4 * g + 2)) + ((uint32_t)(u.w < t2) << (4 * g + 3));
-#endif
+                        pack_group(B1, B2, u, g, t1, t2);
                     }
                     const uint32_t flip = ge2 | (c0 & (B1 | all1)) | B2 | all2;
                     own[q][c] = S ^ flip;
@@ -1231,9 +1223,7 @@ constexpr uint32_t PAD_MAX_GROUPS = 9;
 #ifndef PA_PAD_MIN_BLOCKS
 #define PA_PAD_MIN_BLOCKS 3  // caps registers at 85: 3 CTAs of 256 threads per SM (measured best of 1, 2, 3)
 #endif
-#ifndef PA_PAD_MODE
-#define PA_PAD_MODE 0  // 0: each word's groups drawn by its thread; 1: aligned 32-site chunks, bits through shared memory
-#endif
+
 
 template <bool SG>
 __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off,
@@ -1259,11 +1249,6 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
     uint32_t *pl = smw + rloc * 2 * HW;
     int32_t *acc = reinterpret_cast<int32_t *>(smw + cfg.RPC * 2 * HW);
     if (threadIdx.x < 2 * cfg.RPC) acc[threadIdx.x] = 0;
-#if PA_PAD_MODE == 1
-    // comparison bits in compact site order, one 32-site chunk per thread: [2][HW] per replica
-    uint32_t *cmp = smw + cfg.RPC * 2 * HW + 2 * cfg.RPC + rloc * 2 * HW;
-    const uint32_t Nh = N / 2, n_chunks = (Nh + 31) / 32;
-#endif
 
     const uint32_t ob = (i - 1) & 1u, nbuf = i & 1u;
     uint32_t own[2] = {0u, 0u}, parent = 0;
@@ -1325,25 +1310,6 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
     for (uint32_t t = 0; t < rd.theta; ++t) {
 #pragma unroll
         for (uint32_t c = 0; c < 2; ++c) {
-#if PA_PAD_MODE == 1
-            if (active && w < n_chunks) {  // the 8 groups of compact sites [32 w, 32 w + 32), each drawn once
-                const uint32_t ctr3 = (TAG_SWEEP << 24) | (t << 1) | c;
-                uint32_t m1 = 0, m2 = 0;
-#pragma unroll
-                for (uint32_t g = 0; g < 8; ++g) {
-                    if (32 * w + 4 * g < Nh) {
-                        const uint4 u = philox_rk<false>(8 * w + g, child, ctr3, hi1_0, lo1_0, K);
-                        m1 += ((uint32_t)(u.x < t1) << (4 * g)) + ((uint32_t)(u.y < t1) << (4 * g + 1)) +
-                              ((uint32_t)(u.z < t1) << (4 * g + 2)) + ((uint32_t)(u.w < t1) << (4 * g + 3));
-                        m2 += ((uint32_t)(u.x < t2) << (4 * g)) + ((uint32_t)(u.y < t2) << (4 * g + 1)) +
-                              ((uint32_t)(u.z < t2) << (4 * g + 2)) + ((uint32_t)(u.w < t2) << (4 * g + 3));
-                    }
-                }
-                cmp[w] = m1;
-                cmp[HW + w] = m2;
-            }
-            __syncthreads();
-#endif
             if (active) {
                 uint32_t same, rot, up, dn;
                 neighbours(c, same, rot, up, dn);
@@ -1352,20 +1318,6 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
                 const uint32_t x3 = S ^ up ^ J[c][2], x4 = S ^ dn ^ J[c][3];
                 const uint32_t a = x1 ^ x2, b = x1 & x2, e = x3 ^ x4, f = x3 & x4;
                 const uint32_t c0 = a ^ e, ge2 = b | f | (a & e);
-#if PA_PAD_MODE == 1
-                // the word's compact sites kb .. kb + RW Lh - 1 (<= 32): a window of the chunk bits
-                const uint32_t q0 = kb >> 5, sh0 = kb & 31u;
-                const uint32_t C1 = __funnelshift_r(cmp[q0], q0 + 1 < n_chunks ? cmp[q0 + 1] : 0u, sh0);
-                const uint32_t C2 = __funnelshift_r(cmp[HW + q0], q0 + 1 < n_chunks ? cmp[HW + q0 + 1] : 0u, sh0);
-                uint32_t B1 = 0, B2 = 0;
-#pragma unroll
-                for (uint32_t r = 0; r < 8; ++r) {
-                    if (r < RW) {
-                        B1 |= ((C1 >> (r * Lh)) & ROWMASK) << (r * Pt);
-                        B2 |= ((C2 >> (r * Lh)) & ROWMASK) << (r * Pt);
-                    }
-                }
-#else
                 const uint32_t ctr3 = (TAG_SWEEP << 24) | (t << 1) | c;
                 // comparison bits of the word's compact sites kb..kend-1, in compact order from
                 // bit `off` of C1 / C2 (the Philox groups of 4 start at kb & ~3) ...
@@ -1392,7 +1344,6 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
                         B2 |= ((uint32_t)(C2 >> sh) & ROWMASK) << (r * Pt);
                     }
                 }
-#endif
                 const uint32_t flip = (ge2 | (c0 & (B1 | all1)) | B2 | all2) & VMASK;
                 own[c] = S ^ flip;
                 pl[c * HW + w] = own[c];
@@ -2638,10 +2589,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
                         for (uint32_t q = 0; q < GPL; ++q) {
                             const uint32_t g = sub * GPL + q;
                             const uint4 u = philox_rk<true>(8 * w + g, child, ctr3, hi1_0, lo1_0, K);
-                            B1 += ((uint32_t)(u.x < t1) << (4 * g)) + ((uint32_t)(u.y < t1) << (4 * g + 1)) +
-                                  ((uint32_t)(u.z < t1) << (4 * g + 2)) + ((uint32_t)(u.w < t1) << (4 * g + 3));
-                            B2 += ((uint32_t)(u.x < t2) << (4 * g)) + ((uint32_t)(u.y < t2) << (4 * g + 1)) +
-                                  ((uint32_t)(u.z < t2) << (4 * g + 2)) + ((uint32_t)(u.w < t2) << (4 * g + 3));
+                            pack_group(B1, B2, u, g, t1, t2);
                         }
 #pragma unroll
                         for (uint32_t o = 1; o < LPW; o <<= 1) {  // the word's lanes are adjacent
@@ -3011,7 +2959,7 @@ std::vector<SweepCfg> sweep_candidates(uint32_t L, int allow_fast)
             c.block = c.RPC * HW;
             c.G = (N + 7) / 8;
             c.PS = 0;
-            c.smem = c.RPC * 2 * HW * 4 + 8 * c.RPC + (PA_PAD_MODE == 1 ? c.RPC * 2 * HW * 4 : 0);
+            c.smem = c.RPC * 2 * HW * 4 + 8 * c.RPC;
             v.push_back(c);
         }
         return v;
