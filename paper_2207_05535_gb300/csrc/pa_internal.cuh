@@ -161,8 +161,25 @@ inline bool small_eligible(const RunDev &x)
     return (x.L == 8 || x.L == 16 || x.L == 32) && x.theta != PA_THETA_INF && x.resample == PA_NEAREST &&
            x.overlap == 0 && x.R_cap <= SMALL_MAX_RCAP;
 }
-// Replicas one CTA of the small-population kernel sweeps at a time.
-inline uint32_t small_tile_replicas(uint32_t L) { return L == 8 ? 64u : 16u; }
+// Lanes that share one colour-plane word in the small-population kernel's
+// sweeps (each draws 8 / LPW of the word's Philox groups); the fastest
+// measured for 20 runs of a few hundred replicas: 8 at L = 8, 2 at L = 16,
+// 1 and 2 alike at L = 32.
+#ifndef SMALL_LPW_L8
+#define SMALL_LPW_L8 8
+#endif
+#ifndef SMALL_LPW_L16
+#define SMALL_LPW_L16 2
+#endif
+#ifndef SMALL_LPW_L32
+#define SMALL_LPW_L32 2
+#endif
+// Replicas one CTA (512 threads) of the small-population kernel sweeps at a time.
+inline uint32_t small_tile_replicas(uint32_t L)
+{
+    const uint32_t words = L * L / 64, lpw = L == 8 ? SMALL_LPW_L8 : L == 16 ? SMALL_LPW_L16 : SMALL_LPW_L32;
+    return 512u / (words * lpw);
+}
 
 // Launch wrappers implemented in pa_kernels.cu (all asynchronous on `s`).
 // `runs`: device list of the indices of the runs to process (the two

@@ -1321,6 +1321,7 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
                 const uint32_t ctr3 = (TAG_SWEEP << 24) | (t << 1) | c;
                 // comparison bits of the word's compact sites kb..kend-1, in compact order from
                 // bit `off` of C1 / C2 (the Philox groups of 4 start at kb & ~3) ...
+#if PA_PACK_MODE == 1
                 unsigned long long C1 = 0, C2 = 0;
 #pragma unroll
                 for (uint32_t q = 0; q < PAD_MAX_GROUPS; ++q) {
@@ -1334,6 +1335,23 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
                               << (4 * q);
                     }
                 }
+#else
+                // groups 0..7 fill the low words, group 8 the high words (positions 32..35)
+                uint32_t C1l = 0, C2l = 0, C1h = 0, C2h = 0;
+#pragma unroll
+                for (uint32_t q = 0; q < PAD_MAX_GROUPS - 1; ++q) {
+                    if (q < ng) {
+                        const uint4 u = philox_rk<false>(g0 + q, child, ctr3, hi1_0, lo1_0, K);
+                        pack_group(C1l, C2l, u, q, t1, t2);
+                    }
+                }
+                if (ng == PAD_MAX_GROUPS) {
+                    const uint4 u = philox_rk<false>(g0 + PAD_MAX_GROUPS - 1, child, ctr3, hi1_0, lo1_0, K);
+                    pack_group(C1h, C2h, u, 0, t1, t2);
+                }
+                const unsigned long long C1 = ((unsigned long long)C1h << 32) | C1l;
+                const unsigned long long C2 = ((unsigned long long)C2h << 32) | C2l;
+#endif
                 // ... then each row's Lh bits moved to its padded position r * Pt
                 uint32_t B1 = 0, B2 = 0;
 #pragma unroll
@@ -2464,23 +2482,26 @@ __global__ void wavg_q_kernel(const pa_step_record *recs, const unsigned long lo
 constexpr uint32_t SMALL_THREADS = 512;
 constexpr uint32_t SMALL_MAX_N = 1024;  // L <= 32
 
-template <bool SG, uint32_t HW>  // HW: words of a colour plane (L = 8: 1, 16: 4, 32: 16)
+template <bool SG, uint32_t HW, uint32_t LPW>  // HW: words of a colour plane (L = 8: 1, 16: 4, 32: 16); LPW lanes per word
 __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, const uint32_t *runs, uint32_t n_steps)
 {
-    constexpr uint32_t LPW = HW >= 16 ? 2u : 8u;  // lanes per plane word
     constexpr uint32_t GPL = 8u / LPW;             // Philox groups per lane and word
     constexpr uint32_t LPR = HW * LPW;             // lanes per replica (divides 32)
     constexpr uint32_t TR = SMALL_THREADS / LPR;   // replicas per tile
     static_assert(LPR <= 32 && 32 % LPR == 0, "a replica's lanes lie in one warp");
     __shared__ uint32_t s_pl[TR][2 * HW];
-    __shared__ uint32_t s_cnt[SMALL_MAX_RCAP];
+    __shared__ __align__(16) uint32_t s_cnt[SMALL_MAX_RCAP];  // copy numbers; the measurement's terms h_n w[n]
     __shared__ uint32_t s_hE[SMALL_MAX_N + 1], s_hM[SMALL_MAX_N + 1];
+    double *s_terms = reinterpret_cast<double *>(s_cnt);  // N + 1 <= 1025 doubles, used after the resampling
+    static_assert(sizeof(double) * (SMALL_MAX_N + 1) <= sizeof(uint32_t) * SMALL_MAX_RCAP, "terms fit");
     __shared__ uint32_t sh_u[32];
     __shared__ long long sh_ll[32];
     __shared__ Moments mom[SMALL_THREADS / 32];
     __shared__ uint32_t sh_lo[SMALL_THREADS / 32], sh_hi[SMALL_THREADS / 32];
-    __shared__ double sh_S;
-    __shared__ uint32_t sh_carry;
+    __shared__ double sh_S, sh_logS, sh_logR;
+    __shared__ uint32_t sh_carry, sh_first;
+    __shared__ FamPart s_part[8];  // CTA 0: the family statistics of each CTA's chunk of children
+    __shared__ int32_t sh_eb;      // CTA 0: base of the energy levels of the new population
 
     cg::cluster_group cl = cg::this_cluster();
     const uint32_t CS = cl.num_blocks(), rank = cl.block_rank();
@@ -2516,8 +2537,13 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
         if (i >= rd.n_beta) break;
         const uint32_t ob = (i - 1) & 1u, nb = i & 1u;
 
-        // ---- CTA 0: copy numbers r_j = floor(tau) + [u < threshold] per level, scan, parent map
+        // ---- CTA 0: copy numbers r_j = floor(tau) + [u < threshold] per level, scan, parent map;
+        // its histograms, which every CTA fills during the sweeps, start cleared
         if (rank == 0) {
+            for (uint32_t n = tid; n < n1; n += nt) {
+                s_hE[n] = 0u;
+                s_hM[n] = 0u;
+            }
             const uint32_t Rc = st->R_cur;
             const int32_t *E = P.E[ob] + rd.rep_off;
             const int32_t Emin = st->Emin;
@@ -2623,48 +2649,43 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
                 }
                 if (active && ll == 0) {
                     const uint64_t cc = rd.rep_off + child;
-                    P.E[nb][cc] = 2 * unsat - 2 * (int32_t)N;
-                    P.M[nb][cc] = 2 * up1 - (int32_t)N;
+                    const int32_t Ec = 2 * unsat - 2 * (int32_t)N, Mc = 2 * up1 - (int32_t)N;
+                    P.E[nb][cc] = Ec;
+                    P.M[nb][cc] = Mc;
                     P.fam[nb][cc] = P.fam[ob][rd.rep_off + par];
+                    // counts per energy and magnetisation value into CTA 0's histograms; every
+                    // energy of the population has the residue of E_0 mod 4, so any child gives the base
+                    const int32_t eb = -2 * (int32_t)N + ((Ec + 2 * (int32_t)N) & 3);
+                    if (child == 0) sh_eb = eb;
+                    atomicAdd(cl.map_shared_rank(&s_hE[(uint32_t)(Ec - eb) >> 2], 0), 1u);
+                    atomicAdd(cl.map_shared_rank(&s_hM[(uint32_t)(Mc + (int32_t)N) >> 1], 0), 1u);
                 }
                 __syncwarp();
             }
-        }
-        cl.sync();
-
-        // ---- CTA 0: measurement at beta_i and the next resampling's tables
-        if (rank == 0) {
-            const uint32_t R = st->R_new;
-            const int32_t *E = P.E[nb] + rd.rep_off;
-            const int32_t *M = P.M[nb] + rd.rep_off;
-            const uint32_t *fam = P.fam[nb] + rd.rep_off;
-            const int32_t twoN = 2 * (int32_t)N;
-            const int32_t eb = -twoN + ((E[0] + twoN) & 3);
-            for (uint32_t n = tid; n < n1; n += nt) {
-                s_hE[n] = 0u;
-                s_hM[n] = 0u;
-            }
-            if (tid == 0) sh_carry = 0u;
-            __syncthreads();
-            // per-value counts; family runs: a replica's run starts at the last start at or below it
+            // the family statistics of this CTA's chunk (Eq. rho_t): runs of equal ancestor id; a
+            // replica's run starts at the last start at or below it, the chunk's first counting as one.
+            // A child's family is its parent's, read through the parent map (the neighbouring CTAs'
+            // children may not be written yet)
+            const uint32_t *fam_old = P.fam[ob] + rd.rep_off;
             long long c2 = 0;
             uint32_t nfam = 0, cmax = 0;
-            for (uint32_t base = 0; base < R; base += nt) {
+            if (tid == 0) {
+                sh_carry = c_lo;
+                sh_first = c_hi;
+            }
+            __syncthreads();
+            for (uint32_t base = c_lo; base < c_hi; base += nt) {
                 const uint32_t j = base + tid;
-                const bool ok = j < R;
-                bool start = false;
-                if (ok) {
-                    atomicAdd(&s_hE[(uint32_t)(E[j] - eb) >> 2], 1u);
-                    atomicAdd(&s_hM[(uint32_t)(M[j] + (int32_t)N) >> 1], 1u);
-                    start = j == 0 || fam[j] != fam[j - 1];
-                }
+                const bool ok = j < c_hi;
+                const bool start = ok && (j == 0 || fam_old[parent[j]] != fam_old[parent[j - 1]]);
                 const uint32_t before = sh_carry;
-                uint32_t sj = block_inclusive_max(start ? j : 0u, sh_u);
+                uint32_t sj = block_inclusive_max(start || (ok && j == c_lo) ? j : 0u, sh_u);
                 sj = sj > before ? sj : before;
                 if (ok) {
                     c2 += 2 * (long long)(j - sj) + 1;  // sum over a run of (2r + 1) = length^2
                     cmax = j - sj + 1 > cmax ? j - sj + 1 : cmax;
                     nfam += start ? 1u : 0u;
+                    if (start) atomicMin(&sh_first, j);
                 }
                 __syncthreads();
                 if (tid == nt - 1) sh_carry = sj;
@@ -2673,6 +2694,25 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
             c2 = block_sum(c2, sh_ll);
             nfam = block_sum(nfam, sh_u);
             cmax = block_max(cmax, sh_u, 0u);
+            if (tid == 0) {
+                FamPart f;
+                f.c2 = c2;
+                f.nfam = nfam;
+                f.cmax = cmax;
+                f.lead = sh_first - c_lo;  // replicas continuing the family open before the chunk
+                f.trail = c_hi - sh_carry; // length of the chunk's last run
+                f.len = c_hi - c_lo;
+                f.pad = 0;
+                *cl.map_shared_rank(&s_part[rank], 0) = f;
+            }
+        }
+        cl.sync();
+
+        // ---- CTA 0: measurement at beta_i (from the histograms and chunk statistics every CTA
+        // left in its shared memory) and the next resampling's tables
+        if (rank == 0) {
+            const uint32_t R = st->R_new;
+            const int32_t eb = sh_eb;
             // the moments from the histograms, and the occupied energy levels
             Moments mo = {0, 0, 0, 0, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}};
             uint32_t elo = 0xffffffffu, ehi = 0u;
@@ -2715,68 +2755,83 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
             }
             __syncthreads();
             const bool prep = i + 1 < rd.n_beta;
-            if (tid == 0) {
-                Moments t = mom[0];
-                uint32_t l = sh_lo[0], h = sh_hi[0];
-                for (uint32_t k = 1; k < nw; ++k) {
-                    const Moments &q = mom[k];
-                    t.sE += q.sE;
-                    t.sE2 += q.sE2;
-                    t.sAM += q.sAM;
-                    t.sM2 += q.sM2;
-                    add128(t.sE3, q.sE3);
-                    add128(t.sE4, q.sE4);
-                    add128(t.sAM3, q.sAM3);
-                    add128(t.sM4, q.sM4);
-                    l = sh_lo[k] < l ? sh_lo[k] : l;
-                    h = sh_hi[k] > h ? sh_hi[k] : h;
-                }
-                pa_step_record *rec = P.rec + rd.rec_off + i;
-                const double lnQ = st->lnQ;
-                rec->beta = P.beta[rd.beta_off + i];
-                rec->lnQ = lnQ;
-                rec->minus_betaF = P.rec[rd.rec_off + i - 1].minus_betaF + lnQ;
-                rec->sumE = t.sE;
-                rec->sumE2 = t.sE2;
-                rec->sumAbsM = t.sAM;
-                rec->sumM2 = t.sM2;
-                rec->sum_c2 = c2;
-                rec->sumE3[0] = t.sE3.lo;
-                rec->sumE3[1] = (unsigned long long)t.sE3.hi;
-                rec->sumE4[0] = t.sE4.lo;
-                rec->sumE4[1] = (unsigned long long)t.sE4.hi;
-                rec->sumAbsM3[0] = t.sAM3.lo;
-                rec->sumAbsM3[1] = (unsigned long long)t.sAM3.hi;
-                rec->sumM4[0] = t.sM4.lo;
-                rec->sumM4[1] = (unsigned long long)t.sM4.hi;
-                rec->R = R;
-                rec->R_target = rd.R;
-                rec->n_fam = nfam;
-                rec->max_fam = cmax;
-                rec->N = N;
-                rec->status = 0;
-                st->step = i;
-                st->R_cur = R;
-                st->R_new = R;
-                sh_lo[0] = l;
-                sh_hi[0] = h;
-                if (prep) {  // S in ascending level order by one thread, then ln Q_{i+1} and E_min
-                    const uint32_t nb_l = h - l + 1;
-                    const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
-                    double S = 0.0;
-                    for (uint32_t n = 0; n < nb_l; ++n) S = __dadd_rn(S, __dmul_rn((double)s_hE[l + n], wt[n]));
-                    const int32_t Emin = eb + 4 * (int32_t)l;
-                    const double dbeta = P.beta[rd.beta_off + i + 1] - P.beta[rd.beta_off + i];
-                    sh_S = S;
-                    st->lnQ = (-dbeta) * (double)Emin + log(S) - log((double)R);
-                    st->Emin = Emin;
-                    st->n_levels = nb_l;
+            // every thread: the occupied levels; warp 0: the record; the others: the terms h_n w[n]
+            uint32_t lvl_lo = 0xffffffffu, lvl_hi = 0u;
+            for (uint32_t k = 0; k < nw; ++k) {
+                lvl_lo = sh_lo[k] < lvl_lo ? sh_lo[k] : lvl_lo;
+                lvl_hi = sh_hi[k] > lvl_hi ? sh_hi[k] : lvl_hi;
+            }
+            const uint32_t nb_l = lvl_hi - lvl_lo + 1;
+            if (prep && wid > 0) {
+                const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
+                for (uint32_t n = tid - 32; n < nb_l; n += nt - 32)
+                    s_terms[n] = __dmul_rn((double)s_hE[lvl_lo + n], wt[n]);
+            }
+            if (wid == 0) {  // the warps' partial sums, joined by warp 0
+                Moments t = {0, 0, 0, 0, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}};
+                if (lane < nw) t = mom[lane];
+                t.sE = warp_sum(t.sE);
+                t.sE2 = warp_sum(t.sE2);
+                t.sAM = warp_sum(t.sAM);
+                t.sM2 = warp_sum(t.sM2);
+                t.sE3 = warp_sum128(t.sE3);
+                t.sE4 = warp_sum128(t.sE4);
+                t.sAM3 = warp_sum128(t.sAM3);
+                t.sM4 = warp_sum128(t.sM4);
+                if (lane == 0) {
+                    FamPart f = s_part[0];  // the chunks' family statistics, joined in order
+                    for (uint32_t k = 1; k < CS; ++k) join_part(f, s_part[k]);
+                    const long long c2 = f.c2;
+                    const uint32_t nfam = f.nfam, cmax = f.cmax;
+                    pa_step_record *rec = P.rec + rd.rec_off + i;
+                    const double lnQ = st->lnQ;
+                    rec->beta = P.beta[rd.beta_off + i];
+                    rec->lnQ = lnQ;
+                    rec->minus_betaF = P.rec[rd.rec_off + i - 1].minus_betaF + lnQ;
+                    rec->sumE = t.sE;
+                    rec->sumE2 = t.sE2;
+                    rec->sumAbsM = t.sAM;
+                    rec->sumM2 = t.sM2;
+                    rec->sum_c2 = c2;
+                    rec->sumE3[0] = t.sE3.lo;
+                    rec->sumE3[1] = (unsigned long long)t.sE3.hi;
+                    rec->sumE4[0] = t.sE4.lo;
+                    rec->sumE4[1] = (unsigned long long)t.sE4.hi;
+                    rec->sumAbsM3[0] = t.sAM3.lo;
+                    rec->sumAbsM3[1] = (unsigned long long)t.sAM3.hi;
+                    rec->sumM4[0] = t.sM4.lo;
+                    rec->sumM4[1] = (unsigned long long)t.sM4.hi;
+                    rec->R = R;
+                    rec->R_target = rd.R;
+                    rec->n_fam = nfam;
+                    rec->max_fam = cmax;
+                    rec->N = N;
+                    rec->status = 0;
+                    st->step = i;
+                    st->R_cur = R;
+                    st->R_new = R;
                 }
             }
             __syncthreads();
-            if (prep) {  // per level: floor(tau) and the draw threshold, tau = R_target w[n] / S
-                const uint32_t l = sh_lo[0], nb_l = sh_hi[0] - l + 1;
+            if (prep) {  // S = sum of the terms in ascending level order, then ln Q_{i+1} and E_min
                 const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
+                if (tid == 32) {
+                    double S = 0.0;
+                    for (uint32_t n = 0; n < nb_l; ++n) S = __dadd_rn(S, s_terms[n]);
+                    sh_S = S;
+                    sh_logS = log(S);
+                } else if (tid == 64) {
+                    sh_logR = log((double)R);  // beside the sum, on another warp
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    const int32_t Emin = eb + 4 * (int32_t)lvl_lo;
+                    const double dbeta = P.beta[rd.beta_off + i + 1] - P.beta[rd.beta_off + i];
+                    st->lnQ = (-dbeta) * (double)Emin + sh_logS - sh_logR;
+                    st->Emin = Emin;
+                    st->n_levels = nb_l;
+                }
+                // per level: floor(tau) and the draw threshold, tau = R_target w[n] / S
                 const double S = sh_S;
                 for (uint32_t n = tid; n < nb_l; n += nt) {
                     const double tau = __ddiv_rn(__dmul_rn((double)rd.R, wt[n]), S);
@@ -2842,14 +2897,14 @@ void launch_anneal_small(const Pool &P, const uint32_t *runs, uint32_t n_runs, u
     cfg.attrs = at;
     cfg.numAttrs = 1;
     if (L == 8)
-        any_glass ? cudaLaunchKernelEx(&cfg, anneal_small_kernel<true, 1>, P, runs, n_steps)
-                  : cudaLaunchKernelEx(&cfg, anneal_small_kernel<false, 1>, P, runs, n_steps);
+        any_glass ? cudaLaunchKernelEx(&cfg, anneal_small_kernel<true, 1, SMALL_LPW_L8>, P, runs, n_steps)
+                  : cudaLaunchKernelEx(&cfg, anneal_small_kernel<false, 1, SMALL_LPW_L8>, P, runs, n_steps);
     else if (L == 16)
-        any_glass ? cudaLaunchKernelEx(&cfg, anneal_small_kernel<true, 4>, P, runs, n_steps)
-                  : cudaLaunchKernelEx(&cfg, anneal_small_kernel<false, 4>, P, runs, n_steps);
+        any_glass ? cudaLaunchKernelEx(&cfg, anneal_small_kernel<true, 4, SMALL_LPW_L16>, P, runs, n_steps)
+                  : cudaLaunchKernelEx(&cfg, anneal_small_kernel<false, 4, SMALL_LPW_L16>, P, runs, n_steps);
     else
-        any_glass ? cudaLaunchKernelEx(&cfg, anneal_small_kernel<true, 16>, P, runs, n_steps)
-                  : cudaLaunchKernelEx(&cfg, anneal_small_kernel<false, 16>, P, runs, n_steps);
+        any_glass ? cudaLaunchKernelEx(&cfg, anneal_small_kernel<true, 16, SMALL_LPW_L32>, P, runs, n_steps)
+                  : cudaLaunchKernelEx(&cfg, anneal_small_kernel<false, 16, SMALL_LPW_L32>, P, runs, n_steps);
 }
 
 void launch_gather_records(const Pool &P, const uint32_t *runs, uint32_t n_runs, pa_step_record *out, cudaStream_t s)
