@@ -644,7 +644,15 @@ def temperature_main(args, rank, world, local, cpu, dist, barrier):
     def R_of_steps():
         return [eng.records(k)["R"] for k in range(len(descs))]
 
-    for _ in range(Wm):  # warm-up: the first step also times the candidate sweep shapes
+    # warm-up: the first steps of each lattice size also time its candidate sweep shapes
+    # (pa_tuning_pending); then W more steps, all walking the schedule
+    tuning_steps = 0
+    while _lib.pa_tuning_pending(eng.h) and tuning_steps < n_ticks:
+        fit(1)
+        eng.step(1, True)
+        cur[0] += 1
+        tuning_steps += 1
+    for _ in range(Wm):
         fit(1)
         eng.step(1, True)
         cur[0] += 1
@@ -768,6 +776,7 @@ def temperature_main(args, rank, world, local, cpu, dist, barrier):
             "dtype": "int32/f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[wl], "name": wl, "runs_per_gpu": len(descs),
                        "temperatures": n_ticks + 1, "step": "one temperature of the whole batch",
+                       "tuning_steps_before_warmup": tuning_steps,
                        "timed_temperatures": [temps[0], temps[-1]], "attempted_updates_timed": updates,
                        "l2": "inputs larger than L2 (about 120 GB of populations) and a 256 MB write before each step",
                        "form": "batched: all runs in one launch per kernel, each temperature one CUDA graph replay",

@@ -182,9 +182,10 @@ pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream,
  * small, pa_anneal_step(n) is one launch per lattice size for all n steps).
  * Both paths give identical results; PA_CREATE_GENERIC_SWEEP implies the
  * per-stage kernels.
- * Without it, the first anneal step of a lattice size times every candidate shape
- * and keeps the fastest; the choice is shared with every later engine of the
- * process on the same device, which then skips the timing for that size.
+ * Without it, the first anneal steps of a lattice size time every candidate shape
+ * on the steps' real sweeps (pa_tuning_pending) and keep the fastest; the
+ * choice is shared with every later engine of the process on the same device,
+ * which then skips the timing for that size.
  * Results never depend on the launch shape. */
 enum { PA_CREATE_GENERIC_SWEEP = 1, PA_CREATE_NO_AUTOTUNE = 2, PA_CREATE_SEPARATE_KERNELS = 4 };
 pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, uint32_t flags,
@@ -239,7 +240,8 @@ pa_status pa_run_state(pa_engine *e, uint32_t slot, uint32_t *step, uint32_t *R,
  * couplings and populations and measures step 0.  Asynchronous. */
 pa_status pa_reset(pa_engine *e);
 
-/* Advance every unfinished run by up to n_steps temperatures: resampling
+/* Advance every unfinished run by up to n_steps temperatures (fewer when every
+ * run reaches its last temperature first): resampling
  * (Eqs. tauBoltz, QBoltz and step (iii)), theta checkerboard Metropolis sweeps
  * at beta_i (step (iv)) and measurements (step (v)).  Asynchronous.  With
  * use_graph != 0 the per-step launch sequence is captured once as a CUDA graph
@@ -362,6 +364,13 @@ uint64_t pa_launch_count(const pa_engine *e);
  * byte-plane kernel), threads per CTA, and whether it was chosen by timing. */
 pa_status pa_sweep_shape(const pa_engine *e, uint32_t group, uint32_t *L, uint32_t *words_per_thread,
                          uint32_t *block, uint32_t *tuned);
+
+/* Number of lattice sizes whose sweep launch shape is still being chosen: the
+ * first anneal steps after a size appears run each candidate shape on the
+ * step's real sweep (one warm-up step, then two steps per candidate, timed)
+ * eagerly, before graph replay takes over.  Host bookkeeping; no
+ * synchronisation. */
+pa_status pa_tuning_pending(const pa_engine *e, uint32_t *n);
 
 /* Kernel classes timed by the profiling mode. */
 enum { PA_K_RESAMPLE = 0, PA_K_SWEEP = 1, PA_K_OVERLAP = 2, PA_K_MEASURE = 3, PA_K_INIT = 4, PA_K_WAVG = 5,

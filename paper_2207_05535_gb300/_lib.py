@@ -63,7 +63,7 @@ EXPORTS = ["pa_create", "pa_create_ex", "pa_server_create", "pa_admit", "pa_reti
            "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population", "pa_population_slice",
            "pa_checkpoint", "pa_restore",
            "pa_weighted_average_runs", "pa_weighted_average", "pa_weighted_average_noalloc", "pa_launch_count", "pa_set_profiling",
-           "pa_step_records", "pa_set_allocator",
+           "pa_step_records", "pa_set_allocator", "pa_tuning_pending",
            "pa_kernel_times", "pa_transfer_bytes", "pa_calibrate_philox", "pa_sweep_shape", "pa_destroy", "pa_status_string"]
 KERNEL_KINDS = ["resample", "sweep", "overlap", "measure", "init", "wavg", "small"]
 
@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH):
         lib.pa_records.argtypes = [vp, u32, vp, P(u32), P(u32), P(u32)]
         lib.pa_measure.argtypes = [vp, u32, u32, vp, P(u32), P(u32), P(u32)]
         lib.pa_step_records.argtypes = [vp, P(u32), u32, vp]
+        lib.pa_tuning_pending.argtypes = [vp, P(u32)]
         lib.pa_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
         lib.pa_population.argtypes = [vp, u32, P(C.c_int8), P(C.c_int32), P(C.c_int32), P(u32), P(u32), P(u32)]
         lib.pa_population_slice.argtypes = [vp, u32, u32, u32, P(C.c_int8), P(C.c_int32), P(C.c_int32), P(u32),
@@ -347,6 +348,12 @@ def pa_set_allocator(alloc=None, free=None, ctx=None):
     a, f = ALLOC_FN(alloc), FREE_FN(free)
     _check(load().pa_set_allocator(a, f, ctx), "pa_set_allocator")
     _allocator_keep.append((a, f))
+
+
+def pa_tuning_pending(h):
+    n = C.c_uint32()
+    _check(load().pa_tuning_pending(h, C.byref(n)), "pa_tuning_pending")
+    return int(n.value)
 
 
 def pa_launch_count(h):

@@ -89,6 +89,8 @@ struct Tuning {
     uint32_t pick = 0;
     bool tuned = false;
     float ms = 0.f;
+    uint32_t round = 0;       // tuning steps taken so far
+    std::vector<float> best;  // per candidate: its fastest timed step (ms), 0 = not timed yet
 };
 
 // Launch shapes chosen by timing are shared by every engine of the process on the
@@ -973,46 +975,48 @@ void enqueue_tick(pa_engine *e)
     timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, act, na, e->max_Rcap_active, 0, e->stream); });
 }
 
-// One eager step that first times every candidate sweep shape of the lattice
-// sizes not tuned yet on the real data and keeps the fastest.  Each candidate
-// reads the same parents and writes the same children, so running several is
-// harmless; the last launch leaves the children in place.
+// One eager step of tuning.  A lattice size whose sweep shape is not chosen yet
+// runs this step's real sweep with one of its candidate shapes, in rotation, timed
+// with events: the first tuning step only warms up, then every candidate sweeps
+// two steps, and its faster step counts.  Candidates read the same parents and
+// write identical children, so any of them may do a step's work; timing them on
+// the anneal's own steps measures the steady state without extra launches (one
+// extra launch per candidate on the first step, timed back to back, favoured the
+// shapes that were fastest on the freshly drawn population, not later on).
 pa_status enqueue_tuning_tick(pa_engine *e)
 {
     enqueue_small(e, 1);
     const uint32_t *act = meta(e, e->big_off);
     const uint32_t na = (uint32_t)e->big.size();
     enqueue_resample(e);
+    struct Timing {
+        SweepGroup *g;
+        uint32_t c;
+        cudaEvent_t a, b;
+    };
+    std::vector<Timing> timing;
     for (auto &g : e->groups) {
         Tuning &t = e->tuning[g.L];
         if (t.tuned) {
             timed_launch(e, PA_K_SWEEP, [&] { launch_group_sweep(e, g, t.pick); });
             continue;
         }
-        std::vector<cudaEvent_t> ev(2 * t.candidates.size());
-        for (auto &x : ev) PA_CUDA(cudaEventCreate(&x));
-        for (uint32_t c = 0; c < t.candidates.size(); ++c) {
-            PA_CUDA(cudaEventRecord(ev[2 * c], e->stream));
-            launch_group_sweep(e, g, c);
-            PA_CUDA(cudaEventRecord(ev[2 * c + 1], e->stream));
-            e->launches += 1;
+        bool live = false;  // a run of this size still has a temperature to go
+        for (uint32_t r : g.runs) live |= e->rh[r].steps_done + 1 < e->rh[r].d.n_beta;
+        if (!live) {
+            timed_launch(e, PA_K_SWEEP, [&] { launch_group_sweep(e, g, t.pick); });
+            continue;
         }
-        PA_CUDA(cudaStreamSynchronize(e->stream));
-        PA_CUDA(cudaGetLastError());
-        float best = 0.f;
-        for (uint32_t c = 0; c < t.candidates.size(); ++c) {
-            float ms = 0.f;
-            PA_CUDA(cudaEventElapsedTime(&ms, ev[2 * c], ev[2 * c + 1]));
-            if (c == 0 || ms < best) {
-                best = ms;
-                t.pick = c;
-            }
-        }
-        for (auto &x : ev) cudaEventDestroy(x);
-        t.tuned = true;
-        t.ms = best;
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tuned[tune_key(g.L, e->flags)] = t.pick;
+        const uint32_t nc = (uint32_t)t.candidates.size();
+        const uint32_t c = t.round == 0 ? 0u : (t.round - 1) % nc;
+        Timing x{&g, c, nullptr, nullptr};
+        PA_CUDA(cudaEventCreate(&x.a));
+        PA_CUDA(cudaEventCreate(&x.b));
+        PA_CUDA(cudaEventRecord(x.a, e->stream));
+        launch_group_sweep(e, g, c);
+        PA_CUDA(cudaEventRecord(x.b, e->stream));
+        e->launches += 1;
+        timing.push_back(x);
     }
     enqueue_dos_sample(e);
     if (!e->q_runs.empty())
@@ -1022,6 +1026,28 @@ pa_status enqueue_tuning_tick(pa_engine *e)
     enqueue_wang(e);
     if (na) timed_launch(e, PA_K_MEASURE, [&] { launch_measure(e->P, act, na, e->max_Rcap_active, 0, e->stream); });
     PA_CUDA(cudaGetLastError());
+    if (timing.empty()) return PA_OK;
+    PA_CUDA(cudaStreamSynchronize(e->stream));
+    for (auto &x : timing) {
+        Tuning &t = e->tuning[x.g->L];
+        const uint32_t nc = (uint32_t)t.candidates.size();
+        float ms = 0.f;
+        PA_CUDA(cudaEventElapsedTime(&ms, x.a, x.b));
+        cudaEventDestroy(x.a);
+        cudaEventDestroy(x.b);
+        if (t.best.size() != nc) t.best.assign(nc, 0.f);
+        if (t.round > 0 && (t.best[x.c] == 0.f || ms < t.best[x.c])) t.best[x.c] = ms;
+        t.round += 1;
+        if (t.round == 1 + 2 * nc) {  // every candidate timed on two steps
+            t.pick = 0;
+            for (uint32_t c = 1; c < nc; ++c)
+                if (t.best[c] < t.best[t.pick]) t.pick = c;
+            t.tuned = true;
+            t.ms = t.best[t.pick];
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tuned[tune_key(x.g->L, e->flags)] = t.pick;
+        }
+    }
     return PA_OK;
 }
 
@@ -1342,10 +1368,14 @@ pa_status pa_anneal_step(pa_engine *e, uint32_t n_steps, int use_graph)
     if (!e) return PA_ERR_INVALID_ARG;
     if (e->latched != PA_OK) return e->latched;
     PA_TRY(prepare(e));
+    uint32_t left = 0;  // temperatures any resident run still has to go
+    for (uint32_t s : e->active) left = std::max(left, e->rh[s].d.n_beta - 1 - e->rh[s].steps_done);
+    n_steps = std::min(n_steps, left);
     if (n_steps == 0 || e->active.empty()) return PA_OK;
-    bool untuned = false;
-    for (auto &g : e->groups) untuned |= !e->tuning[g.L].tuned;
-    if (untuned) {
+    for (;;) {  // eager tuning steps while a lattice size's sweep shape is not chosen yet
+        bool untuned = false;
+        for (auto &g : e->groups) untuned |= !e->tuning[g.L].tuned;
+        if (!untuned) break;
         PA_TRY(enqueue_tuning_tick(e));
         advance_host_steps(e, 1);
         if (--n_steps == 0) return PA_OK;
@@ -1386,6 +1416,15 @@ pa_status pa_sync(pa_engine *e)
 }
 
 uint64_t pa_launch_count(const pa_engine *e) { return e ? e->launches : 0; }
+
+pa_status pa_tuning_pending(const pa_engine *e, uint32_t *n)
+{
+    if (!e || !n) return PA_ERR_INVALID_ARG;
+    uint32_t k = 0;
+    for (const auto &g : e->groups) k += e->tuning.at(g.L).tuned ? 0u : 1u;
+    *n = k;
+    return PA_OK;
+}
 
 pa_status pa_sweep_shape(const pa_engine *e, uint32_t group, uint32_t *L, uint32_t *words_per_thread,
                          uint32_t *block, uint32_t *tuned)

@@ -110,7 +110,7 @@ struct SweepCfg {
     uint32_t TPR;    // threads per replica (power of two; fast kernel: words per plane)
     uint32_t RPC;    // replicas per CTA
     uint32_t G;      // Philox groups per colour = ceil(N / 8)
-    uint32_t PS;     // bytes per colour plane = 4 G
+    uint32_t PS;     // bytes per colour plane = 4 G (byte planes); the row pitch (padded rows)
     uint32_t smem;   // dynamic shared memory bytes
     uint32_t WPT;    // fast kernel: plane words per thread
 };

@@ -1064,9 +1064,9 @@ __device__ __forceinline__ uint4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c3
     return make_uint4(x0, x1, x2, x3);
 }
 
-template <bool SG, int WPT, int MAXT>
-__global__ void __launch_bounds__(MAXT) sweep_pow2_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off,
-                                                          uint32_t n_group_runs, SweepCfg cfg)
+template <bool SG, int WPT>
+__device__ __forceinline__ void sweep_pow2_body(const Pool &P, const uint32_t *group_runs, const uint32_t *tile_off,
+                                                uint32_t n_group_runs, const SweepCfg &cfg)
 {
     extern __shared__ __align__(16) uint32_t smw[];
     const uint32_t slot = locate_slot(tile_off, n_group_runs, blockIdx.x);
@@ -1205,6 +1205,25 @@ __global__ void __launch_bounds__(MAXT) sweep_pow2_kernel(Pool P, const uint32_t
     }
 }
 
+// The kernels: the compiler's own register choice for 256 and 1024 threads
+// (78 and 40 registers; an explicit bound of one CTA per SM let it take 150 at
+// 256 threads and run 19 % slower at L = 128), two CTAs per SM for 512 threads
+// (L = 256: +5 % against one, measured).
+template <bool SG, int WPT, int MAXT>
+__global__ void __launch_bounds__(MAXT) sweep_pow2_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off,
+                                                          uint32_t n_group_runs, SweepCfg cfg)
+{
+    sweep_pow2_body<SG, WPT>(P, group_runs, tile_off, n_group_runs, cfg);
+}
+
+template <bool SG, int WPT>
+__global__ void __launch_bounds__(512, 2) sweep_pow2_kernel_2cta(Pool P, const uint32_t *group_runs,
+                                                                 const uint32_t *tile_off, uint32_t n_group_runs,
+                                                                 SweepCfg cfg)
+{
+    sweep_pow2_body<SG, WPT>(P, group_runs, tile_off, n_group_runs, cfg);
+}
+
 // --------------------------------------------------------------------------
 // Bit-sliced sweep for even L whose half-width L/2 is not a power of two but
 // at most 31 (Sec. V.A.1): rows of a colour plane are padded to a pitch P in
@@ -1225,7 +1244,7 @@ constexpr uint32_t PAD_MAX_GROUPS = 9;
 #endif
 
 
-template <bool SG>
+template <bool SG, uint32_t PT>  // PT: the row pitch of the runs' lattice size (8, 16 or 32)
 __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off,
                                                         uint32_t n_group_runs, SweepCfg cfg)
 {
@@ -1242,7 +1261,8 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
     if (tile0 >= Rn) return;  // uniform over the CTA
 
     const uint32_t HW = cfg.TPR;  // words per plane = threads per replica
-    const uint32_t Lh = rd.Lh, Pt = rd.pitch, N = rd.N;
+    constexpr uint32_t Pt = PT;
+    const uint32_t Lh = rd.Lh, N = rd.N;
     const uint32_t rloc = threadIdx.x / HW, w = threadIdx.x - rloc * HW;
     const uint32_t child = tile0 + rloc;
     const bool active = child < Rn;
@@ -1269,12 +1289,13 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
             for (int d = 0; d < 4; ++d) J[c][d] = Jp[(c * 4 + d) * HW + w];
     }
     // word geometry
-    const bool sub = Pt < 32;  // several rows per word
-    const uint32_t RW = sub ? 32 / Pt : 1u, y0 = w * RW;
+    constexpr bool sub = Pt < 32;  // several rows per word
+    constexpr uint32_t RW = sub ? 32 / Pt : 1u;
+    const uint32_t y0 = w * RW;
     const uint32_t wp = (w + HW - 1) % HW, wn = (w + 1) % HW;
-    const uint32_t LOW = !sub ? 1u : Pt == 4 ? 0x11111111u : Pt == 8 ? 0x01010101u : 0x00010001u;
+    constexpr uint32_t LOW = !sub ? 1u : Pt == 4 ? 0x11111111u : Pt == 8 ? 0x01010101u : 0x00010001u;
     const uint32_t HIGH = LOW << (Lh - 1);
-    const uint32_t EVEN = Pt == 4 ? 0x0F0F0F0Fu : Pt == 8 ? 0x00FF00FFu : 0x0000FFFFu;  // rows 0, 2, ... (sub)
+    constexpr uint32_t EVEN = Pt == 4 ? 0x0F0F0F0Fu : Pt == 8 ? 0x00FF00FFu : 0x0000FFFFu;  // rows 0, 2, ... (sub)
     const uint32_t VMASK = LOW * ((1u << Lh) - 1u);                                      // Lh < 32 here
     const uint32_t kb = y0 * Lh, kend = kb + RW * Lh;                                     // compact sites of the word
     const uint32_t g0 = kb >> 2, off = kb & 3u, ng = (kend - 4 * g0 + 3) / 4;          // Philox groups (<= 9)
@@ -3013,7 +3034,7 @@ std::vector<SweepCfg> sweep_candidates(uint32_t L, int allow_fast)
             c.RPC = target / HW > 0 ? target / HW : 1;
             c.block = c.RPC * HW;
             c.G = (N + 7) / 8;
-            c.PS = 0;
+            c.PS = Pt;  // the row pitch selects the kernel instantiation
             c.smem = c.RPC * 2 * HW * 4 + 8 * c.RPC;
             v.push_back(c);
         }
@@ -3046,11 +3067,21 @@ void launch_sweep(const Pool &P, const uint32_t *group_runs, const uint32_t *til
     const dim3 grid(n_tiles);
 #define PA_SWEEP_FAST(SG, WPT, MAXT) \
     sweep_pow2_kernel<SG, WPT, MAXT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg)
-    if (cfg.fast == 2) {
-        if (any_glass)
-            sweep_pad_kernel<true><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg);
+#define PA_SWEEP_FAST2(SG, WPT) \
+    sweep_pow2_kernel_2cta<SG, WPT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg)
+    if (cfg.fast == 2) {  // padded rows: cfg.PS holds the row pitch
+#define PA_SWEEP_PAD(PT)                                                                                 \
+    (any_glass ? sweep_pad_kernel<true, PT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, \
+                                                                               n_group_runs, cfg)      \
+               : sweep_pad_kernel<false, PT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, \
+                                                                                n_group_runs, cfg))
+        if (cfg.PS == 8)
+            PA_SWEEP_PAD(8);
+        else if (cfg.PS == 16)
+            PA_SWEEP_PAD(16);
         else
-            sweep_pad_kernel<false><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg);
+            PA_SWEEP_PAD(32);
+#undef PA_SWEEP_PAD
     } else if (!cfg.fast && cfg.G <= cfg.TPR && cfg.block <= 512)
         sweep_kernel<true, 512><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg);
     else if (!cfg.fast)
@@ -3060,10 +3091,11 @@ void launch_sweep(const Pool &P, const uint32_t *group_runs, const uint32_t *til
     else if (cfg.WPT == 1)
         any_glass ? PA_SWEEP_FAST(true, 1, 1024) : PA_SWEEP_FAST(false, 1, 1024);
     else if (cfg.WPT == 2)
-        any_glass ? PA_SWEEP_FAST(true, 2, 512) : PA_SWEEP_FAST(false, 2, 512);
+        any_glass ? PA_SWEEP_FAST2(true, 2) : PA_SWEEP_FAST2(false, 2);
     else
         any_glass ? PA_SWEEP_FAST(true, 4, 256) : PA_SWEEP_FAST(false, 4, 256);
 #undef PA_SWEEP_FAST
+#undef PA_SWEEP_FAST2
 }
 
 void launch_overlap(const Pool &P, const uint32_t *q_runs, uint32_t n_q_runs, uint32_t max_Rcap, int init,

@@ -247,10 +247,12 @@ def test_philox_calibration_reports_a_plausible_rate():
 
 
 def test_tuned_shapes_are_reused_by_later_engines():
-    b = W.schedule(1.0, 4)
+    b = W.schedule(1.0, 8)
     descs = [W.RunDesc(64, W.FERRO, 100, 2, b, seed=9, run_id=r) for r in range(3)]
     with _lib.Engine(descs) as a:
-        a.step(3, False)
+        assert _lib.pa_tuning_pending(a.h) in (0, 1)  # 0 if an earlier engine of the process chose the shape
+        a.step(7, False)  # one warm-up step, two per candidate shape, then tuned
+        assert _lib.pa_tuning_pending(a.h) == 0
         shape_a = _lib.pa_sweep_shapes(a.h)
         rec_a = a.records(0)
     assert shape_a[0][3] == 1
@@ -262,4 +264,5 @@ def test_tuned_shapes_are_reused_by_later_engines():
             e.step(1, False)
             counts.append(e.launches - l0)
         assert counts[0] == counts[1] == counts[2]   # no candidate launches on the first step
+        e.step(4, False)
         assert np.array_equal(e.records(0), rec_a)
