@@ -105,12 +105,13 @@ struct Pool {
 
 // Sweep launch shape for one lattice size.
 struct SweepCfg {
-    uint32_t fast;   // 0: byte planes; 1: bit-sliced (L/2 a power of two); 2: bit-sliced, padded rows
+    uint32_t fast;   // 0: byte planes; 1: bit-sliced (L/2 a power of two); 2: bit-sliced, padded rows;
+                     // 3: bit-sliced, rows repacked without padding in shared memory
     uint32_t block;  // threads per CTA
-    uint32_t TPR;    // threads per replica (power of two; fast kernel: words per plane)
+    uint32_t TPR;    // threads per replica (power of two; bit-sliced kernels: words per plane / WPT)
     uint32_t RPC;    // replicas per CTA
     uint32_t G;      // Philox groups per colour = ceil(N / 8)
-    uint32_t PS;     // bytes per colour plane = 4 G (byte planes); the row pitch (padded rows)
+    uint32_t PS;     // bytes per colour plane = 4 G (byte planes); the row pitch (padded or compact rows)
     uint32_t smem;   // dynamic shared memory bytes
     uint32_t WPT;    // fast kernel: plane words per thread
 };

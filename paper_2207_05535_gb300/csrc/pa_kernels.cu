@@ -1414,6 +1414,251 @@ __global__ void __launch_bounds__(256, PA_PAD_MIN_BLOCKS) sweep_pad_kernel(Pool 
 }
 
 // --------------------------------------------------------------------------
+// Bit-sliced sweep on compact rows: every even L >= 4 that the power-of-two
+// kernel does not take, colour planes of up to 1024 words.  In HBM the planes
+// keep their padded rows; the kernel repacks each plane in shared memory with
+// no padding, sublattice site k = y L/2 + x' at bit k of the plane's bit
+// string, so a thread's word holds 32 consecutive sites: exactly Philox groups
+// 8 w .. 8 w + 7, drawn unconditionally as in the power-of-two kernel (only a
+// plane's last word is partial, its surplus bits masked).  Rows then begin
+// anywhere in a word, so each thread keeps, for its word, masks of the row
+// starts, the row ends, the even rows, and the bits whose row above or below
+// wraps around the lattice, and reads its neighbours as 32-bit windows of the
+// other plane at fixed offsets (k - L/2, k - L/2 + 1, k - 1, k + 1,
+// k + L/2 - 1, k + L/2: one word offset and shift each for the whole CTA) and,
+// in the words of the first and last rows only, at the wrapped positions.  A
+// plane's string starts after FP = ceil(L/64) words and is followed by
+// L/64 + 2 words, so every window stays inside the array; bits read from those
+// margins are always masked out.  Both this kernel and the padded-row kernel
+// are launch-shape candidates for L <= 64 (the padded rows are faster for some
+// small L, whose compact planes end in a mostly empty word).
+// --------------------------------------------------------------------------
+#ifndef PA_COMPACT_WIDE
+#define PA_COMPACT_WIDE true
+#endif
+
+__device__ __forceinline__ uint32_t low_bits(uint32_t n) { return n >= 32 ? 0xFFFFFFFFu : (1u << n) - 1u; }
+
+// 32 bits of the bit string s from bit p on (words p >> 5 and p >> 5 + 1 exist).
+__device__ __forceinline__ uint32_t bits_at(const uint32_t *s, uint32_t p)
+{
+    const uint32_t q = p >> 5;
+    return __funnelshift_r(s[q], s[q + 1], p & 31);
+}
+
+// Compact word w (sites 32 w .. 32 w + 31 < NB) of a colour plane stored with
+// rows at the given pitch; reads only words that hold the sites.
+__device__ uint32_t compact_from_padded(const uint32_t *g, uint32_t pitch, uint32_t Lh, uint32_t NB, uint32_t w)
+{
+    const uint32_t k0 = 32 * w, k1 = min(k0 + 32, NB);
+    uint32_t y = k0 / Lh, xs = k0 - y * Lh, out = 0;
+    for (uint32_t k = k0; k < k1; ++y, xs = 0) {
+        const uint32_t len = min(Lh - xs, k1 - k), pos = y * pitch + xs, sh = pos & 31;
+        uint32_t v = g[pos >> 5] >> sh;
+        if (sh + len > 32) v |= g[(pos >> 5) + 1] << (32 - sh);
+        out |= (v & low_bits(len)) << (k - k0);
+        k += len;
+    }
+    return out;
+}
+
+// Padded word p of a colour plane from its compact bit string O (site k at bit base + k).
+__device__ uint32_t padded_from_compact(const uint32_t *O, uint32_t base, uint32_t pitch, uint32_t Lh, uint32_t p)
+{
+    if (pitch < 32) {  // 32 / pitch rows per word
+        const uint32_t RW = 32 / pitch;
+        uint32_t v = 0;
+        for (uint32_t r = 0; r < RW; ++r) v |= (bits_at(O, base + (p * RW + r) * Lh) & low_bits(Lh)) << (r * pitch);
+        return v;
+    }
+    const uint32_t y = 32 * p / pitch, x0 = 32 * p - y * pitch;  // pitch a multiple of 32
+    return x0 < Lh ? bits_at(O, base + y * Lh + x0) & low_bits(Lh - x0) : 0u;
+}
+
+// Per-thread geometry of compact word w.
+struct CompactWord {
+    uint32_t RS, RE, EV, VM;  // row starts, row ends, even rows, sites of the plane
+    uint32_t mU, mD;          // bits whose row above (below) is the lattice's last (first) row
+    uint32_t pU, pD;          // window positions of the wrapped rows (the plain ones where none wraps)
+};
+
+__device__ __forceinline__ CompactWord compact_word(uint32_t w, uint32_t Lh, uint32_t NB, uint32_t base)
+{
+    CompactWord g;
+    const uint32_t k0 = 32 * w, k1 = min(k0 + 32, NB);
+    g.VM = low_bits(k1 - k0);
+    g.RS = g.RE = g.EV = 0;
+    uint32_t y = k0 / Lh, xs = k0 - y * Lh;
+    for (uint32_t k = k0; k < k1; ++y, xs = 0) {
+        const uint32_t len = min(Lh - xs, k1 - k), j = k - k0;
+        if (xs == 0) g.RS |= 1u << j;
+        if (xs + len == Lh) g.RE |= 1u << (j + len - 1);
+        if (!(y & 1u)) g.EV |= low_bits(len) << j;
+        k += len;
+    }
+    g.mU = k0 < Lh ? low_bits(Lh - k0) : 0u;
+    const int jt = (int)NB - (int)Lh - (int)k0;  // first bit whose row below wraps
+    g.mD = jt <= 0 ? 0xFFFFFFFFu : jt >= 32 ? 0u : ~low_bits((uint32_t)jt);
+    g.pU = g.mU ? base + k0 + NB - Lh : base + k0 - Lh;
+    g.pD = g.mD ? base + k0 + Lh - NB : base + k0 + Lh;
+    return g;
+}
+
+// Word offsets and bit shifts of the windows at k + L/2 - 1, k - L/2 + 1, k - L/2
+// and k + L/2 from a word's own position: the same for every thread of a CTA.
+struct CompactShifts {
+    int dl, dr, du, dd;
+    uint32_t sl, sr, su, sd;
+};
+
+__device__ __forceinline__ CompactShifts compact_shifts(uint32_t Lh)
+{
+    CompactShifts s;
+    const int off[4] = {(int)Lh - 1, 1 - (int)Lh, -(int)Lh, (int)Lh};
+    s.dl = off[0] >> 5, s.dr = off[1] >> 5, s.du = off[2] >> 5, s.dd = off[3] >> 5;  // floor(off / 32)
+    s.sl = off[0] & 31, s.sr = off[1] & 31, s.su = off[2] & 31, s.sd = off[3] & 31;
+    return s;
+}
+
+// 32 bits from bit sh of word Ow[dq] on.
+__device__ __forceinline__ uint32_t window(const uint32_t *Ow, int dq, uint32_t sh)
+{
+    return __funnelshift_r(Ow[dq], Ow[dq + 1], sh);
+}
+
+// Neighbour masks of compact word w of colour c, read from the other plane's
+// string O; Ow = O + FP + w is the word itself.
+__device__ __forceinline__ void compact_neighbours(const uint32_t *O, const uint32_t *Ow, const CompactShifts &z,
+                                                   const CompactWord &g, uint32_t c, uint32_t &same, uint32_t &rot,
+                                                   uint32_t &up, uint32_t &dn)
+{
+    const uint32_t o = Ow[0];
+    same = o;
+    const uint32_t l1 = __funnelshift_l(Ow[-1], o, 1);  // bit k <- k - 1
+    const uint32_t r1 = __funnelshift_r(o, Ow[1], 1);   // bit k <- k + 1
+    const uint32_t left = (l1 & ~g.RS) | (window(Ow, z.dl, z.sl) & g.RS);   // x' - 1 within the row
+    const uint32_t right = (r1 & ~g.RE) | (window(Ow, z.dr, z.sr) & g.RE);  // x' + 1 within the row
+    rot = c == 0 ? ((left & g.EV) | (right & ~g.EV)) : ((right & g.EV) | (left & ~g.EV));
+    up = window(Ow, z.du, z.su);
+    dn = window(Ow, z.dd, z.sd);
+    if (g.mU) up = (up & ~g.mU) | (bits_at(O, g.pU) & g.mU);  // the first row's row above: the last row
+    if (g.mD) dn = (dn & ~g.mD) | (bits_at(O, g.pD) & g.mD);  // the last row's row below: the first row
+}
+
+#ifndef PA_COMPACT_MIN_BLOCKS
+#define PA_COMPACT_MIN_BLOCKS 4  // caps registers at 64 (no spills); 1-8 % faster than 3 or 2 CTAs of 256 (measured)
+#endif
+
+template <bool SG, int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? PA_COMPACT_MIN_BLOCKS : 1)
+    sweep_compact_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off, uint32_t n_group_runs,
+                         SweepCfg cfg)
+{
+    extern __shared__ __align__(16) uint32_t smw[];
+    const uint32_t slot = locate_slot(tile_off, n_group_runs, blockIdx.x);
+    const uint32_t run = group_runs[slot];
+    const RunDev rd = P.runs[run];
+    const RunState st = P.st[run];
+    if (st.status) return;
+    const uint32_t i = st.step + 1;
+    if (i >= rd.n_beta) return;
+    const uint32_t Rn = st.R_new;
+    const uint32_t tile0 = (blockIdx.x - tile_off[slot]) * cfg.RPC;
+    if (tile0 >= Rn) return;  // uniform over the CTA
+
+    const uint32_t CW = cfg.TPR;  // compact words per plane = threads per replica
+    const uint32_t Lh = rd.Lh, N = rd.N, NB = N / 2, pitch = rd.pitch, PW = rd.pw;
+    const uint32_t FP = (Lh + 31) >> 5, AW = FP + CW + (Lh >> 5) + 2, base = 32 * FP;
+    const uint32_t rloc = threadIdx.x / CW, w = threadIdx.x - rloc * CW;
+    const uint32_t child = tile0 + rloc;
+    const bool active = child < Rn;
+    uint32_t *pl = smw + rloc * 2 * AW;
+    int32_t *acc = reinterpret_cast<int32_t *>(smw + cfg.RPC * 2 * AW);
+    for (uint32_t q = threadIdx.x; q < 2 * cfg.RPC; q += blockDim.x) acc[q] = 0;  // one thread per replica at L <= 6
+
+    const uint32_t ob = (i - 1) & 1u, nbuf = i & 1u;
+    uint32_t own[2] = {0u, 0u}, parent = 0;
+    if (active) {
+        parent = P.parent[rd.rep_off + child];
+        const uint32_t *src = P.spins[ob] + rd.spin_off + (uint64_t)parent * rd.wstride;
+        own[0] = compact_from_padded(src, pitch, Lh, NB, w);
+        own[1] = compact_from_padded(src + PW, pitch, Lh, NB, w);
+    }
+    pl[FP + w] = own[0];
+    pl[AW + FP + w] = own[1];
+    uint32_t J[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    if (SG) {
+        const uint32_t *Jp = P.J + rd.J_off + 2 * rd.wstride;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int d = 0; d < 4; ++d) J[c][d] = compact_from_padded(Jp + (c * 4 + d) * PW, pitch, Lh, NB, w);
+    }
+    const CompactWord g = compact_word(w, Lh, NB, base);
+    const CompactShifts z = compact_shifts(Lh);
+
+    const unsigned long long T1 = P.thr[rd.thr_off + 2 * i], T2 = P.thr[rd.thr_off + 2 * i + 1];
+    const uint32_t t1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T1;
+    const uint32_t t2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T2;
+    const uint32_t all1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : 0u;
+    const uint32_t all2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : 0u;
+    PhiloxKeys K;
+    philox_keys(K, rd.seed, rd.run_id);
+    const uint32_t hi1_0 = __umulhi(0xCD9E8D57u, i), lo1_0 = 0xCD9E8D57u * i;
+    __syncthreads();
+
+    for (uint32_t t = 0; t < rd.theta; ++t) {
+#pragma unroll
+        for (uint32_t c = 0; c < 2; ++c) {
+            if (active) {
+                uint32_t same, rot, up, dn;
+                compact_neighbours(pl + (c ^ 1u) * AW, pl + (c ^ 1u) * AW + FP + w, z, g, c, same, rot, up, dn);
+                const uint32_t S = own[c];
+                const uint32_t x1 = S ^ same ^ J[c][0], x2 = S ^ rot ^ J[c][1];
+                const uint32_t x3 = S ^ up ^ J[c][2], x4 = S ^ dn ^ J[c][3];
+                const uint32_t a = x1 ^ x2, b = x1 & x2, e = x3 ^ x4, f = x3 & x4;
+                const uint32_t c0 = a ^ e, ge2 = b | f | (a & e);
+                const uint32_t ctr3 = (TAG_SWEEP << 24) | (t << 1) | c;
+                uint32_t B1 = 0, B2 = 0;
+#pragma unroll
+                for (uint32_t q = 0; q < 8; ++q) {
+                    const uint4 u = philox_rk<PA_COMPACT_WIDE>(8 * w + q, child, ctr3, hi1_0, lo1_0, K);
+                    pack_group(B1, B2, u, q, t1, t2);
+                }
+                const uint32_t flip = (ge2 | (c0 & (B1 | all1)) | B2 | all2) & g.VM;
+                own[c] = S ^ flip;
+                pl[c * AW + FP + w] = own[c];
+            }
+            __syncthreads();
+        }
+    }
+
+    // child: planes back in their padded rows, E from the final lattice (every bond
+    // touches one colour-0 site), M
+    if (active) {
+        uint32_t *dst = P.spins[nbuf] + rd.spin_off + (uint64_t)child * rd.wstride;
+        for (uint32_t p = w; p < PW; p += CW) {
+            dst[p] = padded_from_compact(pl, base, pitch, Lh, p);
+            dst[PW + p] = padded_from_compact(pl + AW, base, pitch, Lh, p);
+        }
+        uint32_t same, rot, up, dn;
+        compact_neighbours(pl + AW, pl + AW + FP + w, z, g, 0, same, rot, up, dn);
+        const uint32_t S = own[0];
+        const int32_t unsat = __popc((S ^ same ^ J[0][0]) & g.VM) + __popc((S ^ rot ^ J[0][1]) & g.VM) +
+                              __popc((S ^ up ^ J[0][2]) & g.VM) + __popc((S ^ dn ^ J[0][3]) & g.VM);
+        atomicAdd(&acc[2 * rloc], unsat);
+        atomicAdd(&acc[2 * rloc + 1], __popc(own[0]) + __popc(own[1]));
+    }
+    __syncthreads();
+    if (active && w == 0) {
+        const uint64_t pc = rd.rep_off + parent, cc = rd.rep_off + child;
+        P.E[nbuf][cc] = 2 * acc[2 * rloc] - 2 * (int32_t)N;
+        P.M[nbuf][cc] = 2 * acc[2 * rloc + 1] - (int32_t)N;
+        P.fam[nbuf][cc] = P.fam[ob][pc];
+    }
+}
+
+// --------------------------------------------------------------------------
 // Overlaps (Sec. III.D): d = popcount(s XOR s') over the packed spins.
 // --------------------------------------------------------------------------
 // Hamming distance of two replicas' colour planes (nw words; 16-byte loads
@@ -3023,7 +3268,21 @@ std::vector<SweepCfg> sweep_candidates(uint32_t L, int allow_fast)
         }
         return v;
     }
-    const uint32_t Pt = row_pitch(L);
+    const uint32_t Pt = row_pitch(L), Lh = L / 2, CW = (L * Lh + 31) / 32;
+    if (allow_fast && CW <= 1024) {  // compact rows
+        for (uint32_t target : {256u, 128u}) {
+            SweepCfg c{};
+            c.fast = 3;
+            c.WPT = 1;
+            c.TPR = CW;
+            c.RPC = target / CW > 0 ? target / CW : 1;
+            c.block = c.RPC * CW;
+            c.G = (N + 7) / 8;
+            c.PS = Pt;
+            c.smem = c.RPC * 2 * ((Lh + 31) / 32 + CW + Lh / 32 + 2) * 4 + 8 * c.RPC;
+            if (v.empty() || v.back().block != c.block) v.push_back(c);
+        }
+    }
     if (allow_fast && L >= 6 && Pt <= 32 && Pt != L / 2) {  // padded rows
         const uint32_t HW = L * Pt / 32;
         for (uint32_t target : {128u, 256u}) {
@@ -3038,8 +3297,8 @@ std::vector<SweepCfg> sweep_candidates(uint32_t L, int allow_fast)
             c.smem = c.RPC * 2 * HW * 4 + 8 * c.RPC;
             v.push_back(c);
         }
-        return v;
     }
+    if (!v.empty()) return v;
     SweepCfg c{};
     c.fast = 0;
     c.WPT = 1;
@@ -3069,7 +3328,18 @@ void launch_sweep(const Pool &P, const uint32_t *group_runs, const uint32_t *til
     sweep_pow2_kernel<SG, WPT, MAXT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg)
 #define PA_SWEEP_FAST2(SG, WPT) \
     sweep_pow2_kernel_2cta<SG, WPT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg)
-    if (cfg.fast == 2) {  // padded rows: cfg.PS holds the row pitch
+    if (cfg.fast == 3) {  // compact rows
+        if (cfg.block <= 256)
+            any_glass ? sweep_compact_kernel<true, 256><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off,
+                                                                                      n_group_runs, cfg)
+                      : sweep_compact_kernel<false, 256><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off,
+                                                                                       n_group_runs, cfg);
+        else
+            any_glass ? sweep_compact_kernel<true, 1024><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off,
+                                                                                       n_group_runs, cfg)
+                      : sweep_compact_kernel<false, 1024><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off,
+                                                                                        n_group_runs, cfg);
+    } else if (cfg.fast == 2) {  // padded rows: cfg.PS holds the row pitch
 #define PA_SWEEP_PAD(PT)                                                                                 \
     (any_glass ? sweep_pad_kernel<true, PT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, \
                                                                                n_group_runs, cfg)      \

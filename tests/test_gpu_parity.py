@@ -209,13 +209,15 @@ def test_glass_L16_R5000_full_size_sampled_runs():
             assert np.all(rec["status"] == 0) and np.all(rec["R"] > 4000)
 
 
-@pytest.mark.parametrize("L", [6, 8, 10, 12, 14, 16, 18, 30, 32, 46, 62, 64, 128, 256])
+@pytest.mark.parametrize("L", [4, 6, 8, 10, 12, 14, 16, 18, 30, 32, 34, 46, 50, 62, 64, 100, 128, 254, 256])
 def test_bitsliced_and_generic_sweeps_agree(L):
-    """The bit-sliced kernels (L/2 a power of two, or rows padded to a pitch)
-    and the byte-plane kernel flip the same spins: whole anneals agree bit for
-    bit for the ferromagnet and the glass."""
+    """The bit-sliced kernels (L/2 a power of two; rows padded to a pitch;
+    rows repacked without padding) and the byte-plane kernel flip the same
+    spins: whole anneals agree bit for bit for the ferromagnet and the glass.
+    Nine steps take the autotuned engine through every candidate shape of its
+    lattice size (one warm-up step, then two steps per candidate)."""
     R = max(4, 20000 // (L * L) * 8)
-    b = W.schedule(1.5, 5)
+    b = W.schedule(1.5, 10)
     descs = [W.RunDesc(L, W.FERRO, R, 2, b, seed=3, run_id=0),
              W.RunDesc(L, W.EA_PMJ, R, 2, b, seed=3, run_id=1, disorder_id=9, overlap=W.Q_SHIFT)]
     out = []
