@@ -2865,33 +2865,50 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
                     pl[HW + w] = own[1];
                 }
                 __syncwarp();
-                for (uint32_t t = 0; t < rd.theta; ++t) {
+                // The comparison bits of half-sweep h = 2 t + c depend only on the Philox counters,
+                // not on the spins: each step draws (and joins over the word's lanes) those of the
+                // next half-sweep while it applies the current one, which keeps the Philox chains
+                // off the dependent path of spin updates.
+                auto draw = [&](uint32_t h, uint32_t &B1, uint32_t &B2) {
+                    const uint32_t ctr3 = (TAG_SWEEP << 24) | h;
+                    B1 = 0;
+                    B2 = 0;
 #pragma unroll
-                    for (uint32_t c = 0; c < 2; ++c) {
-                        uint32_t same, rot, up, dn;
-                        plane_neighbours(pl + (c ^ 1u) * HW, HW, Lh, c, w, same, rot, up, dn);
-                        const uint32_t S = own[c];
-                        const uint32_t x1 = S ^ same ^ J[c][0], x2 = S ^ rot ^ J[c][1];
-                        const uint32_t x3 = S ^ up ^ J[c][2], x4 = S ^ dn ^ J[c][3];
-                        const uint32_t a = x1 ^ x2, b = x1 & x2, e = x3 ^ x4, f = x3 & x4;
-                        const uint32_t c0 = a ^ e, ge2 = b | f | (a & e);
-                        const uint32_t ctr3 = (TAG_SWEEP << 24) | (t << 1) | c;
-                        uint32_t B1 = 0, B2 = 0;
-#pragma unroll
-                        for (uint32_t q = 0; q < GPL; ++q) {
-                            const uint32_t g = sub * GPL + q;
-                            const uint4 u = philox_rk<true>(8 * w + g, child, ctr3, hi1_0, lo1_0, K);
-                            pack_group(B1, B2, u, g, t1, t2);
-                        }
-#pragma unroll
-                        for (uint32_t o = 1; o < LPW; o <<= 1) {  // the word's lanes are adjacent
-                            B1 |= __shfl_xor_sync(FULL, B1, o);
-                            B2 |= __shfl_xor_sync(FULL, B2, o);
-                        }
-                        own[c] = S ^ (ge2 | (c0 & (B1 | all1)) | B2 | all2);
-                        if (sub == 0) pl[c * HW + w] = own[c];
-                        __syncwarp();
+                    for (uint32_t q = 0; q < GPL; ++q) {
+                        const uint32_t g = sub * GPL + q;
+                        const uint4 u = philox_rk<true>(8 * w + g, child, ctr3, hi1_0, lo1_0, K);
+                        pack_group(B1, B2, u, g, t1, t2);
                     }
+#pragma unroll
+                    for (uint32_t o = 1; o < LPW; o <<= 1) {  // the word's lanes are adjacent
+                        B1 |= __shfl_xor_sync(FULL, B1, o);
+                        B2 |= __shfl_xor_sync(FULL, B2, o);
+                    }
+                };
+                auto apply = [&](uint32_t c, uint32_t B1, uint32_t B2) {
+                    uint32_t same, rot, up, dn;
+                    plane_neighbours(pl + (c ^ 1u) * HW, HW, Lh, c, w, same, rot, up, dn);
+                    const uint32_t S = own[c];
+                    const uint32_t x1 = S ^ same ^ J[c][0], x2 = S ^ rot ^ J[c][1];
+                    const uint32_t x3 = S ^ up ^ J[c][2], x4 = S ^ dn ^ J[c][3];
+                    const uint32_t a = x1 ^ x2, b = x1 & x2, e = x3 ^ x4, f = x3 & x4;
+                    const uint32_t c0 = a ^ e, ge2 = b | f | (a & e);
+                    own[c] = S ^ (ge2 | (c0 & (B1 | all1)) | B2 | all2);
+                    if (sub == 0) pl[c * HW + w] = own[c];
+                    __syncwarp();
+                };
+                if (rd.theta > 0) {
+                    uint32_t B1, B2, N1, N2;
+                    draw(0, B1, B2);
+                    for (uint32_t t = 0; t + 1 < rd.theta; ++t) {
+                        draw(2 * t + 1, N1, N2);
+                        apply(0, B1, B2);
+                        draw(2 * t + 2, B1, B2);
+                        apply(1, N1, N2);
+                    }
+                    draw(2 * rd.theta - 1, N1, N2);
+                    apply(0, B1, B2);
+                    apply(1, N1, N2);
                 }
                 // the child: planes, E from the final lattice (every bond touches one colour-0 site), M
                 int32_t unsat = 0, up1 = 0;
@@ -2975,131 +2992,145 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
         cl.sync();
 
         // ---- CTA 0: measurement at beta_i (from the histograms and chunk statistics every CTA
-        // left in its shared memory) and the next resampling's tables
+        // left in its shared memory) and the next resampling's tables.  The serial chain that the
+        // next step waits for (occupied levels, terms h_n w[n], their ascending sum S and ln S)
+        // runs on warp 1 while warp 2 takes ln R and the other warps form the moments; then warp 0
+        // writes the record beside the tables of floor(tau) and draw thresholds.
         if (rank == 0) {
             const uint32_t R = st->R_new;
             const int32_t eb = sh_eb;
-            // the moments from the histograms, and the occupied energy levels
-            Moments mo = {0, 0, 0, 0, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}};
-            uint32_t elo = 0xffffffffu, ehi = 0u;
-            for (uint32_t n = tid; n < n1; n += nt) {
-                const uint32_t he = s_hE[n], hm = s_hM[n];
-                if (he) {
-                    elo = n < elo ? n : elo;
-                    ehi = n > ehi ? n : ehi;
-                    const long long e = (long long)eb + 4ll * n;
-                    const unsigned long long ae = (unsigned long long)(e < 0 ? -e : e), e2 = ae * ae;
-                    mo.sE += (long long)he * e;
-                    mo.sE2 += (long long)((unsigned long long)he * e2);
-                    const I128 t3 = mul_u64(he, ae * e2);
-                    add128(mo.sE3, e < 0 ? neg128(t3) : t3);
-                    add128(mo.sE4, mul_128_u64(mul_u64(he, e2), e2));
+            const double lnQ_i = st->lnQ;  // read before it is replaced by ln Q_{i+1}
+            const bool prep = i + 1 < rd.n_beta;
+            if (wid == 1) {
+                uint32_t lo = 0xffffffffu, hi = 0u;
+                for (uint32_t n0 = 0; n0 < n1; n0 += 32) {
+                    const uint32_t n = n0 + lane;
+                    const uint32_t m = __ballot_sync(FULL, n < n1 && s_hE[n] != 0u);
+                    if (m) {
+                        lo = lo == 0xffffffffu ? n0 + __ffs(m) - 1 : lo;
+                        hi = n0 + 31 - __clz(m);
+                    }
                 }
-                if (hm) {
-                    const long long m = 2ll * n - (long long)N;
-                    const unsigned long long am = (unsigned long long)(m < 0 ? -m : m), m2 = am * am;
-                    mo.sAM += (long long)((unsigned long long)hm * am);
-                    mo.sM2 += (long long)((unsigned long long)hm * m2);
-                    add128(mo.sAM3, mul_u64(hm, am * m2));
-                    add128(mo.sM4, mul_128_u64(mul_u64(hm, m2), m2));
+                if (lane == 0) {
+                    sh_lo[0] = lo;
+                    sh_hi[0] = hi;
                 }
-            }
-            mo.sE = warp_sum(mo.sE);
-            mo.sE2 = warp_sum(mo.sE2);
-            mo.sAM = warp_sum(mo.sAM);
-            mo.sM2 = warp_sum(mo.sM2);
-            mo.sE3 = warp_sum128(mo.sE3);
-            mo.sE4 = warp_sum128(mo.sE4);
-            mo.sAM3 = warp_sum128(mo.sAM3);
-            mo.sM4 = warp_sum128(mo.sM4);
-            elo = warp_min(elo);
-            ehi = warp_max(ehi);
-            if (lane == 0) {
-                mom[wid] = mo;
-                sh_lo[wid] = elo;
-                sh_hi[wid] = ehi;
+                if (prep) {
+                    const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
+                    const uint32_t nb_l = hi - lo + 1;
+                    for (uint32_t n = lane; n < nb_l; n += 32) s_terms[n] = __dmul_rn((double)s_hE[lo + n], wt[n]);
+                    __syncwarp();
+                    if (lane == 0) {
+                        double S = 0.0;
+                        for (uint32_t n = 0; n < nb_l; ++n) S = __dadd_rn(S, s_terms[n]);
+                        sh_S = S;
+                        sh_logS = log(S);
+                    }
+                }
+            } else if (wid == 2) {
+                if (prep && lane == 0) sh_logR = log((double)R);
+            } else {  // warps 0 and 3.. : the moments' partial sums over the levels, energy then
+                      // magnetisation (half the accumulators live at a time)
+                const uint32_t mt = wid == 0 ? lane : tid - 64, nmt = nt - 64;
+                long long s1 = 0, s2 = 0;
+                I128 s3 = {0ull, 0ll}, s4 = {0ull, 0ll};
+                for (uint32_t n = mt; n < n1; n += nmt) {
+                    const uint32_t he = s_hE[n];
+                    if (he) {
+                        const long long e = (long long)eb + 4ll * n;
+                        const unsigned long long ae = (unsigned long long)(e < 0 ? -e : e), e2 = ae * ae;
+                        s1 += (long long)he * e;
+                        s2 += (long long)((unsigned long long)he * e2);
+                        const I128 t3 = mul_u64(he, ae * e2);
+                        add128(s3, e < 0 ? neg128(t3) : t3);
+                        add128(s4, mul_128_u64(mul_u64(he, e2), e2));
+                    }
+                }
+                s1 = warp_sum(s1);
+                s2 = warp_sum(s2);
+                s3 = warp_sum128(s3);
+                s4 = warp_sum128(s4);
+                if (lane == 0) {
+                    mom[wid].sE = s1;
+                    mom[wid].sE2 = s2;
+                    mom[wid].sE3 = s3;
+                    mom[wid].sE4 = s4;
+                }
+                s1 = s2 = 0;
+                s3 = s4 = I128{0ull, 0ll};
+                for (uint32_t n = mt; n < n1; n += nmt) {
+                    const uint32_t hm = s_hM[n];
+                    if (hm) {
+                        const long long m = 2ll * n - (long long)N;
+                        const unsigned long long am = (unsigned long long)(m < 0 ? -m : m), m2 = am * am;
+                        s1 += (long long)((unsigned long long)hm * am);
+                        s2 += (long long)((unsigned long long)hm * m2);
+                        add128(s3, mul_u64(hm, am * m2));
+                        add128(s4, mul_128_u64(mul_u64(hm, m2), m2));
+                    }
+                }
+                s1 = warp_sum(s1);
+                s2 = warp_sum(s2);
+                s3 = warp_sum128(s3);
+                s4 = warp_sum128(s4);
+                if (lane == 0) {
+                    mom[wid].sAM = s1;
+                    mom[wid].sM2 = s2;
+                    mom[wid].sAM3 = s3;
+                    mom[wid].sM4 = s4;
+                }
             }
             __syncthreads();
-            const bool prep = i + 1 < rd.n_beta;
-            // every thread: the occupied levels; warp 0: the record; the others: the terms h_n w[n]
-            uint32_t lvl_lo = 0xffffffffu, lvl_hi = 0u;
-            for (uint32_t k = 0; k < nw; ++k) {
-                lvl_lo = sh_lo[k] < lvl_lo ? sh_lo[k] : lvl_lo;
-                lvl_hi = sh_hi[k] > lvl_hi ? sh_hi[k] : lvl_hi;
-            }
-            const uint32_t nb_l = lvl_hi - lvl_lo + 1;
-            if (prep && wid > 0) {
-                const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
-                for (uint32_t n = tid - 32; n < nb_l; n += nt - 32)
-                    s_terms[n] = __dmul_rn((double)s_hE[lvl_lo + n], wt[n]);
-            }
-            if (wid == 0) {  // the warps' partial sums, joined by warp 0
-                Moments t = {0, 0, 0, 0, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}};
-                if (lane < nw) t = mom[lane];
-                t.sE = warp_sum(t.sE);
-                t.sE2 = warp_sum(t.sE2);
-                t.sAM = warp_sum(t.sAM);
-                t.sM2 = warp_sum(t.sM2);
-                t.sE3 = warp_sum128(t.sE3);
-                t.sE4 = warp_sum128(t.sE4);
-                t.sAM3 = warp_sum128(t.sAM3);
-                t.sM4 = warp_sum128(t.sM4);
+            const uint32_t lvl_lo = sh_lo[0], nb_l = sh_hi[0] - lvl_lo + 1;
+            if (wid == 0) {  // the warps' partial sums joined, the record
+                const bool has = lane < nw && lane != 1 && lane != 2;
+                const long long sE = warp_sum(has ? mom[lane].sE : 0ll), sE2 = warp_sum(has ? mom[lane].sE2 : 0ll);
+                const long long sAM = warp_sum(has ? mom[lane].sAM : 0ll), sM2 = warp_sum(has ? mom[lane].sM2 : 0ll);
+                const I128 z = {0ull, 0ll};
+                const I128 sE3 = warp_sum128(has ? mom[lane].sE3 : z), sE4 = warp_sum128(has ? mom[lane].sE4 : z);
+                const I128 sAM3 = warp_sum128(has ? mom[lane].sAM3 : z), sM4 = warp_sum128(has ? mom[lane].sM4 : z);
                 if (lane == 0) {
                     FamPart f = s_part[0];  // the chunks' family statistics, joined in order
                     for (uint32_t k = 1; k < CS; ++k) join_part(f, s_part[k]);
-                    const long long c2 = f.c2;
-                    const uint32_t nfam = f.nfam, cmax = f.cmax;
                     pa_step_record *rec = P.rec + rd.rec_off + i;
-                    const double lnQ = st->lnQ;
                     rec->beta = P.beta[rd.beta_off + i];
-                    rec->lnQ = lnQ;
-                    rec->minus_betaF = P.rec[rd.rec_off + i - 1].minus_betaF + lnQ;
-                    rec->sumE = t.sE;
-                    rec->sumE2 = t.sE2;
-                    rec->sumAbsM = t.sAM;
-                    rec->sumM2 = t.sM2;
-                    rec->sum_c2 = c2;
-                    rec->sumE3[0] = t.sE3.lo;
-                    rec->sumE3[1] = (unsigned long long)t.sE3.hi;
-                    rec->sumE4[0] = t.sE4.lo;
-                    rec->sumE4[1] = (unsigned long long)t.sE4.hi;
-                    rec->sumAbsM3[0] = t.sAM3.lo;
-                    rec->sumAbsM3[1] = (unsigned long long)t.sAM3.hi;
-                    rec->sumM4[0] = t.sM4.lo;
-                    rec->sumM4[1] = (unsigned long long)t.sM4.hi;
+                    rec->lnQ = lnQ_i;
+                    rec->minus_betaF = P.rec[rd.rec_off + i - 1].minus_betaF + lnQ_i;
+                    rec->sumE = sE;
+                    rec->sumE2 = sE2;
+                    rec->sumAbsM = sAM;
+                    rec->sumM2 = sM2;
+                    rec->sum_c2 = f.c2;
+                    rec->sumE3[0] = sE3.lo;
+                    rec->sumE3[1] = (unsigned long long)sE3.hi;
+                    rec->sumE4[0] = sE4.lo;
+                    rec->sumE4[1] = (unsigned long long)sE4.hi;
+                    rec->sumAbsM3[0] = sAM3.lo;
+                    rec->sumAbsM3[1] = (unsigned long long)sAM3.hi;
+                    rec->sumM4[0] = sM4.lo;
+                    rec->sumM4[1] = (unsigned long long)sM4.hi;
                     rec->R = R;
                     rec->R_target = rd.R;
-                    rec->n_fam = nfam;
-                    rec->max_fam = cmax;
+                    rec->n_fam = f.nfam;
+                    rec->max_fam = f.cmax;
                     rec->N = N;
                     rec->status = 0;
                     st->step = i;
                     st->R_cur = R;
                     st->R_new = R;
                 }
-            }
-            __syncthreads();
-            if (prep) {  // S = sum of the terms in ascending level order, then ln Q_{i+1} and E_min
-                const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
+            } else if (prep) {  // ln Q_{i+1}, E_min, and per level floor(tau) and the draw threshold,
+                                // tau = R_target w[n] / S
                 if (tid == 32) {
-                    double S = 0.0;
-                    for (uint32_t n = 0; n < nb_l; ++n) S = __dadd_rn(S, s_terms[n]);
-                    sh_S = S;
-                    sh_logS = log(S);
-                } else if (tid == 64) {
-                    sh_logR = log((double)R);  // beside the sum, on another warp
-                }
-                __syncthreads();
-                if (tid == 0) {
                     const int32_t Emin = eb + 4 * (int32_t)lvl_lo;
                     const double dbeta = P.beta[rd.beta_off + i + 1] - P.beta[rd.beta_off + i];
                     st->lnQ = (-dbeta) * (double)Emin + sh_logS - sh_logR;
                     st->Emin = Emin;
                     st->n_levels = nb_l;
                 }
-                // per level: floor(tau) and the draw threshold, tau = R_target w[n] / S
+                const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
                 const double S = sh_S;
-                for (uint32_t n = tid; n < nb_l; n += nt) {
+                for (uint32_t n = tid - 32; n < nb_l; n += nt - 32) {
                     const double tau = __ddiv_rn(__dmul_rn((double)rd.R, wt[n]), S);
                     const double fl = floor(tau);
                     flo_tab[n] = (uint32_t)fl;
