@@ -158,6 +158,8 @@ struct SmallGroup {  // small runs of one lattice size, annealed by anneal_small
     int any_glass = 0;
     std::vector<uint32_t> runs;
     uint64_t runs_off = 0;  // in d_meta
+    uint32_t R_max = 0, R_cap_max = 0;
+    SmallShape shape = {1, 512, 0};
 };
 
 struct SweepGroup {  // runs of one lattice size among the resident runs
@@ -234,7 +236,6 @@ struct pa_engine {
     uint32_t inf_maxR = 0, init_inf_n = 0, init_inf_maxR = 0;
     std::vector<SweepGroup> groups;
     std::vector<SmallGroup> small;     // runs on the one-launch-per-step path
-    uint32_t small_cs = 1;             // CTAs (one cluster) per small run
     std::vector<uint32_t> big;         // the other resident runs (per-stage kernels)
     uint64_t big_off = 0;
     std::map<uint32_t, Tuning> tuning;  // per lattice size
@@ -677,7 +678,6 @@ pa_status rebuild(pa_engine *e)
     e->small.clear();
     e->big.clear();
     const bool fuse = !(e->flags & (PA_CREATE_SEPARATE_KERNELS | PA_CREATE_GENERIC_SWEEP));
-    uint32_t n_small = 0, max_tiles = 1;
     for (uint32_t s : e->active) {
         const RunDev &x = e->rd[s];
         if (!fuse || !small_eligible(x)) {
@@ -692,17 +692,14 @@ pa_status rebuild(pa_engine *e)
         }
         e->small[k].runs.push_back(s);
         if (x.model == PA_EA_PMJ) e->small[k].any_glass = 1;
-        ++n_small;
-        const uint32_t tr = small_tile_replicas(x.L);
-        max_tiles = std::max(max_tiles, (x.R_cap + tr - 1) / tr);
+        e->small[k].R_max = std::max(e->small[k].R_max, x.R);
+        e->small[k].R_cap_max = std::max(e->small[k].R_cap_max, x.R_cap);
     }
-    for (auto &g : e->small) {
+    for (auto &g : e->small) {  // each lattice size is its own launch, with the GPU to itself
         g.runs_off = m.size();
         m.insert(m.end(), g.runs.begin(), g.runs.end());
+        g.shape = small_shape(g.L, g.any_glass, (uint32_t)g.runs.size(), g.R_max, g.R_cap_max);
     }
-    // cluster size: about two CTAs per SM over all small runs, at most 8 (portable), at most the tiles
-    e->small_cs = 1;
-    while (e->small_cs < 8 && 2 * e->small_cs * n_small <= 2u * 152u && 2 * e->small_cs <= max_tiles) e->small_cs *= 2;
     e->big_off = m.size();
     m.insert(m.end(), e->big.begin(), e->big.end());
     e->q_runs.clear();
@@ -953,7 +950,7 @@ void enqueue_small(pa_engine *e, uint32_t n_steps)
 {
     for (auto &g : e->small)
         timed_launch(e, PA_K_SMALL, [&] {
-            launch_anneal_small(e->P, meta(e, g.runs_off), (uint32_t)g.runs.size(), g.L, e->small_cs, g.any_glass,
+            launch_anneal_small(e->P, meta(e, g.runs_off), (uint32_t)g.runs.size(), g.L, g.shape, g.any_glass,
                                 n_steps, e->stream);
         });
 }

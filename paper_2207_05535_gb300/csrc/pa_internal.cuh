@@ -175,12 +175,6 @@ inline bool small_eligible(const RunDev &x)
 #ifndef SMALL_LPW_L32
 #define SMALL_LPW_L32 2
 #endif
-// Replicas one CTA (512 threads) of the small-population kernel sweeps at a time.
-inline uint32_t small_tile_replicas(uint32_t L)
-{
-    const uint32_t words = L * L / 64, lpw = L == 8 ? SMALL_LPW_L8 : L == 16 ? SMALL_LPW_L16 : SMALL_LPW_L32;
-    return 512u / (words * lpw);
-}
 
 // Launch wrappers implemented in pa_kernels.cu (all asynchronous on `s`).
 // `runs`: device list of the indices of the runs to process (the two
@@ -231,8 +225,15 @@ void launch_gather_records(const Pool &P, const uint32_t *runs, uint32_t n_runs,
                            cudaStream_t s);
 // n_steps temperatures of the small runs `runs` (all of lattice size L), cs
 // CTAs (a cluster) per run.
-void launch_anneal_small(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t L, uint32_t cs, int any_glass,
-                         uint32_t n_steps, cudaStream_t s);
+// Launch shape of the small-run kernel: CTAs per cluster (one cluster per run),
+// threads per CTA, and the compiled variant (0: 512 threads two CTAs per SM;
+// 1 / 2: up to 512 / 768 threads one CTA per SM).
+struct SmallShape {
+    uint32_t cs, block, variant;
+};
+SmallShape small_shape(uint32_t L, int any_glass, uint32_t n_runs, uint32_t R_max, uint32_t R_cap_max);
+void launch_anneal_small(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t L, const SmallShape &sh,
+                         int any_glass, uint32_t n_steps, cudaStream_t s);
 cudaError_t prepare_kernels();
 // Philox-only calibration loop: blocks x threads threads, iters x 8 calls each.
 void launch_philox_calibration(uint32_t *out, uint32_t blocks, uint32_t threads, uint32_t iters, bool wide,

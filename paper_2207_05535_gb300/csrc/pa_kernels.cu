@@ -2745,15 +2745,18 @@ __global__ void wavg_q_kernel(const pa_step_record *recs, const unsigned long lo
 // behind (records, scratch tables, run state) are those of the multi-kernel
 // path, so a run can move between the two paths at any step.
 // --------------------------------------------------------------------------
-constexpr uint32_t SMALL_THREADS = 512;
 constexpr uint32_t SMALL_MAX_N = 1024;  // L <= 32
 
-template <bool SG, uint32_t HW, uint32_t LPW>  // HW: words of a colour plane (L = 8: 1, 16: 4, 32: 16); LPW lanes per word
-__global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, const uint32_t *runs, uint32_t n_steps)
+// HW: words of a colour plane (L = 8: 1, 16: 4, 32: 16); LPW lanes per word; NT the
+// largest block (a multiple of 32, at least 128) and MINB the CTAs per SM it is
+// compiled for: 512 threads two per SM (64 registers), or 512 / 768 threads one
+// per SM (the compiler's register choice up to 128 / 85).
+template <bool SG, uint32_t HW, uint32_t LPW, uint32_t NT, uint32_t MINB>
+__global__ void __launch_bounds__(NT, MINB) anneal_small_kernel(Pool P, const uint32_t *runs, uint32_t n_steps)
 {
     constexpr uint32_t GPL = 8u / LPW;             // Philox groups per lane and word
     constexpr uint32_t LPR = HW * LPW;             // lanes per replica (divides 32)
-    constexpr uint32_t TR = SMALL_THREADS / LPR;   // replicas per tile
+    constexpr uint32_t TR = NT / LPR;              // replicas per tile at the largest block
     static_assert(LPR <= 32 && 32 % LPR == 0, "a replica's lanes lie in one warp");
     __shared__ uint32_t s_pl[TR][2 * HW];
     __shared__ __align__(16) uint32_t s_cnt[SMALL_MAX_RCAP];  // copy numbers; the measurement's terms h_n w[n]
@@ -2762,8 +2765,9 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
     static_assert(sizeof(double) * (SMALL_MAX_N + 1) <= sizeof(uint32_t) * SMALL_MAX_RCAP, "terms fit");
     __shared__ uint32_t sh_u[32];
     __shared__ long long sh_ll[32];
-    __shared__ Moments mom[SMALL_THREADS / 32];
-    __shared__ uint32_t sh_lo[SMALL_THREADS / 32], sh_hi[SMALL_THREADS / 32];
+    __shared__ uint32_t sh_u2[32];
+    __shared__ Moments mom[NT / 32];
+    __shared__ uint32_t sh_lvl[2];  // the lowest and highest occupied energy level
     __shared__ double sh_S, sh_logS, sh_logR;
     __shared__ uint32_t sh_carry, sh_first;
     __shared__ FamPart s_part[8];  // CTA 0: the family statistics of each CTA's chunk of children
@@ -2794,12 +2798,17 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
 
     // Every CTA decides from values that no CTA writes between the barriers
     // around the read, so all of them leave the loop at the same point: the
-    // status before any barrier of this launch, the temperature index (written
-    // only by the measurement, between the second and third barrier of a step),
-    // and the status after the resampling (between its first and second barrier).
+    // status and the temperature index before any barrier of this launch (each
+    // CTA then counts the temperatures itself), and the status after the
+    // resampling (between its first and second barrier).  A step has two cluster
+    // barriers: the other CTAs need nothing from the measurement that the next
+    // step's first barrier does not order (CTA 0 measures, then resamples, then
+    // arrives there), and they touch CTA 0's shared memory only between the
+    // first and second barrier of a step.
     if (st->status) return;
+    const uint32_t i0 = st->step + 1;
     for (uint32_t s = 0; s < n_steps; ++s) {
-        const uint32_t i = st->step + 1;
+        const uint32_t i = i0 + s;
         if (i >= rd.n_beta) break;
         const uint32_t ob = (i - 1) & 1u, nb = i & 1u;
 
@@ -2852,7 +2861,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
             const uint32_t all2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : 0u;
             const uint32_t hi1_0 = __umulhi(0xCD9E8D57u, i), lo1_0 = 0xCD9E8D57u * i;
             uint32_t *pl = s_pl[rl];
-            for (uint32_t tile0 = c_lo; tile0 < c_hi; tile0 += TR) {
+            for (uint32_t tile0 = c_lo; tile0 < c_hi; tile0 += nt / LPR) {
                 const uint32_t child = tile0 + rl;
                 const bool active = child < c_hi;
                 const uint32_t par = active ? parent[child] : 0u;
@@ -2974,14 +2983,25 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
                 if (tid == nt - 1) sh_carry = sj;
                 __syncthreads();
             }
-            c2 = block_sum(c2, sh_ll);
-            nfam = block_sum(nfam, sh_u);
-            cmax = block_max(cmax, sh_u, 0u);
+            c2 = warp_sum(c2);  // the three totals in one pass over the warps
+            nfam = warp_sum(nfam);
+            cmax = warp_max(cmax);
+            if (lane == 0) {
+                sh_ll[wid] = c2;
+                sh_u[wid] = nfam;
+                sh_u2[wid] = cmax;
+            }
+            __syncthreads();
             if (tid == 0) {
                 FamPart f;
-                f.c2 = c2;
-                f.nfam = nfam;
-                f.cmax = cmax;
+                f.c2 = 0;
+                f.nfam = 0;
+                f.cmax = 0;
+                for (uint32_t k = 0; k < nw; ++k) {
+                    f.c2 += sh_ll[k];
+                    f.nfam += sh_u[k];
+                    f.cmax = sh_u2[k] > f.cmax ? sh_u2[k] : f.cmax;
+                }
                 f.lead = sh_first - c_lo;  // replicas continuing the family open before the chunk
                 f.trail = c_hi - sh_carry; // length of the chunk's last run
                 f.len = c_hi - c_lo;
@@ -3012,8 +3032,8 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
                     }
                 }
                 if (lane == 0) {
-                    sh_lo[0] = lo;
-                    sh_hi[0] = hi;
+                    sh_lvl[0] = lo;
+                    sh_lvl[1] = hi;
                 }
                 if (prep) {
                     const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
@@ -3081,7 +3101,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
                 }
             }
             __syncthreads();
-            const uint32_t lvl_lo = sh_lo[0], nb_l = sh_hi[0] - lvl_lo + 1;
+            const uint32_t lvl_lo = sh_lvl[0], nb_l = sh_lvl[1] - lvl_lo + 1;
             if (wid == 0) {  // the warps' partial sums joined, the record
                 const bool has = lane < nw && lane != 1 && lane != 2;
                 const long long sE = warp_sum(has ? mom[lane].sE : 0ll), sE2 = warp_sum(has ? mom[lane].sE2 : 0ll);
@@ -3137,8 +3157,8 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) anneal_small_kernel(Pool P, 
                     thr_tab[n] = (unsigned long long)ceil(__dmul_rn(__dsub_rn(tau, fl), 4294967296.0));
                 }
             }
+            __syncthreads();  // the tables and the run state, before the next resampling reads them
         }
-        cl.sync();
     }
 }
 
@@ -3177,31 +3197,88 @@ __global__ void gather_records_kernel(Pool P, const uint32_t *runs, uint32_t n, 
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-void launch_anneal_small(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t L, uint32_t cs, int any_glass,
-                         uint32_t n_steps, cudaStream_t s)
+// The small-run kernel for (L, glass, variant): variant 0 = 512 threads, two
+// CTAs per SM; 1 = up to 512 threads, one per SM; 2 = up to 768, one per SM.
+template <bool SG, uint32_t HW, uint32_t LPW>
+static void *small_kernel_v(uint32_t variant)
 {
-    if (n_runs == 0 || n_steps == 0) return;
+    return variant == 0   ? (void *)anneal_small_kernel<SG, HW, LPW, 512, 2>
+           : variant == 1 ? (void *)anneal_small_kernel<SG, HW, LPW, 512, 1>
+                          : (void *)anneal_small_kernel<SG, HW, LPW, 768, 1>;
+}
+
+static void *small_kernel(uint32_t L, int sg, uint32_t variant)
+{
+    if (L == 8) return sg ? small_kernel_v<true, 1, SMALL_LPW_L8>(variant) : small_kernel_v<false, 1, SMALL_LPW_L8>(variant);
+    if (L == 16)
+        return sg ? small_kernel_v<true, 4, SMALL_LPW_L16>(variant) : small_kernel_v<false, 4, SMALL_LPW_L16>(variant);
+    return sg ? small_kernel_v<true, 16, SMALL_LPW_L32>(variant) : small_kernel_v<false, 16, SMALL_LPW_L32>(variant);
+}
+
+static cudaLaunchConfig_t small_launch_config(uint32_t n_clusters, const SmallShape &sh, cudaStream_t s,
+                                              cudaLaunchAttribute *at)
+{
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(n_runs * cs);
-    cfg.blockDim = dim3(SMALL_THREADS);
+    cfg.gridDim = dim3(n_clusters * sh.cs);
+    cfg.blockDim = dim3(sh.block);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.x = sh.cs;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (L == 8)
-        any_glass ? cudaLaunchKernelEx(&cfg, anneal_small_kernel<true, 1, SMALL_LPW_L8>, P, runs, n_steps)
-                  : cudaLaunchKernelEx(&cfg, anneal_small_kernel<false, 1, SMALL_LPW_L8>, P, runs, n_steps);
-    else if (L == 16)
-        any_glass ? cudaLaunchKernelEx(&cfg, anneal_small_kernel<true, 4, SMALL_LPW_L16>, P, runs, n_steps)
-                  : cudaLaunchKernelEx(&cfg, anneal_small_kernel<false, 4, SMALL_LPW_L16>, P, runs, n_steps);
-    else
-        any_glass ? cudaLaunchKernelEx(&cfg, anneal_small_kernel<true, 16, SMALL_LPW_L32>, P, runs, n_steps)
-                  : cudaLaunchKernelEx(&cfg, anneal_small_kernel<false, 16, SMALL_LPW_L32>, P, runs, n_steps);
+    return cfg;
+}
+
+// Launch shape of the small-run kernel for n runs of lattice size L.  A run's
+// steps are a chain of cluster barriers, so a run whose CTAs share SMs with
+// another run's is slower by the sharing, and the launch lasts as long as its
+// slowest run.  The shape is therefore the largest cluster (at most 8 CTAs)
+// whose block covers a CTA's share of a run's children (R + 3 sqrt(R), beyond
+// the nearest-integer resampling's spread) in one tile and whose clusters all
+// fit the GPU at once with one CTA per SM (asked of the occupancy calculator).
+// Without such a shape: 512-thread CTAs two per SM, about two CTAs per SM over
+// all the runs, the cluster at most the tiles of the largest capacity.
+SmallShape small_shape(uint32_t L, int any_glass, uint32_t n_runs, uint32_t R_max, uint32_t R_cap_max)
+{
+    const uint32_t lpr = (L * L / 64) * (L == 8 ? SMALL_LPW_L8 : L == 16 ? SMALL_LPW_L16 : SMALL_LPW_L32);
+    const double R_est = (double)R_max + 3.0 * sqrt((double)R_max) + 1.0;
+    for (uint32_t cs = 8; cs >= 1; --cs) {
+        const uint32_t chunk = (uint32_t)ceil(R_est / cs);
+        uint32_t block = (chunk * lpr + 31) / 32 * 32;
+        block = block < 128 ? 128 : block;
+        if (block > 768) break;  // smaller clusters only need larger blocks
+        const SmallShape sh = {cs, block, block <= 512 ? 1u : 2u};
+        cudaLaunchAttribute at[1];
+        cudaLaunchConfig_t cfg = small_launch_config(1, sh, 0, at);
+        int fit = 0;
+        if (cudaOccupancyMaxActiveClusters(&fit, small_kernel(L, any_glass, sh.variant), &cfg) != cudaSuccess) {
+            (void)cudaGetLastError();
+            fit = 0;
+        }
+        if (fit >= (int)n_runs) return sh;
+    }
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        sms = 152;
+    }
+    const uint32_t tiles = (R_cap_max + 512 / lpr - 1) / (512 / lpr);
+    SmallShape sh = {1, 512, 0};
+    while (sh.cs < 8 && 2 * sh.cs * n_runs <= 2u * (uint32_t)sms && 2 * sh.cs <= tiles) sh.cs *= 2;
+    return sh;
+}
+
+void launch_anneal_small(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t L, const SmallShape &sh,
+                         int any_glass, uint32_t n_steps, cudaStream_t s)
+{
+    if (n_runs == 0 || n_steps == 0) return;
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = small_launch_config(n_runs, sh, s, at);
+    void *args[] = {(void *)&P, (void *)&runs, (void *)&n_steps};
+    cudaLaunchKernelExC(&cfg, small_kernel(L, any_glass, sh.variant), args);
 }
 
 void launch_gather_records(const Pool &P, const uint32_t *runs, uint32_t n_runs, pa_step_record *out, cudaStream_t s)
