@@ -2227,7 +2227,7 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) mea
     __shared__ FamPart part[32];
     __shared__ Moments mom[PA_MEASURE_THREADS / 32];
     __shared__ uint32_t sh_lohi[2];
-    __shared__ double sh_S;
+    __shared__ double sh_S, sh_logS, sh_logR;
     __shared__ uint32_t sh_last;
     const uint32_t run = runs[blockIdx.x];
     const RunDev rd = P.runs[run];
@@ -2384,133 +2384,156 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) mea
     }
     __syncthreads();
 
-    // the moments from the run's histograms, and the occupied energy levels
-    Moments mo = {0, 0, 0, 0, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}};
-    uint32_t elo = 0xffffffffu, ehi = 0u;
-    for (uint32_t n = tid; n < n1; n += nt) {
-        const uint32_t he = __ldcg(&gE[n]), hm = __ldcg(&gM[n]);
-        if (he) {
-            elo = n < elo ? n : elo;
-            ehi = n > ehi ? n : ehi;
-            const long long e = (long long)eb + 4ll * n;
-            const unsigned long long ae = (unsigned long long)(e < 0 ? -e : e), e2 = ae * ae;  // |E| <= 2^17
-            mo.sE += (long long)he * e;
-            mo.sE2 += (long long)((unsigned long long)he * e2);
-            const I128 t3 = mul_u64(he, ae * e2);
-            add128(mo.sE3, e < 0 ? neg128(t3) : t3);
-            add128(mo.sE4, mul_128_u64(mul_u64(he, e2), e2));
-        }
-        if (hm) {
-            const long long m = 2ll * n - (long long)N;
-            const unsigned long long am = (unsigned long long)(m < 0 ? -m : m), m2 = am * am;  // |M| <= 2^16
-            mo.sAM += (long long)((unsigned long long)hm * am);
-            mo.sM2 += (long long)((unsigned long long)hm * m2);
-            add128(mo.sAM3, mul_u64(hm, am * m2));
-            add128(mo.sM4, mul_128_u64(mul_u64(hm, m2), m2));
-        }
-    }
-    mo.sE = warp_sum(mo.sE);
-    mo.sE2 = warp_sum(mo.sE2);
-    mo.sAM = warp_sum(mo.sAM);
-    mo.sM2 = warp_sum(mo.sM2);
-    mo.sE3 = warp_sum128(mo.sE3);
-    mo.sE4 = warp_sum128(mo.sE4);
-    mo.sAM3 = warp_sum128(mo.sAM3);
-    mo.sM4 = warp_sum128(mo.sM4);
-    elo = warp_min(elo);
-    ehi = warp_max(ehi);
-    if (lane == 0) {
-        mom[wid] = mo;
-        reinterpret_cast<uint32_t *>(sh_h[0])[wid] = elo;  // the counters are no longer needed
-        reinterpret_cast<uint32_t *>(sh_h[1])[wid] = ehi;
-    }
-    __syncthreads();
+    // The run's tail.  The serial chain the next resampling waits for (occupied
+    // levels, terms h_n w[n], their ascending sum S and ln S) runs on warp 1 while
+    // warp 2 takes ln R and the other warps form the moments from the histograms;
+    // then warp 0 writes the record beside the tables of floor(tau) and draw
+    // thresholds (the counters' shared memory is free once the CTAs' counts are in).
     const bool prep = rd.resample != PA_MULTINOMIAL && i + 1 < rd.n_beta;
-    if (tid == 0) {
-        Moments t = mom[0];
-        uint32_t l = sh_h[0][0], h = sh_h[1][0];
-        for (uint32_t k = 1; k < nw; ++k) {
-            const Moments &q = mom[k];
-            t.sE += q.sE;
-            t.sE2 += q.sE2;
-            t.sAM += q.sAM;
-            t.sM2 += q.sM2;
-            add128(t.sE3, q.sE3);
-            add128(t.sE4, q.sE4);
-            add128(t.sAM3, q.sAM3);
-            add128(t.sM4, q.sM4);
-            l = sh_h[0][k] < l ? sh_h[0][k] : l;
-            h = sh_h[1][k] > h ? sh_h[1][k] : h;
+    const double lnQ_i = init ? 0.0 : st->lnQ;  // read before it is replaced by ln Q_{i+1}
+    if (wid == 1) {
+        uint32_t l = 0xffffffffu, h = 0u;
+        for (uint32_t n0 = 0; n0 < n1; n0 += 32) {
+            const uint32_t n = n0 + lane;
+            const uint32_t m = __ballot_sync(FULL, n < n1 && __ldcg(&gE[n]) != 0u);
+            if (m) {
+                l = l == 0xffffffffu ? n0 + __ffs(m) - 1 : l;
+                h = n0 + 31 - __clz(m);
+            }
         }
-        const FamPart f = part[0];
-        pa_step_record *rec = P.rec + rd.rec_off + i;
-        const double lnQ = init ? 0.0 : st->lnQ;
-        rec->beta = P.beta[rd.beta_off + i];
-        rec->lnQ = lnQ;
-        rec->minus_betaF = init ? rd.ln2N : P.rec[rd.rec_off + i - 1].minus_betaF + lnQ;
-        rec->sumE = t.sE;
-        rec->sumE2 = t.sE2;
-        rec->sumAbsM = t.sAM;
-        rec->sumM2 = t.sM2;
-        rec->sum_c2 = f.c2;
-        rec->sumE3[0] = t.sE3.lo;
-        rec->sumE3[1] = (unsigned long long)t.sE3.hi;
-        rec->sumE4[0] = t.sE4.lo;
-        rec->sumE4[1] = (unsigned long long)t.sE4.hi;
-        rec->sumAbsM3[0] = t.sAM3.lo;
-        rec->sumAbsM3[1] = (unsigned long long)t.sAM3.hi;
-        rec->sumM4[0] = t.sM4.lo;
-        rec->sumM4[1] = (unsigned long long)t.sM4.hi;
-        rec->R = R;
-        rec->R_target = rd.R;
-        rec->n_fam = f.nfam;
-        rec->max_fam = f.cmax;
-        rec->N = rd.N;
-        rec->status = 0;
-        st->step = i;
-        st->R_cur = R;
-        st->R_new = R;
-        sh_lohi[0] = l;
-        sh_lohi[1] = h;
+        if (lane == 0) {
+            sh_lohi[0] = l;
+            sh_lohi[1] = h;
+        }
+        if (prep) {
+            const uint32_t nb = h - l + 1;
+            const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];  // exp(-4 n dbeta_{i+1})
+            double *terms = reinterpret_cast<double *>(&sh_h[0][0]);
+            const bool staged = nb <= MEASURE_SMEM_TERMS;
+            if (staged) {
+                for (uint32_t n = lane; n < nb; n += 32) terms[n] = __dmul_rn((double)__ldcg(&gE[l + n]), wt[n]);
+                __syncwarp();
+            }
+            if (lane == 0) {
+                double S = 0.0;
+                if (staged)
+                    for (uint32_t n = 0; n < nb; ++n) S = __dadd_rn(S, terms[n]);
+                else
+                    for (uint32_t n = 0; n < nb; ++n) S = __dadd_rn(S, __dmul_rn((double)__ldcg(&gE[l + n]), wt[n]));
+                sh_S = S;
+                sh_logS = log(S);
+            }
+        }
+    } else if (wid == 2) {
+        if (prep && lane == 0) sh_logR = log((double)R);
+    } else {  // warps 0 and 3.. : partial moments, energy then magnetisation
+        const uint32_t mt = wid == 0 ? lane : tid - 64, nmt = nt - 64;
+        long long s1 = 0, s2 = 0;
+        I128 s3 = {0ull, 0ll}, s4 = {0ull, 0ll};
+        for (uint32_t n = mt; n < n1; n += nmt) {
+            const uint32_t he = __ldcg(&gE[n]);
+            if (he) {
+                const long long e = (long long)eb + 4ll * n;
+                const unsigned long long ae = (unsigned long long)(e < 0 ? -e : e), e2 = ae * ae;  // |E| <= 2^17
+                s1 += (long long)he * e;
+                s2 += (long long)((unsigned long long)he * e2);
+                const I128 t3 = mul_u64(he, ae * e2);
+                add128(s3, e < 0 ? neg128(t3) : t3);
+                add128(s4, mul_128_u64(mul_u64(he, e2), e2));
+            }
+        }
+        s1 = warp_sum(s1);
+        s2 = warp_sum(s2);
+        s3 = warp_sum128(s3);
+        s4 = warp_sum128(s4);
+        if (lane == 0) {
+            mom[wid].sE = s1;
+            mom[wid].sE2 = s2;
+            mom[wid].sE3 = s3;
+            mom[wid].sE4 = s4;
+        }
+        s1 = s2 = 0;
+        s3 = s4 = I128{0ull, 0ll};
+        for (uint32_t n = mt; n < n1; n += nmt) {
+            const uint32_t hm = __ldcg(&gM[n]);
+            if (hm) {
+                const long long m = 2ll * n - (long long)N;
+                const unsigned long long am = (unsigned long long)(m < 0 ? -m : m), m2 = am * am;  // |M| <= 2^16
+                s1 += (long long)((unsigned long long)hm * am);
+                s2 += (long long)((unsigned long long)hm * m2);
+                add128(s3, mul_u64(hm, am * m2));
+                add128(s4, mul_128_u64(mul_u64(hm, m2), m2));
+            }
+        }
+        s1 = warp_sum(s1);
+        s2 = warp_sum(s2);
+        s3 = warp_sum128(s3);
+        s4 = warp_sum128(s4);
+        if (lane == 0) {
+            mom[wid].sAM = s1;
+            mom[wid].sM2 = s2;
+            mom[wid].sAM3 = s3;
+            mom[wid].sM4 = s4;
+        }
     }
     __syncthreads();
-    if (prep) {  // S, ln Q and E_min of the next resampling
-        const uint32_t l = sh_lohi[0], nb = sh_lohi[1] - l + 1;
-        const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];  // exp(-4 n dbeta_{i+1})
-        // the terms h_n w[n] in parallel (the counters' shared memory is free now),
-        // then their sum by one thread in ascending order
-        double *terms = reinterpret_cast<double *>(&sh_h[0][0]);
-        const bool staged = nb <= MEASURE_SMEM_TERMS;
-        if (staged) {
-            for (uint32_t n = tid; n < nb; n += nt) terms[n] = __dmul_rn((double)__ldcg(&gE[l + n]), wt[n]);
-            __syncthreads();
+    if (wid == 0) {  // the warps' partial moments joined, the record
+        const bool has = lane < nw && lane != 1 && lane != 2;
+        const long long sE = warp_sum(has ? mom[lane].sE : 0ll), sE2 = warp_sum(has ? mom[lane].sE2 : 0ll);
+        const long long sAM = warp_sum(has ? mom[lane].sAM : 0ll), sM2 = warp_sum(has ? mom[lane].sM2 : 0ll);
+        const I128 z = {0ull, 0ll};
+        const I128 sE3 = warp_sum128(has ? mom[lane].sE3 : z), sE4 = warp_sum128(has ? mom[lane].sE4 : z);
+        const I128 sAM3 = warp_sum128(has ? mom[lane].sAM3 : z), sM4 = warp_sum128(has ? mom[lane].sM4 : z);
+        if (lane == 0) {
+            const FamPart f = part[0];
+            pa_step_record *rec = P.rec + rd.rec_off + i;
+            rec->beta = P.beta[rd.beta_off + i];
+            rec->lnQ = lnQ_i;
+            rec->minus_betaF = init ? rd.ln2N : P.rec[rd.rec_off + i - 1].minus_betaF + lnQ_i;
+            rec->sumE = sE;
+            rec->sumE2 = sE2;
+            rec->sumAbsM = sAM;
+            rec->sumM2 = sM2;
+            rec->sum_c2 = f.c2;
+            rec->sumE3[0] = sE3.lo;
+            rec->sumE3[1] = (unsigned long long)sE3.hi;
+            rec->sumE4[0] = sE4.lo;
+            rec->sumE4[1] = (unsigned long long)sE4.hi;
+            rec->sumAbsM3[0] = sAM3.lo;
+            rec->sumAbsM3[1] = (unsigned long long)sAM3.hi;
+            rec->sumM4[0] = sM4.lo;
+            rec->sumM4[1] = (unsigned long long)sM4.hi;
+            rec->R = R;
+            rec->R_target = rd.R;
+            rec->n_fam = f.nfam;
+            rec->max_fam = f.cmax;
+            rec->N = rd.N;
+            rec->status = 0;
+            st->step = i;
+            st->R_cur = R;
+            st->R_new = R;
         }
-        if (tid == 0) {
-            double S = 0.0;
-            if (staged)
-                for (uint32_t n = 0; n < nb; ++n) S = __dadd_rn(S, terms[n]);
-            else
-                for (uint32_t n = 0; n < nb; ++n) S = __dadd_rn(S, __dmul_rn((double)__ldcg(&gE[l + n]), wt[n]));
+    } else if (prep) {  // ln Q_{i+1}, E_min, and per level floor(tau) and the draw threshold, tau = R_target w[n] / S
+        const uint32_t l = sh_lohi[0], nb = sh_lohi[1] - l + 1;
+        const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
+        if (tid == 32) {
             const int32_t Emin = eb + 4 * (int32_t)l;
             const double dbeta = P.beta[rd.beta_off + i + 1] - P.beta[rd.beta_off + i];
-            sh_S = S;
-            st->lnQ = (-dbeta) * (double)Emin + log(S) - log((double)R);
+            st->lnQ = (-dbeta) * (double)Emin + sh_logS - sh_logR;
             st->Emin = Emin;
             st->n_levels = nb;
         }
-        __syncthreads();
-        // per level: floor(tau) and the draw threshold, tau = R_target w[n] / S
         const double S = sh_S;
         unsigned long long *thr = scr + scr_table_off(N);
         uint32_t *flo = reinterpret_cast<uint32_t *>(scr + scr_level_off(N));
-        for (uint32_t n = tid; n < nb; n += nt) {
+        for (uint32_t n = tid - 32; n < nb; n += nt - 32) {
             const double tau = __ddiv_rn(__dmul_rn((double)rd.R, wt[n]), S);
             const double fl = floor(tau);
             flo[n] = (uint32_t)fl;
             thr[n] = (unsigned long long)ceil(__dmul_rn(__dsub_rn(tau, fl), 4294967296.0));
         }
     }
-    for (uint32_t n = tid; n < n1; n += nt) {  // cleared for the next step
+    for (uint32_t n = tid; n < n1; n += nt) {  // cleared for the next step (every read of them is done)
         gE[n] = 0u;
         gM[n] = 0u;
     }
@@ -2550,21 +2573,37 @@ __device__ __forceinline__ double central_from_raw(int k, const double *raw)
 // W_F, Wvar_C, Wvar_Chi) in FP64: one warp per group, lanes over the runs m,
 // temperatures in order.  w receives the weights [group][step][m].
 // --------------------------------------------------------------------------
-// pass 1, one thread per (group, run m): log weights over the temperatures,
-// lambda(i, m) = ln R_i + (-beta_i F_i) [+ sum_{k<=i} ln(R_{k-1} / R)], into w[g][i][m]
+// pass 1, one warp per (group, run m): log weights over the temperatures,
+// lambda(i, m) = ln R_i + (-beta_i F_i) [+ sum_{k<=i} ln(R_{k-1} / R)], into w[g][i][m].
+// The lanes take the logarithms of 32 temperatures at once (FP64 logarithms are
+// long dependent chains); the running sum then adds the terms in temperature
+// order, each broadcast to every lane, so every lane holds the sum up to its own
+// temperature: the same additions in the same order as a sequential loop.
 __global__ void __launch_bounds__(128) wavg_lambda_kernel(const pa_step_record *recs,
                                                           const unsigned long long *rec_off, uint32_t n_groups,
                                                           uint32_t M, uint32_t n_steps, uint32_t kind, double *w)
 {
-    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (uint64_t)n_groups * M) return;
+    const uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    if (t >= (uint64_t)n_groups * M) return;  // warp-uniform
     const uint32_t g = (uint32_t)(t / M), m = (uint32_t)(t % M);
     const pa_step_record *r = recs + rec_off[t];
     double *wg = w + (uint64_t)g * n_steps * M;
     double lsum = 0.0;
-    for (uint32_t i = 0; i < n_steps; ++i) {
-        if (kind == PA_WEIGHT_FULL && i > 0) lsum += log((double)r[i - 1].R / (double)r[i].R_target);
-        wg[(uint64_t)i * M + m] = log((double)r[i].R) + r[i].minus_betaF + lsum;
+    for (uint32_t i0 = 0; i0 < n_steps; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        double a = 0.0, b = 0.0;
+        if (i < n_steps) {
+            a = log((double)r[i].R) + r[i].minus_betaF;
+            if (kind == PA_WEIGHT_FULL && i > 0) b = log((double)r[i - 1].R / (double)r[i].R_target);
+        }
+        double mine = 0.0;
+        const uint32_t nk = n_steps - i0 < 32 ? n_steps - i0 : 32u;
+        for (uint32_t k = 0; k < nk; ++k) {
+            lsum += __shfl_sync(FULL, b, k);
+            if (k == lane) mine = lsum;
+        }
+        if (i < n_steps) wg[(uint64_t)i * M + m] = a + mine;
     }
 }
 
@@ -3505,7 +3544,7 @@ void launch_wavg_wang(const pa_step_record *recs, const unsigned long long *rec_
                       double *Pqp, double *Pqw, cudaStream_t s)
 {
     const uint64_t nGM = (uint64_t)n_groups * M;
-    wavg_lambda_kernel<<<(unsigned)((nGM + 127) / 128), 128, 0, s>>>(recs, rec_off, n_groups, M, n_steps, kind, w);
+    wavg_lambda_kernel<<<(unsigned)((32 * nGM + 127) / 128), 128, 0, s>>>(recs, rec_off, n_groups, M, n_steps, kind, w);
     const dim3 grid((n_steps + 3) / 4, n_groups);  // one warp per (temperature, group)
     wavg_step_kernel<<<grid, 128, 0, s>>>(recs, rec_off, n_groups, M, n_steps, N, out, w);
     wavg_finish_kernel<<<grid, 128, 0, s>>>(n_groups, M, n_steps, N, out, w);
