@@ -158,8 +158,9 @@ struct SmallGroup {  // small runs of one lattice size, annealed by anneal_small
     int any_glass = 0;
     std::vector<uint32_t> runs;
     uint64_t runs_off = 0;  // in d_meta
-    uint32_t R_max = 0, R_cap_max = 0;
-    SmallShape shape = {1, 512, 0};
+    uint32_t R_max = 0, R_cap_max = 0, theta_max = 0;
+    SmallShape shape = {1, 512, 0, 0, 0};  // one temperature per launch
+    SmallShape ahead = {0, 0, 0, 0, 0};     // several temperatures per launch (cs = 0: none)
 };
 
 struct SweepGroup {  // runs of one lattice size among the resident runs
@@ -694,11 +695,13 @@ pa_status rebuild(pa_engine *e)
         if (x.model == PA_EA_PMJ) e->small[k].any_glass = 1;
         e->small[k].R_max = std::max(e->small[k].R_max, x.R);
         e->small[k].R_cap_max = std::max(e->small[k].R_cap_max, x.R_cap);
+        e->small[k].theta_max = std::max(e->small[k].theta_max, x.theta);
     }
     for (auto &g : e->small) {  // each lattice size is its own launch, with the GPU to itself
         g.runs_off = m.size();
         m.insert(m.end(), g.runs.begin(), g.runs.end());
         g.shape = small_shape(g.L, g.any_glass, (uint32_t)g.runs.size(), g.R_max, g.R_cap_max);
+        g.ahead = small_shape_ahead(g.L, g.any_glass, (uint32_t)g.runs.size(), g.R_max, g.theta_max);
     }
     e->big_off = m.size();
     m.insert(m.end(), e->big.begin(), e->big.end());
@@ -950,7 +953,8 @@ void enqueue_small(pa_engine *e, uint32_t n_steps)
 {
     for (auto &g : e->small)
         timed_launch(e, PA_K_SMALL, [&] {
-            launch_anneal_small(e->P, meta(e, g.runs_off), (uint32_t)g.runs.size(), g.L, g.shape, g.any_glass,
+            launch_anneal_small(e->P, meta(e, g.runs_off), (uint32_t)g.runs.size(), g.L,
+                                n_steps > 1 && g.ahead.cs ? g.ahead : g.shape, g.any_glass,
                                 n_steps, e->stream);
         });
 }

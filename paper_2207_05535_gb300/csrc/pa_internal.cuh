@@ -226,12 +226,15 @@ void launch_gather_records(const Pool &P, const uint32_t *runs, uint32_t n_runs,
 // n_steps temperatures of the small runs `runs` (all of lattice size L), cs
 // CTAs (a cluster) per run.
 // Launch shape of the small-run kernel: CTAs per cluster (one cluster per run),
-// threads per CTA, and the compiled variant (0: 512 threads two CTAs per SM;
-// 1 / 2: up to 512 / 768 threads one CTA per SM).
+// threads per CTA, the compiled variant (0: 512 threads two CTAs per SM; 1 / 2:
+// up to 512 / 768 threads one CTA per SM; 3 / 4: the same with 4 lanes per word
+// at L = 8), the half-sweeps whose comparison bits are drawn ahead (0: none)
+// and the dynamic shared memory they take.
 struct SmallShape {
-    uint32_t cs, block, variant;
+    uint32_t cs, block, variant, H, smem;
 };
 SmallShape small_shape(uint32_t L, int any_glass, uint32_t n_runs, uint32_t R_max, uint32_t R_cap_max);
+SmallShape small_shape_ahead(uint32_t L, int any_glass, uint32_t n_runs, uint32_t R_max, uint32_t theta_max);
 void launch_anneal_small(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t L, const SmallShape &sh,
                          int any_glass, uint32_t n_steps, cudaStream_t s);
 cudaError_t prepare_kernels();

@@ -40,6 +40,7 @@
 // FP64 arithmetic that decides an integer uses explicit round-to-nearest
 // intrinsics (no contraction), in the same order as the plain definition.
 #include <cooperative_groups.h>
+#include <cmath>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -2791,12 +2792,14 @@ constexpr uint32_t SMALL_MAX_N = 1024;  // L <= 32
 // compiled for: 512 threads two per SM (64 registers), or 512 / 768 threads one
 // per SM (the compiler's register choice up to 128 / 85).
 template <bool SG, uint32_t HW, uint32_t LPW, uint32_t NT, uint32_t MINB>
-__global__ void __launch_bounds__(NT, MINB) anneal_small_kernel(Pool P, const uint32_t *runs, uint32_t n_steps)
+__global__ void __launch_bounds__(NT, MINB) anneal_small_kernel(Pool P, const uint32_t *runs, uint32_t n_steps,
+                                                                uint32_t H)
 {
     constexpr uint32_t GPL = 8u / LPW;             // Philox groups per lane and word
     constexpr uint32_t LPR = HW * LPW;             // lanes per replica (divides 32)
     constexpr uint32_t TR = NT / LPR;              // replicas per tile at the largest block
     static_assert(LPR <= 32 && 32 % LPR == 0, "a replica's lanes lie in one warp");
+    constexpr bool AHEAD = HW == 1 && LPW == 4 && MINB == 1;  // the variants launched with H > 0
     __shared__ uint32_t s_pl[TR][2 * HW];
     __shared__ __align__(16) uint32_t s_cnt[SMALL_MAX_RCAP];  // copy numbers; the measurement's terms h_n w[n]
     __shared__ uint32_t s_hE[SMALL_MAX_N + 1], s_hM[SMALL_MAX_N + 1];
@@ -2811,6 +2814,8 @@ __global__ void __launch_bounds__(NT, MINB) anneal_small_kernel(Pool P, const ui
     __shared__ uint32_t sh_carry, sh_first;
     __shared__ FamPart s_part[8];  // CTA 0: the family statistics of each CTA's chunk of children
     __shared__ int32_t sh_eb;      // CTA 0: base of the energy levels of the new population
+    __shared__ uint32_t sh_pre_step;  // the temperature whose comparison bits s_pre holds
+    extern __shared__ uint2 s_pre[];  // H > 0: [half-sweep][replica of the tile][word] (B1, B2)
 
     cg::cluster_group cl = cg::this_cluster();
     const uint32_t CS = cl.num_blocks(), rank = cl.block_rank();
@@ -2826,6 +2831,21 @@ __global__ void __launch_bounds__(NT, MINB) anneal_small_kernel(Pool P, const ui
     uint32_t *parent = P.parent + rd.rep_off;
     PhiloxKeys K;
     philox_keys(K, rd.seed, rd.run_id);
+    // With H > 0 (and CS >= 2) CTA 0 sweeps no children: it resamples and measures, while
+    // the other CTAs sweep fixed slices of Wc children (from R + 3 sqrt(R), beyond the
+    // nearest-integer resampling's spread; the last slice also takes any child beyond) and,
+    // while CTA 0 measures, draw the next temperature's comparison bits of their slice for
+    // its first H half-sweeps into s_pre.  The bits depend only on the Philox counters, so
+    // the sweeps flip the same spins either way.
+    uint32_t Wc = 0;
+    if (!AHEAD) H = 0;
+    if (H) {
+        uint32_t q = (uint32_t)sqrtf((float)rd.R);  // floor(sqrt(R)), corrected
+        while (q * q > rd.R) --q;
+        while ((q + 1) * (q + 1) <= rd.R) ++q;
+        Wc = (rd.R + 3 * q + 1 + CS - 2) / (CS - 1);
+    }
+    if (tid == 0) sh_pre_step = 0xffffffffu;
     uint32_t J[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
     if (SG) {  // the bond masks of this lane's plane word, both colours
         const uint32_t *Jp = P.J + rd.J_off + 2 * rd.wstride;
@@ -2862,7 +2882,7 @@ __global__ void __launch_bounds__(NT, MINB) anneal_small_kernel(Pool P, const ui
             const int32_t *E = P.E[ob] + rd.rep_off;
             const int32_t Emin = st->Emin;
             for (uint32_t j = tid; j < Rc; j += nt) {
-                const uint32_t n = (uint32_t)(E[j] - Emin) >> 2;
+                const uint32_t n = min((uint32_t)(E[j] - Emin) >> 2, N);  // <= N for any population; bounds the tables
                 const uint32_t u = philox4x32_10(j, 0, i, TAG_RESAMPLE << 24, rd.seed, rd.run_id).x;
                 s_cnt[j] = flo_tab[n] + ((unsigned long long)u < thr_tab[n] ? 1u : 0u);
             }
@@ -2891,8 +2911,15 @@ __global__ void __launch_bounds__(NT, MINB) anneal_small_kernel(Pool P, const ui
         // ---- every CTA: its children, gathered from their parents and swept theta times
         {
             const uint32_t Rn = st->R_new;
-            const uint32_t chunk = (Rn + CS - 1) / CS;
-            const uint32_t c_lo = min(Rn, rank * chunk), c_hi = min(Rn, c_lo + chunk);
+            uint32_t c_lo, c_hi;
+            if (H) {
+                c_lo = min(Rn, rank == 0 ? 0u : (rank - 1) * Wc);
+                c_hi = min(Rn, rank == 0 ? 0u : rank + 1 == CS ? 0xffffffffu : rank * Wc);
+            } else {
+                const uint32_t chunk = (Rn + CS - 1) / CS;
+                c_lo = min(Rn, rank * chunk);
+                c_hi = min(Rn, c_lo + chunk);
+            }
             const unsigned long long T1 = P.thr[rd.thr_off + 2 * i], T2 = P.thr[rd.thr_off + 2 * i + 1];
             const uint32_t t1 = T1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T1;
             const uint32_t t2 = T2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)T2;
@@ -2917,7 +2944,16 @@ __global__ void __launch_bounds__(NT, MINB) anneal_small_kernel(Pool P, const ui
                 // not on the spins: each step draws (and joins over the word's lanes) those of the
                 // next half-sweep while it applies the current one, which keeps the Philox chains
                 // off the dependent path of spin updates.
+                // the first tile of a slice may find its bits drawn already
+                const bool pre = AHEAD && H && tile0 == c_lo && rank != 0 && sh_pre_step == i;
+                const uint32_t Hh = min(H, 2 * rd.theta);
                 auto draw = [&](uint32_t h, uint32_t &B1, uint32_t &B2) {
+                    if (AHEAD && pre && h < Hh) {
+                        const uint2 v = s_pre[(h * (nt / LPR) + rl) * HW + w];
+                        B1 = v.x;
+                        B2 = v.y;
+                        return;
+                    }
                     const uint32_t ctr3 = (TAG_SWEEP << 24) | h;
                     B1 = 0;
                     B2 = 0;
@@ -2987,7 +3023,7 @@ __global__ void __launch_bounds__(NT, MINB) anneal_small_kernel(Pool P, const ui
                     // counts per energy and magnetisation value into CTA 0's histograms; every
                     // energy of the population has the residue of E_0 mod 4, so any child gives the base
                     const int32_t eb = -2 * (int32_t)N + ((Ec + 2 * (int32_t)N) & 3);
-                    if (child == 0) sh_eb = eb;
+                    if (child == 0) *cl.map_shared_rank(&sh_eb, 0) = eb;  // child 0 may be another CTA's
                     atomicAdd(cl.map_shared_rank(&s_hE[(uint32_t)(Ec - eb) >> 2], 0), 1u);
                     atomicAdd(cl.map_shared_rank(&s_hM[(uint32_t)(Mc + (int32_t)N) >> 1], 0), 1u);
                 }
@@ -3049,6 +3085,36 @@ __global__ void __launch_bounds__(NT, MINB) anneal_small_kernel(Pool P, const ui
             }
         }
         cl.sync();
+
+        // ---- the other CTAs, while CTA 0 measures and resamples: the next temperature's
+        // comparison bits of their slice (every lane draws, so the shuffles see full warps)
+        if (AHEAD && H && rank != 0 && s + 1 < n_steps && i + 1 < rd.n_beta) {
+            const uint32_t i2 = i + 1, lo_k = (rank - 1) * Wc;
+            const uint32_t cnt = rd.R_cap > lo_k ? min(Wc, rd.R_cap - lo_k) : 0u;
+            const unsigned long long U1 = P.thr[rd.thr_off + 2 * i2], U2 = P.thr[rd.thr_off + 2 * i2 + 1];
+            const uint32_t u1 = U1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)U1;
+            const uint32_t u2 = U2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)U2;
+            const uint32_t g1 = __umulhi(0xCD9E8D57u, i2), g0 = 0xCD9E8D57u * i2;
+            const uint32_t child = lo_k + rl, Hh = min(H, 2 * rd.theta), tr = nt / LPR;
+#pragma unroll 2
+            for (uint32_t h = 0; h < Hh; ++h) {
+                const uint32_t ctr3 = (TAG_SWEEP << 24) | h;
+                uint32_t B1 = 0, B2 = 0;
+#pragma unroll
+                for (uint32_t q = 0; q < GPL; ++q) {
+                    const uint32_t g = sub * GPL + q;
+                    const uint4 u = philox_rk<true>(8 * w + g, child, ctr3, g1, g0, K);
+                    pack_group(B1, B2, u, g, u1, u2);
+                }
+#pragma unroll
+                for (uint32_t o = 1; o < LPW; o <<= 1) {
+                    B1 |= __shfl_xor_sync(FULL, B1, o);
+                    B2 |= __shfl_xor_sync(FULL, B2, o);
+                }
+                if (sub == 0 && rl < cnt) s_pre[(h * tr + rl) * HW + w] = make_uint2(B1, B2);
+            }
+            if (tid == 0) sh_pre_step = i2;
+        }
 
         // ---- CTA 0: measurement at beta_i (from the histograms and chunk statistics every CTA
         // left in its shared memory) and the next resampling's tables.  The serial chain that the
@@ -3237,7 +3303,8 @@ __global__ void gather_records_kernel(Pool P, const uint32_t *runs, uint32_t n, 
 
 // ------------------------------------------------------------------ launchers
 // The small-run kernel for (L, glass, variant): variant 0 = 512 threads, two
-// CTAs per SM; 1 = up to 512 threads, one per SM; 2 = up to 768, one per SM.
+// CTAs per SM; 1 = up to 512 threads, one per SM; 2 = up to 768, one per SM;
+// 3 and 4 = as 1 and 2 with 4 lanes per plane word (L = 8, precomputed draws).
 template <bool SG, uint32_t HW, uint32_t LPW>
 static void *small_kernel_v(uint32_t variant)
 {
@@ -3248,11 +3315,15 @@ static void *small_kernel_v(uint32_t variant)
 
 static void *small_kernel(uint32_t L, int sg, uint32_t variant)
 {
+    if (L == 8 && variant >= 3)
+        return sg ? small_kernel_v<true, 1, 4>(variant - 2) : small_kernel_v<false, 1, 4>(variant - 2);
     if (L == 8) return sg ? small_kernel_v<true, 1, SMALL_LPW_L8>(variant) : small_kernel_v<false, 1, SMALL_LPW_L8>(variant);
     if (L == 16)
         return sg ? small_kernel_v<true, 4, SMALL_LPW_L16>(variant) : small_kernel_v<false, 4, SMALL_LPW_L16>(variant);
     return sg ? small_kernel_v<true, 16, SMALL_LPW_L32>(variant) : small_kernel_v<false, 16, SMALL_LPW_L32>(variant);
 }
+
+constexpr uint32_t SMALL_PRE_BYTES = 96 * 1024;  // shared memory for precomputed comparison bits
 
 static cudaLaunchConfig_t small_launch_config(uint32_t n_clusters, const SmallShape &sh, cudaStream_t s,
                                               cudaLaunchAttribute *at)
@@ -3260,7 +3331,7 @@ static cudaLaunchConfig_t small_launch_config(uint32_t n_clusters, const SmallSh
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_clusters * sh.cs);
     cfg.blockDim = dim3(sh.block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = sh.smem;
     cfg.stream = s;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = sh.cs;
@@ -3271,33 +3342,48 @@ static cudaLaunchConfig_t small_launch_config(uint32_t n_clusters, const SmallSh
     return cfg;
 }
 
-// Launch shape of the small-run kernel for n runs of lattice size L.  A run's
+static int small_fit(uint32_t L, int any_glass, const SmallShape &sh)
+{
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = small_launch_config(1, sh, 0, at);
+    int fit = 0;
+    if (cudaOccupancyMaxActiveClusters(&fit, small_kernel(L, any_glass, sh.variant), &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        fit = 0;
+    }
+    return fit;
+}
+
+// floor(sqrt(R)), the same integer the kernel computes
+static uint32_t isqrt_u32(uint32_t R)
+{
+    uint32_t q = (uint32_t)std::sqrt((float)R);
+    while (q * q > R) --q;
+    while ((q + 1) * (q + 1) <= R) ++q;
+    return q;
+}
+
+// Launch shapes of the small-run kernel for n runs of lattice size L.  A run's
 // steps are a chain of cluster barriers, so a run whose CTAs share SMs with
 // another run's is slower by the sharing, and the launch lasts as long as its
-// slowest run.  The shape is therefore the largest cluster (at most 8 CTAs)
-// whose block covers a CTA's share of a run's children (R + 3 sqrt(R), beyond
-// the nearest-integer resampling's spread) in one tile and whose clusters all
-// fit the GPU at once with one CTA per SM (asked of the occupancy calculator).
-// Without such a shape: 512-thread CTAs two per SM, about two CTAs per SM over
-// all the runs, the cluster at most the tiles of the largest capacity.
+// slowest run: every shape here keeps all clusters on SMs of their own (asked
+// of the occupancy calculator), the largest cluster first (at most 8 CTAs).
+// small_shape: a block covering a CTA's equal share of R + 3 sqrt(R) + 1
+// children (beyond the nearest-integer resampling's spread); without one,
+// 512-thread CTAs two per SM, about two CTAs per SM over all the runs, the
+// cluster at most the tiles of the largest capacity.
 SmallShape small_shape(uint32_t L, int any_glass, uint32_t n_runs, uint32_t R_max, uint32_t R_cap_max)
 {
-    const uint32_t lpr = (L * L / 64) * (L == 8 ? SMALL_LPW_L8 : L == 16 ? SMALL_LPW_L16 : SMALL_LPW_L32);
-    const double R_est = (double)R_max + 3.0 * sqrt((double)R_max) + 1.0;
+    const uint32_t hw = L * L / 64;
+    const uint32_t lpr = hw * (L == 8 ? SMALL_LPW_L8 : L == 16 ? SMALL_LPW_L16 : SMALL_LPW_L32);
+    const uint32_t R_est = R_max + 3 * isqrt_u32(R_max) + 1;
     for (uint32_t cs = 8; cs >= 1; --cs) {
-        const uint32_t chunk = (uint32_t)ceil(R_est / cs);
+        const uint32_t chunk = (R_est + cs - 1) / cs;
         uint32_t block = (chunk * lpr + 31) / 32 * 32;
         block = block < 128 ? 128 : block;
         if (block > 768) break;  // smaller clusters only need larger blocks
-        const SmallShape sh = {cs, block, block <= 512 ? 1u : 2u};
-        cudaLaunchAttribute at[1];
-        cudaLaunchConfig_t cfg = small_launch_config(1, sh, 0, at);
-        int fit = 0;
-        if (cudaOccupancyMaxActiveClusters(&fit, small_kernel(L, any_glass, sh.variant), &cfg) != cudaSuccess) {
-            (void)cudaGetLastError();
-            fit = 0;
-        }
-        if (fit >= (int)n_runs) return sh;
+        const SmallShape sh = {cs, block, block <= 512 ? 1u : 2u, 0u, 0u};
+        if (small_fit(L, any_glass, sh) >= (int)n_runs) return sh;
     }
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -3305,9 +3391,33 @@ SmallShape small_shape(uint32_t L, int any_glass, uint32_t n_runs, uint32_t R_ma
         sms = 152;
     }
     const uint32_t tiles = (R_cap_max + 512 / lpr - 1) / (512 / lpr);
-    SmallShape sh = {1, 512, 0};
+    SmallShape sh = {1, 512, 0, 0, 0};
     while (sh.cs < 8 && 2 * sh.cs * n_runs <= 2u * (uint32_t)sms && 2 * sh.cs <= tiles) sh.cs *= 2;
     return sh;
+}
+
+// small_shape_ahead, for launches that cover several temperatures (L = 8): CTA 0
+// resamples and measures while the others sweep slices of (R + 3 sqrt(R) + 1) /
+// (CS - 1) children in one tile, 4 lanes per word, drawing the next
+// temperature's comparison bits while CTA 0 measures.  cs = 0 when none fits.
+SmallShape small_shape_ahead(uint32_t L, int any_glass, uint32_t n_runs, uint32_t R_max, uint32_t theta_max)
+{
+    const SmallShape none = {0, 0, 0, 0, 0};
+    if (L != 8 || theta_max == 0) return none;
+    const uint32_t hw = 1, lpr4 = 4;
+    const uint32_t R_est = R_max + 3 * isqrt_u32(R_max) + 1;
+    for (uint32_t cs = 8; cs >= 2; --cs) {
+        const uint32_t Wc = (R_est + cs - 2) / (cs - 1);
+        uint32_t block = (Wc * lpr4 + 31) / 32 * 32;
+        block = block < 128 ? 128 : block;
+        if (block > 768) break;
+        const uint32_t per_h = (block / lpr4) * hw * 8;  // bytes of one half-sweep's bits
+        uint32_t H = SMALL_PRE_BYTES / per_h;
+        H = H < 2 * theta_max ? H : 2 * theta_max;
+        const SmallShape sh = {cs, block, block <= 512 ? 3u : 4u, H, H * per_h};
+        if (small_fit(L, any_glass, sh) >= (int)n_runs) return sh;
+    }
+    return none;
 }
 
 void launch_anneal_small(const Pool &P, const uint32_t *runs, uint32_t n_runs, uint32_t L, const SmallShape &sh,
@@ -3316,7 +3426,8 @@ void launch_anneal_small(const Pool &P, const uint32_t *runs, uint32_t n_runs, u
     if (n_runs == 0 || n_steps == 0) return;
     cudaLaunchAttribute at[1];
     const cudaLaunchConfig_t cfg = small_launch_config(n_runs, sh, s, at);
-    void *args[] = {(void *)&P, (void *)&runs, (void *)&n_steps};
+    uint32_t H = sh.H;
+    void *args[] = {(void *)&P, (void *)&runs, (void *)&n_steps, (void *)&H};
     cudaLaunchKernelExC(&cfg, small_kernel(L, any_glass, sh.variant), args);
 }
 
@@ -3327,6 +3438,14 @@ void launch_gather_records(const Pool &P, const uint32_t *runs, uint32_t n_runs,
 
 cudaError_t prepare_kernels()
 {
+    for (uint32_t L : {8u, 16u, 32u})
+        for (int sg = 0; sg < 2; ++sg)
+            for (uint32_t v = 1; v <= (L == 8 ? 4u : 2u); ++v) {
+                const cudaError_t e = cudaFuncSetAttribute(small_kernel(L, sg, v),
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)SMALL_PRE_BYTES);
+                if (e != cudaSuccess) return e;
+            }
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          200 * 1024);
     if (e == cudaSuccess)
