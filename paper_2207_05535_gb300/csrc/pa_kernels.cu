@@ -2799,7 +2799,7 @@ __global__ void __launch_bounds__(NT, MINB) anneal_small_kernel(Pool P, const ui
     constexpr uint32_t LPR = HW * LPW;             // lanes per replica (divides 32)
     constexpr uint32_t TR = NT / LPR;              // replicas per tile at the largest block
     static_assert(LPR <= 32 && 32 % LPR == 0, "a replica's lanes lie in one warp");
-    constexpr bool AHEAD = HW == 1 && LPW == 4 && MINB == 1;  // the variants launched with H > 0
+    constexpr bool AHEAD = LPR == 4 && MINB == 1;  // the variants launched with H > 0 (L = 8 and 16)
     __shared__ uint32_t s_pl[TR][2 * HW];
     __shared__ __align__(16) uint32_t s_cnt[SMALL_MAX_RCAP];  // copy numbers; the measurement's terms h_n w[n]
     __shared__ uint32_t s_hE[SMALL_MAX_N + 1], s_hM[SMALL_MAX_N + 1];
@@ -3304,7 +3304,8 @@ __global__ void gather_records_kernel(Pool P, const uint32_t *runs, uint32_t n, 
 // ------------------------------------------------------------------ launchers
 // The small-run kernel for (L, glass, variant): variant 0 = 512 threads, two
 // CTAs per SM; 1 = up to 512 threads, one per SM; 2 = up to 768, one per SM;
-// 3 and 4 = as 1 and 2 with 4 lanes per plane word (L = 8, precomputed draws).
+// 3 and 4 = as 1 and 2 with 4 lanes per replica (L = 8: 4 per word; L = 16: 1 per
+// word), launched with the comparison bits drawn ahead.
 template <bool SG, uint32_t HW, uint32_t LPW>
 static void *small_kernel_v(uint32_t variant)
 {
@@ -3317,6 +3318,8 @@ static void *small_kernel(uint32_t L, int sg, uint32_t variant)
 {
     if (L == 8 && variant >= 3)
         return sg ? small_kernel_v<true, 1, 4>(variant - 2) : small_kernel_v<false, 1, 4>(variant - 2);
+    if (L == 16 && variant >= 3)
+        return sg ? small_kernel_v<true, 4, 1>(variant - 2) : small_kernel_v<false, 4, 1>(variant - 2);
     if (L == 8) return sg ? small_kernel_v<true, 1, SMALL_LPW_L8>(variant) : small_kernel_v<false, 1, SMALL_LPW_L8>(variant);
     if (L == 16)
         return sg ? small_kernel_v<true, 4, SMALL_LPW_L16>(variant) : small_kernel_v<false, 4, SMALL_LPW_L16>(variant);
@@ -3396,15 +3399,16 @@ SmallShape small_shape(uint32_t L, int any_glass, uint32_t n_runs, uint32_t R_ma
     return sh;
 }
 
-// small_shape_ahead, for launches that cover several temperatures (L = 8): CTA 0
-// resamples and measures while the others sweep slices of (R + 3 sqrt(R) + 1) /
-// (CS - 1) children in one tile, 4 lanes per word, drawing the next
-// temperature's comparison bits while CTA 0 measures.  cs = 0 when none fits.
+// small_shape_ahead, for launches that cover several temperatures (L = 8, 16):
+// CTA 0 resamples and measures while the others sweep slices of
+// (R + 3 sqrt(R) + 1) / (CS - 1) children in one tile, 4 lanes per replica,
+// drawing the next temperature's comparison bits while CTA 0 measures.  cs = 0
+// when none fits.
 SmallShape small_shape_ahead(uint32_t L, int any_glass, uint32_t n_runs, uint32_t R_max, uint32_t theta_max)
 {
     const SmallShape none = {0, 0, 0, 0, 0};
-    if (L != 8 || theta_max == 0) return none;
-    const uint32_t hw = 1, lpr4 = 4;
+    if ((L != 8 && L != 16) || theta_max == 0) return none;
+    const uint32_t hw = L * L / 64, lpr4 = 4;
     const uint32_t R_est = R_max + 3 * isqrt_u32(R_max) + 1;
     for (uint32_t cs = 8; cs >= 2; --cs) {
         const uint32_t Wc = (R_est + cs - 2) / (cs - 1);
@@ -3440,7 +3444,7 @@ cudaError_t prepare_kernels()
 {
     for (uint32_t L : {8u, 16u, 32u})
         for (int sg = 0; sg < 2; ++sg)
-            for (uint32_t v = 1; v <= (L == 8 ? 4u : 2u); ++v) {
+            for (uint32_t v = 1; v <= (L == 32 ? 2u : 4u); ++v) {
                 const cudaError_t e = cudaFuncSetAttribute(small_kernel(L, sg, v),
                                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                            (int)SMALL_PRE_BYTES);
