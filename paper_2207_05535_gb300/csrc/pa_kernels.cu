@@ -1529,19 +1529,32 @@ __device__ __forceinline__ uint32_t window(const uint32_t *Ow, int dq, uint32_t 
 
 // Neighbour masks of compact word w of colour c, read from the other plane's
 // string O; Ow = O + FP + w is the word itself.
+// NARROW (L/2 <= 31): every window lies in the words w - 1, w and w + 1, so
+// they are funnel shifts of those three.
+template <bool NARROW>
 __device__ __forceinline__ void compact_neighbours(const uint32_t *O, const uint32_t *Ow, const CompactShifts &z,
                                                    const CompactWord &g, uint32_t c, uint32_t &same, uint32_t &rot,
                                                    uint32_t &up, uint32_t &dn)
 {
-    const uint32_t o = Ow[0];
+    const uint32_t om = Ow[-1], o = Ow[0], op = Ow[1];
     same = o;
-    const uint32_t l1 = __funnelshift_l(Ow[-1], o, 1);  // bit k <- k - 1
-    const uint32_t r1 = __funnelshift_r(o, Ow[1], 1);   // bit k <- k + 1
-    const uint32_t left = (l1 & ~g.RS) | (window(Ow, z.dl, z.sl) & g.RS);   // x' - 1 within the row
-    const uint32_t right = (r1 & ~g.RE) | (window(Ow, z.dr, z.sr) & g.RE);  // x' + 1 within the row
+    const uint32_t l1 = __funnelshift_l(om, o, 1);  // bit k <- k - 1
+    const uint32_t r1 = __funnelshift_r(o, op, 1);  // bit k <- k + 1
+    uint32_t lw, rw;
+    if (NARROW) {  // offsets L/2 - 1 and L/2 in word 0, -(L/2 - 1) and -L/2 in word -1
+        lw = __funnelshift_r(o, op, z.sl);
+        rw = __funnelshift_r(om, o, z.sr);
+        up = __funnelshift_r(om, o, z.su);
+        dn = __funnelshift_r(o, op, z.sd);
+    } else {
+        lw = window(Ow, z.dl, z.sl);
+        rw = window(Ow, z.dr, z.sr);
+        up = window(Ow, z.du, z.su);
+        dn = window(Ow, z.dd, z.sd);
+    }
+    const uint32_t left = (l1 & ~g.RS) | (lw & g.RS);   // x' - 1 within the row
+    const uint32_t right = (r1 & ~g.RE) | (rw & g.RE);  // x' + 1 within the row
     rot = c == 0 ? ((left & g.EV) | (right & ~g.EV)) : ((right & g.EV) | (left & ~g.EV));
-    up = window(Ow, z.du, z.su);
-    dn = window(Ow, z.dd, z.sd);
     if (g.mU) up = (up & ~g.mU) | (bits_at(O, g.pU) & g.mU);  // the first row's row above: the last row
     if (g.mD) dn = (dn & ~g.mD) | (bits_at(O, g.pD) & g.mD);  // the last row's row below: the first row
 }
@@ -1550,7 +1563,7 @@ __device__ __forceinline__ void compact_neighbours(const uint32_t *O, const uint
 #define PA_COMPACT_MIN_BLOCKS 4  // caps registers at 64 (no spills); 1-8 % faster than 3 or 2 CTAs of 256 (measured)
 #endif
 
-template <bool SG, int MAXT>
+template <bool SG, int MAXT, bool NARROW>
 __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? PA_COMPACT_MIN_BLOCKS : 1)
     sweep_compact_kernel(Pool P, const uint32_t *group_runs, const uint32_t *tile_off, uint32_t n_group_runs,
                          SweepCfg cfg)
@@ -1613,7 +1626,8 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? PA_COMPACT_MIN_BLOCKS : 1)
         for (uint32_t c = 0; c < 2; ++c) {
             if (active) {
                 uint32_t same, rot, up, dn;
-                compact_neighbours(pl + (c ^ 1u) * AW, pl + (c ^ 1u) * AW + FP + w, z, g, c, same, rot, up, dn);
+                compact_neighbours<NARROW>(pl + (c ^ 1u) * AW, pl + (c ^ 1u) * AW + FP + w, z, g, c, same, rot, up,
+                                           dn);
                 const uint32_t S = own[c];
                 const uint32_t x1 = S ^ same ^ J[c][0], x2 = S ^ rot ^ J[c][1];
                 const uint32_t x3 = S ^ up ^ J[c][2], x4 = S ^ dn ^ J[c][3];
@@ -1643,7 +1657,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? PA_COMPACT_MIN_BLOCKS : 1)
             dst[PW + p] = padded_from_compact(pl + AW, base, pitch, Lh, p);
         }
         uint32_t same, rot, up, dn;
-        compact_neighbours(pl + AW, pl + AW + FP + w, z, g, 0, same, rot, up, dn);
+        compact_neighbours<NARROW>(pl + AW, pl + AW + FP + w, z, g, 0, same, rot, up, dn);
         const uint32_t S = own[0];
         const int32_t unsat = __popc((S ^ same ^ J[0][0]) & g.VM) + __popc((S ^ rot ^ J[0][1]) & g.VM) +
                               __popc((S ^ up ^ J[0][2]) & g.VM) + __popc((S ^ dn ^ J[0][3]) & g.VM);
@@ -3598,17 +3612,19 @@ void launch_sweep(const Pool &P, const uint32_t *group_runs, const uint32_t *til
     sweep_pow2_kernel<SG, WPT, MAXT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg)
 #define PA_SWEEP_FAST2(SG, WPT) \
     sweep_pow2_kernel_2cta<SG, WPT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, n_group_runs, cfg)
-    if (cfg.fast == 3) {  // compact rows
-        if (cfg.block <= 256)
-            any_glass ? sweep_compact_kernel<true, 256><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off,
-                                                                                      n_group_runs, cfg)
-                      : sweep_compact_kernel<false, 256><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off,
-                                                                                       n_group_runs, cfg);
+    if (cfg.fast == 3) {  // compact rows; the row pitch is at most 32 exactly when L/2 <= 31
+#define PA_SWEEP_COMPACT(MAXT, NARROW)                                                                            \
+    (any_glass ? sweep_compact_kernel<true, MAXT, NARROW><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, \
+                                                                                          n_group_runs, cfg)      \
+               : sweep_compact_kernel<false, MAXT, NARROW><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs,         \
+                                                                                           tile_off, n_group_runs, cfg))
+        if (cfg.block <= 256 && cfg.PS <= 32)
+            PA_SWEEP_COMPACT(256, true);
+        else if (cfg.block <= 256)
+            PA_SWEEP_COMPACT(256, false);
         else
-            any_glass ? sweep_compact_kernel<true, 1024><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off,
-                                                                                       n_group_runs, cfg)
-                      : sweep_compact_kernel<false, 1024><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off,
-                                                                                        n_group_runs, cfg);
+            PA_SWEEP_COMPACT(1024, false);
+#undef PA_SWEEP_COMPACT
     } else if (cfg.fast == 2) {  // padded rows: cfg.PS holds the row pitch
 #define PA_SWEEP_PAD(PT)                                                                                 \
     (any_glass ? sweep_pad_kernel<true, PT><<<grid, cfg.block, cfg.smem, s>>>(P, group_runs, tile_off, \
