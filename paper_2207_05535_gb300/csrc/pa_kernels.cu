@@ -2243,6 +2243,7 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) mea
     __shared__ Moments mom[PA_MEASURE_THREADS / 32];
     __shared__ uint32_t sh_lohi[2];
     __shared__ double sh_S, sh_logS, sh_logR;
+    __shared__ uint32_t sh_wlo[PA_MEASURE_THREADS / 32], sh_whi[PA_MEASURE_THREADS / 32];
     __shared__ uint32_t sh_last;
     const uint32_t run = runs[blockIdx.x];
     const RunDev rd = P.runs[run];
@@ -2399,23 +2400,58 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) mea
     }
     __syncthreads();
 
-    // The run's tail.  The serial chain the next resampling waits for (occupied
-    // levels, terms h_n w[n], their ascending sum S and ln S) runs on warp 1 while
-    // warp 2 takes ln R and the other warps form the moments from the histograms;
-    // then warp 0 writes the record beside the tables of floor(tau) and draw
-    // thresholds (the counters' shared memory is free once the CTAs' counts are in).
+    // The run's tail.  Every thread forms partial moments and the occupied levels
+    // over its share of the N + 1 histogram entries; then warp 1 joins the levels
+    // and forms the terms h_n w[n], their ascending sum S and ln S (the chain the
+    // next resampling waits for) while warp 2 takes ln R and warp 0 joins the
+    // moments and writes the record; then the tables of floor(tau) and draw thresholds.
     const bool prep = rd.resample != PA_MULTINOMIAL && i + 1 < rd.n_beta;
     const double lnQ_i = init ? 0.0 : st->lnQ;  // read before it is replaced by ln Q_{i+1}
-    if (wid == 1) {
-        uint32_t l = 0xffffffffu, h = 0u;
-        for (uint32_t n0 = 0; n0 < n1; n0 += 32) {
-            const uint32_t n = n0 + lane;
-            const uint32_t m = __ballot_sync(FULL, n < n1 && __ldcg(&gE[n]) != 0u);
-            if (m) {
-                l = l == 0xffffffffu ? n0 + __ffs(m) - 1 : l;
-                h = n0 + 31 - __clz(m);
+    {
+        Moments mo = {0, 0, 0, 0, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}};
+        uint32_t elo = 0xffffffffu, ehi = 0u;
+        for (uint32_t n = tid; n < n1; n += nt) {
+            const uint32_t he = __ldcg(&gE[n]), hm = __ldcg(&gM[n]);
+            if (he) {
+                elo = n < elo ? n : elo;
+                ehi = n > ehi ? n : ehi;
+                const long long e = (long long)eb + 4ll * n;
+                const unsigned long long ae = (unsigned long long)(e < 0 ? -e : e), e2 = ae * ae;  // |E| <= 2^17
+                mo.sE += (long long)he * e;
+                mo.sE2 += (long long)((unsigned long long)he * e2);
+                const I128 t3 = mul_u64(he, ae * e2);
+                add128(mo.sE3, e < 0 ? neg128(t3) : t3);
+                add128(mo.sE4, mul_128_u64(mul_u64(he, e2), e2));
+            }
+            if (hm) {
+                const long long m = 2ll * n - (long long)N;
+                const unsigned long long am = (unsigned long long)(m < 0 ? -m : m), m2 = am * am;  // |M| <= 2^16
+                mo.sAM += (long long)((unsigned long long)hm * am);
+                mo.sM2 += (long long)((unsigned long long)hm * m2);
+                add128(mo.sAM3, mul_u64(hm, am * m2));
+                add128(mo.sM4, mul_128_u64(mul_u64(hm, m2), m2));
             }
         }
+        mo.sE = warp_sum(mo.sE);
+        mo.sE2 = warp_sum(mo.sE2);
+        mo.sAM = warp_sum(mo.sAM);
+        mo.sM2 = warp_sum(mo.sM2);
+        mo.sE3 = warp_sum128(mo.sE3);
+        mo.sE4 = warp_sum128(mo.sE4);
+        mo.sAM3 = warp_sum128(mo.sAM3);
+        mo.sM4 = warp_sum128(mo.sM4);
+        elo = warp_min(elo);
+        ehi = warp_max(ehi);
+        if (lane == 0) {
+            mom[wid] = mo;
+            sh_wlo[wid] = elo;
+            sh_whi[wid] = ehi;
+        }
+    }
+    __syncthreads();
+    if (wid == 1) {
+        const uint32_t l = warp_min(lane < nw ? sh_wlo[lane] : 0xffffffffu);
+        const uint32_t h = warp_max(lane < nw ? sh_whi[lane] : 0u);
         if (lane == 0) {
             sh_lohi[0] = l;
             sh_lohi[1] = h;
@@ -2423,7 +2459,7 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) mea
         if (prep) {
             const uint32_t nb = h - l + 1;
             const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];  // exp(-4 n dbeta_{i+1})
-            double *terms = reinterpret_cast<double *>(&sh_h[0][0]);
+            double *terms = reinterpret_cast<double *>(&sh_h[0][0]);  // the counters are no longer needed
             const bool staged = nb <= MEASURE_SMEM_TERMS;
             if (staged) {
                 for (uint32_t n = lane; n < nb; n += 32) terms[n] = __dmul_rn((double)__ldcg(&gE[l + n]), wt[n]);
@@ -2441,59 +2477,8 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) mea
         }
     } else if (wid == 2) {
         if (prep && lane == 0) sh_logR = log((double)R);
-    } else {  // warps 0 and 3.. : partial moments, energy then magnetisation
-        const uint32_t mt = wid == 0 ? lane : tid - 64, nmt = nt - 64;
-        long long s1 = 0, s2 = 0;
-        I128 s3 = {0ull, 0ll}, s4 = {0ull, 0ll};
-        for (uint32_t n = mt; n < n1; n += nmt) {
-            const uint32_t he = __ldcg(&gE[n]);
-            if (he) {
-                const long long e = (long long)eb + 4ll * n;
-                const unsigned long long ae = (unsigned long long)(e < 0 ? -e : e), e2 = ae * ae;  // |E| <= 2^17
-                s1 += (long long)he * e;
-                s2 += (long long)((unsigned long long)he * e2);
-                const I128 t3 = mul_u64(he, ae * e2);
-                add128(s3, e < 0 ? neg128(t3) : t3);
-                add128(s4, mul_128_u64(mul_u64(he, e2), e2));
-            }
-        }
-        s1 = warp_sum(s1);
-        s2 = warp_sum(s2);
-        s3 = warp_sum128(s3);
-        s4 = warp_sum128(s4);
-        if (lane == 0) {
-            mom[wid].sE = s1;
-            mom[wid].sE2 = s2;
-            mom[wid].sE3 = s3;
-            mom[wid].sE4 = s4;
-        }
-        s1 = s2 = 0;
-        s3 = s4 = I128{0ull, 0ll};
-        for (uint32_t n = mt; n < n1; n += nmt) {
-            const uint32_t hm = __ldcg(&gM[n]);
-            if (hm) {
-                const long long m = 2ll * n - (long long)N;
-                const unsigned long long am = (unsigned long long)(m < 0 ? -m : m), m2 = am * am;  // |M| <= 2^16
-                s1 += (long long)((unsigned long long)hm * am);
-                s2 += (long long)((unsigned long long)hm * m2);
-                add128(s3, mul_u64(hm, am * m2));
-                add128(s4, mul_128_u64(mul_u64(hm, m2), m2));
-            }
-        }
-        s1 = warp_sum(s1);
-        s2 = warp_sum(s2);
-        s3 = warp_sum128(s3);
-        s4 = warp_sum128(s4);
-        if (lane == 0) {
-            mom[wid].sAM = s1;
-            mom[wid].sM2 = s2;
-            mom[wid].sAM3 = s3;
-            mom[wid].sM4 = s4;
-        }
-    }
-    __syncthreads();
-    if (wid == 0) {  // the warps' partial moments joined, the record
-        const bool has = lane < nw && lane != 1 && lane != 2;
+    } else if (wid == 0) {  // the warps' partial moments joined, the record
+        const bool has = lane < nw;
         const long long sE = warp_sum(has ? mom[lane].sE : 0ll), sE2 = warp_sum(has ? mom[lane].sE2 : 0ll);
         const long long sAM = warp_sum(has ? mom[lane].sAM : 0ll), sM2 = warp_sum(has ? mom[lane].sM2 : 0ll);
         const I128 z = {0ull, 0ll};
@@ -2528,7 +2513,9 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) mea
             st->R_cur = R;
             st->R_new = R;
         }
-    } else if (prep) {  // ln Q_{i+1}, E_min, and per level floor(tau) and the draw threshold, tau = R_target w[n] / S
+    }
+    __syncthreads();
+    if (prep) {  // ln Q_{i+1}, E_min, and per level floor(tau) and the draw threshold, tau = R_target w[n] / S
         const uint32_t l = sh_lohi[0], nb = sh_lohi[1] - l + 1;
         const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
         if (tid == 32) {
@@ -2541,7 +2528,7 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) mea
         const double S = sh_S;
         unsigned long long *thr = scr + scr_table_off(N);
         uint32_t *flo = reinterpret_cast<uint32_t *>(scr + scr_level_off(N));
-        for (uint32_t n = tid - 32; n < nb; n += nt - 32) {
+        for (uint32_t n = tid; n < nb; n += nt) {
             const double tau = __ddiv_rn(__dmul_rn((double)rd.R, wt[n]), S);
             const double fl = floor(tau);
             flo[n] = (uint32_t)fl;
