@@ -11,7 +11,8 @@ paper's statistics:
     partitioned into S = floor(n / M) groups of M, the group estimates are
     averaged);
   - least-squares fits of a M^-b to bias data with jackknife errors
-    (Table III);
+    (Table III), and bootstrap errors, which the paper uses for the
+    ferromagnet's bias (Sec. V.B.3);
   - the root-mean-square deviation RMSD = sqrt(bias^2 + variance) (Eq. RMSD);
   - the predicted variance of free-energy weights
     var w ~ (exp(var beta F) - 1) / M^2 (Eq. varWpred).
@@ -90,6 +91,19 @@ def jackknife(values, stat=np.mean):
     return float(full), err
 
 
+def bootstrap(values, stat=np.mean, n_boot=2000, seed=0):
+    """Bootstrap estimate and standard error of stat over the first axis: stat
+    of the full sample, and the standard deviation of stat over n_boot
+    resamples drawn with replacement (seeded, so the error is reproducible)."""
+    v = np.asarray(values)
+    n = len(v)
+    if n < 2:
+        return float(stat(v)), float("nan")
+    rng = np.random.default_rng(seed)
+    reps = np.array([stat(v[rng.integers(0, n, size=n)]) for _ in range(n_boot)])
+    return float(stat(v)), float(np.std(reps, ddof=1))
+
+
 def fit_power_law(M, bias, sigma=None):
     """Least-squares fit of |bias| = a M^-b on log-log axes (weights 1/sigma_log^2).
     Returns (a, b, sigma_b) with the standard fit error of b."""
@@ -140,12 +154,17 @@ def grouped_estimates(engine, runs, M, kind=0):
     return engine.weighted_average(runs[:S * M], M, kind)
 
 
-def bias_vs_M(engine, runs, Ms, exact_fn, obs="W_e", kind=0, steps=None, relative=False):
+def bias_vs_M(engine, runs, Ms, exact_fn, obs="W_e", kind=0, steps=None, relative=False, errors="spread",
+              n_boot=2000, seed=0):
     """Bias of a weighted estimator for each M: mean over the S groups of the
     group estimate minus the exact value, averaged in absolute value over the
     selected temperature indices.  exact_fn(beta array) -> exact values.
-    Returns rows (M, S, bias, stderr) with the standard error from the spread
-    of the groups (absolute value taken after averaging the groups)."""
+    Returns rows (M, S, bias, stderr).  The standard error: "spread", from the
+    spread of the groups' temperature-averaged biases; "bootstrap", of the bias
+    itself over resamples of the S groups (with replacement); "jackknife", of
+    the bias over the S groups left out one at a time."""
+    if errors not in ("spread", "bootstrap", "jackknife"):
+        raise ValueError("errors: spread, bootstrap or jackknife")
     rows = []
     for M in Ms:
         est = grouped_estimates(engine, runs, M, kind)
@@ -158,8 +177,14 @@ def bias_vs_M(engine, runs, Ms, exact_fn, obs="W_e", kind=0, steps=None, relativ
             diff = diff / np.abs(ex)[None, :]
         per_group = np.mean(diff, axis=1)            # bias of one group, averaged over the temperatures
         b = np.mean(np.abs(np.mean(diff, axis=0)))   # |mean bias| per temperature, averaged
-        se = float(np.std(per_group, ddof=1) / math.sqrt(len(per_group))) if len(per_group) > 1 else float("nan")
-        rows.append((int(M), int(len(per_group)), float(b), se))
+        stat = lambda d: np.mean(np.abs(np.mean(d, axis=0)))
+        if errors == "bootstrap":
+            se = bootstrap(diff, stat, n_boot=n_boot, seed=seed)[1]
+        elif errors == "jackknife":
+            se = jackknife(diff, stat)[1]
+        else:
+            se = float(np.std(per_group, ddof=1) / math.sqrt(len(per_group))) if len(per_group) > 1 else float("nan")
+        rows.append((int(M), int(len(per_group)), float(b), float(se)))
     return rows
 
 
@@ -185,6 +210,8 @@ def main(argv=None):
     ap.add_argument("--temps", type=int, default=51)
     ap.add_argument("--Ms", default="1,2,4,8,16,32,64,128")
     ap.add_argument("--window", default="0.42,0.46", help="beta range the bias is averaged over")
+    ap.add_argument("--errors", default="bootstrap", choices=["bootstrap", "jackknife", "spread"],
+                    help="standard error of the bias (the paper uses the bootstrap for the ferromagnet)")
     ap.add_argument("--fit-min-snr", type=float, default=2.0,
                     help="fit a M^-b only to the M whose bias exceeds this many standard errors (the rest is the "
                          "statistical floor of all runs together)")
@@ -206,7 +233,7 @@ def main(argv=None):
     out = {}
     for obs, key, rel in (("W_e", "e", False), ("Wvar_c", "c", True), ("W_minus_betaF", "lnZ", False)):
         rows = bias_vs_M(eng, runs, Ms, lambda b, k=key: exact_ferro(a.L, b)[k], obs=obs, steps=steps,
-                         relative=rel)
+                         relative=rel, errors=a.errors)
         use = [r for r in rows if r[2] > a.fit_min_snr * r[3]]
         fit = fit_power_law([r[0] for r in use], [r[2] for r in use], [r[3] for r in use]) if len(use) >= 3 else None
         out[obs] = {"rows": rows, "fit_a_b_sigma": fit, "fit_M": [r[0] for r in use]}

@@ -80,3 +80,52 @@ def test_analysis_on_engine_records_equals_analysis_on_oracle_records():
         diff = est["W_e"] - ex(est["beta"][0])[None, :]
         assert bias == pytest.approx(np.mean(np.abs(diff.mean(axis=0))), rel=1e-10, abs=1e-14)
         assert S == 48 // M
+
+
+def test_bootstrap_standard_error():
+    """The bootstrap standard error of a sample mean approaches the exact
+    sqrt(var / n) (population variance of the sample) as resamples grow; it
+    is reproducible with its seed and zero for a constant sample."""
+    rng = np.random.default_rng(5)
+    x = rng.normal(2.0, 3.0, size=400)
+    m, se = A.bootstrap(x, n_boot=8000, seed=1)
+    assert m == pytest.approx(x.mean())
+    assert se == pytest.approx(x.std(ddof=0) / math.sqrt(len(x)), rel=0.05)
+    assert A.bootstrap(x, n_boot=500, seed=7) == A.bootstrap(x, n_boot=500, seed=7)
+    assert A.bootstrap(np.full(30, 1.5), n_boot=200)[1] == 0.0
+    # a statistic over rows of a 2-D sample (as bias_vs_M resamples groups)
+    y = rng.normal(size=(300, 4))
+    _, se2 = A.bootstrap(y, lambda d: d.mean(axis=0)[0], n_boot=8000, seed=2)
+    assert se2 == pytest.approx(y[:, 0].std(ddof=0) / math.sqrt(300), rel=0.05)
+
+
+class _GroupedRecords:
+    """Stands in for an engine: weighted_average returns fixed group estimates."""
+
+    def __init__(self, est):
+        self.est = est
+
+    def weighted_average(self, runs, M, kind):
+        return self.est[M]
+
+
+def test_bias_vs_M_error_kinds():
+    rng = np.random.default_rng(11)
+    beta = np.array([0.40, 0.42, 0.44])
+    est = {}
+    for M, S in ((1, 64), (4, 16)):
+        a = np.zeros((S, 3), dtype=[("beta", "f8"), ("W_e", "f8")])
+        a["beta"] = beta
+        a["W_e"] = 0.1 / M + rng.normal(0.0, 0.05, size=(S, 3))
+        est[M] = a
+    eng = _GroupedRecords(est)
+    ex = lambda b: np.zeros_like(b)
+    spread = A.bias_vs_M(eng, np.arange(64), [1, 4], ex)
+    boot = A.bias_vs_M(eng, np.arange(64), [1, 4], ex, errors="bootstrap", n_boot=4000)
+    jack = A.bias_vs_M(eng, np.arange(64), [1, 4], ex, errors="jackknife")
+    for r_s, r_b, r_j in zip(spread, boot, jack):
+        assert r_s[:3] == r_b[:3] == r_j[:3]              # same M, S and bias
+        assert r_b[3] == pytest.approx(r_j[3], rel=0.25)  # two estimates of one standard error
+        assert r_b[3] > 0 and r_s[3] > 0
+    with pytest.raises(ValueError):
+        A.bias_vs_M(eng, np.arange(64), [1], ex, errors="median")
