@@ -159,10 +159,11 @@ def bias_vs_M(engine, runs, Ms, exact_fn, obs="W_e", kind=0, steps=None, relativ
     """Bias of a weighted estimator for each M: mean over the S groups of the
     group estimate minus the exact value, averaged in absolute value over the
     selected temperature indices.  exact_fn(beta array) -> exact values.
-    Returns rows (M, S, bias, stderr).  The standard error: "spread", from the
-    spread of the groups' temperature-averaged biases; "bootstrap", of the bias
-    itself over resamples of the S groups (with replacement); "jackknife", of
-    the bias over the S groups left out one at a time."""
+    Returns rows (M, S, bias, stderr); stderr is the standard error of the
+    signed bias averaged over the groups and temperatures: "spread", from the
+    spread of the groups' temperature-averaged biases; "bootstrap", over
+    resamples of the S groups (with replacement); "jackknife", over the S groups
+    left out one at a time (equal to the spread's for this mean)."""
     if errors not in ("spread", "bootstrap", "jackknife"):
         raise ValueError("errors: spread, bootstrap or jackknife")
     rows = []
@@ -177,7 +178,7 @@ def bias_vs_M(engine, runs, Ms, exact_fn, obs="W_e", kind=0, steps=None, relativ
             diff = diff / np.abs(ex)[None, :]
         per_group = np.mean(diff, axis=1)            # bias of one group, averaged over the temperatures
         b = np.mean(np.abs(np.mean(diff, axis=0)))   # |mean bias| per temperature, averaged
-        stat = lambda d: np.mean(np.abs(np.mean(d, axis=0)))
+        stat = lambda d: float(np.mean(d))
         if errors == "bootstrap":
             se = bootstrap(diff, stat, n_boot=n_boot, seed=seed)[1]
         elif errors == "jackknife":

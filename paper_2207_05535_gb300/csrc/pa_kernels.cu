@@ -2626,7 +2626,7 @@ __global__ void __launch_bounds__(128) wavg_step_kernel(const pa_step_record *re
                                                         uint32_t n_groups, uint32_t M, uint32_t n_steps, uint32_t N,
                                                         pa_wavg *out, const double *w)
 {
-    const uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), g = blockIdx.y, lane = threadIdx.x & 31;
+    const uint32_t i = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5), g = blockIdx.x, lane = threadIdx.x & 31;
     if (i >= n_steps) return;  // warp-uniform
     const unsigned long long *off = rec_off + (uint64_t)g * M;
     const double *li = w + ((uint64_t)g * n_steps + i) * M;
@@ -2723,14 +2723,14 @@ __global__ void __launch_bounds__(128) wavg_step_kernel(const pa_step_record *re
 __global__ void __launch_bounds__(128) wavg_finish_kernel(uint32_t n_groups, uint32_t M, uint32_t n_steps,
                                                           uint32_t N, pa_wavg *out, double *w)
 {
-    const uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), g = blockIdx.y, lane = threadIdx.x & 31;
+    const uint32_t i = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5), g = blockIdx.x, lane = threadIdx.x & 31;
     if (i < n_steps) {
         double *li = w + ((uint64_t)g * n_steps + i) * M;
         double lmax, z;
         weight_norm(li, M, lane, lmax, z);
         for (uint32_t m = lane; m < M; m += 32) li[m] = exp(li[m] - lmax) / z;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.y == 0 && threadIdx.x == 0) {
         pa_wavg *og = out + (uint64_t)g * n_steps;
         double WF = (double)N * log(2.0);
         for (uint32_t k = 0; k < n_steps; ++k) {
@@ -2745,7 +2745,7 @@ __global__ void wavg_q_kernel(const pa_step_record *recs, const unsigned long lo
                               const uint32_t *qhp, const uint32_t *qhw, const unsigned long long *qh_off, uint32_t M,
                               uint32_t n_steps, uint32_t N, const double *w, double *Pq, double *Pqp, double *Pqw)
 {
-    const uint32_t i = blockIdx.x, g = blockIdx.y;
+    const uint32_t i = blockIdx.y, g = blockIdx.x;
     const double *wi = w + ((uint64_t)g * n_steps + i) * M;
     const unsigned long long *ro = rec_off + (uint64_t)g * M, *qo = qh_off + (uint64_t)g * M;
     for (uint32_t d = threadIdx.x; d <= N; d += blockDim.x) {
@@ -3672,11 +3672,12 @@ void launch_wavg_wang(const pa_step_record *recs, const unsigned long long *rec_
 {
     const uint64_t nGM = (uint64_t)n_groups * M;
     wavg_lambda_kernel<<<(unsigned)((32 * nGM + 127) / 128), 128, 0, s>>>(recs, rec_off, n_groups, M, n_steps, kind, w);
-    const dim3 grid((n_steps + 3) / 4, n_groups);  // one warp per (temperature, group)
+    // groups on x (up to 2^31 - 1 of them), temperatures on y
+    const dim3 grid(n_groups, (n_steps + 3) / 4);  // one warp per (group, temperature)
     wavg_step_kernel<<<grid, 128, 0, s>>>(recs, rec_off, n_groups, M, n_steps, N, out, w);
     wavg_finish_kernel<<<grid, 128, 0, s>>>(n_groups, M, n_steps, N, out, w);
     if (Pq || Pqp || Pqw) {
-        dim3 grid(n_steps, n_groups);
+        dim3 grid(n_groups, n_steps);
         wavg_q_kernel<<<grid, 256, 0, s>>>(recs, rec_off, qh, qhp, qhw, qh_off, M, n_steps, N, w, Pq, Pqp, Pqw);
     }
 }

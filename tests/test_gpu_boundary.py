@@ -147,3 +147,19 @@ def test_cancelled_job_leaves_the_others_unchanged():
             assert got.tobytes() == alone[k].tobytes(), k
     finally:
         _lib.pa_destroy(h)
+
+
+def test_weighted_average_beyond_65535_groups():
+    """Groups run along the grid's x dimension: 65,600 groups of one run each
+    (more than a grid's y dimension holds).  With M = 1 every weight is 1, so a
+    group's W[e] is its run's own mean energy per site at each temperature."""
+    n = 65600
+    descs = [W.RunDesc(4, W.FERRO, 4, 1, W.schedule(0.5, 3), seed=5, run_id=r) for r in range(n)]
+    with _lib.Engine(descs) as eng:
+        eng.run_to_end()
+        est = eng.weighted_average(np.arange(n, dtype=np.uint32), 1)
+        assert est.shape == (n, 3)
+        for k in (0, 1, 65534, 65535, 65536, n - 1):
+            rec = eng.records(k)
+            e = rec["sumE"].astype(np.float64) / (16.0 * rec["R"].astype(np.float64))
+            assert np.allclose(est["W_e"][k], e, rtol=1e-12, atol=0.0), k
