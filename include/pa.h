@@ -171,15 +171,19 @@ pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream,
 
 /* pa_create with options (bit flags):
  *   PA_CREATE_GENERIC_SWEEP keeps every lattice size on the general byte-plane
- *     sweep kernel instead of the bit-sliced kernel used for L = 8, 16, ..., 256
- *     (both give identical results; the option exists to check that);
- *   PA_CREATE_NO_AUTOTUNE skips timing the bit-sliced kernel's launch shapes on
- *     the first anneal step and uses the default shape;
+ *     sweep kernel instead of the bit-sliced kernels (rows tiling 32-bit words
+ *     when L/2 is a power of two, otherwise rows repacked without padding or
+ *     padded rows, whichever the autotuner finds faster); all give identical
+ *     results, and the option exists to check that;
+ *   PA_CREATE_NO_AUTOTUNE skips timing the bit-sliced kernels' launch shapes on
+ *     the first anneal steps and uses the default shape;
  *   PA_CREATE_SEPARATE_KERNELS keeps small runs on the per-stage kernels.
  * Without it, a small run (L = 8, 16 or 32, nearest-integer resampling, no
  * overlaps, R_cap <= 8192) is annealed by one launch per step: a cluster of
  * CTAs that resamples, sweeps and measures it (when every resident run is
- * small, pa_anneal_step(n) is one launch per lattice size for all n steps).
+ * small, pa_anneal_step(n) is one launch per lattice size for all n steps, and
+ * at L = 8 and 16 the cluster draws each next temperature's random numbers
+ * while it measures the current one).
  * Both paths give identical results; PA_CREATE_GENERIC_SWEEP implies the
  * per-stage kernels.
  * Without it, the first anneal steps of a lattice size time every candidate shape

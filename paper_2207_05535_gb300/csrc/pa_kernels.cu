@@ -11,10 +11,16 @@
 //   resample_multinomial_kernel
 //                    multinomial resampling, one CTA per run (level histogram,
 //                    Q_i of Eq. QBoltz, R draws, scan, parent map)
-//   sweep_pow2_kernel / sweep_pad_kernel / sweep_kernel
+//   sweep_pow2_kernel / sweep_compact_kernel / sweep_pad_kernel / sweep_kernel
 //                    per lattice size: each replica is gathered from its parent
 //                    (the resampling copy) and swept theta times with Philox
-//                    thresholds (Sec. V.A.1), bit-sliced where L/2 allows
+//                    thresholds (Sec. V.A.1), bit-sliced: rows tiling words (L/2 a
+//                    power of two), rows repacked without padding in shared memory,
+//                    or padded rows; byte planes as the cross-check
+//   anneal_small_kernel
+//                    small runs (L = 8, 16, 32, nearest-integer, no overlaps): one
+//                    thread-block cluster per run resamples, sweeps and measures,
+//                    several temperatures per launch
 //   dos_sample_kernel
 //                    theta = infinity runs (Sec. V.B): fresh energies from the exact
 //                    distribution instead of sweeps
