@@ -96,9 +96,9 @@ def work_units(d, R):
 # capture of the kernel, valid only for the kernel source it was taken on.
 # The uneven batch: the four lattice-size groups' sweep launches of one temperature
 # (temperature 7, full size, one ncu pass), read + write summed: bytes per step.
-TRAFFIC = [{"kernel": "sweep", "workload": "uneven_4096", "source_sha256_16": "589e779d62c0a98e",
-            "bytes_per_launch": 80.975e9,
-            "captured": "L=128: 15.04 + 40.82 GB, L=64: 7.15 + 10.86 GB, L=32: 2.49 + 3.00 GB, L=16: 0.79 + 0.82 GB "
+TRAFFIC = [{"kernel": "sweep", "workload": "uneven_4096", "source_sha256_16": "009194d71dfeaa51",
+            "bytes_per_launch": 81.124e9,
+            "captured": "L=128: 15.06 + 40.83 GB, L=64: 7.15 + 10.86 GB, L=32: 2.53 + 3.06 GB, L=16: 0.80 + 0.83 GB "
                         "(dram__bytes_read.sum + dram__bytes_write.sum)"}]
 MULADD_LANES_PER_SM = 64
 

@@ -179,8 +179,10 @@ pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream,
  *     the first anneal steps and uses the default shape;
  *   PA_CREATE_SEPARATE_KERNELS keeps small runs on the per-stage kernels.
  * Without it, a small run (L = 8, 16 or 32, nearest-integer resampling, no
- * overlaps, R_cap <= 8192) is annealed by one launch per step: a cluster of
- * CTAs that resamples, sweeps and measures it (when every resident run is
+ * overlaps, R_cap <= 8192) is annealed by one launch per step when its lattice
+ * size's runs can each have a cluster of CTAs on SMs of their own (few runs,
+ * populations of a few thousand at most): the cluster resamples, sweeps and
+ * measures it (when every resident run is
  * small, pa_anneal_step(n) is one launch per lattice size for all n steps, and
  * at L = 8 and 16 the cluster draws each next temperature's random numbers
  * while it measures the current one).

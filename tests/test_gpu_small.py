@@ -69,8 +69,9 @@ def test_small_path_equals_separate_kernels(use_graph):
 
 def test_small_runs_beside_other_runs_and_cluster_sizes():
     """Small runs share every tick with runs on the per-stage kernels (graph
-    replays); a run's result does not depend on its cluster size (one run
-    alone gets 8 CTAs, 200 runs get 1)."""
+    replays); a run's result does not depend on the path or the cluster size
+    (one run alone gets a cluster of 8 CTAs; 200 runs, too many for a cluster
+    each, go to the per-stage kernels)."""
     small = _small_mix()
     big = [W.RunDesc(10, W.EA_PMJ, 200, 2, W.schedule(2.0, 8), seed=2, run_id=10, disorder_id=1,
                      overlap=W.Q_SHIFT),
@@ -92,8 +93,10 @@ def test_small_runs_beside_other_runs_and_cluster_sizes():
 
 
 def test_small_run_near_capacity_and_overflow():
-    """R_cap = 8192, the largest small population; then a capacity overflow on
-    the small path stops the run with its status, like the per-stage path."""
+    """R_cap = 8192, the largest population the small path accepts (this one
+    gets no launch shape that keeps its cluster's CTAs to one tile each, so the
+    engine anneals it per stage); then a capacity overflow on the small path
+    stops the run with its status, like the per-stage path."""
     d = [W.RunDesc(16, W.EA_PMJ, 7600, 1, W.schedule(2.0, 5), seed=3, run_id=0, disorder_id=2, R_cap=8192)]
     ora = oracle_runs(d)
     with _lib.Engine(d) as eng:
