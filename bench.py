@@ -449,12 +449,16 @@ def main():
                 "frac": ach / hbm_peak, "traffic": traffic, "bytes_per_step": nbytes, "ms_per_step": ms_,
                 "basis": basis + f"; peak = HBM copy bandwidth from MEASURED_PEAKS.json ({pk_kind})"}
 
-    roof_meas = hbm_roof("measure_kernel", "measure", meas_bytes, measured_traffic("measure", wl),
-                         "12 B read per measured replica (E, M, family)")
+    # small runs are measured inside their own step kernel (anneal_small_kernel);
+    # measure_kernel then runs only at beta_0
+    roof_meas = None if small else hbm_roof("measure_kernel", "measure", meas_bytes,
+                                                      measured_traffic("measure", wl),
+                                                      "12 B read per measured replica (E, M, family)")
     roof_res = hbm_roof("resample_counts_kernel + resample_parents_kernel", "resample", res_bytes, None,
                         "per parent: E read, copy number written and read back (12 B); per child: its parent "
                         "index written (4 B)")
-    dominant = max(("sweep", "measure", "resample", "small"), key=lambda k_: kt_tot.get(k_, (0.0, 0))[0])
+    dominant = max(("sweep", "measure", "resample", "small") if roof_meas else ("sweep", "resample", "small"),
+                   key=lambda k_: kt_tot.get(k_, (0.0, 0))[0])
     dominant = "sweep" if dominant == "small" else dominant
     roofline = {"sweep": sweep_roof, "measure": roof_meas, "resample": roof_res}[dominant] or sweep_roof
     # overlap kernels (a10): HBM-bound; algorithmic bytes = both replicas' colour planes per pair

@@ -414,7 +414,7 @@ pa_status alloc_pools(pa_engine *e, const pa_server_config &c)
     PA_TRY(dalloc(e, &e->d_thr, 2 * c.record_capacity));
     PA_TRY(dalloc(e, &e->d_wtoff, c.record_capacity));
     PA_TRY(dalloc(e, &e->d_wt, c.table_doubles));
-    e->meta_cap = 16ull * e->S + 3ull * 128 + 1024;
+    e->meta_cap = 20ull * e->S + 3ull * 128 + 1024;  // every work list of rebuild() (up to 16 per run slot)
     PA_TRY(dalloc(e, &e->d_meta, e->meta_cap));
     PA_CUDA(cudaMemsetAsync(e->P.status, 0, sizeof(uint32_t), e->stream));
     e->P.runs = e->d_runs;

@@ -2241,15 +2241,172 @@ constexpr uint32_t MEASURE_SMEM_BINS = 4097;  // L <= 64: counts in shared memor
 constexpr uint32_t MEASURE_BATCH = 4;         // rows of 32 replicas a warp loads at once
 constexpr uint32_t MEASURE_SMEM_TERMS = MEASURE_SMEM_BINS;  // doubles that fit in the counters' space
 
+// The shared memory of a run's measurement tail (CTAs of up to 1024 threads).
+struct TailSmem {
+    Moments mom[32];
+    uint32_t wlo[32], whi[32], lohi[2];
+    double S, logS, logR;
+};
+
+// The tail of a run's measurement at beta_i, by the one CTA that finishes the run
+// once every CTA's counts are in the run's histograms gE, gM (levels from the
+// energy base eb) and the family statistics are joined in *fam: the moments, the
+// step record, and for a nearest-integer run with a next temperature that
+// resampling's E_min, ln Q_{i+1} and per-level tables; the histograms are left
+// cleared.  terms: shared memory for n_terms doubles (the terms h_n w[n]).
+// Needs at least three warps.
+__device__ void run_tail(const Pool &P, const RunDev &rd, RunState *st, uint32_t i, int init, uint32_t R, int32_t eb,
+                         uint32_t *gE, uint32_t *gM, unsigned long long *scr, const FamPart *fam, double *terms,
+                         uint32_t n_terms, TailSmem &ts)
+{
+    // The run's tail.  Every thread forms partial moments and the occupied levels
+    // over its share of the N + 1 histogram entries; then warp 1 joins the levels
+    // and forms the terms h_n w[n], their ascending sum S and ln S (the chain the
+    // next resampling waits for) while warp 2 takes ln R and warp 0 joins the
+    // moments and writes the record; then the tables of floor(tau) and draw thresholds.
+    const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31u, wid = tid >> 5, nw = nt >> 5;
+    const uint32_t N = rd.N, n1 = N + 1;
+    const bool prep = rd.resample != PA_MULTINOMIAL && i + 1 < rd.n_beta;
+    const double lnQ_i = init ? 0.0 : st->lnQ;  // read before it is replaced by ln Q_{i+1}
+    {
+        Moments mo = {0, 0, 0, 0, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}};
+        uint32_t elo = 0xffffffffu, ehi = 0u;
+        for (uint32_t n = tid; n < n1; n += nt) {
+            const uint32_t he = __ldcg(&gE[n]), hm = __ldcg(&gM[n]);
+            if (he) {
+                elo = n < elo ? n : elo;
+                ehi = n > ehi ? n : ehi;
+                const long long e = (long long)eb + 4ll * n;
+                const unsigned long long ae = (unsigned long long)(e < 0 ? -e : e), e2 = ae * ae;  // |E| <= 2^17
+                mo.sE += (long long)he * e;
+                mo.sE2 += (long long)((unsigned long long)he * e2);
+                const I128 t3 = mul_u64(he, ae * e2);
+                add128(mo.sE3, e < 0 ? neg128(t3) : t3);
+                add128(mo.sE4, mul_128_u64(mul_u64(he, e2), e2));
+            }
+            if (hm) {
+                const long long m = 2ll * n - (long long)N;
+                const unsigned long long am = (unsigned long long)(m < 0 ? -m : m), m2 = am * am;  // |M| <= 2^16
+                mo.sAM += (long long)((unsigned long long)hm * am);
+                mo.sM2 += (long long)((unsigned long long)hm * m2);
+                add128(mo.sAM3, mul_u64(hm, am * m2));
+                add128(mo.sM4, mul_128_u64(mul_u64(hm, m2), m2));
+            }
+        }
+        mo.sE = warp_sum(mo.sE);
+        mo.sE2 = warp_sum(mo.sE2);
+        mo.sAM = warp_sum(mo.sAM);
+        mo.sM2 = warp_sum(mo.sM2);
+        mo.sE3 = warp_sum128(mo.sE3);
+        mo.sE4 = warp_sum128(mo.sE4);
+        mo.sAM3 = warp_sum128(mo.sAM3);
+        mo.sM4 = warp_sum128(mo.sM4);
+        elo = warp_min(elo);
+        ehi = warp_max(ehi);
+        if (lane == 0) {
+            ts.mom[wid] = mo;
+            ts.wlo[wid] = elo;
+            ts.whi[wid] = ehi;
+        }
+    }
+    __syncthreads();
+    if (wid == 1) {
+        const uint32_t l = warp_min(lane < nw ? ts.wlo[lane] : 0xffffffffu);
+        const uint32_t h = warp_max(lane < nw ? ts.whi[lane] : 0u);
+        if (lane == 0) {
+            ts.lohi[0] = l;
+            ts.lohi[1] = h;
+        }
+        if (prep) {
+            const uint32_t nb = h - l + 1;
+            const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];  // exp(-4 n dbeta_{i+1})
+            const bool staged = nb <= n_terms;
+            if (staged) {
+                for (uint32_t n = lane; n < nb; n += 32) terms[n] = __dmul_rn((double)__ldcg(&gE[l + n]), wt[n]);
+                __syncwarp();
+            }
+            if (lane == 0) {
+                double S = 0.0;
+                if (staged)
+                    for (uint32_t n = 0; n < nb; ++n) S = __dadd_rn(S, terms[n]);
+                else
+                    for (uint32_t n = 0; n < nb; ++n) S = __dadd_rn(S, __dmul_rn((double)__ldcg(&gE[l + n]), wt[n]));
+                ts.S = S;
+                ts.logS = log(S);
+            }
+        }
+    } else if (wid == 2) {
+        if (prep && lane == 0) ts.logR = log((double)R);
+    } else if (wid == 0) {  // the warps' partial moments joined, the record
+        const bool has = lane < nw;
+        const long long sE = warp_sum(has ? ts.mom[lane].sE : 0ll), sE2 = warp_sum(has ? ts.mom[lane].sE2 : 0ll);
+        const long long sAM = warp_sum(has ? ts.mom[lane].sAM : 0ll), sM2 = warp_sum(has ? ts.mom[lane].sM2 : 0ll);
+        const I128 z = {0ull, 0ll};
+        const I128 sE3 = warp_sum128(has ? ts.mom[lane].sE3 : z), sE4 = warp_sum128(has ? ts.mom[lane].sE4 : z);
+        const I128 sAM3 = warp_sum128(has ? ts.mom[lane].sAM3 : z), sM4 = warp_sum128(has ? ts.mom[lane].sM4 : z);
+        if (lane == 0) {
+            const FamPart f = *fam;
+            pa_step_record *rec = P.rec + rd.rec_off + i;
+            rec->beta = P.beta[rd.beta_off + i];
+            rec->lnQ = lnQ_i;
+            rec->minus_betaF = init ? rd.ln2N : P.rec[rd.rec_off + i - 1].minus_betaF + lnQ_i;
+            rec->sumE = sE;
+            rec->sumE2 = sE2;
+            rec->sumAbsM = sAM;
+            rec->sumM2 = sM2;
+            rec->sum_c2 = f.c2;
+            rec->sumE3[0] = sE3.lo;
+            rec->sumE3[1] = (unsigned long long)sE3.hi;
+            rec->sumE4[0] = sE4.lo;
+            rec->sumE4[1] = (unsigned long long)sE4.hi;
+            rec->sumAbsM3[0] = sAM3.lo;
+            rec->sumAbsM3[1] = (unsigned long long)sAM3.hi;
+            rec->sumM4[0] = sM4.lo;
+            rec->sumM4[1] = (unsigned long long)sM4.hi;
+            rec->R = R;
+            rec->R_target = rd.R;
+            rec->n_fam = f.nfam;
+            rec->max_fam = f.cmax;
+            rec->N = rd.N;
+            rec->status = 0;
+            st->step = i;
+            st->R_cur = R;
+            st->R_new = R;
+        }
+    }
+    __syncthreads();
+    if (prep) {  // ln Q_{i+1}, E_min, and per level floor(tau) and the draw threshold, tau = R_target w[n] / S
+        const uint32_t l = ts.lohi[0], nb = ts.lohi[1] - l + 1;
+        const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
+        if (tid == 32) {
+            const int32_t Emin = eb + 4 * (int32_t)l;
+            const double dbeta = P.beta[rd.beta_off + i + 1] - P.beta[rd.beta_off + i];
+            st->lnQ = (-dbeta) * (double)Emin + ts.logS - ts.logR;
+            st->Emin = Emin;
+            st->n_levels = nb;
+        }
+        const double S = ts.S;
+        unsigned long long *thr = scr + scr_table_off(N);
+        uint32_t *flo = reinterpret_cast<uint32_t *>(scr + scr_level_off(N));
+        for (uint32_t n = tid; n < nb; n += nt) {
+            const double tau = __ddiv_rn(__dmul_rn((double)rd.R, wt[n]), S);
+            const double fl = floor(tau);
+            flo[n] = (uint32_t)fl;
+            thr[n] = (unsigned long long)ceil(__dmul_rn(__dsub_rn(tau, fl), 4294967296.0));
+        }
+    }
+    for (uint32_t n = tid; n < n1; n += nt) {  // cleared for the next step (every read of them is done)
+        gE[n] = 0u;
+        gM[n] = 0u;
+    }
+}
+
 __global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) measure_kernel(Pool P, const uint32_t *runs,
                                                                                            int init)
 {
     __shared__ __align__(16) uint32_t sh_h[2][MEASURE_SMEM_BINS];
     __shared__ FamPart part[32];
-    __shared__ Moments mom[PA_MEASURE_THREADS / 32];
-    __shared__ uint32_t sh_lohi[2];
-    __shared__ double sh_S, sh_logS, sh_logR;
-    __shared__ uint32_t sh_wlo[PA_MEASURE_THREADS / 32], sh_whi[PA_MEASURE_THREADS / 32];
+    __shared__ TailSmem ts;
     __shared__ uint32_t sh_last;
     const uint32_t run = runs[blockIdx.x];
     const RunDev rd = P.runs[run];
@@ -2406,145 +2563,8 @@ __global__ void __launch_bounds__(PA_MEASURE_THREADS, PA_MEASURE_MIN_BLOCKS) mea
     }
     __syncthreads();
 
-    // The run's tail.  Every thread forms partial moments and the occupied levels
-    // over its share of the N + 1 histogram entries; then warp 1 joins the levels
-    // and forms the terms h_n w[n], their ascending sum S and ln S (the chain the
-    // next resampling waits for) while warp 2 takes ln R and warp 0 joins the
-    // moments and writes the record; then the tables of floor(tau) and draw thresholds.
-    const bool prep = rd.resample != PA_MULTINOMIAL && i + 1 < rd.n_beta;
-    const double lnQ_i = init ? 0.0 : st->lnQ;  // read before it is replaced by ln Q_{i+1}
-    {
-        Moments mo = {0, 0, 0, 0, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}, {0ull, 0ll}};
-        uint32_t elo = 0xffffffffu, ehi = 0u;
-        for (uint32_t n = tid; n < n1; n += nt) {
-            const uint32_t he = __ldcg(&gE[n]), hm = __ldcg(&gM[n]);
-            if (he) {
-                elo = n < elo ? n : elo;
-                ehi = n > ehi ? n : ehi;
-                const long long e = (long long)eb + 4ll * n;
-                const unsigned long long ae = (unsigned long long)(e < 0 ? -e : e), e2 = ae * ae;  // |E| <= 2^17
-                mo.sE += (long long)he * e;
-                mo.sE2 += (long long)((unsigned long long)he * e2);
-                const I128 t3 = mul_u64(he, ae * e2);
-                add128(mo.sE3, e < 0 ? neg128(t3) : t3);
-                add128(mo.sE4, mul_128_u64(mul_u64(he, e2), e2));
-            }
-            if (hm) {
-                const long long m = 2ll * n - (long long)N;
-                const unsigned long long am = (unsigned long long)(m < 0 ? -m : m), m2 = am * am;  // |M| <= 2^16
-                mo.sAM += (long long)((unsigned long long)hm * am);
-                mo.sM2 += (long long)((unsigned long long)hm * m2);
-                add128(mo.sAM3, mul_u64(hm, am * m2));
-                add128(mo.sM4, mul_128_u64(mul_u64(hm, m2), m2));
-            }
-        }
-        mo.sE = warp_sum(mo.sE);
-        mo.sE2 = warp_sum(mo.sE2);
-        mo.sAM = warp_sum(mo.sAM);
-        mo.sM2 = warp_sum(mo.sM2);
-        mo.sE3 = warp_sum128(mo.sE3);
-        mo.sE4 = warp_sum128(mo.sE4);
-        mo.sAM3 = warp_sum128(mo.sAM3);
-        mo.sM4 = warp_sum128(mo.sM4);
-        elo = warp_min(elo);
-        ehi = warp_max(ehi);
-        if (lane == 0) {
-            mom[wid] = mo;
-            sh_wlo[wid] = elo;
-            sh_whi[wid] = ehi;
-        }
-    }
-    __syncthreads();
-    if (wid == 1) {
-        const uint32_t l = warp_min(lane < nw ? sh_wlo[lane] : 0xffffffffu);
-        const uint32_t h = warp_max(lane < nw ? sh_whi[lane] : 0u);
-        if (lane == 0) {
-            sh_lohi[0] = l;
-            sh_lohi[1] = h;
-        }
-        if (prep) {
-            const uint32_t nb = h - l + 1;
-            const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];  // exp(-4 n dbeta_{i+1})
-            double *terms = reinterpret_cast<double *>(&sh_h[0][0]);  // the counters are no longer needed
-            const bool staged = nb <= MEASURE_SMEM_TERMS;
-            if (staged) {
-                for (uint32_t n = lane; n < nb; n += 32) terms[n] = __dmul_rn((double)__ldcg(&gE[l + n]), wt[n]);
-                __syncwarp();
-            }
-            if (lane == 0) {
-                double S = 0.0;
-                if (staged)
-                    for (uint32_t n = 0; n < nb; ++n) S = __dadd_rn(S, terms[n]);
-                else
-                    for (uint32_t n = 0; n < nb; ++n) S = __dadd_rn(S, __dmul_rn((double)__ldcg(&gE[l + n]), wt[n]));
-                sh_S = S;
-                sh_logS = log(S);
-            }
-        }
-    } else if (wid == 2) {
-        if (prep && lane == 0) sh_logR = log((double)R);
-    } else if (wid == 0) {  // the warps' partial moments joined, the record
-        const bool has = lane < nw;
-        const long long sE = warp_sum(has ? mom[lane].sE : 0ll), sE2 = warp_sum(has ? mom[lane].sE2 : 0ll);
-        const long long sAM = warp_sum(has ? mom[lane].sAM : 0ll), sM2 = warp_sum(has ? mom[lane].sM2 : 0ll);
-        const I128 z = {0ull, 0ll};
-        const I128 sE3 = warp_sum128(has ? mom[lane].sE3 : z), sE4 = warp_sum128(has ? mom[lane].sE4 : z);
-        const I128 sAM3 = warp_sum128(has ? mom[lane].sAM3 : z), sM4 = warp_sum128(has ? mom[lane].sM4 : z);
-        if (lane == 0) {
-            const FamPart f = part[0];
-            pa_step_record *rec = P.rec + rd.rec_off + i;
-            rec->beta = P.beta[rd.beta_off + i];
-            rec->lnQ = lnQ_i;
-            rec->minus_betaF = init ? rd.ln2N : P.rec[rd.rec_off + i - 1].minus_betaF + lnQ_i;
-            rec->sumE = sE;
-            rec->sumE2 = sE2;
-            rec->sumAbsM = sAM;
-            rec->sumM2 = sM2;
-            rec->sum_c2 = f.c2;
-            rec->sumE3[0] = sE3.lo;
-            rec->sumE3[1] = (unsigned long long)sE3.hi;
-            rec->sumE4[0] = sE4.lo;
-            rec->sumE4[1] = (unsigned long long)sE4.hi;
-            rec->sumAbsM3[0] = sAM3.lo;
-            rec->sumAbsM3[1] = (unsigned long long)sAM3.hi;
-            rec->sumM4[0] = sM4.lo;
-            rec->sumM4[1] = (unsigned long long)sM4.hi;
-            rec->R = R;
-            rec->R_target = rd.R;
-            rec->n_fam = f.nfam;
-            rec->max_fam = f.cmax;
-            rec->N = rd.N;
-            rec->status = 0;
-            st->step = i;
-            st->R_cur = R;
-            st->R_new = R;
-        }
-    }
-    __syncthreads();
-    if (prep) {  // ln Q_{i+1}, E_min, and per level floor(tau) and the draw threshold, tau = R_target w[n] / S
-        const uint32_t l = sh_lohi[0], nb = sh_lohi[1] - l + 1;
-        const double *wt = P.wt + P.wtoff[rd.wt_off + i + 1];
-        if (tid == 32) {
-            const int32_t Emin = eb + 4 * (int32_t)l;
-            const double dbeta = P.beta[rd.beta_off + i + 1] - P.beta[rd.beta_off + i];
-            st->lnQ = (-dbeta) * (double)Emin + sh_logS - sh_logR;
-            st->Emin = Emin;
-            st->n_levels = nb;
-        }
-        const double S = sh_S;
-        unsigned long long *thr = scr + scr_table_off(N);
-        uint32_t *flo = reinterpret_cast<uint32_t *>(scr + scr_level_off(N));
-        for (uint32_t n = tid; n < nb; n += nt) {
-            const double tau = __ddiv_rn(__dmul_rn((double)rd.R, wt[n]), S);
-            const double fl = floor(tau);
-            flo[n] = (uint32_t)fl;
-            thr[n] = (unsigned long long)ceil(__dmul_rn(__dsub_rn(tau, fl), 4294967296.0));
-        }
-    }
-    for (uint32_t n = tid; n < n1; n += nt) {  // cleared for the next step (every read of them is done)
-        gE[n] = 0u;
-        gM[n] = 0u;
-    }
+    run_tail(P, rd, st, i, init, R, eb, gE, gM, scr, &part[0], reinterpret_cast<double *>(&sh_h[0][0]),
+             MEASURE_SMEM_TERMS, ts);
 }
 
 // A record's 128-bit sum as a double: sign and magnitude, then hi 2^64 + lo
