@@ -2804,11 +2804,15 @@ __global__ void wavg_q_kernel(const pa_step_record *recs, const unsigned long lo
 //               few hundred replicas fill the SMs of the cluster;
 //   CTA 0       the measurement of the new population and the next
 //               resampling's tables (as measure_kernel with one CTA per run).
-// The phases are separated by cluster barriers (barrier.cluster arrive with
-// release and wait with acquire semantics at cluster scope, so each phase sees
-// the global memory the previous one wrote).  Every CTA of a cluster reads the
-// same run state after the same barrier, so all of them take the same number
-// of barriers.  The arithmetic, the Philox counters and the device state left
+// With drawing ahead (H > 0, launches of several temperatures at L = 8, 16) CTA 0
+// sweeps no children, and while it measures and resamples the other CTAs draw the
+// next temperature's comparison bits for their slices into shared memory.
+// The phases are separated by two cluster barriers per temperature
+// (barrier.cluster arrive with release and wait with acquire semantics at cluster
+// scope, so each phase sees the global memory the previous one wrote): after
+// the resampling and after the sweeps.  Every CTA of a cluster reads the same
+// run state after the same barrier, so all of them take the same number of
+// barriers.  The arithmetic, the Philox counters and the device state left
 // behind (records, scratch tables, run state) are those of the multi-kernel
 // path, so a run can move between the two paths at any step.
 // --------------------------------------------------------------------------
