@@ -353,9 +353,9 @@ pa_status pa_weighted_average(const pa_step_record *recs, const uint32_t *qhist,
  * M * n_steps > PA_NOALLOC_MAX_WEIGHTS is rejected with PA_ERR_INVALID_ARG
  * (and a message on stderr).  The first call on each device looks up the
  * array's device address (with that device current) and keeps it for the
- * life of the process; make that first call before any stream capture.  A
- * cudaDeviceReset of that device makes the kept address stale: do not call
- * this entry point on a device after resetting it.  The work is enqueued on cuda_stream (a
+ * life of the process.  A cudaDeviceReset of that device makes the kept
+ * address stale: do not call this entry point on a device after resetting
+ * it.  The work is enqueued on cuda_stream (a
  * cudaStream_t or NULL) and the call returns without waiting.  Every call
  * shares the one array: calls whose work overlaps on the GPU (other streams,
  * or other host threads) race and must be serialised by the caller. */
