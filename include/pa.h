@@ -16,7 +16,7 @@
  *  - The engine owns all device memory it allocates (from cudaMalloc, or from
  *    the allocator installed by pa_set_allocator) and frees it in
  *    pa_destroy.  Work is enqueued asynchronously on the engine's CUDA stream;
- *    device-side errors (capacity overflow, extinction, timeouts) are latched in
+ *    device-side run errors (capacity overflow, extinction) are latched in
  *    a device status word and returned by pa_sync and pa_weighted_average_runs;
  *    pa_anneal_step refuses to continue once one is latched.  The read calls
  *    (pa_records, pa_measure, pa_population) report CUDA errors only, so the
@@ -43,7 +43,10 @@ typedef enum {
     PA_ERR_CAPACITY = 3,    /* a run's population exceeded its capacity R_cap */
     PA_ERR_EXTINCT = 4,     /* a run's population became empty */
     PA_ERR_CUDA = 5,        /* a CUDA runtime call failed */
-    PA_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    PA_ERR_TIMEOUT = 6,     /* reserved for a bounded device-side wait that gave up.  No CTA of
+                               this engine spins on another: CTAs of one run meet only at
+                               cluster barriers, or the last to finish takes over by a ticket,
+                               so no call returns it */
     PA_ERR_STATE = 7,       /* call not valid in the engine's current state */
     PA_ERR_BUSY = 8         /* no room to admit another run */
 } pa_status;
