@@ -202,7 +202,13 @@ pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stre
 
 /* ---- Serving: continuous batching of PA jobs ----------------------------
  * A server engine owns fixed device pools sized by this configuration (all
- * counts, not bytes; see pa_server_bytes).  Jobs (runs) are admitted and
+ * counts, not bytes; a word is 4 bytes except where 64-bit words are named).
+ * A run takes from each pool what its descriptor implies, in the units below,
+ * where a colour plane holds P(L) = ceil(L * pitch / 32) words, the pitch is
+ * L/2 when that is a power of two, else the smallest of 4, 8, 16, 32 that is
+ * >= L/2 with L * pitch a multiple of 32 (L/2 < 32), else L/2 rounded up to a
+ * multiple of 32, and a replica's spin stride is S(L) = 2 P(L) rounded up to
+ * a multiple of 4.  Jobs (runs) are admitted and
  * retired between anneal steps; every pa_anneal_step advances all resident,
  * unfinished runs by one temperature in shared launches, each at its own
  * temperature index.  A run's results do not depend on which other runs were
@@ -211,13 +217,26 @@ typedef struct pa_server_config {
     uint32_t max_runs;          /* slots */
     uint32_t reserved;          /* must be 0 */
     uint64_t replica_capacity;  /* sum over resident runs of R_cap */
-    uint64_t spin_words;        /* sum of R_cap * (2 ceil(L^2/64) rounded up to 4) */
+    uint64_t spin_words;        /* sum of R_cap * S(L) */
     uint64_t record_capacity;   /* sum of n_beta */
     uint64_t qhist_words;       /* sum over overlap runs of n_beta (L^2 + 1) */
-    uint64_t scratch_words;     /* per run about 2 (L^2 + 1) + R_cap / 2 64-bit words */
-    uint64_t coupling_words;    /* per run 2 * spin stride + 8 ceil(L^2/64) */
+    uint64_t scratch_words;     /* 64-bit words, per run 3 floor((L^2 + 2) / 2) + L^2 + 5
+                                   + max(floor((R_cap + 1) / 2), 128, 4 ceil(R_cap / 16384)) */
+    uint64_t coupling_words;    /* per run 2 S(L) + 8 P(L) */
     uint64_t table_doubles;     /* cache of weight tables, (L^2 + 1) per distinct (L, dbeta) */
 } pa_server_config;
+
+/* The pools that hold these n_runs runs at once (the sizes pa_create gives an
+ * engine for them): *out receives, per pool, the sum of the runs' needs in the
+ * units above, max_runs = n_runs, and table_doubles for their distinct
+ * (L^2, beta_i - beta_{i-1}) weight tables plus, for theta = PA_THETA_INF runs,
+ * n_beta (2 L^2 + 2) per distinct (log_g, schedule).  A server created with it
+ * admits exactly these runs (a server's tables are a cache that keeps every
+ * distinct table it has built, so a long-lived server needs table space for
+ * every distinct one it will meet).  Sums of several calls size a server for a
+ * mix.  Host only: no device work, usable without a GPU.  Errors:
+ * PA_ERR_INVALID_ARG (as pa_create for the descriptors, or out NULL). */
+pa_status pa_pool_sizes(const pa_run_desc *runs, uint32_t n_runs, pa_server_config *out);
 
 /* Create an empty server engine (flags as for pa_create_ex).  Errors:
  * PA_ERR_INVALID_ARG, PA_ERR_OOM, PA_ERR_CUDA. */

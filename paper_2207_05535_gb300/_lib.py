@@ -59,7 +59,7 @@ WAVG_DTYPE = np.dtype([
     ("W_U4", "f8"), ("W_U4_conf", "f8"), ("W_absq_wang", "f8"),
 ])
 
-EXPORTS = ["pa_create", "pa_create_ex", "pa_server_create", "pa_admit", "pa_retire", "pa_finished", "pa_run_state",
+EXPORTS = ["pa_create", "pa_create_ex", "pa_pool_sizes", "pa_server_create", "pa_admit", "pa_retire", "pa_finished", "pa_run_state",
            "pa_reset", "pa_anneal_step", "pa_sync", "pa_records", "pa_measure", "pa_population", "pa_population_slice",
            "pa_checkpoint", "pa_restore",
            "pa_weighted_average_runs", "pa_weighted_average", "pa_weighted_average_noalloc", "pa_launch_count", "pa_set_profiling",
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
         P, u32, vp = C.POINTER, C.c_uint32, C.c_void_p
         lib.pa_create.argtypes = [P(pa_run_desc), u32, vp, P(vp)]
         lib.pa_create_ex.argtypes = [P(pa_run_desc), u32, vp, u32, P(vp)]
+        lib.pa_pool_sizes.argtypes = [P(pa_run_desc), u32, P(pa_server_config)]
         lib.pa_server_create.argtypes = [P(pa_server_config), vp, u32, P(vp)]
         lib.pa_admit.argtypes = [vp, P(pa_run_desc), u32, P(u32)]
         lib.pa_retire.argtypes = [vp, u32]
@@ -173,6 +174,13 @@ def pa_create_ex(runs, stream=None, flags=0):
     s = C.c_void_p(stream) if stream else None
     _check(lib.pa_create_ex(d, len(runs), s, flags, C.byref(h)), "pa_create_ex")
     return h
+
+
+def pa_pool_sizes(runs):
+    """Pool sizes (a pa_server_config) that hold these runs at once; host only."""
+    cfg = pa_server_config()
+    _check(load().pa_pool_sizes(make_descs(runs), len(runs), C.byref(cfg)), "pa_pool_sizes")
+    return cfg
 
 
 def pa_server_create(cfg, stream=None, flags=0):

@@ -1178,6 +1178,39 @@ size_t ckpt_bytes(const RunDev &x, const std::vector<CkptSection> &v)
     return n;
 }
 
+// Pools sized exactly for these (validated) runs: each run's ranges, and weight
+// tables for their distinct (N, dbeta) plus the theta = infinity CDF tables of
+// their distinct (density of states, schedule).
+void pool_sizes(const pa_run_desc *runs, uint32_t n_runs, pa_server_config &c)
+{
+    c = pa_server_config{};
+    c.max_runs = n_runs;
+    std::map<std::pair<uint32_t, uint64_t>, int> keys;
+    std::map<std::vector<double>, int> dos_keys;
+    for (uint32_t r = 0; r < n_runs; ++r) {
+        const Ranges z = sizes_of(runs[r]);
+        c.replica_capacity += z.rep;
+        c.spin_words += z.spin;
+        c.record_capacity += z.rec;
+        c.qhist_words += z.qh;
+        c.scratch_words += z.scr;
+        c.coupling_words += z.J;
+        const uint32_t N = runs[r].L * runs[r].L;
+        for (uint32_t i = 1; i < runs[r].n_beta; ++i) {
+            const double db = runs[r].beta[i] - runs[r].beta[i - 1];
+            uint64_t bits;
+            std::memcpy(&bits, &db, sizeof bits);
+            if (keys.emplace(std::make_pair(N, bits), 0).second) c.table_doubles += N + 1;
+        }
+        if (runs[r].theta == PA_THETA_INF) {
+            std::vector<double> key(runs[r].log_g, runs[r].log_g + 2 * N + 1);
+            key.insert(key.end(), runs[r].beta, runs[r].beta + runs[r].n_beta);
+            key.push_back((double)N);
+            if (dos_keys.emplace(std::move(key), 0).second) c.table_doubles += (uint64_t)runs[r].n_beta * (2 * N + 2);
+        }
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -1222,38 +1255,21 @@ pa_status pa_create(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream,
     return pa_create_ex(runs, n_runs, cuda_stream, 0u, out);
 }
 
+pa_status pa_pool_sizes(const pa_run_desc *runs, uint32_t n_runs, pa_server_config *out)
+{
+    if (!out) return PA_ERR_INVALID_ARG;
+    PA_TRY(validate(runs, n_runs));
+    pool_sizes(runs, n_runs, *out);
+    return PA_OK;
+}
+
 pa_status pa_create_ex(const pa_run_desc *runs, uint32_t n_runs, void *cuda_stream, uint32_t flags, pa_engine **out)
 {
     if (!out) return PA_ERR_INVALID_ARG;
     *out = nullptr;
     PA_TRY(validate(runs, n_runs));
-    // pools sized exactly for these runs; tables for their distinct (N, dbeta)
-    pa_server_config c{};
-    c.max_runs = n_runs;
-    std::map<std::pair<uint32_t, uint64_t>, int> keys;
-    std::map<std::vector<double>, int> dos_keys;
-    for (uint32_t r = 0; r < n_runs; ++r) {
-        const Ranges z = sizes_of(runs[r]);
-        c.replica_capacity += z.rep;
-        c.spin_words += z.spin;
-        c.record_capacity += z.rec;
-        c.qhist_words += z.qh;
-        c.scratch_words += z.scr;
-        c.coupling_words += z.J;
-        const uint32_t N = runs[r].L * runs[r].L;
-        for (uint32_t i = 1; i < runs[r].n_beta; ++i) {
-            const double db = runs[r].beta[i] - runs[r].beta[i - 1];
-            uint64_t bits;
-            std::memcpy(&bits, &db, sizeof bits);
-            if (keys.emplace(std::make_pair(N, bits), 0).second) c.table_doubles += N + 1;
-        }
-        if (runs[r].theta == PA_THETA_INF) {
-            std::vector<double> key(runs[r].log_g, runs[r].log_g + 2 * N + 1);
-            key.insert(key.end(), runs[r].beta, runs[r].beta + runs[r].n_beta);
-            key.push_back((double)N);
-            if (dos_keys.emplace(std::move(key), 0).second) c.table_doubles += (uint64_t)runs[r].n_beta * (2 * N + 2);
-        }
-    }
+    pa_server_config c;
+    pool_sizes(runs, n_runs, c);
     pa_engine *e = nullptr;
     PA_TRY(engine_new(cuda_stream, flags, &e));
     pa_status s = alloc_pools(e, c);

@@ -18,20 +18,33 @@ import time
 import numpy as np
 
 from . import _lib
+from . import workloads as W
 
 BUSY = 8
 
 
-def config_for_budget(budget_bytes: int, max_runs: int = 4096, max_L: int = 64, max_n_beta: int = 300,
-                      mean_L2: float = 1600.0, overlap_frac: float = 0.0, table_bytes: int = 512 << 20):
-    """Pool sizes for a device-memory budget, for jobs with L <= max_L (mean L^2
-    about mean_L2) and at most max_n_beta temperatures."""
-    words_per_replica = 2 * math.ceil(mean_L2 / 64) + 2       # spin stride incl. rounding
-    bytes_per_replica = 2 * 4 * words_per_replica + 6 * 4 + 2 * 4 + 4  # spins x2, E/M/fam x2, parent, cnt, scratch
+def config_for_budget(budget_bytes: int, max_runs: int = 4096, min_L: int = 8, max_L: int = 64,
+                      max_n_beta: int = 300, overlap_frac: float = 0.0, table_bytes: int = 512 << 20):
+    """Pool sizes for a device-memory budget, for jobs with even L uniform in
+    min_L..max_L and at most max_n_beta temperatures.  Per-replica and per-run
+    words come from the engine's own layout (pa_pool_sizes of one small run per
+    lattice size); the replicas share what the per-run parts leave."""
+    Ls = range(min_L + (min_L & 1), max_L + 1, 2)
+    if not Ls:
+        raise ValueError("no even lattice size in min_L..max_L")
+    one = [_lib.pa_pool_sizes([W.RunDesc(L, W.FERRO, 1, 1, W.schedule(1.0, 2))]) for L in Ls]
+    words_per_replica = math.ceil(sum(c.spin_words // c.replica_capacity for c in one) / len(one))
+    # per replica: both spin buffers, E, M and family in both buffers, parent and copy
+    # number, and half a 64-bit scratch word (the multinomial member list)
+    bytes_per_replica = 2 * 4 * words_per_replica + 2 * 3 * 4 + 2 * 4 + 4
     N_max = max_L * max_L
-    per_run_fixed = (176 * max_n_beta + 8 * 2 * (N_max + 1) + 4 * (2 * (2 * math.ceil(N_max / 64) + 4)
-                     + 8 * math.ceil(N_max / 64)) + 8 * 4 * max_n_beta)
-    rest = budget_bytes - table_bytes - max_runs * per_run_fixed
+    coupling = max(c.coupling_words for c in one)          # 32-bit words per run
+    scratch_run = max(c.scratch_words for c in one) + 1    # 64-bit words per run (histograms, level tables)
+    per_step = _lib.RECORD_DTYPE.itemsize + 8 + 16 + 8     # record, beta, two thresholds, table offset
+    n_q = int(overlap_frac * max_runs)
+    qhist_bytes = 3 * 4 * n_q * max_n_beta * (N_max + 1)  # index-shift, two-population and Wang histograms
+    per_run_fixed = per_step * max_n_beta + 8 * scratch_run + 4 * coupling
+    rest = budget_bytes - table_bytes - max_runs * per_run_fixed - qhist_bytes
     if rest <= 0:
         raise ValueError("budget too small for the slot count")
     reps = int(rest // bytes_per_replica)
@@ -40,9 +53,9 @@ def config_for_budget(budget_bytes: int, max_runs: int = 4096, max_L: int = 64, 
     cfg.replica_capacity = reps
     cfg.spin_words = reps * words_per_replica
     cfg.record_capacity = max_runs * max_n_beta
-    cfg.qhist_words = int(overlap_frac * max_runs) * max_n_beta * (N_max + 1)
-    cfg.scratch_words = reps // 2 + max_runs * (2 * (N_max + 1) + 8)
-    cfg.coupling_words = max_runs * (2 * (2 * math.ceil(N_max / 64) + 4) + 8 * math.ceil(N_max / 64))
+    cfg.qhist_words = n_q * max_n_beta * (N_max + 1)
+    cfg.scratch_words = reps // 2 + max_runs * scratch_run
+    cfg.coupling_words = max_runs * coupling
     cfg.table_doubles = table_bytes // 8
     return cfg
 

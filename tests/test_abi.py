@@ -126,6 +126,69 @@ def test_binding_argument_counts_match_the_header(lib):
         assert len(getattr(lib, name).argtypes) == len(params), name
 
 
+def _documented_plane_words(L):
+    """P(L) as the pool units of include/pa.h state it."""
+    Lh = L // 2
+    if Lh & (Lh - 1) == 0:
+        pitch = Lh
+    elif Lh < 32:
+        pitch = min(p for p in (4, 8, 16, 32) if p >= Lh and L * p % 32 == 0)
+    else:
+        pitch = -(-Lh // 32) * 32
+    return -(-L * pitch // 32)
+
+
+def test_pool_sizes_follow_the_documented_units(lib):
+    for L in range(4, 257, 2):
+        for R, resample in ((100, W.NEAREST), (40000, W.NEAREST), (300, W.MULTINOMIAL)):
+            d = W.RunDesc(L, W.FERRO, R, 2, W.schedule(1.0, 11), resample=resample)
+            c = _lib.pa_pool_sizes([d])
+            N, P = L * L, _documented_plane_words(L)
+            S = -(-2 * P // 4) * 4
+            assert d.R_cap == (R if resample == W.MULTINOMIAL else W.default_cap(R))
+            assert (c.max_runs, c.replica_capacity, c.record_capacity, c.qhist_words) == (1, d.R_cap, 11, 0)
+            assert c.spin_words == d.R_cap * S, L
+            assert c.coupling_words == 2 * S + 8 * P, L
+            assert c.scratch_words == (3 * ((N + 2) // 2) + N + 5
+                                       + max((d.R_cap + 1) // 2, 128, 4 * -(-d.R_cap // 16384))), (L, R)
+            n_db = len({x.tobytes() for x in np.diff(d.betas)})  # distinct dbeta bit patterns
+            assert c.table_doubles == n_db * (N + 1), L
+
+
+def test_pool_sizes_share_tables_and_count_overlaps(lib):
+    b = W.schedule(1.0, 5)
+    n_db = len({x.tobytes() for x in np.diff(b)})
+    a = W.RunDesc(8, W.EA_PMJ, 50, 1, b, overlap=W.Q_SHIFT | W.Q_PAIR, paired=1)
+    p = W.RunDesc(8, W.EA_PMJ, 50, 1, b, run_id=1, overlap=W.Q_SHIFT | W.Q_PAIR, paired=0)
+    f16 = W.RunDesc(16, W.FERRO, 50, 1, b)
+    alone = W.RunDesc(8, W.EA_PMJ, 50, 1, b, overlap=W.Q_SHIFT)  # a's needs without its partner
+    one = [_lib.pa_pool_sizes([r]) for r in (alone, f16)]
+    assert one[0].qhist_words == 5 * 65
+    both = _lib.pa_pool_sizes([a, p, f16])
+    assert both.max_runs == 3
+    assert both.qhist_words == 2 * 5 * 65
+    assert both.replica_capacity == 2 * one[0].replica_capacity + one[1].replica_capacity
+    assert both.spin_words == 2 * one[0].spin_words + one[1].spin_words
+    assert both.table_doubles == n_db * (65 + 257)  # one table per distinct (N, dbeta), shared by the pair
+    # theta = infinity: n_beta (2N + 2) per distinct (ln g, schedule), on top of the weight tables
+    g = np.full(2 * 16 + 1, -np.inf)
+    g[0::2] = 0.0
+    t1 = W.RunDesc(4, W.FERRO, 50, W.THETA_INF, b, log_g=g)
+    t2 = W.RunDesc(4, W.FERRO, 50, W.THETA_INF, b, run_id=1, log_g=g)
+    t3 = W.RunDesc(4, W.FERRO, 50, W.THETA_INF, W.schedule(0.5, 5), run_id=2, log_g=g)
+    n_db3 = len({x.tobytes() for x in np.diff(W.schedule(0.5, 5))})
+    c = _lib.pa_pool_sizes([t1, t2, t3])
+    assert c.table_doubles == (n_db + n_db3) * 17 + 2 * 5 * 34
+
+
+def test_pool_sizes_reject_what_pa_create_rejects(lib):
+    with pytest.raises(_lib.PAError) as ei:
+        _lib.pa_pool_sizes([W.RunDesc(9, W.FERRO, 10, 1, W.schedule(1.0, 3))])  # odd L
+    assert ei.value.code == 1
+    d = _lib.make_descs([W.RunDesc(8, W.FERRO, 10, 1, W.schedule(1.0, 3))])
+    assert lib.pa_pool_sizes(d, 1, None) == 1
+
+
 def test_benchmark_plane_words_follow_the_engine_layout(tmp_path):
     """bench.py's byte counts use the engine's colour-plane size (row pitch)."""
     import bench

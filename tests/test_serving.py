@@ -8,7 +8,7 @@ the oracle.  The CPU test drives the request loop with a fake engine.
 import numpy as np
 import pytest
 
-from paper_2207_05535_gb300 import _lib, serve
+from paper_2207_05535_gb300 import _lib, build, serve
 from paper_2207_05535_gb300 import workloads as W
 
 
@@ -150,10 +150,26 @@ def test_request_loop_admits_fifo_and_accounts_latency():
     assert s["jobs"] == 5 and s["p99_latency_s"] >= s["p50_latency_s"] > 0
 
 
+def _pool_bytes(c):
+    """Device bytes of a server's pools (both spin and E/M/family buffers; records with
+    their beta, two thresholds and table offset; three overlap histograms)."""
+    return (2 * 4 * c.spin_words + (2 * 3 + 2) * 4 * c.replica_capacity
+            + (_lib.RECORD_DTYPE.itemsize + 32) * c.record_capacity + 3 * 4 * c.qhist_words
+            + 4 * c.coupling_words + 8 * c.scratch_words + 8 * c.table_doubles)
+
+
 def test_config_for_budget_scales_with_memory():
+    build.build()
     a = serve.config_for_budget(8 << 30)
     b = serve.config_for_budget(32 << 30)
+    q = serve.config_for_budget(8 << 30, max_runs=256, overlap_frac=0.5)
     assert b.replica_capacity > 3 * a.replica_capacity
-    assert a.spin_words > a.replica_capacity and a.record_capacity == 4096 * 300
+    assert a.record_capacity == 4096 * 300 and q.qhist_words == 128 * 300 * 4097
+    for c, budget in ((a, 8 << 30), (b, 32 << 30), (q, 8 << 30)):
+        assert 0.95 * budget < _pool_bytes(c) <= budget
+    # the spin pool holds the replica pool at the mean stride of the even L in 8..64
+    one = [_lib.pa_pool_sizes([W.RunDesc(L, W.FERRO, 1, 1, W.schedule(1.0, 2))]) for L in range(8, 65, 2)]
+    mean = sum(c.spin_words / c.replica_capacity for c in one) / len(one)
+    assert a.spin_words >= a.replica_capacity * mean
     with pytest.raises(ValueError):
         serve.config_for_budget(1 << 20)
