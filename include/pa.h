@@ -238,7 +238,9 @@ typedef struct pa_server_config {
  * PA_ERR_INVALID_ARG (as pa_create for the descriptors, or out NULL). */
 pa_status pa_pool_sizes(const pa_run_desc *runs, uint32_t n_runs, pa_server_config *out);
 
-/* Create an empty server engine (flags as for pa_create_ex).  Errors:
+/* Create an empty server engine (flags as for pa_create_ex).  Serving has no
+ * counterpart in the paper: each admitted run is the PA run of Sec. II.B,
+ * unchanged by which other runs share the server.  Errors:
  * PA_ERR_INVALID_ARG, PA_ERR_OOM, PA_ERR_CUDA. */
 pa_status pa_server_create(const pa_server_config *cfg, void *cuda_stream, uint32_t flags, pa_engine **out);
 
@@ -262,10 +264,11 @@ pa_status pa_finished(const pa_engine *e, uint32_t *slots_out, uint32_t cap, uin
  * (0 or the pa_status that stopped it).  Synchronises. */
 pa_status pa_run_state(pa_engine *e, uint32_t slot, uint32_t *step, uint32_t *R, uint32_t *status);
 
-/* Return every run of the engine to its beta_0 population (same descriptors,
- * same randomness, so the next anneal repeats the first one bit for bit)
- * without reallocating: clears records, histograms and statuses, redraws the
- * couplings and populations and measures step 0.  Asynchronous. */
+/* Return every run of the engine to its beta_0 population (Sec. II.B step
+ * (i); same descriptors, same randomness, so the next anneal repeats the first
+ * one bit for bit) without reallocating: clears records, histograms and
+ * statuses, redraws the couplings and populations and measures step 0.
+ * Asynchronous. */
 pa_status pa_reset(pa_engine *e);
 
 /* Advance every unfinished run by up to n_steps temperatures (fewer when every
@@ -280,7 +283,8 @@ pa_status pa_anneal_step(pa_engine *e, uint32_t n_steps, int use_graph);
 pa_status pa_sync(pa_engine *e);
 
 /* Copy the records of run `run` (index in pa_create order) for steps
- * 0..n_beta-1 into host_out[n_beta] (steps not reached yet are zero), and the
+ * 0..n_beta-1 into host_out[n_beta] (the population sums, ln Q_i and -beta_i F_i
+ * of Sec. III.B-D; steps not reached yet are zero), and the
  * overlap histograms over d = 0..N (d = Hamming distance, q = 1 - 2d/N) into
  * host_qhist[n_beta][N+1] / host_qhist_pair[n_beta][N+1] / host_qhist_wang[n_beta][N+1]
  * (index shift, paired population, Wang pairs) when non-NULL.  Synchronises. */
@@ -294,11 +298,13 @@ pa_status pa_records(pa_engine *e, uint32_t run, pa_step_record *host_out, uint3
  * is not resident. */
 pa_status pa_step_records(pa_engine *e, const uint32_t *runs, uint32_t n_runs, pa_step_record *host_out);
 
-/* Copy one record (and optional histograms, N+1 entries each). Synchronises. */
+/* Copy the record of one run at one step (Sec. III.B-D; and optional overlap
+ * histograms, N+1 entries each).  Synchronises. */
 pa_status pa_measure(pa_engine *e, uint32_t run, uint32_t step, pa_step_record *host_out, uint32_t *host_qhist,
                      uint32_t *host_qhist_pair, uint32_t *host_qhist_wang);
 
-/* Copy the current population of run `run`: host_spins[R_i][N] as int8 +-1
+/* Copy the current population of run `run` (the R_i replicas of Sec. II.B at
+ * the temperature reached): host_spins[R_i][N] as int8 +-1
  * (site n = y*L + x), energies, magnetisations and family ids (index of the
  * beta_0 ancestor), each R_i entries, caller-sized to at least R_cap; *R_out = R_i;
  * *step_out = current temperature index.  Any pointer may be NULL.  Synchronises. */
@@ -346,7 +352,8 @@ pa_status pa_weighted_average_runs(pa_engine *e, const uint32_t *run_idx, uint32
                                    uint32_t weight_kind, pa_wavg *host_out, double *host_Pq,
                                    double *host_Pq_pair, double *host_Pq_wang);
 
-/* Weighted averages from host records: recs[m*n_steps + i] for M runs of N spins,
+/* Weighted averages (Sec. IV; Eqs. appropriateWeight or simpleWeight, W_conf,
+ * W_F, Wvar_C, Wvar_Chi, W_conf_q, W_k) from host records: recs[m*n_steps + i] for M runs of N spins,
  * optional histograms qhist[(m*n_steps + i)*(N+1) + d] (likewise qhist_pair,
  * qhist_wang).  Writes out[n_steps] and Pq / Pq_pair / Pq_wang [n_steps][N+1]
  * when non-NULL.  Computes on the device of the current CUDA context (stream:
@@ -360,8 +367,8 @@ pa_status pa_weighted_average(const pa_step_record *recs, const uint32_t *qhist,
 #define PA_NOALLOC_MAX_RUNS 4096u      /* M */
 #define PA_NOALLOC_MAX_WEIGHTS 65536u  /* M * n_steps */
 
-/* Weighted averages (same arithmetic as pa_weighted_average, no overlap
- * distributions) for callers that cannot allocate device memory: serving
+/* Weighted averages (Sec. IV, the same arithmetic as pa_weighted_average, no
+ * overlap distributions) for callers that cannot allocate device memory: serving
  * loops that reserve all device memory up front and must not call into the
  * allocator in the steady state (cudaMalloc can synchronise the device and
  * stall the other streams), or processes whose device memory belongs to
@@ -415,7 +422,8 @@ pa_status pa_kernel_times(pa_engine *e, double *ms_out, uint64_t *launches_out);
 /* Bytes this engine has copied host->device and device->host so far. */
 pa_status pa_transfer_bytes(const pa_engine *e, uint64_t *h2d, uint64_t *d2h);
 
-/* Throughput of Philox4x32-10 alone on the current device, in calls per second:
+/* Throughput of Philox4x32-10 (Salmon et al., SC'11; the generator behind every
+ * random decision of the engine) alone on the current device, in calls per second:
  * a loop of independent calls (8 per thread, 2432 CTAs of 128 threads, 64
  * iterations), timed with CUDA events after one warm-up launch, best of `reps`.
  * wide = 0 writes each 32x32->64 multiply as separate high and low halves, 1 as
